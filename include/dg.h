@@ -1,0 +1,203 @@
+/*
+ * dg.h -- C ABI of the GB300 nodal discontinuous Galerkin library (libdg).
+ *
+ * The library evaluates the semi-discrete right-hand side of the nodal DG
+ * scheme of Modave, St-Cyr & Warburton (arXiv:1602.07997) on straight-sided
+ * tetrahedra, for the acoustic pressure-velocity system (4 fields: p, vx,
+ * vy, vz) and the isotropic elastic velocity-stress system (9 fields: vx,
+ * vy, vz, sxx, syy, szz, sxy, sxz, syz), and advances it with the
+ * third-order Adams-Bashforth scheme:
+ *
+ *   physics and upwind penalty terms ............ Section 2.1
+ *   local RHS  r_k = sum_ij g^vol D_j f + sum_f g^sur L_f p ... Section 2.2, Eq. dgLocalRhs
+ *   AB3 update q^{m+1} = q^m + dt sum_s a_s r^{m-s+1} ...... Section 2.2, Eq. updateScheme
+ *   acoustic kernel form of the RHS .............. Section 3.2, Eqs. dgRhsAcou1-2
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Polynomial degree N in 1..8; Np = (N+1)(N+2)(N+3)/6 nodes per element,
+ *    Nfp = (N+1)(N+2)/2 nodes per face, Nf = 4 (acoustic) or 9 (elastic).
+ *  - Nodal arrays use the layout [K][Nf][Np] in float32, node index fastest
+ *    (the one-node-per-thread granularity of Table 1).  Node n of an element
+ *    is the n-th point of the warp-and-blend set (blend parameter 0) in the
+ *    order of the equispaced lattice (i along r fastest, then s, then t),
+ *    reference tetrahedron v1=(-1,-1,-1), v2=(1,-1,-1), v3=(-1,1,-1),
+ *    v4=(-1,-1,1); dg_node_coords returns the physical positions.
+ *  - Meshes: vertex coordinates double [nverts][3]; tetrahedra int64
+ *    [ntets][4] (0-based vertex indices), positively oriented
+ *    (det[x2-x1, x3-x1, x4-x1] > 0).  The mesh must be conforming (each
+ *    face shared by at most two tetrahedra); unshared faces are outer
+ *    boundary faces.
+ *  - Coefficients, constant per element: acoustic double [K][2] = (rho, c);
+ *    elastic double [K][3] = (lambda, mu, rho).
+ *  - Ownership: every pointer argument is borrowed for the duration of the
+ *    call only; dg_setup copies the mesh, coefficients and operators it
+ *    needs.  Device state (fields, AB3 history, geometry) belongs to the
+ *    handle and is freed by dg_destroy.  Output buffers are allocated by the
+ *    caller.  `on_device` = 1 means the pointer is a CUDA device pointer on
+ *    the handle's device (e.g. torch.Tensor.data_ptr()), 0 means host memory.
+ *  - Asynchrony: kernels and copies are issued on the CUDA stream given in
+ *    dg_opts.stream (NULL = the legacy default stream).  Host outputs are
+ *    complete when the call returns; device outputs are complete in stream
+ *    order.  dg_sync waits for the stream and reports device-side errors.
+ *  - Errors: functions return DG_OK (0) or a negative code below; a
+ *    thread-local message is available from dg_last_error().  No function
+ *    aborts the process and no kernel traps.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DG_OK = 0,
+  DG_EINVAL = -1,      /* bad argument, N outside 1..8, bad mesh (inverted or
+                          degenerate tet, non-conforming face, index out of range) */
+  DG_ENOMEM = -2,      /* device or host allocation failed, or over the budget  */
+  DG_ECUDA = -3,       /* a CUDA runtime call failed (message has the CUDA error) */
+  DG_ENONFINITE = -4,  /* a NaN/Inf was found in the state                        */
+  DG_ETIMEOUT = -5,    /* a bounded device-side wait expired                      */
+  DG_EAGAIN = -6,      /* dg_poll: the request is not finished yet                */
+  DG_ECANCELED = -7,   /* dg_poll: the request was cancelled                      */
+  DG_ENOENT = -8       /* dg_poll / dg_cancel: unknown ticket                     */
+};
+
+enum { DG_ACOUSTIC = 0, DG_ELASTIC = 1 };
+enum { DG_FLUX_UPWIND = 0, DG_FLUX_CENTERED = 1 };
+/* outer boundary: DEFAULT = rigid wall (acoustic) / traction-free (elastic).
+ * Mirror ghost states: acoustic rigid p+ = p-, v+ = v- - 2 (v-.n) n;
+ * elastic free v+ = v-, sigma+ = -sigma-; elastic rigid v+ = -v-, sigma+ = sigma-. */
+enum { DG_BC_DEFAULT = 0, DG_BC_RIGID = 1, DG_BC_FREE = 2 };
+/* arithmetic of the operator contractions; flux and AB3 are always float32 */
+enum { DG_FP32 = 0 };
+
+typedef struct {
+  int64_t nverts;
+  int64_t ntets;
+  const double *verts;  /* [nverts][3] */
+  const int64_t *tets;  /* [ntets][4]  */
+} dg_mesh;
+
+typedef struct {
+  int flux;         /* DG_FLUX_*                                         */
+  int bc;           /* DG_BC_*                                           */
+  int precision;    /* DG_FP32                                           */
+  int block_elems;  /* elements per CTA; 0 = the tuned default for (model, N) */
+  double dt;        /* time step used by dg_step (may be changed by dg_set_dt) */
+  void *stream;     /* cudaStream_t; NULL = legacy default stream        */
+} dg_opts;
+
+typedef struct dg_handle dg_handle;
+
+/* Build a solver for one mesh (Section 2.2): reference operators (warp-and-
+ * blend nodes, orthonormal-basis Vandermonde route: D_r = V_r V^{-1},
+ * M^{-1} = V V^T, LIFT = M^{-1} [E_1..E_4]), per-element geometric factors
+ * g^vol_{ij} = dr_j/dx_i, face normals and g^sur = sJ/J, face connectivity,
+ * and the device state.  The state starts at q = 0 with an empty AB3 history.
+ * Returns DG_EINVAL for N outside 1..8, a negative or zero Jacobian, a face
+ * shared by more than two tetrahedra, or a vertex index out of range.      */
+int dg_setup(const dg_mesh *mesh, const double *coeffs, int N, int model,
+             const dg_opts *opts, dg_handle **out);
+void dg_destroy(dg_handle *h);
+
+/* Sizes: number of elements, nodes per element, nodes per face, fields.     */
+int dg_info(const dg_handle *h, int64_t *K, int *Np, int *Nfp, int *Nf);
+
+/* Replace the state.  q [K][Nf][Np].  r1 = r^{m-1} and r2 = r^{m-2} (same
+ * layout) are either both NULL -- the next steps then start AB3 with a
+ * forward-Euler step and an AB2 step -- or both given (full AB3 history).
+ * `step` is the time-step index m of q (it indexes source amplitudes).     */
+int dg_set_state(dg_handle *h, const float *q, const float *r1, const float *r2,
+                 int64_t step, int on_device);
+/* Read the state; r1 / r2 may be NULL.  *step / *history (0, 1 or 2 stored
+ * RHS levels) may be NULL.                                                  */
+int dg_get_state(dg_handle *h, float *q, float *r1, float *r2, int64_t *step,
+                 int *history, int on_device);
+
+/* r_out [K][Nf][Np] = r(q^m, t_m): volume term + lifted penalty terms
+ * (Eq. dgLocalRhs) at the current state, plus the source term of step m;
+ * the state is not changed.                                                 */
+int dg_rhs(dg_handle *h, float *r_out, int on_device);
+
+/* Advance nsteps AB3 steps (Eq. updateScheme) with the handle's dt; each step
+ * is one fused launch (RHS + update).  Asynchronous on the handle's stream.  */
+int dg_step(dg_handle *h, int nsteps);
+int dg_set_dt(dg_handle *h, double dt);
+/* Wait for the handle's stream; DG_ETIMEOUT if a device wait expired.       */
+int dg_sync(dg_handle *h);
+
+/* Physical node coordinates, double [K][Np][3].                             */
+int dg_node_coords(const dg_handle *h, double *xyz);
+
+/* Point source at xs: at step m the RHS gets amp[m] M_k^{-1} l(xs) on p
+ * (acoustic) or amp[m] (dir_i / rho_k) M_k^{-1} l(xs) on v_i (elastic), in
+ * the tet whose smallest barycentric coordinate of xs is largest; amp[m] = 0
+ * for m >= namp.  amp == NULL removes the source.  Host pointers.           */
+int dg_set_source(dg_handle *h, const double xs[3], const double dir[3],
+                  const double *amp, int64_t namp);
+
+/* dt = cfl * min_{k,f} 1 / (c_max,k Fscale_{k,f} (N+1)^2), host only.       */
+int dg_suggest_dt(const dg_mesh *mesh, const double *coeffs, int N, int model,
+                  double cfl, double *dt);
+
+/* Host-only reference element of degree N, double precision, for checking
+ * the set-up: nodes [Np][3], Dr/Ds/Dt [Np][Np] (D[i][j] = dl_j/dr(x_i)),
+ * LIFT [Np][4 Nfp] with columns in face-major order and, within a face, in
+ * the order of fmask [4][Nfp] (the node index of each face node).  Any
+ * pointer may be NULL.                                                      */
+int dg_reference_element(int N, double *nodes, double *Dr, double *Ds, double *Dt,
+                         double *LIFT, int *fmask);
+
+/* Thread-local message of the last failing call on this thread.             */
+const char *dg_last_error(void);
+
+/* ----------------------------------------------------------------------------
+ * Served solves.  A server owns a host thread and one CUDA stream.  Each
+ * request is an independent time-domain solve (mesh, coefficients, N, model,
+ * initial state, source, nsteps).  Requests are admitted while free device
+ * memory (cudaMemGetInfo) minus a safety margin, and the optional budget,
+ * cover their state; admitted solves of the same degree and model are
+ * advanced together, one batched launch per (model, N) class per time step,
+ * and new requests join between steps (continuous batching).  A finished
+ * solve's q is copied to host memory owned by the server until dg_poll
+ * copies it out.
+ * ------------------------------------------------------------------------ */
+typedef struct dg_server dg_server;
+
+typedef struct {
+  const dg_mesh *mesh;
+  const double *coeffs;
+  int N;
+  int model;
+  dg_opts opts;          /* flux, bc, dt; block_elems and stream are ignored */
+  const float *q0;       /* host [K][Nf][Np]; NULL = zero state              */
+  const double *src_xyz; /* NULL = no source                                  */
+  const double *src_dir; /* elastic only; NULL = (0,0,1)                      */
+  const double *src_amp; /* amplitudes per step                               */
+  int64_t src_namp;
+  int nsteps;
+} dg_request;
+
+/* hbm_budget_bytes = 0: no budget beyond the free device memory.           */
+int dg_server_create(size_t hbm_budget_bytes, int max_batch, dg_server **out);
+int dg_submit(dg_server *s, const dg_request *req, uint64_t *ticket);
+/* DG_OK and q_out filled (host, caller-allocated [K][Nf][Np]) when finished;
+ * DG_EAGAIN while queued or running.  latency_s (may be NULL) = finish time
+ * minus submit time.  A finished ticket can be polled once.                 */
+int dg_poll(dg_server *s, uint64_t ticket, float *q_out, double *latency_s);
+int dg_cancel(dg_server *s, uint64_t ticket);
+/* Counters: queued, running, finished-not-polled, total batched launches.   */
+int dg_server_stats(dg_server *s, int64_t *queued, int64_t *running,
+                    int64_t *done, int64_t *launches);
+void dg_server_destroy(dg_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_H */

@@ -1,0 +1,246 @@
+"""ctypes binding of libdg (argument marshalling only; all compute runs in the library).
+
+The shared library is built in-tree by ``paper_1602_07997_gb300.build``.
+Importing this module never falls back to anything: if ``libdg.so`` is
+missing the first call raises.
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdg.so")
+
+DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONFINITE, DG_ETIMEOUT, DG_EAGAIN, DG_ECANCELED, DG_ENOENT = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+ACOUSTIC, ELASTIC = 0, 1
+FLUX = {"upwind": 0, "centered": 1, "centred": 1}
+BC = {None: 0, "default": 0, "rigid": 1, "free": 2}
+
+# every symbol that include/dg.h declares
+EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", "dg_rhs", "dg_step",
+           "dg_set_dt", "dg_sync", "dg_node_coords", "dg_set_source", "dg_suggest_dt",
+           "dg_reference_element", "dg_last_error", "dg_server_create", "dg_submit", "dg_poll",
+           "dg_cancel", "dg_server_stats", "dg_server_destroy")
+
+
+class DGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libdg error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Mesh(C.Structure):
+    _fields_ = [("nverts", C.c_int64), ("ntets", C.c_int64),
+                ("verts", C.POINTER(C.c_double)), ("tets", C.POINTER(C.c_int64))]
+
+
+class Opts(C.Structure):
+    _fields_ = [("flux", C.c_int), ("bc", C.c_int), ("precision", C.c_int),
+                ("block_elems", C.c_int), ("dt", C.c_double), ("stream", C.c_void_p)]
+
+
+class Request(C.Structure):
+    _fields_ = [("mesh", C.POINTER(Mesh)), ("coeffs", C.POINTER(C.c_double)), ("N", C.c_int),
+                ("model", C.c_int), ("opts", Opts), ("q0", C.POINTER(C.c_float)),
+                ("src_xyz", C.POINTER(C.c_double)), ("src_dir", C.POINTER(C.c_double)),
+                ("src_amp", C.POINTER(C.c_double)), ("src_namp", C.c_int64), ("nsteps", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libdg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libdg.so not found at %s: build it with "
+                           "`python -m paper_1602_07997_gb300.build`" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    P = C.POINTER
+    sig = {
+        "dg_setup": (i32, [P(Mesh), P(dbl), i32, i32, P(Opts), P(vp)]),
+        "dg_destroy": (None, [vp]),
+        "dg_info": (i32, [vp, P(i64), P(i32), P(i32), P(i32)]),
+        "dg_set_state": (i32, [vp, vp, vp, vp, i64, i32]),
+        "dg_get_state": (i32, [vp, vp, vp, vp, P(i64), P(i32), i32]),
+        "dg_rhs": (i32, [vp, vp, i32]),
+        "dg_step": (i32, [vp, i32]),
+        "dg_set_dt": (i32, [vp, dbl]),
+        "dg_sync": (i32, [vp]),
+        "dg_node_coords": (i32, [vp, P(dbl)]),
+        "dg_set_source": (i32, [vp, P(dbl), P(dbl), P(dbl), i64]),
+        "dg_suggest_dt": (i32, [P(Mesh), P(dbl), i32, i32, dbl, P(dbl)]),
+        "dg_reference_element": (i32, [i32, P(dbl), P(dbl), P(dbl), P(dbl), P(dbl), P(i32)]),
+        "dg_last_error": (C.c_char_p, []),
+        "dg_server_create": (i32, [C.c_size_t, i32, P(vp)]),
+        "dg_submit": (i32, [vp, P(Request), P(C.c_uint64)]),
+        "dg_poll": (i32, [vp, C.c_uint64, vp, P(dbl)]),
+        "dg_cancel": (i32, [vp, C.c_uint64]),
+        "dg_server_stats": (i32, [vp, P(i64), P(i64), P(i64), P(i64)]),
+        "dg_server_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        if not hasattr(L, name):
+            continue
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(rc):
+    if rc != DG_OK:
+        msg = lib().dg_last_error()
+        raise DGError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_mesh(verts, tets):
+    verts = np.ascontiguousarray(verts, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int64)
+    m = Mesh(verts.shape[0], tets.shape[0], _dptr(verts), tets.ctypes.data_as(C.POINTER(C.c_int64)))
+    return m, (verts, tets)  # keep the arrays alive with the struct
+
+
+def _model(model):
+    if isinstance(model, str):
+        return ACOUSTIC if model == "acoustic" else ELASTIC
+    return int(model)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _buf(x, dtype, count, write=False):
+    """(pointer, on_device, keepalive) for a numpy array or a torch tensor."""
+    if _is_torch(x):
+        import torch
+        if x.dtype != {np.float32: torch.float32, np.float64: torch.float64}[dtype]:
+            raise TypeError("tensor dtype must be %s" % dtype)
+        if not x.is_contiguous() or x.numel() != count:
+            raise ValueError("tensor must be contiguous with %d elements" % count)
+        return C.c_void_p(x.data_ptr()), int(x.is_cuda), x
+    a = np.asarray(x)
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        if write:
+            raise TypeError("output array must be C-contiguous %s" % np.dtype(dtype))
+        a = np.ascontiguousarray(a, dtype=dtype)
+    if a.size != count:
+        raise ValueError("array must have %d elements, got %d" % (count, a.size))
+    return C.c_void_p(a.ctypes.data), 0, a
+
+
+def suggest_dt(verts, tets, coeffs, N, model, cfl=0.5):
+    m, keep = make_mesh(verts, tets)
+    cf = np.ascontiguousarray(coeffs, dtype=np.float64)
+    out = C.c_double()
+    check(lib().dg_suggest_dt(C.byref(m), _dptr(cf), int(N), _model(model), float(cfl), C.byref(out)))
+    return out.value
+
+
+def reference_element(N):
+    Np = (N + 1) * (N + 2) * (N + 3) // 6
+    Nfp = (N + 1) * (N + 2) // 2
+    nodes = np.zeros((Np, 3))
+    Dr, Ds, Dt = (np.zeros((Np, Np)) for _ in range(3))
+    LIFT = np.zeros((Np, 4 * Nfp))
+    fm = np.zeros((4, Nfp), dtype=np.int32)
+    check(lib().dg_reference_element(int(N), _dptr(nodes), _dptr(Dr), _dptr(Ds), _dptr(Dt), _dptr(LIFT),
+                                     fm.ctypes.data_as(C.POINTER(C.c_int32))))
+    return dict(nodes=nodes, Dr=Dr, Ds=Ds, Dt=Dt, LIFT=LIFT, fmask=fm)
+
+
+class Solver:
+    """One DG discretisation on the GPU (a dg_handle)."""
+
+    def __init__(self, verts, tets, coeffs, N, model="acoustic", flux="upwind", bc=None, dt=0.0,
+                 stream=None):
+        m, keep = make_mesh(verts, tets)
+        cf = np.ascontiguousarray(coeffs, dtype=np.float64)
+        o = Opts(FLUX[flux], BC[bc], 0, 0, float(dt), C.c_void_p(stream or 0))
+        h = C.c_void_p()
+        check(lib().dg_setup(C.byref(m), _dptr(cf), int(N), _model(model), C.byref(o), C.byref(h)))
+        self.h = h
+        K, Np, Nfp, Nf = C.c_int64(), C.c_int(), C.c_int(), C.c_int()
+        check(lib().dg_info(h, C.byref(K), C.byref(Np), C.byref(Nfp), C.byref(Nf)))
+        self.K, self.Np, self.Nfp, self.Nf = K.value, Np.value, Nfp.value, Nf.value
+        self.N, self.model = int(N), _model(model)
+        self.shape = (self.K, self.Nf, self.Np)
+
+    @property
+    def size(self):
+        return self.K * self.Nf * self.Np
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dg_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_state(self, q, r1=None, r2=None, step=0):
+        pq, dq, kq = _buf(q, np.float32, self.size)
+        p1 = p2 = None
+        keep = []
+        if r1 is not None:
+            p1, d1, k1 = _buf(r1, np.float32, self.size)
+            p2, d2, k2 = _buf(r2, np.float32, self.size)
+            keep += [k1, k2]
+            if not (dq == d1 == d2):
+                raise ValueError("q, r1 and r2 must all be host or all device")
+        check(lib().dg_set_state(self.h, pq, p1, p2, int(step), dq))
+
+    def get_state(self, q=None, r1=None, r2=None):
+        ret = q is None
+        if q is None:
+            q = np.empty(self.shape, dtype=np.float32)
+        pq, dq, _ = _buf(q, np.float32, self.size, write=True)
+        p1 = _buf(r1, np.float32, self.size, write=True)[0] if r1 is not None else None
+        p2 = _buf(r2, np.float32, self.size, write=True)[0] if r2 is not None else None
+        step, hist = C.c_int64(), C.c_int()
+        check(lib().dg_get_state(self.h, pq, p1, p2, C.byref(step), C.byref(hist), dq))
+        self.step_index, self.history = step.value, hist.value
+        return q if ret else None
+
+    def rhs(self, out=None):
+        ret = out is None
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float32)
+        p, d, _ = _buf(out, np.float32, self.size, write=True)
+        check(lib().dg_rhs(self.h, p, d))
+        return out if ret else None
+
+    def set_dt(self, dt):
+        check(lib().dg_set_dt(self.h, float(dt)))
+
+    def step(self, n=1):
+        check(lib().dg_step(self.h, int(n)))
+
+    def sync(self):
+        check(lib().dg_sync(self.h))
+
+    def node_coords(self):
+        x = np.empty((self.K, self.Np, 3))
+        check(lib().dg_node_coords(self.h, _dptr(x)))
+        return x
+
+    def set_source(self, xs, amp, direction=(0.0, 0.0, 1.0)):
+        if amp is None:
+            check(lib().dg_set_source(self.h, None, None, None, 0))
+            return
+        xs = np.ascontiguousarray(xs, dtype=np.float64)
+        d = np.ascontiguousarray(direction, dtype=np.float64)
+        a = np.ascontiguousarray(amp, dtype=np.float64)
+        check(lib().dg_set_source(self.h, _dptr(xs), _dptr(d), _dptr(a), a.size))

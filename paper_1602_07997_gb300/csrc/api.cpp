@@ -1,0 +1,438 @@
+// C ABI of libdg: set-up, state management and the time loop (see include/dg.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "dg_args.h"
+#include "dg_internal.h"
+#include "dg_handle.h"
+
+namespace dg {
+
+static thread_local std::string g_err;
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(DG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define DG_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t _e = (call);                           \
+    if (_e != cudaSuccess) return dg::cuda_fail(_e, #call); \
+  } while (0)
+
+// Pack the element records of kernel layout kGeo (see dg_args.h).
+static void pack_geo(const HostMesh& m, const double* coeffs, int model, int64_t Kpad,
+                     std::vector<float>& geo) {
+  geo.assign(size_t(Kpad) * dgk::kGeo, 0.0f);
+  for (int64_t k = 0; k < Kpad; ++k) {
+    float* o = &geo[size_t(k) * dgk::kGeo];
+    if (k >= m.K) {  // padding element: identity geometry, unit medium
+      o[0] = o[4] = o[8] = 1.0f;
+      for (int i = 9; i < 16; ++i) o[i] = 1.0f;
+      continue;
+    }
+    for (int i = 0; i < 9; ++i) o[i] = float(m.g[9 * k + i]);
+    if (model == DG_ACOUSTIC) {
+      double rho = coeffs[2 * k], c = coeffs[2 * k + 1];
+      o[9] = float(rho * c * c);
+      o[10] = float(1.0 / rho);
+      o[11] = float(rho * c);
+      o[12] = float(c);
+    } else {
+      double lam = coeffs[3 * k], mu = coeffs[3 * k + 1], rho = coeffs[3 * k + 2];
+      double cp = std::sqrt((lam + 2 * mu) / rho), cs = std::sqrt(mu / rho);
+      o[9] = float(lam);
+      o[10] = float(mu);
+      o[11] = float(1.0 / rho);
+      o[12] = float(rho * cp);
+      o[13] = float(rho * cs);
+      o[14] = float(cp);
+      o[15] = float(cs);
+    }
+  }
+}
+
+int check_coeffs(const double* coeffs, int64_t K, int model) {
+  if (!coeffs) return fail(DG_EINVAL, "coefficients are NULL");
+  const int nc = model == DG_ACOUSTIC ? 2 : 3;
+  for (int64_t k = 0; k < K; ++k)
+    for (int c = 0; c < nc; ++c) {
+      double v = coeffs[nc * k + c];
+      bool ok = std::isfinite(v) && (model == DG_ELASTIC && c == 0 ? v >= 0 : v > 0);
+      if (!ok) return fail(DG_EINVAL, "non-physical coefficient at element " + std::to_string(k));
+    }
+  return DG_OK;
+}
+
+// Build operator blob [KD][Mpad] and face tables in kernel layout.
+void pack_ops(const RefElement& R, std::vector<float>& ops, std::vector<int>& ftab) {
+  const int Np = R.Np, Nfp = R.Nfp, Mpad = (Np + 3) & ~3, KD = 3 * Np + 4 * Nfp;
+  ops.assign(size_t(KD) * Mpad, 0.0f);
+  const std::vector<double>* D[3] = {&R.Dr, &R.Ds, &R.Dt};
+  for (int d = 0; d < 3; ++d)
+    for (int j = 0; j < Np; ++j)
+      for (int i = 0; i < Np; ++i) ops[size_t(d * Np + j) * Mpad + i] = float((*D[d])[size_t(i) * Np + j]);
+  for (int c = 0; c < 4 * Nfp; ++c)
+    for (int i = 0; i < Np; ++i) ops[size_t(3 * Np + c) * Mpad + i] = float(R.LIFT[size_t(i) * 4 * Nfp + c]);
+  ftab.assign(10 * Nfp, 0);
+  for (int i = 0; i < 4 * Nfp; ++i) ftab[i] = R.fmask[i];
+  for (int i = 0; i < 6 * Nfp; ++i) ftab[4 * Nfp + i] = R.perm[i];
+}
+
+double suggest_dt(const HostMesh& m, const double* coeffs, int N, int model, double cfl) {
+  double best = 1e300;
+  for (int64_t k = 0; k < m.K; ++k) {
+    double cmax;
+    if (model == DG_ACOUSTIC) cmax = coeffs[2 * k + 1];
+    else cmax = std::sqrt((coeffs[3 * k] + 2 * coeffs[3 * k + 1]) / coeffs[3 * k + 2]);
+    for (int f = 0; f < 4; ++f)
+      best = std::min(best, 1.0 / (cmax * m.fscale[4 * k + f] * (N + 1) * (N + 1)));
+  }
+  return cfl * best;
+}
+
+// ---------------------------------------------------------------- handle
+int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_, const dg_opts* o) {
+  if (model_ != DG_ACOUSTIC && model_ != DG_ELASTIC) return fail(DG_EINVAL, "unknown model");
+  if (N_ < 1 || N_ > 8) return fail(DG_EINVAL, "polynomial degree N must be in 1..8");
+  model = model_;
+  N = N_;
+  if (o) opts = *o;
+  if (opts.flux != DG_FLUX_UPWIND && opts.flux != DG_FLUX_CENTERED) return fail(DG_EINVAL, "unknown flux");
+  if (opts.bc < DG_BC_DEFAULT || opts.bc > DG_BC_FREE) return fail(DG_EINVAL, "unknown boundary condition");
+  if (model == DG_ACOUSTIC && opts.bc == DG_BC_FREE)
+    return fail(DG_EINVAL, "acoustic model supports rigid walls only");
+  if (opts.precision != DG_FP32) return fail(DG_EINVAL, "unknown precision mode");
+  stream = static_cast<cudaStream_t>(opts.stream);
+  int rc = ref.build(N);
+  if (rc) return rc;
+  rc = hm.build(mesh);
+  if (rc) return rc;
+  rc = check_coeffs(coeffs_, hm.K, model);
+  if (rc) return rc;
+  Np = ref.Np;
+  Nfp = ref.Nfp;
+  Nf = num_fields(model);
+  K = hm.K;
+  cfg = dgk::kernel_cfg(model, N);
+  // every launch reads whole blocks of EB <= 128 elements with bulk copies:
+  // pad the element arrays so that the last block stays inside the allocation
+  Kpad = (K + 3) / 4 * 4 + 128;
+  coeffs.assign(coeffs_, coeffs_ + K * (model == DG_ACOUSTIC ? 2 : 3));
+  verts.assign(mesh->verts, mesh->verts + 3 * mesh->nverts);
+  tets.assign(mesh->tets, mesh->tets + 4 * mesh->ntets);
+  DG_CUDA(cudaGetDevice(&device));
+
+  std::vector<float> geo, ops;
+  std::vector<int> ftab;
+  pack_geo(hm, coeffs.data(), model, Kpad, geo);
+  pack_ops(ref, ops, ftab);
+  std::vector<int32_t> nbr(size_t(Kpad) * 4, -1);
+  std::vector<uint32_t> code(Kpad, 0x80808080u);
+  std::copy(hm.nbr.begin(), hm.nbr.end(), nbr.begin());
+  std::copy(hm.code.begin(), hm.code.end(), code.begin());
+
+  const size_t nstate = size_t(Kpad) * Nf * Np;
+  state_bytes = nstate * 4;
+  auto rnd = [](size_t b) { return (b + 255) & ~size_t(255); };
+  size_t need = 0;
+  for (size_t b : {state_bytes, state_bytes, state_bytes, state_bytes, geo.size() * 4, nbr.size() * 4,
+                   code.size() * 4, ops.size() * 4, ftab.size() * 4, size_t(Nf) * Np * 4, size_t(4)})
+    need += rnd(b);
+  DG_CUDA(cudaMalloc(&d_base, need));
+  device_bytes = need;
+  char* p = static_cast<char*>(d_base);
+  auto take = [&](size_t bytes) {
+    char* r = p;
+    p += rnd(bytes);
+    return r;
+  };
+  d_q[0] = reinterpret_cast<float*>(take(state_bytes));
+  d_q[1] = reinterpret_cast<float*>(take(state_bytes));
+  d_r[0] = reinterpret_cast<float*>(take(state_bytes));
+  d_r[1] = reinterpret_cast<float*>(take(state_bytes));
+  d_geo = reinterpret_cast<float*>(take(geo.size() * 4));
+  d_nbr = reinterpret_cast<int32_t*>(take(nbr.size() * 4));
+  d_code = reinterpret_cast<uint32_t*>(take(code.size() * 4));
+  d_ops = reinterpret_cast<float*>(take(ops.size() * 4));
+  d_ftab = reinterpret_cast<int*>(take(ftab.size() * 4));
+  d_src = reinterpret_cast<float*>(take(size_t(Nf) * Np * 4));
+  d_err = reinterpret_cast<int*>(take(4));
+  DG_CUDA(cudaMemsetAsync(d_base, 0, 4 * state_bytes, stream));
+  DG_CUDA(cudaMemcpyAsync(d_geo, geo.data(), geo.size() * 4, cudaMemcpyHostToDevice, stream));
+  DG_CUDA(cudaMemcpyAsync(d_nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice, stream));
+  DG_CUDA(cudaMemcpyAsync(d_code, code.data(), code.size() * 4, cudaMemcpyHostToDevice, stream));
+  DG_CUDA(cudaMemcpyAsync(d_ops, ops.data(), ops.size() * 4, cudaMemcpyHostToDevice, stream));
+  DG_CUDA(cudaMemcpyAsync(d_ftab, ftab.data(), ftab.size() * 4, cudaMemcpyHostToDevice, stream));
+  DG_CUDA(cudaMemsetAsync(d_err, 0, 4, stream));
+  DG_CUDA(cudaStreamSynchronize(stream));  // host vectors go out of scope
+  qcur = 0;
+  r1slot = 0;
+  step = 0;
+  have = 0;
+  return DG_OK;
+}
+
+Handle::~Handle() {
+  if (d_base) cudaFree(d_base);
+}
+
+dgk::StepArgs Handle::args(int mode) const {
+  dgk::StepArgs a{};
+  a.q = d_q[qcur];
+  a.qn = d_q[1 - qcur];
+  a.r1 = d_r[r1slot];
+  a.r2 = d_r[1 - r1slot];
+  a.geo = d_geo;
+  a.nbr = reinterpret_cast<const int4*>(d_nbr);
+  a.code = d_code;
+  a.ops = d_ops;
+  a.ftab = d_ftab;
+  a.srcvec = src_elem >= 0 ? d_src : nullptr;
+  a.src_elem = src_elem;
+  a.src_amp = (src_elem >= 0 && step >= 0 && step < int64_t(src_amp.size())) ? float(src_amp[step]) : 0.0f;
+  a.K = int(K);
+  a.mode = mode;
+  a.flux = opts.flux;
+  a.bc = (model == DG_ELASTIC && opts.bc == DG_BC_RIGID) ? 1 : 0;
+  a.dt = float(opts.dt);
+  if (have == 0) { a.a1 = 1.0f; a.a2 = 0.0f; a.a3 = 0.0f; }
+  else if (have == 1) { a.a1 = 1.5f; a.a2 = -0.5f; a.a3 = 0.0f; }
+  else { a.a1 = float(23.0 / 12.0); a.a2 = float(-16.0 / 12.0); a.a3 = float(5.0 / 12.0); }
+  a.err = d_err;
+  return a;
+}
+
+int Handle::advance(int nsteps) {
+  for (int s = 0; s < nsteps; ++s) {
+    dgk::StepArgs a = args(0);
+    DG_CUDA(dgk::launch_step(model, N, a, stream));
+    qcur ^= 1;
+    r1slot ^= 1;  // r^m was written into the r^{m-2} slot
+    ++step;
+    have = std::min(have + 1, 2);
+  }
+  return DG_OK;
+}
+
+}  // namespace dg
+
+using dg::fail;
+
+extern "C" {
+
+const char* dg_last_error(void) { return dg::g_err.c_str(); }
+
+int dg_setup(const dg_mesh* mesh, const double* coeffs, int N, int model, const dg_opts* opts,
+             dg_handle** out) {
+  if (!out) return fail(DG_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto* h = new (std::nothrow) dg_handle();
+  if (!h) return fail(DG_ENOMEM, "host allocation failed");
+  int rc = h->init(mesh, coeffs, N, model, opts);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return DG_OK;
+}
+
+void dg_destroy(dg_handle* h) { delete h; }
+
+int dg_info(const dg_handle* h, int64_t* K, int* Np, int* Nfp, int* Nf) {
+  if (!h) return fail(DG_EINVAL, "NULL handle");
+  if (K) *K = h->K;
+  if (Np) *Np = h->Np;
+  if (Nfp) *Nfp = h->Nfp;
+  if (Nf) *Nf = h->Nf;
+  return DG_OK;
+}
+
+int dg_set_state(dg_handle* h, const float* q, const float* r1, const float* r2, int64_t step,
+                 int on_device) {
+  if (!h || !q) return fail(DG_EINVAL, "NULL handle or state");
+  if ((r1 == nullptr) != (r2 == nullptr)) return fail(DG_EINVAL, "give both r1 and r2 or neither");
+  const size_t bytes = size_t(h->K) * h->Nf * h->Np * 4;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  DG_CUDA(cudaMemcpyAsync(h->d_q[h->qcur], q, bytes, kind, h->stream));
+  if (r1) {
+    DG_CUDA(cudaMemcpyAsync(h->d_r[h->r1slot], r1, bytes, kind, h->stream));
+    DG_CUDA(cudaMemcpyAsync(h->d_r[1 - h->r1slot], r2, bytes, kind, h->stream));
+    h->have = 2;
+  } else {
+    DG_CUDA(cudaMemsetAsync(h->d_r[0], 0, h->state_bytes, h->stream));
+    DG_CUDA(cudaMemsetAsync(h->d_r[1], 0, h->state_bytes, h->stream));
+    h->have = 0;
+  }
+  h->step = step;
+  if (!on_device) DG_CUDA(cudaStreamSynchronize(h->stream));
+  return DG_OK;
+}
+
+int dg_get_state(dg_handle* h, float* q, float* r1, float* r2, int64_t* step, int* history,
+                 int on_device) {
+  if (!h) return fail(DG_EINVAL, "NULL handle");
+  const size_t bytes = size_t(h->K) * h->Nf * h->Np * 4;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (q) DG_CUDA(cudaMemcpyAsync(q, h->d_q[h->qcur], bytes, kind, h->stream));
+  if (r1) DG_CUDA(cudaMemcpyAsync(r1, h->d_r[h->r1slot], bytes, kind, h->stream));
+  if (r2) DG_CUDA(cudaMemcpyAsync(r2, h->d_r[1 - h->r1slot], bytes, kind, h->stream));
+  if (step) *step = h->step;
+  if (history) *history = h->have;
+  if (!on_device) DG_CUDA(cudaStreamSynchronize(h->stream));
+  return DG_OK;
+}
+
+int dg_rhs(dg_handle* h, float* r_out, int on_device) {
+  if (!h || !r_out) return fail(DG_EINVAL, "NULL handle or output");
+  dgk::StepArgs a = h->args(1);
+  float* tmp = nullptr;
+  const size_t bytes = size_t(h->K) * h->Nf * h->Np * 4;
+  if (on_device) {
+    a.rout = r_out;
+  } else {
+    DG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&tmp), bytes, h->stream));
+    a.rout = tmp;
+  }
+  cudaError_t e = dgk::launch_step(h->model, h->N, a, h->stream);
+  if (e != cudaSuccess) {
+    if (tmp) cudaFreeAsync(tmp, h->stream);
+    return dg::cuda_fail(e, "launch");
+  }
+  if (!on_device) {
+    DG_CUDA(cudaMemcpyAsync(r_out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream));
+    DG_CUDA(cudaFreeAsync(tmp, h->stream));
+    DG_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  return DG_OK;
+}
+
+int dg_step(dg_handle* h, int nsteps) {
+  if (!h || nsteps < 0) return fail(DG_EINVAL, "NULL handle or negative step count");
+  if (!(h->opts.dt > 0)) return fail(DG_EINVAL, "dt must be positive (dg_opts.dt or dg_set_dt)");
+  return h->advance(nsteps);
+}
+
+int dg_set_dt(dg_handle* h, double dt) {
+  if (!h || !(dt > 0) || !std::isfinite(dt)) return fail(DG_EINVAL, "dt must be positive");
+  h->opts.dt = dt;
+  return DG_OK;
+}
+
+int dg_sync(dg_handle* h) {
+  if (!h) return fail(DG_EINVAL, "NULL handle");
+  DG_CUDA(cudaStreamSynchronize(h->stream));
+  int err = 0;
+  DG_CUDA(cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost));
+  if (err) return fail(DG_ETIMEOUT, "a bounded device-side wait expired");
+  return DG_OK;
+}
+
+int dg_node_coords(const dg_handle* h, double* xyz) {
+  if (!h || !xyz) return fail(DG_EINVAL, "NULL handle or output");
+  const auto& R = h->ref;
+  for (int64_t k = 0; k < h->K; ++k) {
+    const double* x1 = &h->verts[3 * h->tets[4 * k]];
+    const double* A = &h->hm.A[9 * k];
+    for (int n = 0; n < R.Np; ++n) {
+      double u[3] = {1 + R.r[n], 1 + R.s[n], 1 + R.t[n]};
+      for (int i = 0; i < 3; ++i)
+        xyz[(size_t(k) * R.Np + n) * 3 + i] = x1[i] + A[3 * i] * u[0] + A[3 * i + 1] * u[1] + A[3 * i + 2] * u[2];
+    }
+  }
+  return DG_OK;
+}
+
+int dg_set_source(dg_handle* h, const double xs[3], const double dir[3], const double* amp, int64_t namp) {
+  if (!h) return fail(DG_EINVAL, "NULL handle");
+  if (!amp || namp <= 0) {
+    h->src_elem = -1;
+    h->src_amp.clear();
+    return DG_OK;
+  }
+  if (!xs) return fail(DG_EINVAL, "source position is NULL");
+  // element whose smallest barycentric coordinate of xs is largest
+  int64_t best = -1;
+  double bestmin = -1e300, brst[3] = {0, 0, 0};
+  for (int64_t k = 0; k < h->K; ++k) {
+    const double* x1 = &h->verts[3 * h->tets[4 * k]];
+    const double* gk = &h->hm.g[9 * k];
+    double d[3] = {xs[0] - x1[0], xs[1] - x1[1], xs[2] - x1[2]};
+    double rst[3];
+    for (int j = 0; j < 3; ++j) rst[j] = gk[j] * d[0] + gk[3 + j] * d[1] + gk[6 + j] * d[2] - 1.0;
+    double lam[4] = {-(1 + rst[0] + rst[1] + rst[2]) / 2, (1 + rst[0]) / 2, (1 + rst[1]) / 2, (1 + rst[2]) / 2};
+    double mn = std::min(std::min(lam[0], lam[1]), std::min(lam[2], lam[3]));
+    if (mn > bestmin) {
+      bestmin = mn;
+      best = k;
+      std::memcpy(brst, rst, sizeof(brst));
+    }
+  }
+  if (best < 0 || bestmin < -1e-9) return fail(DG_EINVAL, "source position outside the mesh");
+  // M_k^{-1} l(x_s) = V psi(x_s) / J_k  (V orthonormal Vandermonde)
+  const auto& R = h->ref;
+  std::vector<double> psi(R.Np), b(R.Np, 0.0);
+  R.basis(brst[0], brst[1], brst[2], psi.data());
+  for (int i = 0; i < R.Np; ++i) {
+    double acc = 0;
+    for (int m = 0; m < R.Np; ++m) acc += R.V[size_t(i) * R.Np + m] * psi[m];
+    b[i] = acc / h->hm.J[best];
+  }
+  std::vector<float> vec(size_t(h->Nf) * R.Np, 0.0f);
+  if (h->model == DG_ACOUSTIC) {
+    for (int i = 0; i < R.Np; ++i) vec[i] = float(b[i]);
+  } else {
+    double dd[3] = {0, 0, 1};
+    if (dir) std::memcpy(dd, dir, sizeof(dd));
+    double rho = h->coeffs[3 * best + 2];
+    for (int c = 0; c < 3; ++c)
+      for (int i = 0; i < R.Np; ++i) vec[size_t(c) * R.Np + i] = float(dd[c] / rho * b[i]);
+  }
+  DG_CUDA(cudaMemcpyAsync(h->d_src, vec.data(), vec.size() * 4, cudaMemcpyHostToDevice, h->stream));
+  DG_CUDA(cudaStreamSynchronize(h->stream));
+  h->src_elem = int(best);
+  h->src_amp.assign(amp, amp + namp);
+  return DG_OK;
+}
+
+int dg_suggest_dt(const dg_mesh* mesh, const double* coeffs, int N, int model, double cfl, double* dt) {
+  if (!dt || !(cfl > 0)) return fail(DG_EINVAL, "bad arguments");
+  if (N < 1 || N > 8) return fail(DG_EINVAL, "polynomial degree N must be in 1..8");
+  dg::HostMesh m;
+  int rc = m.build(mesh);
+  if (rc) return rc;
+  rc = dg::check_coeffs(coeffs, m.K, model);
+  if (rc) return rc;
+  *dt = dg::suggest_dt(m, coeffs, N, model, cfl);
+  return DG_OK;
+}
+
+int dg_reference_element(int N, double* nodes, double* Dr, double* Ds, double* Dt, double* LIFT, int* fmask) {
+  dg::RefElement R;
+  int rc = R.build(N);
+  if (rc) return rc;
+  const size_t Np = R.Np;
+  if (nodes)
+    for (size_t n = 0; n < Np; ++n) {
+      nodes[3 * n] = R.r[n];
+      nodes[3 * n + 1] = R.s[n];
+      nodes[3 * n + 2] = R.t[n];
+    }
+  if (Dr) std::memcpy(Dr, R.Dr.data(), Np * Np * sizeof(double));
+  if (Ds) std::memcpy(Ds, R.Ds.data(), Np * Np * sizeof(double));
+  if (Dt) std::memcpy(Dt, R.Dt.data(), Np * Np * sizeof(double));
+  if (LIFT) std::memcpy(LIFT, R.LIFT.data(), R.LIFT.size() * sizeof(double));
+  if (fmask) std::memcpy(fmask, R.fmask.data(), R.fmask.size() * sizeof(int));
+  return DG_OK;
+}
+
+}  // extern "C"

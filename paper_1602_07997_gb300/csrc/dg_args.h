@@ -1,0 +1,48 @@
+// Kernel argument block and launch table of the fused step kernel
+// (plain C++; shared by the host library and the CUDA units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgk {
+
+constexpr int kGeo = 16;  // floats per element record
+// acoustic record: g[9] (row-major g[c][d] = dr_d/dx_c), kappa, 1/rho, Z, c
+// elastic  record: g[9], lambda, mu, 1/rho, Zp, Zs, cp, cs
+
+struct StepArgs {
+  const float* q;        // q^m   [Kpad][Nf][Np]
+  float* qn;             // q^m+1 [Kpad][Nf][Np]            (mode 0)
+  const float* r1;       // r^m-1                            (mode 0)
+  float* r2;             // in r^m-2, out r^m                (mode 0)
+  float* rout;           // r^m [K][Nf][Np]                  (mode 1)
+  const float* geo;      // [Kpad][kGeo]
+  const int4* nbr;       // [Kpad] neighbour per face, -1 = boundary
+  const uint32_t* code;  // [Kpad] per face: f' (bits 0-1), rotation (2-4), boundary (7)
+  const float* ops;      // [KD][Mpad]: rows d*Np+j -> D_d[i][j]; rows 3Np+c -> LIFT[i][c]
+  const int* ftab;       // [4][Nfp] face masks, then [6][Nfp] rotations
+  const float* srcvec;   // [Nf][Np] source shape (times amplitude) or null
+  float src_amp;
+  int src_elem;          // element holding the source, -1 = none
+  int K;
+  int mode;              // 0 = AB3 step, 1 = RHS only
+  int flux;              // 0 upwind, 1 centred
+  int bc;                // acoustic: rigid; elastic: 0 free, 1 rigid
+  float dt, a1, a2, a3;
+  int* err;              // device error word (bounded-wait expiry)
+};
+
+// Host-visible launch configuration of one (model, N) instantiation.
+struct KernelCfg {
+  int EB, TN, NT;
+  bool ops_smem;
+  size_t smem;
+  void (*fn)(StepArgs);
+};
+
+const KernelCfg* kernel_cfg(int model, int N);
+
+cudaError_t launch_step(int model, int N, const StepArgs& args, cudaStream_t stream);
+
+}  // namespace dgk

@@ -1,0 +1,58 @@
+// The solver handle behind the opaque dg_handle of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "dg_args.h"
+#include "dg_internal.h"
+
+namespace dg {
+
+int cuda_fail(cudaError_t e, const char* what);
+int check_coeffs(const double* coeffs, int64_t K, int model);
+void pack_ops(const RefElement& R, std::vector<float>& ops, std::vector<int>& ftab);
+double suggest_dt(const HostMesh& m, const double* coeffs, int N, int model, double cfl);
+
+struct Handle {
+  int model = 0, N = 0, Np = 0, Nfp = 0, Nf = 0, device = 0;
+  int64_t K = 0, Kpad = 0;
+  dg_opts opts{};
+  cudaStream_t stream = nullptr;
+  RefElement ref;
+  HostMesh hm;
+  std::vector<double> coeffs, verts;
+  std::vector<int64_t> tets;
+  const dgk::KernelCfg* cfg = nullptr;
+
+  // device memory: one allocation carved into the pieces below
+  void* d_base = nullptr;
+  size_t device_bytes = 0, state_bytes = 0;
+  float* d_q[2] = {nullptr, nullptr};  // ping-pong q^m / q^{m+1}
+  float* d_r[2] = {nullptr, nullptr};  // AB3 history slots
+  float* d_geo = nullptr;
+  int32_t* d_nbr = nullptr;
+  uint32_t* d_code = nullptr;
+  float* d_ops = nullptr;
+  int* d_ftab = nullptr;
+  float* d_src = nullptr;
+  int* d_err = nullptr;
+
+  int qcur = 0;    // which q buffer holds q^m
+  int r1slot = 0;  // which r buffer holds r^{m-1}; the other holds r^{m-2}
+  int64_t step = 0;
+  int have = 0;    // stored RHS levels (0, 1, 2)
+  int src_elem = -1;
+  std::vector<double> src_amp;
+
+  int init(const dg_mesh* mesh, const double* coeffs, int N, int model, const dg_opts* o);
+  dgk::StepArgs args(int mode) const;
+  int advance(int nsteps);
+  ~Handle();
+};
+
+}  // namespace dg
+
+struct dg_handle : dg::Handle {};

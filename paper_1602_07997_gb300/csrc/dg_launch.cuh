@@ -1,0 +1,19 @@
+// Launch helpers shared by the per-model instantiation units.
+#pragma once
+#include "dg_kernels.cuh"
+
+namespace dgk {
+
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM>
+KernelCfg make_cfg() {
+  KernelCfg c;
+  c.EB = EB;
+  c.TN = TN;
+  c.NT = NT;
+  c.ops_smem = OPS_SMEM;
+  c.smem = Plan<MODEL, N, EB, OPS_SMEM>::bytes;
+  c.fn = dg_step_kernel<MODEL, N, EB, TN, NT, OPS_SMEM>;
+  return c;
+}
+
+}  // namespace dgk

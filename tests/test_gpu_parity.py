@@ -1,0 +1,164 @@
+"""GPU parity: libdg (FP32, CUDA) against the FP64 oracle on the same seeded inputs.
+
+Bar (relative L2 per field group, max over groups; acoustic {p},{v},
+elastic {v},{sigma}): <= 1e-5 after one RHS evaluation and <= 1e-4 after 100
+AB3 steps.  Meshes span several CTA blocks plus a ragged tail for every N.
+"""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.dg import Solver as OSolver, AB3Stepper
+
+RHS_TOL = 1e-5
+STEP_TOL = 1e-4
+
+
+def groups(model):
+    return ((0,), (1, 2, 3)) if model == "acoustic" else ((0, 1, 2), tuple(range(3, 9)))
+
+
+def rel_l2(model, a, b):
+    out = 0.0
+    for g in groups(model):
+        num = np.linalg.norm((np.asarray(a, np.float64)[:, g] - b[:, g]).ravel())
+        den = np.linalg.norm(b[:, g].ravel())
+        out = max(out, num / den)
+    return out
+
+
+def _mesh(model, n, seed):
+    verts, tets = W.kuhn_cube_mesh(n, 0.1, seed=seed)
+    K = tets.shape[0]
+    coeffs = (W.acoustic_coefficients(K, 1, 3, seed=seed + 1) if model == "acoustic"
+              else W.elastic_two_layer(verts, tets, seed=seed + 1))
+    return verts, tets, coeffs
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import paper_1602_07997_gb300 as P
+    P.lib()
+    return P
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("model", ["acoustic", "elastic"])
+@pytest.mark.parametrize("N", range(1, 9))
+def test_rhs_parity_random_state(dg, model, N):
+    n = 5 if N <= 2 else (4 if N <= 5 else 3)
+    verts, tets, coeffs = _mesh(model, n, 10 + N)
+    o = OSolver(model, N, verts, tets, coeffs)
+    g = dg.Solver(verts, tets, coeffs, N, model)
+    assert np.abs(g.node_coords() - o.mesh.x).max() < 1e-12
+    q = W.random_state(o.K, o.Nf, o.ref.Np, seed=N).astype(np.float32)
+    g.set_state(q)
+    r = g.rhs()
+    ro = o.rhs(q.astype(np.float64))
+    err = rel_l2(model, r, ro)
+    assert err <= RHS_TOL, err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("model,N,flux,bc", [("acoustic", 3, "centered", None),
+                                              ("elastic", 3, "centered", None),
+                                              ("elastic", 2, "upwind", "rigid"),
+                                              ("elastic", 4, "centered", "rigid")])
+def test_rhs_parity_flux_and_bc_variants(dg, model, N, flux, bc):
+    verts, tets, coeffs = _mesh(model, 3, 40 + N)
+    o = OSolver(model, N, verts, tets, coeffs, flux=flux, bc=bc)
+    g = dg.Solver(verts, tets, coeffs, N, model, flux=flux, bc=bc)
+    q = W.random_state(o.K, o.Nf, o.ref.Np, seed=3).astype(np.float32)
+    g.set_state(q)
+    assert rel_l2(model, g.rhs(), o.rhs(q.astype(np.float64))) <= RHS_TOL
+
+
+@pytest.mark.gpu
+def test_config1_100_steps(dg):
+    """Config 1: 384 tets, N=2, Gaussian pulse, rigid walls, upwind, 100 AB3 steps."""
+    cfg = W.config1_acoustic_small()
+    o = OSolver("acoustic", 2, cfg["verts"], cfg["tets"], cfg["coeffs"])
+    dt = o.suggest_dt(cfg["cfl"])
+    q0 = np.zeros((o.K, 4, o.ref.Np))
+    q0[:, 0] = W.gaussian_pulse(o.mesh.x)
+    g = dg.Solver(cfg["verts"], cfg["tets"], cfg["coeffs"], 2, "acoustic", dt=dt)
+    assert abs(dg.suggest_dt(cfg["verts"], cfg["tets"], cfg["coeffs"], 2, "acoustic", cfg["cfl"]) - dt) < 1e-15
+    g.set_state(q0.astype(np.float32))
+    g.step(100)
+    g.sync()
+    st = AB3Stepper(o, q0, dt)
+    st.step(100)
+    err = rel_l2("acoustic", g.get_state(), st.q)
+    assert err <= STEP_TOL, err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("model,N", [("acoustic", 1), ("acoustic", 4), ("acoustic", 7),
+                                     ("elastic", 1), ("elastic", 3), ("elastic", 6)])
+def test_100_steps_with_source(dg, model, N):
+    """100 AB3 steps from a Gaussian / quiescent state with a Ricker point source."""
+    n = 3 if N <= 4 else 2
+    verts, tets, coeffs = _mesh(model, n, 70 + N)
+    o = OSolver(model, N, verts, tets, coeffs)
+    dt = o.suggest_dt(0.5)
+    amp = W.ricker(np.arange(100) * dt, f0=4.0, t0=0.05) * 10.0
+    xs = (0.4321, 0.5678, 0.4876)
+    ko = o.set_source(xs, amp, direction=(0.3, -0.2, 0.9))
+    q0 = np.zeros((o.K, o.Nf, o.ref.Np))
+    q0[:, 0] = W.gaussian_pulse(o.mesh.x, width=0.3)
+    g = dg.Solver(verts, tets, coeffs, N, model, dt=dt)
+    g.set_source(xs, amp, direction=(0.3, -0.2, 0.9))
+    g.set_state(q0.astype(np.float32))
+    g.step(100)
+    g.sync()
+    st = AB3Stepper(o, q0, dt)
+    st.step(100)
+    err = rel_l2(model, g.get_state(), st.q)
+    assert err <= STEP_TOL, (err, ko)
+
+
+@pytest.mark.gpu
+def test_rhs_device_buffers_and_history(dg):
+    """Device (torch) buffers give the same results as host buffers; a given
+    AB3 history is used; get_state returns what set_state put."""
+    import torch
+    model, N = "acoustic", 3
+    verts, tets, coeffs = _mesh(model, 3, 5)
+    g = dg.Solver(verts, tets, coeffs, N, model, dt=1e-3)
+    rng = np.random.default_rng(0)
+    q, r1, r2 = (rng.uniform(-1, 1, size=g.shape).astype(np.float32) for _ in range(3))
+    g.set_state(q, r1, r2, step=7)
+    qh = g.get_state()
+    assert np.array_equal(qh, q) and g.step_index == 7 and g.history == 2
+    rh = g.rhs()
+    rd = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    g.rhs(rd)
+    torch.cuda.synchronize()
+    assert np.array_equal(rd.cpu().numpy(), rh)
+    # one AB3 step with the supplied history
+    g.step(1)
+    q1 = g.get_state()
+    expect = q + 1e-3 * (23 * rh + -16 * r1 + 5 * r2) / 12.0
+    assert np.abs(q1 - expect).max() <= 1e-6 * np.abs(expect).max()
+    # device-side set_state
+    qd = torch.from_numpy(q).cuda()
+    g.set_state(qd)
+    assert np.array_equal(g.get_state(), q)
+
+
+@pytest.mark.gpu
+def test_setup_rejects_bad_meshes(dg):
+    verts, tets = W.kuhn_cube_mesh(2, 0.1, seed=1)
+    K = tets.shape[0]
+    coeffs = np.ones((K, 2))
+    bad = tets.copy()
+    bad[0, [2, 3]] = bad[0, [3, 2]]        # inverted
+    with pytest.raises(dg.DGError) as e:
+        dg.Solver(verts, bad, coeffs, 2)
+    assert e.value.code == -1
+    dup = np.concatenate([tets, tets[:1]])  # face shared by 3 tets
+    with pytest.raises(dg.DGError):
+        dg.Solver(verts, dup, np.ones((K + 1, 2)), 2)
+    with pytest.raises(dg.DGError):
+        dg.Solver(verts, tets, coeffs, 9)
