@@ -1,0 +1,378 @@
+"""Benchmark: DG node-field updates/s of the fused RHS + AB3 step on GB300.
+
+Workload: the acoustic degree sweep N = 1..8, one jittered Kuhn cube mesh of
+~2 M nodes per degree (rho, c ~ U[1,3], rigid walls, upwind flux, random
+initial state), FP32.  One bench step = one AB3 time step on each of the
+eight meshes (eight launches of the fused kernel).  value = sum over meshes
+of K*Np*Nf field updates / device time of the step.  The eight meshes hold
+~1.3 GB, so consecutive steps on one mesh never find its state in L2.
+
+Extra keys: per_N (time, updates/s, algorithmic GB/s and GFLOP/s per
+degree), roofline (dominant kernel), cpu_baseline (FP64 oracle on the host),
+e2e (same metric through the C ABI with pinned host buffers, copies inside
+the timed region), clocks (nvidia-smi samples during the timed region).
+
+Multi-GPU: replicas only (the single-GPU path does not shard); each rank runs
+the whole sweep and value = sum of the ranks' updates / max rank time.
+
+``--impl reference`` times the FP64 oracle (the reference arm) instead.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DG node-field updates/s and % HBM/FP32 roofline per N; served p50/p99 solve latency"
+UNIT = "node-field updates/s"
+WORKLOAD = ("acoustic DG sweep N=1..8, jittered Kuhn cube meshes of ~2M nodes per degree, "
+            "rho,c~U[1,3], rigid walls, upwind flux, FP32, AB3")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def peaks():
+    p = {"hbm_gbs": 6758.9, "source": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        p["hbm_gbs"] = float(m["hbm_gbs"])
+        p["source"] = "measured"
+    except Exception:
+        pass
+    # FP32 CUDA-core peak from unit counts and the maximum SM clock
+    p["fp32_tflops"] = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    return p
+
+
+def algorithmic(model, N, K):
+    """Bytes and FLOPs of one fused step over K elements (unpadded, estimated
+    convention): AB3 state 5 arrays x 4 B per field-node (read q^m, r^m-1,
+    r^m-2; write q^m+1, r^m) + 84 B of element records; FLOPs = 2 x the
+    multiply-adds of the operator products + 8 per field-node for AB3."""
+    Np = (N + 1) * (N + 2) * (N + 3) // 6
+    Nfp = (N + 1) * (N + 2) // 2
+    Nf = 4 if model == "acoustic" else 9
+    byt = K * (20 * Nf * Np + 84)
+    if model == "acoustic":
+        mac = 6 * Np * Np + 16 * Np * Nfp
+    else:
+        mac = 18 * Np * Np + 36 * Np * Nfp
+    flop = K * (2 * mac + 8 * Nf * Np)
+    return byt, flop
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_meshes(model, Ns):
+    import workloads as W
+    out = []
+    for N in Ns:
+        cfg = W.sweep_mesh(model, N)
+        out.append(cfg)
+    return out
+
+
+def cpu_baseline(model="acoustic", Ns=(2, 4), steps=1):
+    """FP64 oracle, single thread, one AB3 step on the full ~2 M-node meshes of
+    the listed degrees (a bounded sample of the sweep)."""
+    code = r"""
+import json, sys, time, os
+sys.path.insert(0, %r)
+import numpy as np
+import workloads as W
+from oracle.dg import Solver, AB3Stepper
+res = []
+for N in %r:
+    cfg = W.sweep_mesh(%r, N)
+    S = Solver(%r, N, cfg["verts"], cfg["tets"], cfg["coeffs"])
+    q = W.random_state(S.K, S.Nf, S.ref.Np, seed=0)
+    st = AB3Stepper(S, q, 1e-6)
+    t0 = time.perf_counter()
+    st.step(%d)
+    dt = time.perf_counter() - t0
+    res.append((S.K * S.ref.Np * S.Nf * %d, dt))
+print(json.dumps(res))
+""" % (ROOT, tuple(Ns), model, model, steps, steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if p.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": p.stderr[-500:]}
+    res = json.loads(p.stdout.strip().splitlines()[-1])
+    upd = sum(r[0] for r in res)
+    t = sum(r[1] for r in res)
+    return {"value": upd / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 oracle, %d AB3 step(s) on the full %s meshes for N=%s, single thread"
+                      % (steps, model, ",".join(str(n) for n in Ns)),
+            "seconds": round(t, 2)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    t0 = time.time()
+    base = cpu_baseline("acoustic", Ns=(2, 4), steps=1)
+    per_step = []
+    for _ in range(args.steps):
+        b = cpu_baseline("acoustic", Ns=(2,), steps=1)
+        per_step.append(b)
+    vals = [b["value"] for b in per_step if b["value"]]
+    v = statistics.median(vals) if vals else base["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "oracle on the N=2 mesh per step"},
+            "cpu_baseline": dict(base, value=v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(time.time() - t0, 1)}
+    print(json.dumps(line), flush=True)
+
+
+def run(args, rank, world, local_rank):
+    import torch
+    import paper_1602_07997_gb300 as P
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    model = "acoustic"
+    Ns = [int(x) for x in args.degrees.split(",")]
+    stream = torch.cuda.Stream(device=dev)
+    cfgs = build_meshes(model, Ns)
+    solvers = []
+    for cfg in cfgs:
+        N = cfg["N"]
+        dt = P.suggest_dt(cfg["verts"], cfg["tets"], cfg["coeffs"], N, model, 0.4)
+        g = P.Solver(cfg["verts"], cfg["tets"], cfg["coeffs"], N, model, dt=dt,
+                     stream=stream.cuda_stream)
+        q = np.random.default_rng(N).uniform(-1, 1, size=g.shape).astype(np.float32)
+        g.set_state(q)
+        solvers.append(g)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(args.warmup):
+        for g in solvers:
+            g.step(1)
+    barrier()
+    nN = len(solvers)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(nN)] for _ in range(args.steps)]
+    e_all0, e_all1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        e_all0.record(stream)
+        for s in range(args.steps):
+            for i, g in enumerate(solvers):
+                ev[s][i][0].record(stream)
+                g.step(1)
+                ev[s][i][1].record(stream)
+        e_all1.record(stream)
+        barrier()
+    total_ms = e_all0.elapsed_time(e_all1)
+    per_ms = [statistics.mean(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
+              for i in range(nN)]
+    for g in solvers:
+        g.sync()
+    updates = sum(g.K * g.Np * g.Nf for g in solvers) * args.steps
+    t_local = total_ms / 1e3
+    if world > 1:
+        tt = torch.tensor([t_local, float(updates)], device=dev, dtype=torch.float64)
+        tmax = tt.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        t_job, upd_job = float(tmax[0]), float(tt[1])
+    else:
+        t_job, upd_job = t_local, float(updates)
+    value = upd_job / t_job
+
+    pk = peaks()
+    per_N = {}
+    dom = None
+    for g, ms in zip(solvers, per_ms):
+        byt, flop = algorithmic(model, g.N, g.K)
+        gbs = byt / (ms * 1e-3) / 1e9
+        gfl = flop / (ms * 1e-3) / 1e9
+        intensity = flop / byt
+        ridge = pk["fp32_tflops"] * 1e3 / pk["hbm_gbs"]
+        bound = "hbm" if intensity < ridge else "alu"
+        frac = gbs / pk["hbm_gbs"] if bound == "hbm" else gfl / (pk["fp32_tflops"] * 1e3)
+        per_N[str(g.N)] = {"K": g.K, "nodes": g.K * g.Np, "ms": round(ms, 5),
+                           "updates_per_s": g.K * g.Np * g.Nf / (ms * 1e-3),
+                           "alg_GBs": round(gbs, 1), "alg_GFLOPs": round(gfl, 1),
+                           "bound": bound, "roofline_frac": round(frac, 4)}
+        if dom is None or ms > dom[1]:
+            dom = (g, ms, byt, flop, bound)
+    g, ms, byt, flop, bound = dom
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        ent = tr.get("%s_N%d" % (model, g.N))
+        if ent and ent.get("kernel_rev") == kernel_rev():
+            traffic = ent["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    if bound == "hbm":
+        roof = {"bound": "hbm", "achieved": byt / (ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s"}
+    else:
+        roof = {"bound": "alu", "achieved": flop / (ms * 1e-3) / 1e12, "peak": pk["fp32_tflops"],
+                "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic
+    roof["kernel"] = "dg_step_kernel<acoustic, N=%d>" % g.N
+    roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs (burst copy)" if bound == "hbm"
+                           else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz")
+
+    # e2e through the C ABI: pinned host buffers, H2D of the state and D2H of the
+    # result inside the timed region, every step
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.empty(g.shape, dtype=torch.float32).pin_memory() for g in solvers]
+        for p, g in zip(pinned, solvers):
+            g.get_state(p)
+        e_steps = max(1, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            for p, g in zip(pinned, solvers):
+                g.set_state(p)
+                g.step(1)
+                g.get_state(p)
+        barrier()
+        te = time.perf_counter() - t0
+        e_upd = sum(g.K * g.Np * g.Nf for g in solvers) * e_steps
+        nbytes = sum(g.size * 4 for g in solvers)
+        e2e = {"value": e_upd * world / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": e_steps,
+               "note": "per step and mesh: dg_set_state(pinned host q) + dg_step(1) + dg_get_state(pinned host)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        cpu = cpu_baseline(model, Ns=(2, 4), steps=1)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "degrees": Ns,
+                           "meshes": {str(g.N): g.K for g in solvers},
+                           "l2": "inputs larger than L2: the 8 meshes hold ~1.3 GB, each ~130 MB",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "gpu_launches": nN * args.steps, "roofline": roof, "per_N": per_N,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    for g in solvers:
+        g.close()
+
+
+def kernel_rev():
+    """Hash of the kernel sources (a traffic figure is only valid for them)."""
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_1602_07997_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--degrees", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    from paper_1602_07997_gb300 import build as B
+    if not os.path.exists(B.LIB):
+        raise RuntimeError("libdg.so is not built: run __graft_entry__.build() first")
+    run(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

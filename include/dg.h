@@ -141,7 +141,9 @@ int dg_node_coords(const dg_handle *h, double *xyz);
 int dg_set_source(dg_handle *h, const double xs[3], const double dir[3],
                   const double *amp, int64_t namp);
 
-/* dt = cfl * min_{k,f} 1 / (c_max,k Fscale_{k,f} (N+1)^2), host only.       */
+/* dt = cfl * min_{k,f} 1 / (c_max,k Fscale_{k,f} ((N+1)(N+2)/2 + 2)), host
+ * only; c_max = c (acoustic) or c_p (elastic).  cfl = 0.4 keeps the upwind
+ * spectrum inside the AB3 stability region for N = 1..8.                   */
 int dg_suggest_dt(const dg_mesh *mesh, const double *coeffs, int N, int model,
                   double cfl, double *dt);
 

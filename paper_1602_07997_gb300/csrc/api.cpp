@@ -28,34 +28,60 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (_e != cudaSuccess) return dg::cuda_fail(_e, #call); \
   } while (0)
 
-// Pack the element records of kernel layout kGeo (see dg_args.h).
-static void pack_geo(const HostMesh& m, const double* coeffs, int model, int64_t Kpad,
-                     std::vector<float>& geo) {
-  geo.assign(size_t(Kpad) * dgk::kGeo, 0.0f);
+// Per-element material numbers (acoustic: kappa, 1/rho, Z; elastic: lambda,
+// mu, 1/rho, Zp, Zs, cp, cs) and the impedances seen across each face.
+static void materials(const double* coeffs, int model, int64_t k, double* m) {
+  if (model == DG_ACOUSTIC) {
+    double rho = coeffs[2 * k], c = coeffs[2 * k + 1];
+    m[0] = rho * c * c;
+    m[1] = 1.0 / rho;
+    m[2] = rho * c;
+  } else {
+    double lam = coeffs[3 * k], mu = coeffs[3 * k + 1], rho = coeffs[3 * k + 2];
+    double cp = std::sqrt((lam + 2 * mu) / rho), cs = std::sqrt(mu / rho);
+    m[0] = lam;
+    m[1] = mu;
+    m[2] = 1.0 / rho;
+    m[3] = rho * cp;
+    m[4] = rho * cs;
+    m[5] = cp;
+    m[6] = cs;
+  }
+}
+
+// Pack element records (layout of dgk::Rec) and neighbour words.
+void pack_records(const HostMesh& hm, const double* coeffs, int model, int64_t Kpad, std::vector<float>& rec,
+                  std::vector<int32_t>& nbr) {
+  const int R = model == DG_ACOUSTIC ? dgk::Rec<0>::size : dgk::Rec<1>::size;
+  rec.assign(size_t(Kpad) * R, 0.0f);
+  nbr.assign(size_t(Kpad) * 4, -1);
   for (int64_t k = 0; k < Kpad; ++k) {
-    float* o = &geo[size_t(k) * dgk::kGeo];
-    if (k >= m.K) {  // padding element: identity geometry, unit medium
+    float* o = &rec[size_t(k) * R];
+    if (k >= hm.K) {  // padding element: identity geometry, unit medium
       o[0] = o[4] = o[8] = 1.0f;
-      for (int i = 9; i < 16; ++i) o[i] = 1.0f;
+      for (int i = 9; i < R; ++i) o[i] = 1.0f;
       continue;
     }
-    for (int i = 0; i < 9; ++i) o[i] = float(m.g[9 * k + i]);
-    if (model == DG_ACOUSTIC) {
-      double rho = coeffs[2 * k], c = coeffs[2 * k + 1];
-      o[9] = float(rho * c * c);
-      o[10] = float(1.0 / rho);
-      o[11] = float(rho * c);
-      o[12] = float(c);
-    } else {
-      double lam = coeffs[3 * k], mu = coeffs[3 * k + 1], rho = coeffs[3 * k + 2];
-      double cp = std::sqrt((lam + 2 * mu) / rho), cs = std::sqrt(mu / rho);
-      o[9] = float(lam);
-      o[10] = float(mu);
-      o[11] = float(1.0 / rho);
-      o[12] = float(rho * cp);
-      o[13] = float(rho * cs);
-      o[14] = float(cp);
-      o[15] = float(cs);
+    for (int i = 0; i < 9; ++i) o[i] = float(hm.g[9 * k + i]);
+    double m[7];
+    materials(coeffs, model, k, m);
+    const int nm = model == DG_ACOUSTIC ? 3 : 7;
+    for (int i = 0; i < nm; ++i) o[9 + i] = float(m[i]);
+    for (int f = 0; f < 4; ++f) {
+      const int32_t kn = hm.nbr[4 * k + f];
+      double mp[7];
+      if (kn >= 0) materials(coeffs, model, kn, mp);
+      else materials(coeffs, model, k, mp);
+      if (model == DG_ACOUSTIC) {
+        o[12 + f] = float(mp[2]);
+      } else {
+        o[16 + f] = float(mp[3]);
+        o[20 + f] = float(mp[4]);
+      }
+      if (kn >= 0) {
+        const uint32_t b = (hm.code[k] >> (8 * f)) & 0xffu;
+        nbr[4 * k + f] = int32_t((uint32_t(kn) << dgk::kNbrShift) | (((b >> 2) & 7u) << 2) | (b & 3u));
+      }
     }
   }
 }
@@ -94,7 +120,7 @@ double suggest_dt(const HostMesh& m, const double* coeffs, int N, int model, dou
     if (model == DG_ACOUSTIC) cmax = coeffs[2 * k + 1];
     else cmax = std::sqrt((coeffs[3 * k] + 2 * coeffs[3 * k + 1]) / coeffs[3 * k + 2]);
     for (int f = 0; f < 4; ++f)
-      best = std::min(best, 1.0 / (cmax * m.fscale[4 * k + f] * (N + 1) * (N + 1)));
+      best = std::min(best, 1.0 / (cmax * m.fscale[4 * k + f] * ((N + 1) * (N + 2) / 2.0 + 2.0)));
   }
   return cfl * best;
 }
@@ -131,21 +157,19 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
   tets.assign(mesh->tets, mesh->tets + 4 * mesh->ntets);
   DG_CUDA(cudaGetDevice(&device));
 
+  if (K >= (int64_t(1) << (31 - dgk::kNbrShift))) return fail(DG_EINVAL, "too many elements for one handle");
   std::vector<float> geo, ops;
   std::vector<int> ftab;
-  pack_geo(hm, coeffs.data(), model, Kpad, geo);
+  std::vector<int32_t> nbr;
+  pack_records(hm, coeffs.data(), model, Kpad, geo, nbr);
   pack_ops(ref, ops, ftab);
-  std::vector<int32_t> nbr(size_t(Kpad) * 4, -1);
-  std::vector<uint32_t> code(Kpad, 0x80808080u);
-  std::copy(hm.nbr.begin(), hm.nbr.end(), nbr.begin());
-  std::copy(hm.code.begin(), hm.code.end(), code.begin());
 
   const size_t nstate = size_t(Kpad) * Nf * Np;
   state_bytes = nstate * 4;
   auto rnd = [](size_t b) { return (b + 255) & ~size_t(255); };
   size_t need = 0;
   for (size_t b : {state_bytes, state_bytes, state_bytes, state_bytes, geo.size() * 4, nbr.size() * 4,
-                   code.size() * 4, ops.size() * 4, ftab.size() * 4, size_t(Nf) * Np * 4, size_t(4)})
+                   ops.size() * 4, ftab.size() * 4, size_t(Nf) * Np * 4, size_t(4)})
     need += rnd(b);
   DG_CUDA(cudaMalloc(&d_base, need));
   device_bytes = need;
@@ -161,7 +185,6 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
   d_r[1] = reinterpret_cast<float*>(take(state_bytes));
   d_geo = reinterpret_cast<float*>(take(geo.size() * 4));
   d_nbr = reinterpret_cast<int32_t*>(take(nbr.size() * 4));
-  d_code = reinterpret_cast<uint32_t*>(take(code.size() * 4));
   d_ops = reinterpret_cast<float*>(take(ops.size() * 4));
   d_ftab = reinterpret_cast<int*>(take(ftab.size() * 4));
   d_src = reinterpret_cast<float*>(take(size_t(Nf) * Np * 4));
@@ -169,7 +192,6 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
   DG_CUDA(cudaMemsetAsync(d_base, 0, 4 * state_bytes, stream));
   DG_CUDA(cudaMemcpyAsync(d_geo, geo.data(), geo.size() * 4, cudaMemcpyHostToDevice, stream));
   DG_CUDA(cudaMemcpyAsync(d_nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice, stream));
-  DG_CUDA(cudaMemcpyAsync(d_code, code.data(), code.size() * 4, cudaMemcpyHostToDevice, stream));
   DG_CUDA(cudaMemcpyAsync(d_ops, ops.data(), ops.size() * 4, cudaMemcpyHostToDevice, stream));
   DG_CUDA(cudaMemcpyAsync(d_ftab, ftab.data(), ftab.size() * 4, cudaMemcpyHostToDevice, stream));
   DG_CUDA(cudaMemsetAsync(d_err, 0, 4, stream));
@@ -191,9 +213,8 @@ dgk::StepArgs Handle::args(int mode) const {
   a.qn = d_q[1 - qcur];
   a.r1 = d_r[r1slot];
   a.r2 = d_r[1 - r1slot];
-  a.geo = d_geo;
+  a.rec = d_geo;
   a.nbr = reinterpret_cast<const int4*>(d_nbr);
-  a.code = d_code;
   a.ops = d_ops;
   a.ftab = d_ftab;
   a.srcvec = src_elem >= 0 ? d_src : nullptr;

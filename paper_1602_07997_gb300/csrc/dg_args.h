@@ -7,9 +7,19 @@
 
 namespace dgk {
 
-constexpr int kGeo = 16;  // floats per element record
-// acoustic record: g[9] (row-major g[c][d] = dr_d/dx_c), kappa, 1/rho, Z, c
-// elastic  record: g[9], lambda, mu, 1/rho, Zp, Zs, cp, cs
+// Element record, floats per element:
+//   acoustic (16): g[9] (row-major g[c][d] = dr_d/dx_c), kappa, 1/rho, Z,
+//                  Z+ of the element across each face [4] (own Z on the boundary)
+//   elastic  (24): g[9], lambda, mu, 1/rho, Zp, Zs, cp, cs,
+//                  Zp+ per face [4], Zs+ per face [4]
+template <int MODEL>
+struct Rec {
+  static constexpr int size = MODEL == 0 ? 16 : 24;
+};
+// Neighbour word per face: -1 on the outer boundary, otherwise
+// (k' << 5) | (rotation << 2) | f' with k' the neighbour element, f' its
+// face and rotation one of the 6 face-node permutations.
+constexpr int kNbrShift = 5;
 
 struct StepArgs {
   const float* q;        // q^m   [Kpad][Nf][Np]
@@ -17,12 +27,11 @@ struct StepArgs {
   const float* r1;       // r^m-1                            (mode 0)
   float* r2;             // in r^m-2, out r^m                (mode 0)
   float* rout;           // r^m [K][Nf][Np]                  (mode 1)
-  const float* geo;      // [Kpad][kGeo]
-  const int4* nbr;       // [Kpad] neighbour per face, -1 = boundary
-  const uint32_t* code;  // [Kpad] per face: f' (bits 0-1), rotation (2-4), boundary (7)
+  const float* rec;      // [Kpad][Rec::size]
+  const int4* nbr;       // [Kpad] neighbour words
   const float* ops;      // [KD][Mpad]: rows d*Np+j -> D_d[i][j]; rows 3Np+c -> LIFT[i][c]
   const int* ftab;       // [4][Nfp] face masks, then [6][Nfp] rotations
-  const float* srcvec;   // [Nf][Np] source shape (times amplitude) or null
+  const float* srcvec;   // [Nf][Np] source shape or null
   float src_amp;
   int src_elem;          // element holding the source, -1 = none
   int K;
@@ -36,13 +45,14 @@ struct StepArgs {
 // Host-visible launch configuration of one (model, N) instantiation.
 struct KernelCfg {
   int EB, TN, NT;
-  bool ops_smem;
+  bool ops_smem, r_smem;
   size_t smem;
   void (*fn)(StepArgs);
 };
 
 const KernelCfg* kernel_cfg(int model, int N);
 
+// Launch the persistent step kernel on `stream` (grid = min(blocks, SMs x occupancy)).
 cudaError_t launch_step(int model, int N, const StepArgs& args, cudaStream_t stream);
 
 }  // namespace dgk

@@ -14,6 +14,8 @@ namespace dg {
 int cuda_fail(cudaError_t e, const char* what);
 int check_coeffs(const double* coeffs, int64_t K, int model);
 void pack_ops(const RefElement& R, std::vector<float>& ops, std::vector<int>& ftab);
+void pack_records(const HostMesh& hm, const double* coeffs, int model, int64_t Kpad, std::vector<float>& rec,
+                  std::vector<int32_t>& nbr);
 double suggest_dt(const HostMesh& m, const double* coeffs, int N, int model, double cfl);
 
 struct Handle {
@@ -32,9 +34,8 @@ struct Handle {
   size_t device_bytes = 0, state_bytes = 0;
   float* d_q[2] = {nullptr, nullptr};  // ping-pong q^m / q^{m+1}
   float* d_r[2] = {nullptr, nullptr};  // AB3 history slots
-  float* d_geo = nullptr;
+  float* d_geo = nullptr;  // element records, dgk::Rec layout
   int32_t* d_nbr = nullptr;
-  uint32_t* d_code = nullptr;
   float* d_ops = nullptr;
   int* d_ftab = nullptr;
   float* d_src = nullptr;

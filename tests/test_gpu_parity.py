@@ -101,7 +101,7 @@ def test_100_steps_with_source(dg, model, N):
     n = 3 if N <= 4 else 2
     verts, tets, coeffs = _mesh(model, n, 70 + N)
     o = OSolver(model, N, verts, tets, coeffs)
-    dt = o.suggest_dt(0.5)
+    dt = o.suggest_dt(0.4)
     amp = W.ricker(np.arange(100) * dt, f0=4.0, t0=0.05) * 10.0
     xs = (0.4321, 0.5678, 0.4876)
     ko = o.set_source(xs, amp, direction=(0.3, -0.2, 0.9))

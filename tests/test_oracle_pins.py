@@ -369,3 +369,24 @@ def test_upwind_energy_monotone_config1():
     assert np.all(np.diff(E[1:]) <= 1e-14 * E[0])
     assert E[1] - E[0] < 1e-2 * E[0]
     assert E[-1] < E[0]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("model,N", [("acoustic", 1), ("acoustic", 4), ("acoustic", 8),
+                                     ("elastic", 1), ("elastic", 5)])
+def test_suggested_dt_is_ab3_stable(model, N):
+    """At the suggested dt (cfl 0.4) upwind + AB3 never increases E_h after
+    the bootstrap steps, from rough random data (all modes excited)."""
+    verts, tets = _small_mesh(2, seed=N)
+    K = tets.shape[0]
+    coeffs = (W.acoustic_coefficients(K, 1, 3, seed=N) if model == "acoustic"
+              else W.elastic_two_layer(verts, tets, seed=N))
+    S = Solver(model, N, verts, tets, coeffs)
+    q0 = W.random_state(K, S.Nf, S.ref.Np, seed=5)
+    st = AB3Stepper(S, q0, S.suggest_dt())
+    E = [S.energy(st.q)]
+    for _ in range(150):
+        st.step()
+        E.append(S.energy(st.q))
+    E = np.array(E)
+    assert np.all(np.diff(E[2:]) <= 1e-13 * E[0]), np.max(np.diff(E[2:]))

@@ -27,7 +27,7 @@ def config1_acoustic_small():
     verts, tets = kuhn_cube_mesh(4, jitter=0.1, seed=1001)
     coeffs = acoustic_coefficients(tets.shape[0], 1.0, 2.0, seed=2001)
     return dict(model="acoustic", N=2, verts=verts, tets=tets, coeffs=coeffs,
-                steps=100, flux="upwind", cfl=0.5)
+                steps=100, flux="upwind", cfl=0.4)
 
 
 def sweep_mesh(model, N, target_nodes=2_000_000, n=None):
@@ -45,7 +45,7 @@ def sweep_mesh(model, N, target_nodes=2_000_000, n=None):
     else:
         raise ValueError(model)
     return dict(model=model, N=N, n=n, verts=verts, tets=tets, coeffs=coeffs,
-                steps=steps, flux="upwind", cfl=0.5, source=DEFAULT_SOURCE)
+                steps=steps, flux="upwind", cfl=0.4, source=DEFAULT_SOURCE)
 
 
 def config4_requests(count=64, rate=None, seed=1004):
@@ -77,4 +77,4 @@ def config5_elastic_large(n=28):
     verts, tets = kuhn_cube_mesh(n, jitter=0.1, seed=1005)
     coeffs = elastic_layered(verts, tets, seed=2005)
     return dict(model="elastic", N=7, n=n, verts=verts, tets=tets, coeffs=coeffs,
-                steps=2000, flux="upwind", cfl=0.5, source=DEFAULT_SOURCE)
+                steps=2000, flux="upwind", cfl=0.4, source=DEFAULT_SOURCE)
