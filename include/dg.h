@@ -87,7 +87,8 @@ typedef struct {
   int flux;         /* DG_FLUX_*                                         */
   int bc;           /* DG_BC_*                                           */
   int precision;    /* DG_FP32                                           */
-  int block_elems;  /* elements per CTA; 0 = the tuned default for (model, N) */
+  int block_elems;  /* elements per CTA of a compiled variant; 0 = the autotuned
+                       choice for (model, N) if any, else the default variant */
   double dt;        /* time step used by dg_step (may be changed by dg_set_dt) */
   void *stream;     /* cudaStream_t; NULL = legacy default stream        */
 } dg_opts;
@@ -128,6 +129,21 @@ int dg_rhs(dg_handle *h, float *r_out, int on_device);
  * is one fused launch (RHS + update).  Asynchronous on the handle's stream.  */
 int dg_step(dg_handle *h, int nsteps);
 int dg_set_dt(dg_handle *h, double dt);
+/* Autotuner: time every compiled variant of the step kernel (elements per
+ * CTA and threads per CTA) for this handle's (model, N) on its own mesh,
+ * `reps` launches each, on scratch copies of the state (the handle's state
+ * and history are untouched), keep the fastest for this handle and for
+ * handles created later in the process on the same device, model and N.
+ * block_elems / ms_per_step (may be NULL) receive the choice and its time;
+ * variant_ms (NULL or [variants]) receives every variant's time per step.
+ * Allocates and frees scratch device memory of 4 state sizes; synchronous. */
+int dg_autotune(dg_handle *h, int reps, int *block_elems, double *ms_per_step, double *variant_ms);
+/* Launch configuration in use: elements per CTA, threads per CTA, dynamic
+ * shared memory per CTA, number of compiled variants, elements per thread
+ * tile.  Pointers may be NULL.                                              */
+int dg_kernel_info(const dg_handle *h, int *block_elems, int *threads, int64_t *smem_bytes,
+                   int *variants, int *tile_elems);
+
 /* Wait for the handle's stream; DG_ETIMEOUT if a device wait expired.       */
 int dg_sync(dg_handle *h);
 

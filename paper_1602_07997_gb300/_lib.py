@@ -21,7 +21,7 @@ BC = {None: 0, "default": 0, "rigid": 1, "free": 2}
 
 # every symbol that include/dg.h declares
 EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", "dg_rhs", "dg_step",
-           "dg_set_dt", "dg_sync", "dg_node_coords", "dg_set_source", "dg_suggest_dt",
+           "dg_set_dt", "dg_sync", "dg_autotune", "dg_kernel_info", "dg_node_coords", "dg_set_source", "dg_suggest_dt",
            "dg_reference_element", "dg_last_error", "dg_server_create", "dg_submit", "dg_poll",
            "dg_cancel", "dg_server_stats", "dg_server_destroy")
 
@@ -73,6 +73,8 @@ def lib():
         "dg_step": (i32, [vp, i32]),
         "dg_set_dt": (i32, [vp, dbl]),
         "dg_sync": (i32, [vp]),
+        "dg_autotune": (i32, [vp, i32, P(i32), P(dbl), P(dbl)]),
+        "dg_kernel_info": (i32, [vp, P(i32), P(i32), P(i64), P(i32), P(i32)]),
         "dg_node_coords": (i32, [vp, P(dbl)]),
         "dg_set_source": (i32, [vp, P(dbl), P(dbl), P(dbl), i64]),
         "dg_suggest_dt": (i32, [P(Mesh), P(dbl), i32, i32, dbl, P(dbl)]),
@@ -166,10 +168,10 @@ class Solver:
     """One DG discretisation on the GPU (a dg_handle)."""
 
     def __init__(self, verts, tets, coeffs, N, model="acoustic", flux="upwind", bc=None, dt=0.0,
-                 stream=None):
+                 stream=None, block_elems=0):
         m, keep = make_mesh(verts, tets)
         cf = np.ascontiguousarray(coeffs, dtype=np.float64)
-        o = Opts(FLUX[flux], BC[bc], 0, 0, float(dt), C.c_void_p(stream or 0))
+        o = Opts(FLUX[flux], BC[bc], 0, int(block_elems), float(dt), C.c_void_p(stream or 0))
         h = C.c_void_p()
         check(lib().dg_setup(C.byref(m), _dptr(cf), int(N), _model(model), C.byref(o), C.byref(h)))
         self.h = h
@@ -230,6 +232,22 @@ class Solver:
 
     def sync(self):
         check(lib().dg_sync(self.h))
+
+    def autotune(self, reps=5):
+        """Time every compiled kernel variant on this mesh and keep the fastest.
+
+        Returns (block_elems, ms_per_step, [ms per variant])."""
+        nv = self.kernel_info()["variants"]
+        eb, ms = C.c_int(), C.c_double()
+        vms = (C.c_double * max(nv, 1))()
+        check(lib().dg_autotune(self.h, int(reps), C.byref(eb), C.byref(ms), vms))
+        return eb.value, ms.value, list(vms)[:nv]
+
+    def kernel_info(self):
+        eb, nt, sm, nv, tn = C.c_int(), C.c_int(), C.c_int64(), C.c_int(), C.c_int()
+        check(lib().dg_kernel_info(self.h, C.byref(eb), C.byref(nt), C.byref(sm), C.byref(nv), C.byref(tn)))
+        return dict(block_elems=eb.value, threads=nt.value, smem_bytes=sm.value, variants=nv.value,
+                    tile_elems=tn.value)
 
     def node_coords(self):
         x = np.empty((self.K, self.Np, 3))

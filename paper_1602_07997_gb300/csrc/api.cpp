@@ -2,7 +2,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -125,6 +128,31 @@ double suggest_dt(const HostMesh& m, const double* coeffs, int N, int model, dou
   return cfl * best;
 }
 
+// ---------------------------------------------------------------- variants
+// Autotuned choice per (device, model, N), shared by every handle of the process.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tuned;
+
+static int device_of_current() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return 0;
+  return d;
+}
+
+const dgk::KernelCfg* select_variant(int model, int N, int block_elems, int device) {
+  int n = 0;
+  const dgk::KernelCfg* v = dgk::kernel_variants(model, N, &n);
+  if (!v) return nullptr;
+  if (block_elems > 0) {
+    for (int i = 0; i < n; ++i)
+      if (v[i].EB == block_elems) return &v[i];
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(std::make_tuple(device, model, N));
+  return it != g_tuned.end() ? &v[it->second] : &v[0];
+}
+
 // ---------------------------------------------------------------- handle
 int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_, const dg_opts* o) {
   if (model_ != DG_ACOUSTIC && model_ != DG_ELASTIC) return fail(DG_EINVAL, "unknown model");
@@ -148,7 +176,8 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
   Nfp = ref.Nfp;
   Nf = num_fields(model);
   K = hm.K;
-  cfg = dgk::kernel_cfg(model, N);
+  cfg = select_variant(model, N, opts.block_elems, device_of_current());
+  if (!cfg) return fail(DG_EINVAL, "no compiled kernel variant with block_elems = " + std::to_string(opts.block_elems));
   // every launch reads whole blocks of EB <= 128 elements with bulk copies:
   // pad the element arrays so that the last block stays inside the allocation
   Kpad = (K + 3) / 4 * 4 + 128;
@@ -235,7 +264,7 @@ dgk::StepArgs Handle::args(int mode) const {
 int Handle::advance(int nsteps) {
   for (int s = 0; s < nsteps; ++s) {
     dgk::StepArgs a = args(0);
-    DG_CUDA(dgk::launch_step(model, N, a, stream));
+    DG_CUDA(dgk::launch_step(cfg, a, stream));
     qcur ^= 1;
     r1slot ^= 1;  // r^m was written into the r^{m-2} slot
     ++step;
@@ -324,7 +353,7 @@ int dg_rhs(dg_handle* h, float* r_out, int on_device) {
     DG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&tmp), bytes, h->stream));
     a.rout = tmp;
   }
-  cudaError_t e = dgk::launch_step(h->model, h->N, a, h->stream);
+  cudaError_t e = dgk::launch_step(h->cfg, a, h->stream);
   if (e != cudaSuccess) {
     if (tmp) cudaFreeAsync(tmp, h->stream);
     return dg::cuda_fail(e, "launch");
@@ -422,6 +451,92 @@ int dg_set_source(dg_handle* h, const double xs[3], const double dir[3], const d
   DG_CUDA(cudaStreamSynchronize(h->stream));
   h->src_elem = int(best);
   h->src_amp.assign(amp, amp + namp);
+  return DG_OK;
+}
+
+int dg_autotune(dg_handle* h, int reps, int* block_elems, double* ms_per_step, double* variant_ms) {
+  if (!h || reps < 1) return fail(DG_EINVAL, "NULL handle or reps < 1");
+  int n = 0;
+  const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n);
+  // scratch copies of the state so that the handle's state and history stay untouched
+  void* scratch = nullptr;
+  DG_CUDA(cudaMallocAsync(&scratch, 4 * h->state_bytes, h->stream));
+  float* sq[2] = {static_cast<float*>(scratch), static_cast<float*>(scratch) + h->state_bytes / 4};
+  float* sr[2] = {sq[1] + h->state_bytes / 4, sq[1] + 2 * (h->state_bytes / 4)};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = DG_OK;
+  int best = -1;
+  float best_ms = 0.0f;
+  auto run = [&]() -> int {
+    for (int c = 0; c < 2; ++c) {
+      DG_CUDA(cudaMemcpyAsync(sq[c], h->d_q[h->qcur], h->state_bytes, cudaMemcpyDeviceToDevice, h->stream));
+      DG_CUDA(cudaMemcpyAsync(sr[c], h->d_r[c], h->state_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    DG_CUDA(cudaEventCreate(&e0));
+    DG_CUDA(cudaEventCreate(&e1));
+    for (int i = 0; i < n; ++i) {
+      dgk::StepArgs a = h->args(0);
+      a.a1 = 1.0f;
+      a.a2 = a.a3 = 0.0f;
+      a.src_elem = -1;
+      a.srcvec = nullptr;
+      int cur = 0;
+      auto one = [&]() -> int {
+        a.q = sq[cur];
+        a.qn = sq[1 - cur];
+        a.r1 = sr[cur];
+        a.r2 = sr[1 - cur];
+        DG_CUDA(dgk::launch_step(&v[i], a, h->stream));
+        cur ^= 1;
+        return DG_OK;
+      };
+      int r = one();  // warm-up (and shared-memory opt-in)
+      if (r) return r;
+      DG_CUDA(cudaEventRecord(e0, h->stream));
+      for (int k = 0; k < reps; ++k) {
+        r = one();
+        if (r) return r;
+      }
+      DG_CUDA(cudaEventRecord(e1, h->stream));
+      DG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      DG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= reps;
+      if (variant_ms) variant_ms[i] = ms;
+      if (best < 0 || ms < best_ms) {
+        best = i;
+        best_ms = ms;
+      }
+    }
+    return DG_OK;
+  };
+  rc = run();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(scratch, h->stream);
+  cudaStreamSynchronize(h->stream);
+  if (rc) return rc;
+  int err = 0;
+  DG_CUDA(cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost));
+  if (err) return fail(DG_ETIMEOUT, "a bounded device-side wait expired during tuning");
+  h->cfg = &v[best];
+  {
+    std::lock_guard<std::mutex> lock(dg::g_tune_mu);
+    dg::g_tuned[std::make_tuple(h->device, h->model, h->N)] = best;
+  }
+  if (block_elems) *block_elems = v[best].EB;
+  if (ms_per_step) *ms_per_step = best_ms;
+  return DG_OK;
+}
+
+int dg_kernel_info(const dg_handle* h, int* block_elems, int* threads, int64_t* smem_bytes, int* variants,
+                   int* tile_elems) {
+  if (!h || !h->cfg) return fail(DG_EINVAL, "NULL handle");
+  if (tile_elems) *tile_elems = h->cfg->TN;
+  if (block_elems) *block_elems = h->cfg->EB;
+  if (threads) *threads = h->cfg->NT;
+  if (smem_bytes) *smem_bytes = int64_t(h->cfg->smem);
+  if (variants) dgk::kernel_variants(h->model, h->N, variants);
   return DG_OK;
 }
 

@@ -7,14 +7,15 @@
 
 namespace dgk {
 
-// Element record, floats per element:
-//   acoustic (16): g[9] (row-major g[c][d] = dr_d/dx_c), kappa, 1/rho, Z,
-//                  Z+ of the element across each face [4] (own Z on the boundary)
-//   elastic  (24): g[9], lambda, mu, 1/rho, Zp, Zs, cp, cs,
-//                  Zp+ per face [4], Zs+ per face [4]
+// Element record, floats per element (odd length: element-strided reads of
+// the records in shared memory are then free of bank conflicts):
+//   acoustic (17): g[9] (row-major g[c][d] = dr_d/dx_c), kappa, 1/rho, Z,
+//                  Z+ of the element across each face [4] (own Z on the boundary), pad
+//   elastic  (25): g[9], lambda, mu, 1/rho, Zp, Zs, cp, cs,
+//                  Zp+ per face [4], Zs+ per face [4], pad
 template <int MODEL>
 struct Rec {
-  static constexpr int size = MODEL == 0 ? 16 : 24;
+  static constexpr int size = MODEL == 0 ? 17 : 25;
 };
 // Neighbour word per face: -1 on the outer boundary, otherwise
 // (k' << 5) | (rotation << 2) | f' with k' the neighbour element, f' its
@@ -50,9 +51,12 @@ struct KernelCfg {
   void (*fn)(StepArgs);
 };
 
+// Compiled variants of one (model, N): different elements per block (EB) and
+// threads per CTA.  Variant 0 is the default.
+const KernelCfg* kernel_variants(int model, int N, int* count);
 const KernelCfg* kernel_cfg(int model, int N);
 
 // Launch the persistent step kernel on `stream` (grid = min(blocks, SMs x occupancy)).
-cudaError_t launch_step(int model, int N, const StepArgs& args, cudaStream_t stream);
+cudaError_t launch_step(const KernelCfg* cfg, const StepArgs& args, cudaStream_t stream);
 
 }  // namespace dgk

@@ -1,61 +1,59 @@
-// Kernel table and launch of the persistent fused step kernel.
+// Kernel variant tables and launch of the persistent fused step kernel.
+#include <map>
 #include <mutex>
 
 #include "dg_kernels.cuh"
 
 namespace dgk {
 
-const KernelCfg* kernel_cfg_acoustic(int N);
-const KernelCfg* kernel_cfg_elastic(int N);
+const KernelCfg* kernel_variants_acoustic(int N, int* count);
+const KernelCfg* kernel_variants_elastic(int N, int* count);
 
-const KernelCfg* kernel_cfg(int model, int N) {
-  return model == 0 ? kernel_cfg_acoustic(N) : kernel_cfg_elastic(N);
+const KernelCfg* kernel_variants(int model, int N, int* count) {
+  int c = 0;
+  const KernelCfg* v = model == 0 ? kernel_variants_acoustic(N, &c) : kernel_variants_elastic(N, &c);
+  if (count) *count = v ? c : 0;
+  return v;
 }
 
-namespace {
-constexpr int kMaxDev = 64;
-struct DevInfo {
-  bool init = false;
-  int sms = 0;
-  int occ[2][8] = {};  // resident CTAs per SM for each instantiation
-};
-std::mutex g_mu;
-DevInfo g_dev[kMaxDev];
+const KernelCfg* kernel_cfg(int model, int N) { return kernel_variants(model, N, nullptr); }
 
-// Opt the instantiation into its dynamic shared memory and read its occupancy.
-cudaError_t prepare(int model, int N, const KernelCfg* c, int* grid_cap) {
+namespace {
+std::mutex g_mu;
+std::map<std::pair<int, const KernelCfg*>, int> g_cap;  // (device, variant) -> max resident CTAs
+
+// Opt the variant into its dynamic shared memory and read its occupancy (once per device).
+cudaError_t prepare(const KernelCfg* c, int* grid_cap) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mu);
-  DevInfo& d = g_dev[dev];
-  if (!d.init) {
-    e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    d.init = true;
+  auto key = std::make_pair(dev, c);
+  auto it = g_cap.find(key);
+  if (it != g_cap.end()) {
+    *grid_cap = it->second;
+    return cudaSuccess;
   }
-  int& occ = d.occ[model][N - 1];
-  if (occ == 0) {
-    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(c->fn),
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(c->smem));
-    if (e != cudaSuccess) return e;
-    int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, reinterpret_cast<const void*>(c->fn), c->NT,
-                                                      c->smem);
-    if (e != cudaSuccess) return e;
-    occ = n > 0 ? n : 1;
-  }
-  *grid_cap = d.sms * occ;
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(reinterpret_cast<const void*>(c->fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(c->smem));
+  if (e != cudaSuccess) return e;
+  int n = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, reinterpret_cast<const void*>(c->fn), c->NT, c->smem);
+  if (e != cudaSuccess) return e;
+  const int cap = sms * (n > 0 ? n : 1);
+  g_cap[key] = cap;
+  *grid_cap = cap;
   return cudaSuccess;
 }
 }  // namespace
 
-cudaError_t launch_step(int model, int N, const StepArgs& args, cudaStream_t stream) {
-  const KernelCfg* c = kernel_cfg(model, N);
+cudaError_t launch_step(const KernelCfg* c, const StepArgs& args, cudaStream_t stream) {
   if (!c) return cudaErrorInvalidValue;
   int cap = 0;
-  cudaError_t e = prepare(model, N, c, &cap);
+  cudaError_t e = prepare(c, &cap);
   if (e != cudaSuccess) return e;
   const int nblk = (args.K + c->EB - 1) / c->EB;
   if (nblk == 0) return cudaSuccess;

@@ -17,6 +17,7 @@ void pack_ops(const RefElement& R, std::vector<float>& ops, std::vector<int>& ft
 void pack_records(const HostMesh& hm, const double* coeffs, int model, int64_t Kpad, std::vector<float>& rec,
                   std::vector<int32_t>& nbr);
 double suggest_dt(const HostMesh& m, const double* coeffs, int N, int model, double cfl);
+const dgk::KernelCfg* select_variant(int model, int N, int block_elems, int device);
 
 struct Handle {
   int model = 0, N = 0, Np = 0, Nfp = 0, Nf = 0, device = 0;

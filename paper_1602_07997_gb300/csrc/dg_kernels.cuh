@@ -15,8 +15,9 @@
 //      neighbour trace via the neighbour's face mask and one of the 6 face
 //      rotations; neighbours in the block come from shared memory, the
 //      others from global memory, several face nodes per thread in flight);
-//   4. each thread owns tiles of 4 output nodes x TN elements and
-//      accumulates every operator product of its tile in registers
+//   4. each thread owns a tile of 4 output nodes x TN elements (element
+//      index fastest across lanes) and accumulates every operator product of
+//      its tile in registers
 //      (Section 3.2: 6 Np x Np products + the merged LIFT product for the
 //      acoustic model, 18 + LIFT for the elastic model), operator rows as
 //      float4 from shared memory (or L1 when the blob exceeds the budget);
@@ -97,6 +98,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void tma_bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 template <int TN>
 struct VecT;
 template <>
@@ -133,31 +151,36 @@ __device__ __forceinline__ constexpr float ref_normal(int f, int i) {
 }
 
 // ---------------------------------------------------------------- smem plan
+constexpr int round4(int x) { return (x + 3) & ~3; }
+
 template <int MODEL, int N, int EB, bool OPS_SMEM, bool R_SMEM>
 struct Plan {
   using S = Sz<N>;
   static constexpr int Nf = MODEL == 0 ? 4 : 9;
   static constexpr int REC = Rec<MODEL>::size;
+  static constexpr int EBP = EB + 1;                      // odd row stride of element-fastest arrays
   static constexpr int nQ = EB * Nf * S::Np;
-  static constexpr int nStage = nQ + EB * REC + EB * 4;  // q, records, neighbour words
+  static constexpr int nStage = round4(nQ + EB * REC) + EB * 4;  // q, records, neighbour words
+  static constexpr int sQ = 0, sRec = nQ, sNbr = round4(nQ + EB * REC);
   static constexpr int nR = R_SMEM ? 2 * nQ : 0;
-  static constexpr int nXvol = (MODEL == 0 ? 4 : 12) * S::Np * EB;
-  static constexpr int nXsur = Nf * S::NFN * EB;
+  static constexpr int nXvol = (MODEL == 0 ? 4 : 12) * S::Np * EBP;
+  static constexpr int nXsur = Nf * S::NFN * EBP;
+  static constexpr int nT = Nf * S::NFN * EBP;             // neighbour traces [Nf][4Nfp][EBP]
   static constexpr int nOps = OPS_SMEM ? S::KD * S::Mpad : 0;
   static constexpr int oStage0 = 0;
   static constexpr int oStage1 = oStage0 + nStage;
   static constexpr int oR = oStage1 + nStage;
-  static constexpr int oXvol = oR + nR;
-  static constexpr int oXsur = oXvol + nXvol;
-  static constexpr int oOps = oXsur + nXsur;
-  static constexpr int oFn = oOps + nOps;                 // [EB][4][4] n, Fscale
+  static constexpr int oXvol = round4(oR + nR);
+  static constexpr int oXsur = round4(oXvol + nXvol);
+  static constexpr int oT0 = round4(oXsur + nXsur);
+  static constexpr int oT1 = round4(oT0 + nT);
+  static constexpr int oOps = round4(oT1 + nT);
+  static constexpr int oFn = round4(oOps + nOps);          // [EB][4] float4: n, Fscale
   static constexpr int oFtab = oFn + EB * 16;              // int [10][Nfp]
-  static constexpr int oBar = ((oFtab + 10 * S::Nfp) + 3) & ~3;
+  static constexpr int oBar = round4(oFtab + 10 * S::Nfp);
   static constexpr int nFloats = oBar + 8;                 // 3 mbarriers
   static constexpr size_t bytes = size_t(nFloats) * 4;
-  // offsets inside a stage
-  static constexpr int sQ = 0, sRec = nQ, sNbr = nQ + EB * REC;
-  static_assert((nQ % 4) == 0 && ((EB * REC) % 4) == 0, "16-byte aligned stage pieces");
+  static_assert(nXvol >= nQ, "the RHS of a block is staged in the volume-input buffer");
 };
 
 // ---------------------------------------------------------------- kernel
@@ -166,11 +189,11 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   using S = Sz<N>;
   using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM>;
   constexpr int Np = S::Np, Nfp = S::Nfp, NFN = S::NFN, Mpad = S::Mpad, RT = S::RT;
-  constexpr int Nf = P::Nf, REC = P::REC;
-  constexpr int CT = EB / TN;
-  constexpr int NTILE = RT * CT;
+  constexpr int Nf = P::Nf, REC = P::REC, EBP = P::EBP;
+  constexpr int NTILE = RT * (EB / TN);  // tiles of 4 output nodes x TN elements
+  static_assert(EB % 4 == 0, "EB must be a multiple of 4 (16-byte TMA pieces)");
   static_assert(EB % TN == 0, "EB must be a multiple of TN");
-  static_assert(EB % 4 == 0, "EB must be a multiple of 4 (TMA 16-byte granularity)");
+  static_assert(NTILE <= NT, "one output tile per thread");
 
   extern __shared__ __align__(16) float smem[];
   float* sR = smem + P::oR;
@@ -184,18 +207,43 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   const int tid = threadIdx.x;
   const int nblk = (a.K + EB - 1) / EB;
   const int G = gridDim.x;
-  constexpr uint32_t kStageBytes = uint32_t((P::nQ + EB * REC + EB * 4) * 4);
   constexpr uint32_t kQBytes = uint32_t(P::nQ * 4);
+  constexpr uint32_t kRecBytes = uint32_t(EB * REC * 4);
+  constexpr uint32_t kStageBytes = kQBytes + kRecBytes + uint32_t(EB * 16);
 
+  auto stage = [&](int s) { return smem + (s ? P::oStage1 : P::oStage0); };
   auto issue_stage = [&](int b, int s, bool with_ops) {
-    float* st = smem + (s ? P::oStage1 : P::oStage0);
+    float* st = stage(s);
     const int k0 = b * EB;
     const uint32_t bo = (OPS_SMEM && with_ops) ? uint32_t(S::KD * Mpad * 4) : 0u;
     mbar_arrive_expect_tx(&bars[s], kStageBytes + bo);
     tma_bulk_g2s(st + P::sQ, a.q + size_t(k0) * Nf * Np, kQBytes, &bars[s]);
-    tma_bulk_g2s(st + P::sRec, a.rec + size_t(k0) * REC, uint32_t(EB * REC * 4), &bars[s]);
+    tma_bulk_g2s(st + P::sRec, a.rec + size_t(k0) * REC, kRecBytes, &bars[s]);
     tma_bulk_g2s(st + P::sNbr, a.nbr + k0, uint32_t(EB * 16), &bars[s]);
     if (OPS_SMEM && with_ops) tma_bulk_g2s(smem + P::oOps, a.ops, bo, &bars[s]);
+  };
+  // neighbour traces of block b that live outside it: 4-byte async copies
+  // (cp.async) into trace buffer s, layout [Nf][4 Nfp][EBP], face node fastest
+  auto issue_gathers = [&](int b, int s) {
+    const int k0 = b * EB;
+    const int4* nb_s = reinterpret_cast<const int4*>(stage(s) + P::sNbr);
+    float* T = smem + (s ? P::oT1 : P::oT0);
+    for (int i = tid; i < EB * NFN; i += NT) {
+      const int fm = i % NFN, e = i / NFN;
+      const int f = fm / Nfp, m = fm - f * Nfp;
+      const int4 nb = nb_s[e];
+      const int w = (f == 0) ? nb.x : (f == 1) ? nb.y : (f == 2) ? nb.z : nb.w;
+      if (w < 0) continue;
+      const int kn = w >> kNbrShift;
+      const int le = kn - k0;
+      if (le >= 0 && le < EB) continue;
+      const int rot = (w >> 2) & 7, f2 = w & 3;
+      const int nP = sFtab[f2 * Nfp + sFtab[4 * Nfp + rot * Nfp + m]];
+      const float* src = a.q + size_t(kn) * Nf * Np + nP;
+#pragma unroll
+      for (int c = 0; c < Nf; ++c) cp_async4(T + (c * NFN + fm) * EBP + e, src + c * Np);
+    }
+    cp_async_commit();
   };
 
   if (tid == 0) {
@@ -207,23 +255,34 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   __syncthreads();
   if (tid == 0 && (int)blockIdx.x < nblk) issue_stage(blockIdx.x, 0, true);
   for (int i = tid; i < 10 * Nfp; i += NT) sFtab[i] = a.ftab[i];
+  __syncthreads();
+  if ((int)blockIdx.x < nblk) {
+    if (!__syncthreads_and(mbar_wait_bounded(&bars[0], 0u, a.err))) {
+      mbar_wait_bounded(&bars[0], 0u, nullptr);
+      return;
+    }
+    issue_gathers(blockIdx.x, 0);
+  }
 
   int it = 0;
   for (int b = blockIdx.x; b < nblk; b += G, ++it) {
     const int s = it & 1;
     const int k0 = b * EB;
     bool ok = mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), a.err);
+    cp_async_wait_all();  // this block's neighbour traces
     if (!__syncthreads_and(ok)) {
       mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), nullptr);
       return;
     }
-    // everyone is past the previous block: stage s^1, the history buffer and X are free
-    const float* sQ = smem + (s ? P::oStage1 : P::oStage0) + P::sQ;
-    const float* sRec = smem + (s ? P::oStage1 : P::oStage0) + P::sRec;
-    const int4* sNbr = reinterpret_cast<const int4*>(smem + (s ? P::oStage1 : P::oStage0) + P::sNbr);
+    // everyone is past the previous block: stage s^1, sR, the inputs and trace buffer s^1 are free
+    const float* sQ = stage(s) + P::sQ;
+    const float* sRec = stage(s) + P::sRec;
+    const int4* sNbr = reinterpret_cast<const int4*>(stage(s) + P::sNbr);
+    const float* sT = smem + (s ? P::oT1 : P::oT0);
     if (tid == 0) {
       if (b + G < nblk) issue_stage(b + G, s ^ 1, false);
       if (R_SMEM && a.mode == 0) {
+        if (it > 0) bulk_wait_read();  // the previous block's outputs have left sR
         mbar_arrive_expect_tx(&bars[2], 2 * kQBytes);
         tma_bulk_g2s(sR, a.r1 + size_t(k0) * Nf * Np, kQBytes, &bars[2]);
         tma_bulk_g2s(sR + P::nQ, a.r2 + size_t(k0) * Nf * Np, kQBytes, &bars[2]);
@@ -240,21 +299,20 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
         nv[c] = gk[3 * c] * ref_normal(f, 0) + gk[3 * c + 1] * ref_normal(f, 1) + gk[3 * c + 2] * ref_normal(f, 2);
       const float fs = sqrtf(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
       const float inv = 1.0f / fs;
-      float4 o = make_float4(nv[0] * inv, nv[1] * inv, nv[2] * inv, fs);
-      *reinterpret_cast<float4*>(sFn + i * 4) = o;
+      *reinterpret_cast<float4*>(sFn + i * 4) = make_float4(nv[0] * inv, nv[1] * inv, nv[2] * inv, fs);
     }
-    // -------- volume inputs
+    // -------- volume inputs (node index fastest: conflict-free reads of q)
     for (int i = tid; i < EB * Np; i += NT) {
-      const int e = i % EB, j = i / EB;
+      const int j = i % Np, e = i / Np;
       const float* gk = sRec + e * REC;
       const float* qe = sQ + e * Nf * Np;
       if constexpr (MODEL == 0) {
         const float kap = gk[9];
         const float v0 = qe[Np + j], v1 = qe[2 * Np + j], v2 = qe[3 * Np + j];
-        sXv[(0 * Np + j) * EB + e] = qe[j];
+        sXv[(0 * Np + j) * EBP + e] = qe[j];
 #pragma unroll
         for (int d = 0; d < 3; ++d)
-          sXv[((1 + d) * Np + j) * EB + e] = -kap * (gk[d] * v0 + gk[3 + d] * v1 + gk[6 + d] * v2);
+          sXv[((1 + d) * Np + j) * EBP + e] = -kap * (gk[d] * v0 + gk[3 + d] * v1 + gk[6 + d] * v2);
       } else {
         const float rinv = gk[11];
         float sg[3][3];
@@ -263,248 +321,203 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
         sg[0][2] = sg[2][0] = qe[7 * Np + j];
         sg[1][2] = sg[2][1] = qe[8 * Np + j];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) sXv[(c * Np + j) * EB + e] = qe[c * Np + j];
+        for (int c = 0; c < 3; ++c) sXv[(c * Np + j) * EBP + e] = qe[c * Np + j];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int d = 0; d < 3; ++d)
-            sXv[((3 + 3 * c + d) * Np + j) * EB + e] =
+            sXv[((3 + 3 * c + d) * Np + j) * EBP + e] =
                 rinv * (gk[d] * sg[c][0] + gk[3 + d] * sg[c][1] + gk[6 + d] * sg[c][2]);
       }
     }
     __syncthreads();  // sFn ready
 
-    // -------- traces and penalty terms at the 4 Nfp face nodes
-    constexpr int BATCH = MODEL == 0 ? 4 : 2;
-    for (int base = tid; base < EB * NFN; base += NT * BATCH) {
-      float qP[BATCH][Nf];
-      int nMv[BATCH], bndv[BATCH];
-#pragma unroll
-      for (int u = 0; u < BATCH; ++u) {
-        const int i = base + u * NT;
-        bndv[u] = 1;
-        nMv[u] = 0;
-        if (i >= EB * NFN) continue;
-        const int e = i % EB, fm = i / EB;
-        const int f = fm / Nfp, m = fm - f * Nfp;
-        nMv[u] = sFtab[f * Nfp + m];
-        const int4 nb = sNbr[e];
-        const int w = (f == 0) ? nb.x : (f == 1) ? nb.y : (f == 2) ? nb.z : nb.w;
-        if (w < 0) continue;
-        bndv[u] = 0;
-        const int kn = w >> kNbrShift, rot = (w >> 2) & 7, f2 = w & 3;
-        const int nP = sFtab[f2 * Nfp + sFtab[4 * Nfp + rot * Nfp + m]];
+    // -------- traces and penalty terms at the 4 Nfp face nodes (face node fastest)
+    for (int i = tid; i < EB * NFN; i += NT) {
+      const int fm = i % NFN, e = i / NFN;
+      const int f = fm / Nfp, m = fm - f * Nfp;
+      const int nM = sFtab[f * Nfp + m];
+      const int4 nb = sNbr[e];
+      const int w = (f == 0) ? nb.x : (f == 1) ? nb.y : (f == 2) ? nb.z : nb.w;
+      const bool bnd = w < 0;
+      float qPv[Nf];
+      if (!bnd) {
+        const int kn = w >> kNbrShift;
         const int le = kn - k0;
         if (le >= 0 && le < EB) {
+          const int rot = (w >> 2) & 7, f2 = w & 3;
+          const int nP = sFtab[f2 * Nfp + sFtab[4 * Nfp + rot * Nfp + m]];
           const float* qn = sQ + le * Nf * Np;
 #pragma unroll
-          for (int c = 0; c < Nf; ++c) qP[u][c] = qn[c * Np + nP];
+          for (int c = 0; c < Nf; ++c) qPv[c] = qn[c * Np + nP];
         } else {
-          const float* qn = a.q + size_t(kn) * Nf * Np;
 #pragma unroll
-          for (int c = 0; c < Nf; ++c) qP[u][c] = __ldg(qn + c * Np + nP);
+          for (int c = 0; c < Nf; ++c) qPv[c] = sT[(c * NFN + fm) * EBP + e];
         }
       }
+      const float* qe = sQ + e * Nf * Np;
+      const float4 fn = *reinterpret_cast<const float4*>(sFn + (e * 4 + f) * 4);
+      const float nx = fn.x, ny = fn.y, nz = fn.z, fs = fn.w;
+      const float* gM = sRec + e * REC;
+      float qM[Nf];
 #pragma unroll
-      for (int u = 0; u < BATCH; ++u) {
-        const int i = base + u * NT;
-        if (i >= EB * NFN) continue;
-        const int e = i % EB, fm = i / EB;
-        const int f = fm / Nfp;
-        const int nM = nMv[u];
-        const bool bnd = bndv[u] != 0;
-        const float* qe = sQ + e * Nf * Np;
-        const float4 fn = *reinterpret_cast<const float4*>(sFn + (e * 4 + f) * 4);
-        const float nx = fn.x, ny = fn.y, nz = fn.z, fs = fn.w;
-        const float* gM = sRec + e * REC;
-        float qM[Nf];
-#pragma unroll
-        for (int c = 0; c < Nf; ++c) qM[c] = qe[c * Np + nM];
-        float* X = sXs + fm * EB + e;
-        if constexpr (MODEL == 0) {
-          const float kap = gM[9], rinv = gM[10], ZM = gM[11], zP = gM[12 + f];
-          float pP, vP0, vP1, vP2;
-          if (bnd) {  // rigid wall: p+ = p-, v+ = v- - 2 (v-.n) n
-            const float vn = qM[1] * nx + qM[2] * ny + qM[3] * nz;
-            pP = qM[0];
-            vP0 = qM[1] - 2.f * vn * nx;
-            vP1 = qM[2] - 2.f * vn * ny;
-            vP2 = qM[3] - 2.f * vn * nz;
-          } else {
-            pP = qP[u][0]; vP0 = qP[u][1]; vP1 = qP[u][2]; vP2 = qP[u][3];
-          }
-          const float jp = 0.5f * (pP - qM[0]);
-          const float jvn = 0.5f * ((vP0 - qM[1]) * nx + (vP1 - qM[2]) * ny + (vP2 - qM[3]) * nz);
-          float dp, sv;  // dv = sv * n
-          if (a.flux == 0) {
-            const float kc = 2.f / (ZM + zP);
-            const float ac = jp - zP * jvn;
-            dp = kap * kc * ac;
-            sv = -(ZM * rinv) * kc * ac;  // c^- = Z^- / rho^-
-          } else {
-            dp = -kap * jvn;
-            sv = -rinv * jp;
-          }
-          X[0] = fs * dp;
-          X[NFN * EB] = fs * sv * nx;
-          X[2 * NFN * EB] = fs * sv * ny;
-          X[3 * NFN * EB] = fs * sv * nz;
+      for (int c = 0; c < Nf; ++c) qM[c] = qe[c * Np + nM];
+      float* X = sXs + fm * EBP + e;
+      constexpr int XS = NFN * EBP;
+      if constexpr (MODEL == 0) {
+        const float kap = gM[9], rinv = gM[10], ZM = gM[11], zP = gM[12 + f];
+        float pP, vP0, vP1, vP2;
+        if (bnd) {  // rigid wall: p+ = p-, v+ = v- - 2 (v-.n) n
+          const float vn = qM[1] * nx + qM[2] * ny + qM[3] * nz;
+          pP = qM[0];
+          vP0 = qM[1] - 2.f * vn * nx;
+          vP1 = qM[2] - 2.f * vn * ny;
+          vP2 = qM[3] - 2.f * vn * nz;
         } else {
-          const float lam = gM[9], mu = gM[10], rinv = gM[11], ZpM = gM[12], ZsM = gM[13], cpM = gM[14],
-                      csM = gM[15], zP0 = gM[16 + f], zP1 = gM[20 + f];
-          float vP[3], sPd[6];
-          if (bnd) {
-            const float sv = (a.bc == 0) ? 1.f : -1.f;  // free: v+ = v-, sigma+ = -sigma-
-#pragma unroll
-            for (int c = 0; c < 3; ++c) vP[c] = sv * qM[c];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) sPd[c] = -sv * qM[3 + c];
-          } else {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) vP[c] = qP[u][c];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) sPd[c] = qP[u][3 + c];
-          }
-          const float n[3] = {nx, ny, nz};
-          float ds[6];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) ds[c] = sPd[c] - qM[3 + c];
-          float jt[3], jv[3];  // [[sigma n]], [[v]]  (sxx syy szz sxy sxz syz)
-          jt[0] = 0.5f * (ds[0] * nx + ds[3] * ny + ds[4] * nz);
-          jt[1] = 0.5f * (ds[3] * nx + ds[1] * ny + ds[5] * nz);
-          jt[2] = 0.5f * (ds[4] * nx + ds[5] * ny + ds[2] * nz);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) jv[c] = 0.5f * (vP[c] - qM[c]);
-          float pv[3], dv[3];  // p_v and the velocity jump with P_sigma = C:sym(n (x) dv)
-          if (a.flux == 0) {
-            const float jsnn = jt[0] * nx + jt[1] * ny + jt[2] * nz;
-            const float jvn = jv[0] * nx + jv[1] * ny + jv[2] * nz;
-            const float ap = jsnn + zP0 * jvn;
-            const float as = jsnn + zP1 * jvn;
-            const float kp = 2.f / (ZpM + zP0), ks = 2.f / (ZsM + zP1);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const float tang = (jt[c] + zP1 * jv[c]) - as * n[c];
-              dv[c] = kp * ap * n[c] + ks * tang;
-              pv[c] = kp * ap * cpM * n[c] + ks * csM * tang;
-            }
-          } else {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              dv[c] = jv[c];
-              pv[c] = rinv * jt[c];
-            }
-          }
-          const float ndv = nx * dv[0] + ny * dv[1] + nz * dv[2];
-          X[0 * NFN * EB] = fs * pv[0];
-          X[1 * NFN * EB] = fs * pv[1];
-          X[2 * NFN * EB] = fs * pv[2];
-          X[3 * NFN * EB] = fs * (lam * ndv + 2.f * mu * nx * dv[0]);
-          X[4 * NFN * EB] = fs * (lam * ndv + 2.f * mu * ny * dv[1]);
-          X[5 * NFN * EB] = fs * (lam * ndv + 2.f * mu * nz * dv[2]);
-          X[6 * NFN * EB] = fs * (mu * (nx * dv[1] + ny * dv[0]));
-          X[7 * NFN * EB] = fs * (mu * (nx * dv[2] + nz * dv[0]));
-          X[8 * NFN * EB] = fs * (mu * (ny * dv[2] + nz * dv[1]));
+          pP = qPv[0]; vP0 = qPv[1]; vP1 = qPv[2]; vP2 = qPv[3];
         }
+        const float jp = 0.5f * (pP - qM[0]);
+        const float jvn = 0.5f * ((vP0 - qM[1]) * nx + (vP1 - qM[2]) * ny + (vP2 - qM[3]) * nz);
+        float dp, sv;  // dv = sv * n
+        if (a.flux == 0) {
+          const float kc = 2.f / (ZM + zP);
+          const float ac = jp - zP * jvn;
+          dp = kap * kc * ac;
+          sv = -(ZM * rinv) * kc * ac;  // c^- = Z^- / rho^-
+        } else {
+          dp = -kap * jvn;
+          sv = -rinv * jp;
+        }
+        X[0] = fs * dp;
+        X[XS] = fs * sv * nx;
+        X[2 * XS] = fs * sv * ny;
+        X[3 * XS] = fs * sv * nz;
+      } else {
+        const float lam = gM[9], mu = gM[10], rinv = gM[11], ZpM = gM[12], ZsM = gM[13], cpM = gM[14],
+                    csM = gM[15], zP0 = gM[16 + f], zP1 = gM[20 + f];
+        float vP[3], sPd[6];
+        if (bnd) {
+          const float sv = (a.bc == 0) ? 1.f : -1.f;  // free: v+ = v-, sigma+ = -sigma-
+#pragma unroll
+          for (int c = 0; c < 3; ++c) vP[c] = sv * qM[c];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) sPd[c] = -sv * qM[3 + c];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) vP[c] = qPv[c];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) sPd[c] = qPv[3 + c];
+        }
+        const float n[3] = {nx, ny, nz};
+        float ds[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) ds[c] = sPd[c] - qM[3 + c];
+        float jt[3], jv[3];  // [[sigma n]], [[v]]  (sxx syy szz sxy sxz syz)
+        jt[0] = 0.5f * (ds[0] * nx + ds[3] * ny + ds[4] * nz);
+        jt[1] = 0.5f * (ds[3] * nx + ds[1] * ny + ds[5] * nz);
+        jt[2] = 0.5f * (ds[4] * nx + ds[5] * ny + ds[2] * nz);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) jv[c] = 0.5f * (vP[c] - qM[c]);
+        float pv[3], dv[3];  // p_v and the velocity jump with P_sigma = C:sym(n (x) dv)
+        if (a.flux == 0) {
+          const float jsnn = jt[0] * nx + jt[1] * ny + jt[2] * nz;
+          const float jvn = jv[0] * nx + jv[1] * ny + jv[2] * nz;
+          const float ap = jsnn + zP0 * jvn;
+          const float as = jsnn + zP1 * jvn;
+          const float kp = 2.f / (ZpM + zP0), ks = 2.f / (ZsM + zP1);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float tang = (jt[c] + zP1 * jv[c]) - as * n[c];
+            dv[c] = kp * ap * n[c] + ks * tang;
+            pv[c] = kp * ap * cpM * n[c] + ks * csM * tang;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            dv[c] = jv[c];
+            pv[c] = rinv * jt[c];
+          }
+        }
+        const float ndv = nx * dv[0] + ny * dv[1] + nz * dv[2];
+        X[0 * XS] = fs * pv[0];
+        X[1 * XS] = fs * pv[1];
+        X[2 * XS] = fs * pv[2];
+        X[3 * XS] = fs * (lam * ndv + 2.f * mu * nx * dv[0]);
+        X[4 * XS] = fs * (lam * ndv + 2.f * mu * ny * dv[1]);
+        X[5 * XS] = fs * (lam * ndv + 2.f * mu * nz * dv[2]);
+        X[6 * XS] = fs * (mu * (nx * dv[1] + ny * dv[0]));
+        X[7 * XS] = fs * (mu * (nx * dv[2] + nz * dv[0]));
+        X[8 * XS] = fs * (mu * (ny * dv[2] + nz * dv[1]));
       }
     }
     __syncthreads();
-    if (R_SMEM && a.mode == 0) {
-      bool okr = mbar_wait_bounded(&bars[2], uint32_t(it & 1), a.err);
-      if (!__syncthreads_and(okr)) {
-        mbar_wait_bounded(&bars[2], uint32_t(it & 1), nullptr);
-        return;
-      }
+    // the next block's stage was issued at the top of this block: once it has
+    // landed, start its neighbour gathers so that they overlap the products
+    if (b + G < nblk) {
+      if (mbar_wait_bounded(&bars[s ^ 1], uint32_t(((it + 1) >> 1) & 1), a.err)) issue_gathers(b + G, s ^ 1);
     }
 
-    // -------- register-tiled operator products + epilogue
-    for (int tile = tid; tile < NTILE; tile += NT) {
-      const int rt = tile % RT, ct = tile / RT;
-      const int i0 = 4 * rt, e0 = TN * ct;
+    // -------- register-tiled operator products (one tile of 4 nodes x TN elements per thread)
+    float r[TN][Nf][4];
+    const bool has_tile = tid < NTILE;
+    // element index fastest across lanes: a warp shares each operator row
+    // segment (one broadcast wavefront) and reads consecutive input columns
+    constexpr int CT = EB / TN;
+    const int e0 = (tid % CT) * TN, rt = tid / CT;
+    const int i0 = 4 * rt;
+    if (has_tile) {
       const float* A = sOps + i0;
       if constexpr (MODEL == 0) {
-        float G[3][TN][4], R[TN][4], L[3][TN][4];
+        float G3[3][TN][4], R[TN][4], L[3][TN][4];
 #pragma unroll
         for (int t = 0; t < TN; ++t)
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             R[t][v] = 0.f;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) G[d][t][v] = L[d][t][v] = 0.f;
+            for (int d = 0; d < 3; ++d) G3[d][t][v] = L[d][t][v] = 0.f;
           }
 #pragma unroll 4
         for (int j = 0; j < Np; ++j) {
           const float4 a0 = load_op<OPS_SMEM>(A + (0 * Np + j) * Mpad);
           const float4 a1 = load_op<OPS_SMEM>(A + (1 * Np + j) * Mpad);
           const float4 a2 = load_op<OPS_SMEM>(A + (2 * Np + j) * Mpad);
-          float xp[TN], x0[TN], x1[TN], x2[TN];
-          VecT<TN>::load(sXv + (0 * Np + j) * EB + e0, xp);
-          VecT<TN>::load(sXv + (1 * Np + j) * EB + e0, x0);
-          VecT<TN>::load(sXv + (2 * Np + j) * EB + e0, x1);
-          VecT<TN>::load(sXv + (3 * Np + j) * EB + e0, x2);
 #pragma unroll
           for (int t = 0; t < TN; ++t) {
-            fma4(G[0][t], a0, xp[t]);
-            fma4(G[1][t], a1, xp[t]);
-            fma4(G[2][t], a2, xp[t]);
-            fma4(R[t], a0, x0[t]);
-            fma4(R[t], a1, x1[t]);
-            fma4(R[t], a2, x2[t]);
+            const float xp = sXv[(0 * Np + j) * EBP + e0 + t];
+            const float x0 = sXv[(1 * Np + j) * EBP + e0 + t];
+            const float x1 = sXv[(2 * Np + j) * EBP + e0 + t];
+            const float x2 = sXv[(3 * Np + j) * EBP + e0 + t];
+            fma4(G3[0][t], a0, xp);
+            fma4(G3[1][t], a1, xp);
+            fma4(G3[2][t], a2, xp);
+            fma4(R[t], a0, x0);
+            fma4(R[t], a1, x1);
+            fma4(R[t], a2, x2);
           }
         }
 #pragma unroll 4
         for (int c = 0; c < NFN; ++c) {
           const float4 l = load_op<OPS_SMEM>(A + (3 * Np + c) * Mpad);
-          float pp[TN], p0[TN], p1[TN], p2[TN];
-          VecT<TN>::load(sXs + (0 * NFN + c) * EB + e0, pp);
-          VecT<TN>::load(sXs + (1 * NFN + c) * EB + e0, p0);
-          VecT<TN>::load(sXs + (2 * NFN + c) * EB + e0, p1);
-          VecT<TN>::load(sXs + (3 * NFN + c) * EB + e0, p2);
 #pragma unroll
           for (int t = 0; t < TN; ++t) {
-            fma4(R[t], l, pp[t]);
-            fma4(L[0][t], l, p0[t]);
-            fma4(L[1][t], l, p1[t]);
-            fma4(L[2][t], l, p2[t]);
+            fma4(R[t], l, sXs[(0 * NFN + c) * EBP + e0 + t]);
+            fma4(L[0][t], l, sXs[(1 * NFN + c) * EBP + e0 + t]);
+            fma4(L[1][t], l, sXs[(2 * NFN + c) * EBP + e0 + t]);
+            fma4(L[2][t], l, sXs[(3 * NFN + c) * EBP + e0 + t]);
           }
         }
 #pragma unroll
         for (int t = 0; t < TN; ++t) {
-          const int e = e0 + t;
-          const int k = k0 + e;
-          if (k >= a.K) continue;
-          const float* gk = sRec + e * REC;
+          const float* gk = sRec + (e0 + t) * REC;
           const float rinv = gk[10];
-          const bool src = (k == a.src_elem) && a.srcvec;
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
-            const int i = i0 + v;
-            if (i >= Np) continue;
-            float r[4];
-            r[0] = R[t][v];
+            r[t][0][v] = R[t][v];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-              r[1 + c] = L[c][t][v] - rinv * (gk[3 * c] * G[0][t][v] + gk[3 * c + 1] * G[1][t][v] +
-                                              gk[3 * c + 2] * G[2][t][v]);
-            if (src) {
-#pragma unroll
-              for (int c = 0; c < 4; ++c) r[c] = fmaf(a.src_amp, __ldg(a.srcvec + c * Np + i), r[c]);
-            }
-            const size_t base = size_t(k) * Nf * Np + i;
-            if (a.mode == 0) {
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const int li = e * Nf * Np + c * Np + i;
-                const float r1v = R_SMEM ? sR[li] : __ldg(a.r1 + base + c * Np);
-                const float r2v = R_SMEM ? sR[P::nQ + li] : a.r2[base + c * Np];
-                const float acc = a.a1 * r[c] + a.a2 * r1v + a.a3 * r2v;
-                a.qn[base + c * Np] = fmaf(a.dt, acc, sQ[li]);
-                a.r2[base + c * Np] = r[c];
-              }
-            } else {
-#pragma unroll
-              for (int c = 0; c < 4; ++c) a.rout[base + c * Np] = r[c];
-            }
+              r[t][1 + c][v] = L[c][t][v] - rinv * (gk[3 * c] * G3[0][t][v] + gk[3 * c + 1] * G3[1][t][v] +
+                                                    gk[3 * c + 2] * G3[2][t][v]);
           }
         }
       } else {
@@ -525,21 +538,15 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
 #pragma unroll
           for (int d = 0; d < 3; ++d) ad[d] = load_op<OPS_SMEM>(A + (d * Np + j) * Mpad);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float xv[TN];
-            VecT<TN>::load(sXv + (c * Np + j) * EB + e0, xv);
+          for (int t = 0; t < TN; ++t)
 #pragma unroll
-            for (int t = 0; t < TN; ++t)
+            for (int c = 0; c < 3; ++c) {
+              const float xv = sXv[(c * Np + j) * EBP + e0 + t];
 #pragma unroll
-              for (int d = 0; d < 3; ++d) fma4(U[c][d][t], ad[d], xv[t]);
+              for (int d = 0; d < 3; ++d) fma4(U[c][d][t], ad[d], xv);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              float xs[TN];
-              VecT<TN>::load(sXv + ((3 + 3 * c + d) * Np + j) * EB + e0, xs);
-#pragma unroll
-              for (int t = 0; t < TN; ++t) fma4(Rv[c][t], ad[d], xs[t]);
+              for (int d = 0; d < 3; ++d) fma4(Rv[c][t], ad[d], sXv[((3 + 3 * c + d) * Np + j) * EBP + e0 + t]);
             }
-          }
         }
         float Rs[6][TN][4];
 #pragma unroll
@@ -567,59 +574,110 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
         for (int c = 0; c < NFN; ++c) {
           const float4 l = load_op<OPS_SMEM>(A + (3 * Np + c) * Mpad);
 #pragma unroll
-          for (int fld = 0; fld < 3; ++fld) {
-            float p[TN];
-            VecT<TN>::load(sXs + (fld * NFN + c) * EB + e0, p);
+          for (int t = 0; t < TN; ++t) {
 #pragma unroll
-            for (int t = 0; t < TN; ++t) fma4(Rv[fld][t], l, p[t]);
-          }
+            for (int fld = 0; fld < 3; ++fld) fma4(Rv[fld][t], l, sXs[(fld * NFN + c) * EBP + e0 + t]);
 #pragma unroll
-          for (int fld = 0; fld < 6; ++fld) {
-            float p[TN];
-            VecT<TN>::load(sXs + ((3 + fld) * NFN + c) * EB + e0, p);
-#pragma unroll
-            for (int t = 0; t < TN; ++t) fma4(Rs[fld][t], l, p[t]);
+            for (int fld = 0; fld < 6; ++fld) fma4(Rs[fld][t], l, sXs[((3 + fld) * NFN + c) * EBP + e0 + t]);
           }
         }
 #pragma unroll
-        for (int t = 0; t < TN; ++t) {
-          const int e = e0 + t;
-          const int k = k0 + e;
-          if (k >= a.K) continue;
-          const bool src = (k == a.src_elem) && a.srcvec;
+        for (int t = 0; t < TN; ++t)
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
-            const int i = i0 + v;
-            if (i >= Np) continue;
-            float r[9];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) r[c] = Rv[c][t][v];
+            for (int c = 0; c < 3; ++c) r[t][c][v] = Rv[c][t][v];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) r[3 + c] = Rs[c][t][v];
-            if (src) {
-#pragma unroll
-              for (int c = 0; c < 9; ++c) r[c] = fmaf(a.src_amp, __ldg(a.srcvec + c * Np + i), r[c]);
-            }
-            const size_t base = size_t(k) * Nf * Np + i;
-            if (a.mode == 0) {
-#pragma unroll
-              for (int c = 0; c < 9; ++c) {
-                const int li = e * Nf * Np + c * Np + i;
-                const float r1v = R_SMEM ? sR[li] : __ldg(a.r1 + base + c * Np);
-                const float r2v = R_SMEM ? sR[P::nQ + li] : a.r2[base + c * Np];
-                const float acc = a.a1 * r[c] + a.a2 * r1v + a.a3 * r2v;
-                a.qn[base + c * Np] = fmaf(a.dt, acc, sQ[li]);
-                a.r2[base + c * Np] = r[c];
-              }
-            } else {
-#pragma unroll
-              for (int c = 0; c < 9; ++c) a.rout[base + c * Np] = r[c];
-            }
+            for (int c = 0; c < 6; ++c) r[t][3 + c][v] = Rs[c][t][v];
           }
+      }
+#pragma unroll
+      for (int t = 0; t < TN; ++t) {
+        const int k = k0 + e0 + t;
+        if (k == a.src_elem && a.srcvec) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (i0 + v < Np)
+#pragma unroll
+              for (int c = 0; c < Nf; ++c) r[t][c][v] = fmaf(a.src_amp, __ldg(a.srcvec + c * Np + i0 + v), r[t][c][v]);
         }
       }
     }
+
+    if (a.mode != 0) {  // RHS only: straight to the caller's buffer
+#pragma unroll
+      for (int t = 0; t < TN; ++t) {
+        const int k = k0 + e0 + t;
+        if (has_tile && k < a.K) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (i0 + v < Np)
+#pragma unroll
+              for (int c = 0; c < Nf; ++c) a.rout[size_t(k) * Nf * Np + c * Np + i0 + v] = r[t][c][v];
+        }
+      }
+      continue;
+    }
+
+    // -------- AB3 update: the block's RHS goes to the (now free) volume-input
+    // buffer as [EB][Nf][Np]; one flat, vectorised pass then updates the block
+    __syncthreads();  // every tile has finished reading the GEMM inputs
+    float* sRhs = sXv;
+    if (has_tile) {
+#pragma unroll
+      for (int t = 0; t < TN; ++t)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (i0 + v < Np)
+#pragma unroll
+            for (int c = 0; c < Nf; ++c) sRhs[(e0 + t) * Nf * Np + c * Np + i0 + v] = r[t][c][v];
+    }
+    bool okr = true;
+    if constexpr (R_SMEM) okr = mbar_wait_bounded(&bars[2], uint32_t(it & 1), a.err);  // history landed
+    if (!__syncthreads_and(okr)) {
+      if (R_SMEM) mbar_wait_bounded(&bars[2], uint32_t(it & 1), nullptr);
+      return;
+    }
+    const float a1 = a.a1, a2 = a.a2, a3 = a.a3, dt = a.dt;
+    if constexpr (R_SMEM) {
+      // q^{m+1} replaces r^{m-1} and r^m replaces r^{m-2} in sR, then both are bulk-stored
+      for (int i = tid; i < P::nQ / 4; i += NT) {
+        const float4 q4 = reinterpret_cast<const float4*>(sQ)[i];
+        const float4 r4 = reinterpret_cast<const float4*>(sRhs)[i];
+        float4* h1 = reinterpret_cast<float4*>(sR) + i;
+        float4* h2 = reinterpret_cast<float4*>(sR + P::nQ) + i;
+        const float4 p1 = *h1, p2 = *h2;
+        *h1 = make_float4(fmaf(dt, a1 * r4.x + a2 * p1.x + a3 * p2.x, q4.x),
+                          fmaf(dt, a1 * r4.y + a2 * p1.y + a3 * p2.y, q4.y),
+                          fmaf(dt, a1 * r4.z + a2 * p1.z + a3 * p2.z, q4.z),
+                          fmaf(dt, a1 * r4.w + a2 * p1.w + a3 * p2.w, q4.w));
+        *h2 = r4;
+      }
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tma_bulk_s2g(a.qn + size_t(k0) * Nf * Np, sR, kQBytes);
+        tma_bulk_s2g(a.r2 + size_t(k0) * Nf * Np, sR + P::nQ, kQBytes);
+        bulk_commit();
+      }
+    } else {
+      const size_t g0 = size_t(k0) * Nf * Np / 4;
+      const float4* gr1 = reinterpret_cast<const float4*>(a.r1) + g0;
+      float4* gr2 = reinterpret_cast<float4*>(a.r2) + g0;
+      float4* gqn = reinterpret_cast<float4*>(a.qn) + g0;
+      for (int i = tid; i < P::nQ / 4; i += NT) {
+        const float4 q4 = reinterpret_cast<const float4*>(sQ)[i];
+        const float4 r4 = reinterpret_cast<const float4*>(sRhs)[i];
+        const float4 p1 = __ldg(gr1 + i), p2 = gr2[i];
+        gqn[i] = make_float4(fmaf(dt, a1 * r4.x + a2 * p1.x + a3 * p2.x, q4.x),
+                             fmaf(dt, a1 * r4.y + a2 * p1.y + a3 * p2.y, q4.y),
+                             fmaf(dt, a1 * r4.z + a2 * p1.z + a3 * p2.z, q4.z),
+                             fmaf(dt, a1 * r4.w + a2 * p1.w + a3 * p2.w, q4.w));
+        gr2[i] = r4;
+      }
+    }
   }
+  if (R_SMEM && tid == 0) bulk_wait_all();
 }
 
 }  // namespace dgk

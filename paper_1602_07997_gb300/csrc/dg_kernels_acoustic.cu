@@ -1,21 +1,34 @@
 // Acoustic (4-field) instantiations of the fused step kernel, N = 1..8.
-// EB elements per block are chosen so that a CTA needs <= ~113 KB of shared
-// memory (two CTAs per SM overlap each other's gather and product phases);
-// the operator blob stays in shared memory up to N = 5 and is read through
-// L1 above; the AB3 history of a block is bulk-copied into shared memory.
+// Each degree has a few variants (elements per block EB; threads = one
+// 4-node x 1-element tile each); the autotuner times them on the caller's
+// mesh and keeps the fastest, variant 0 is the default.  The operator blob
+// is staged in shared memory up to N = 4 and read through L1 above.
 #include "dg_launch.cuh"
 
 namespace dgk {
 
-const KernelCfg* kernel_cfg_acoustic(int N) {
-  //                                    N   EB TN  NT  ops_smem r_smem
-  static const KernelCfg cfg[8] = {
-      make_cfg<0, 1, 128, 1, 128, true, true>(), make_cfg<0, 2, 64, 1, 192, true, true>(),
-      make_cfg<0, 3, 32, 1, 160, true, true>(),  make_cfg<0, 4, 20, 1, 192, true, true>(),
-      make_cfg<0, 5, 8, 1, 128, true, true>(),   make_cfg<0, 6, 12, 1, 256, false, true>(),
-      make_cfg<0, 7, 8, 1, 256, false, true>(),  make_cfg<0, 8, 4, 1, 192, false, true>(),
-  };
-  return (N >= 1 && N <= 8) ? &cfg[N - 1] : nullptr;
+const KernelCfg* kernel_variants_acoustic(int N, int* count) {
+  static const KernelCfg v1[] = {make_cfg<0, 1, 16, true, true>(), make_cfg<0, 1, 64, true, true>(),
+                                 make_cfg<0, 1, 32, true, true>(), make_cfg<0, 1, 128, true, true>()};
+  static const KernelCfg v2[] = {make_cfg<0, 2, 8, true, true>(), make_cfg<0, 2, 32, true, true>(),
+                                 make_cfg<0, 2, 16, true, true>(), make_cfg<0, 2, 64, true, true>()};
+  static const KernelCfg v3[] = {make_cfg<0, 3, 16, true, true>(), make_cfg<0, 3, 4, true, true>(),
+                                 make_cfg<0, 3, 8, true, true>(), make_cfg<0, 3, 32, true, true>()};
+  static const KernelCfg v4[] = {make_cfg<0, 4, 8, true, true>(), make_cfg<0, 4, 4, true, true>(),
+                                 make_cfg<0, 4, 8, true, true, 2>(), make_cfg<0, 4, 12, true, true>()};
+  static const KernelCfg v5[] = {make_cfg<0, 5, 8, false, true>(), make_cfg<0, 5, 8, false, true, 2>(),
+                                 make_cfg<0, 5, 4, true, true>(), make_cfg<0, 5, 12, false, true, 2>()};
+  static const KernelCfg v6[] = {make_cfg<0, 6, 8, false, true, 2>(), make_cfg<0, 6, 4, false, true>(),
+                                 make_cfg<0, 6, 8, false, true>(), make_cfg<0, 6, 4, false, true, 2>()};
+  static const KernelCfg v7[] = {make_cfg<0, 7, 4, false, true, 2>(), make_cfg<0, 7, 4, false, true>(),
+                                 make_cfg<0, 7, 8, false, true, 2>(), make_cfg<0, 7, 4, false, true, 4>()};
+  static const KernelCfg v8[] = {make_cfg<0, 8, 4, false, true, 2>(), make_cfg<0, 8, 4, false, true>(),
+                                 make_cfg<0, 8, 4, false, true, 4>(), make_cfg<0, 8, 8, false, true, 2>()};
+  static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
+  static const int cnt[8] = {4, 4, 4, 4, 4, 4, 4, 4};
+  if (N < 1 || N > 8) return nullptr;
+  *count = cnt[N - 1];
+  return tab[N - 1];
 }
 
 }  // namespace dgk

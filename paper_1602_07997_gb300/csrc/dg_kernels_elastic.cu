@@ -1,19 +1,29 @@
-// Elastic (9-field) instantiations of the fused step kernel, N = 1..8.
-// TN = 1 (the 12 accumulator tiles of the volume products take 48
-// registers).  Above N = 4 the AB3 history is read from global memory in
-// the epilogue instead of being staged, to keep two CTAs per SM.
+// Elastic (9-field) instantiations of the fused step kernel, N = 1..8, with
+// the same variant scheme as the acoustic model.  Above N = 4 the AB3
+// history is read from global memory in the update pass instead of being
+// staged, to keep the shared-memory footprint down.
 #include "dg_launch.cuh"
 
 namespace dgk {
 
-const KernelCfg* kernel_cfg_elastic(int N) {
-  static const KernelCfg cfg[8] = {
-      make_cfg<1, 1, 64, 1, 128, true, true>(),  make_cfg<1, 2, 32, 1, 128, true, true>(),
-      make_cfg<1, 3, 16, 1, 128, true, true>(),  make_cfg<1, 4, 8, 1, 128, true, true>(),
-      make_cfg<1, 5, 8, 1, 128, false, false>(), make_cfg<1, 6, 4, 1, 128, false, false>(),
-      make_cfg<1, 7, 4, 1, 128, false, false>(), make_cfg<1, 8, 4, 1, 192, false, false>(),
-  };
-  return (N >= 1 && N <= 8) ? &cfg[N - 1] : nullptr;
+const KernelCfg* kernel_variants_elastic(int N, int* count) {
+  static const KernelCfg v1[] = {make_cfg<1, 1, 16, true, true>(), make_cfg<1, 1, 8, true, true>(),
+                                 make_cfg<1, 1, 32, true, true>()};
+  static const KernelCfg v2[] = {make_cfg<1, 2, 16, true, true>(), make_cfg<1, 2, 4, true, true>(),
+                                 make_cfg<1, 2, 8, true, true>()};
+  static const KernelCfg v3[] = {make_cfg<1, 3, 8, true, true>(), make_cfg<1, 3, 4, true, true>(),
+                                 make_cfg<1, 3, 16, true, true>()};
+  static const KernelCfg v4[] = {make_cfg<1, 4, 4, true, true>(), make_cfg<1, 4, 8, false, true>(),
+                                 make_cfg<1, 4, 4, false, true>()};
+  static const KernelCfg v5[] = {make_cfg<1, 5, 4, false, false>(), make_cfg<1, 5, 4, false, true>()};
+  static const KernelCfg v6[] = {make_cfg<1, 6, 4, false, false>(), make_cfg<1, 6, 4, false, false, 2>()};
+  static const KernelCfg v7[] = {make_cfg<1, 7, 4, false, false>(), make_cfg<1, 7, 4, false, false, 2>()};
+  static const KernelCfg v8[] = {make_cfg<1, 8, 4, false, false>(), make_cfg<1, 8, 4, false, false, 2>()};
+  static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
+  static const int cnt[8] = {3, 3, 3, 3, 2, 2, 2, 2};
+  if (N < 1 || N > 8) return nullptr;
+  *count = cnt[N - 1];
+  return tab[N - 1];
 }
 
 }  // namespace dgk
