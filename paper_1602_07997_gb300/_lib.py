@@ -88,8 +88,6 @@ def lib():
         "dg_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
-        if not hasattr(L, name):
-            continue
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
@@ -262,3 +260,80 @@ class Solver:
         d = np.ascontiguousarray(direction, dtype=np.float64)
         a = np.ascontiguousarray(amp, dtype=np.float64)
         check(lib().dg_set_source(self.h, _dptr(xs), _dptr(d), _dptr(a), a.size))
+
+
+class Server:
+    """Continuous-batching solve server (dg_server): submit / poll / cancel."""
+
+    def __init__(self, hbm_budget_bytes=0, max_batch=64):
+        s = C.c_void_p()
+        check(lib().dg_server_create(C.c_size_t(hbm_budget_bytes), int(max_batch), C.byref(s)))
+        self.s = s
+        self._meta = {}
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().dg_server_destroy(self.s)
+            self.s = None
+
+    __del__ = close
+
+    def submit(self, verts, tets, coeffs, N, model="acoustic", q0=None, dt=0.0, nsteps=1, flux="upwind",
+               bc=None, source=None, amp=None, direction=(0.0, 0.0, 1.0)):
+        m, keep = make_mesh(verts, tets)
+        cf = np.ascontiguousarray(coeffs, dtype=np.float64)
+        model = _model(model)
+        Nf = 4 if model == ACOUSTIC else 9
+        Np = (N + 1) * (N + 2) * (N + 3) // 6
+        K = keep[1].shape[0]
+        r = Request()
+        r.mesh = C.pointer(m)
+        r.coeffs = _dptr(cf)
+        r.N, r.model, r.nsteps = int(N), model, int(nsteps)
+        r.opts = Opts(FLUX[flux], BC[bc], 0, 0, float(dt), None)
+        q0a = None
+        if q0 is not None:
+            q0a = np.ascontiguousarray(q0, dtype=np.float32)
+            r.q0 = q0a.ctypes.data_as(C.POINTER(C.c_float))
+        xs = d = a = None
+        if source is not None and amp is not None:
+            xs = np.ascontiguousarray(source, dtype=np.float64)
+            d = np.ascontiguousarray(direction, dtype=np.float64)
+            a = np.ascontiguousarray(amp, dtype=np.float64)
+            r.src_xyz, r.src_dir, r.src_amp, r.src_namp = _dptr(xs), _dptr(d), _dptr(a), a.size
+        t = C.c_uint64()
+        check(lib().dg_submit(self.s, C.byref(r), C.byref(t)))
+        self._meta[t.value] = (K, Nf, Np)
+        return t.value
+
+    def poll(self, ticket):
+        """None while running; (q [K][Nf][Np], latency_s) when finished; raises on failure."""
+        K, Nf, Np = self._meta.get(ticket, (0, 0, 0))
+        out = np.empty((K, Nf, Np), dtype=np.float32)
+        lat = C.c_double()
+        ptr = C.c_void_p(out.ctypes.data) if out.size else None
+        rc = lib().dg_poll(self.s, C.c_uint64(ticket), ptr, C.byref(lat))
+        if rc == DG_EAGAIN:
+            return None
+        self._meta.pop(ticket, None)
+        check(rc)
+        return out, lat.value
+
+    def wait(self, ticket, timeout=300.0, interval=0.001):
+        import time
+        t0 = time.time()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.time() - t0 > timeout:
+                raise TimeoutError("request %d did not finish in %.0f s" % (ticket, timeout))
+            time.sleep(interval)
+
+    def cancel(self, ticket):
+        check(lib().dg_cancel(self.s, C.c_uint64(ticket)))
+
+    def stats(self):
+        q, r, d, n = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().dg_server_stats(self.s, C.byref(q), C.byref(r), C.byref(d), C.byref(n)))
+        return dict(queued=q.value, running=r.value, done=d.value, launches=n.value)

@@ -17,7 +17,7 @@ NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["dg_kernels_acoustic.cu", "dg_kernels_elastic.cu", "dg_dispatch.cu"]
-CPP_SOURCES = ["api.cpp", "refelem.cpp", "mesh.cpp"]
+CPP_SOURCES = ["api.cpp", "refelem.cpp", "mesh.cpp", "server.cpp"]
 
 
 def _run(cmd):
@@ -52,7 +52,7 @@ def build(verbose=False, force=False, ptxas_info=False):
         src = os.path.join(CSRC, f)
         obj = os.path.join(OUT, f + ".o")
         if force or _newer([src] + headers, obj):
-            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-I" + os.path.join(CUDA, "include"),
+            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-I" + os.path.join(CUDA, "include"),
                          "-c", src, "-o", obj])
     with ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
         outs = list(ex.map(_run, jobs))
@@ -62,7 +62,7 @@ def build(verbose=False, force=False, ptxas_info=False):
                 print(o)
     objs = [os.path.join(OUT, f + ".o") for f in CU_SOURCES + CPP_SOURCES]
     if force or jobs or not os.path.exists(LIB):
-        _run([NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs,
+        _run([NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs, "-lpthread",
               "-Xlinker", "-rpath=" + os.path.join(CUDA, "lib64")])
     return LIB
 

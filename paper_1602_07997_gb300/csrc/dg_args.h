@@ -43,12 +43,44 @@ struct StepArgs {
   int* err;              // device error word (bounded-wait expiry)
 };
 
+// Per-solve device state of a batched launch (served mode).  The step index,
+// AB3 start-up phase and buffer parities advance on the device (advance kernel).
+struct SolveDev {
+  float* q[2];           // ping-pong fields
+  float* r[2];           // AB3 history slots
+  const float* rec;
+  const int4* nbr;
+  const float* srcvec;   // [Nf][Np] or null
+  const float* amp;      // source amplitude per step (device) or null
+  long long step;        // time-step index m
+  int namp;
+  int src_elem;
+  int K;
+  int flux, bc;
+  float dt;
+  int have;              // stored RHS levels (0, 1, 2)
+  int qcur;              // q[qcur] holds q^m
+  int r1slot;            // r[r1slot] holds r^{m-1}
+  int steps_left;        // the advance kernel stops moving a solve at 0
+};
+
+struct BatchArgs {
+  SolveDev* solves;      // [nsolves]
+  const int* block_start;  // [nsolves + 1] first global block of each solve
+  int nsolves;
+  int total_blocks;
+  const float* ops;      // operators of the batch's (model, N)
+  const int* ftab;
+  int* err;
+};
+
 // Host-visible launch configuration of one (model, N) instantiation.
 struct KernelCfg {
   int EB, TN, NT;
   bool ops_smem, r_smem;
   size_t smem;
   void (*fn)(StepArgs);
+  void (*fn_batched)(BatchArgs);
 };
 
 // Compiled variants of one (model, N): different elements per block (EB) and
@@ -58,5 +90,9 @@ const KernelCfg* kernel_cfg(int model, int N);
 
 // Launch the persistent step kernel on `stream` (grid = min(blocks, SMs x occupancy)).
 cudaError_t launch_step(const KernelCfg* cfg, const StepArgs& args, cudaStream_t stream);
+// One batched step over every solve of `args` (same model and N).
+cudaError_t launch_step_batched(const KernelCfg* cfg, const BatchArgs& args, cudaStream_t stream);
+// Advance the device-side step state of the solves (one thread per solve).
+cudaError_t launch_advance(SolveDev* solves, int nsolves, cudaStream_t stream);
 
 }  // namespace dgk

@@ -20,15 +20,15 @@ const KernelCfg* kernel_cfg(int model, int N) { return kernel_variants(model, N,
 
 namespace {
 std::mutex g_mu;
-std::map<std::pair<int, const KernelCfg*>, int> g_cap;  // (device, variant) -> max resident CTAs
+std::map<std::pair<int, const void*>, int> g_cap;  // (device, kernel) -> max resident CTAs
 
-// Opt the variant into its dynamic shared memory and read its occupancy (once per device).
-cudaError_t prepare(const KernelCfg* c, int* grid_cap) {
+// Opt the kernel into its dynamic shared memory and read its occupancy (once per device).
+cudaError_t prepare_fn(const KernelCfg* c, const void* fn, int* grid_cap) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_mu);
-  auto key = std::make_pair(dev, c);
+  auto key = std::make_pair(dev, fn);
   auto it = g_cap.find(key);
   if (it != g_cap.end()) {
     *grid_cap = it->second;
@@ -37,11 +37,10 @@ cudaError_t prepare(const KernelCfg* c, int* grid_cap) {
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(reinterpret_cast<const void*>(c->fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(c->smem));
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(c->smem));
   if (e != cudaSuccess) return e;
   int n = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, reinterpret_cast<const void*>(c->fn), c->NT, c->smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, c->NT, c->smem);
   if (e != cudaSuccess) return e;
   const int cap = sms * (n > 0 ? n : 1);
   g_cap[key] = cap;
@@ -53,7 +52,7 @@ cudaError_t prepare(const KernelCfg* c, int* grid_cap) {
 cudaError_t launch_step(const KernelCfg* c, const StepArgs& args, cudaStream_t stream) {
   if (!c) return cudaErrorInvalidValue;
   int cap = 0;
-  cudaError_t e = prepare(c, &cap);
+  cudaError_t e = prepare_fn(c, reinterpret_cast<const void*>(c->fn), &cap);
   if (e != cudaSuccess) return e;
   const int nblk = (args.K + c->EB - 1) / c->EB;
   if (nblk == 0) return cudaSuccess;
@@ -62,6 +61,35 @@ cudaError_t launch_step(const KernelCfg* c, const StepArgs& args, cudaStream_t s
   void* params[] = {&a};
   return cudaLaunchKernel(reinterpret_cast<const void*>(c->fn), dim3(grid), dim3(c->NT), params, c->smem,
                           stream);
+}
+
+__global__ void advance_kernel(SolveDev* s, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || s[i].steps_left <= 0) return;
+  s[i].step += 1;
+  s[i].have = s[i].have < 2 ? s[i].have + 1 : 2;
+  s[i].qcur ^= 1;
+  s[i].r1slot ^= 1;  // r^m was written into the r^{m-2} slot
+  s[i].steps_left -= 1;
+}
+
+cudaError_t launch_step_batched(const KernelCfg* c, const BatchArgs& args, cudaStream_t stream) {
+  if (!c || !c->fn_batched) return cudaErrorInvalidValue;
+  int cap = 0;
+  cudaError_t e = prepare_fn(c, reinterpret_cast<const void*>(c->fn_batched), &cap);
+  if (e != cudaSuccess) return e;
+  if (args.total_blocks == 0) return cudaSuccess;
+  const int grid = args.total_blocks < cap ? args.total_blocks : cap;
+  BatchArgs a = args;
+  void* params[] = {&a};
+  return cudaLaunchKernel(reinterpret_cast<const void*>(c->fn_batched), dim3(grid), dim3(c->NT), params,
+                          c->smem, stream);
+}
+
+cudaError_t launch_advance(SolveDev* solves, int nsolves, cudaStream_t stream) {
+  if (nsolves <= 0) return cudaSuccess;
+  advance_kernel<<<(nsolves + 127) / 128, 128, 0, stream>>>(solves, nsolves);
+  return cudaGetLastError();
 }
 
 }  // namespace dgk

@@ -183,9 +183,68 @@ struct Plan {
   static_assert(nXvol >= nQ, "the RHS of a block is staged in the volume-input buffer");
 };
 
-// ---------------------------------------------------------------- kernel
-template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM>
-__global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
+// ---------------------------------------------------------------- block providers
+// A provider maps a global block index to the arguments of the solve it
+// belongs to and to its local block index; operators, face tables, error word
+// and mode are common to every block of one launch.
+struct SingleSolve {
+  const StepArgs& a;
+  int EB;
+  __device__ int nblocks() const { return (a.K + EB - 1) / EB; }
+  __device__ void get(int b, StepArgs& A, int& lb) const {
+    A = a;
+    lb = b;
+  }
+  __device__ const float* ops() const { return a.ops; }
+  __device__ const int* ftab() const { return a.ftab; }
+  __device__ int* err() const { return a.err; }
+  __device__ int mode() const { return a.mode; }
+};
+
+struct SolveBatch {
+  const BatchArgs& B;
+  __device__ int nblocks() const { return B.total_blocks; }
+  __device__ void get(int b, StepArgs& A, int& lb) const {
+    int lo = 0, hi = B.nsolves - 1;  // last solve whose first block is <= b
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(B.block_start + mid) <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    const SolveDev& d = B.solves[lo];
+    lb = b - __ldg(B.block_start + lo);
+    const int qc = d.qcur, r1s = d.r1slot;
+    A.q = d.q[qc];
+    A.qn = d.q[1 - qc];
+    A.r1 = d.r[r1s];
+    A.r2 = d.r[1 - r1s];
+    A.rout = nullptr;
+    A.rec = d.rec;
+    A.nbr = d.nbr;
+    A.ops = B.ops;
+    A.ftab = B.ftab;
+    A.srcvec = d.src_elem >= 0 ? d.srcvec : nullptr;
+    A.src_elem = d.src_elem;
+    A.src_amp = (d.src_elem >= 0 && d.step < d.namp) ? d.amp[d.step] : 0.0f;
+    A.K = d.K;
+    A.mode = 0;
+    A.flux = d.flux;
+    A.bc = d.bc;
+    A.dt = d.dt;
+    if (d.have == 0) { A.a1 = 1.f; A.a2 = 0.f; A.a3 = 0.f; }
+    else if (d.have == 1) { A.a1 = 1.5f; A.a2 = -0.5f; A.a3 = 0.f; }
+    else { A.a1 = 23.f / 12.f; A.a2 = -16.f / 12.f; A.a3 = 5.f / 12.f; }
+    A.err = B.err;
+  }
+  __device__ const float* ops() const { return B.ops; }
+  __device__ const int* ftab() const { return B.ftab; }
+  __device__ int* err() const { return B.err; }
+  __device__ int mode() const { return 0; }
+};
+
+// ---------------------------------------------------------------- kernel body
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, class Prov>
+__device__ __forceinline__ void step_body(const Prov& prov) {
   using S = Sz<N>;
   using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM>;
   constexpr int Np = S::Np, Nfp = S::Nfp, NFN = S::NFN, Mpad = S::Mpad, RT = S::RT;
@@ -199,13 +258,15 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   float* sR = smem + P::oR;
   float* sXv = smem + P::oXvol;
   float* sXs = smem + P::oXsur;
-  const float* sOps = OPS_SMEM ? smem + P::oOps : a.ops;
+  const float* sOps = OPS_SMEM ? smem + P::oOps : prov.ops();
+  int* const err = prov.err();
+  const int mode = prov.mode();
   float* sFn = smem + P::oFn;
   int* sFtab = reinterpret_cast<int*>(smem + P::oFtab);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P::oBar);
 
   const int tid = threadIdx.x;
-  const int nblk = (a.K + EB - 1) / EB;
+  const int nblk = prov.nblocks();
   const int G = gridDim.x;
   constexpr uint32_t kQBytes = uint32_t(P::nQ * 4);
   constexpr uint32_t kRecBytes = uint32_t(EB * REC * 4);
@@ -214,7 +275,10 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   auto stage = [&](int s) { return smem + (s ? P::oStage1 : P::oStage0); };
   auto issue_stage = [&](int b, int s, bool with_ops) {
     float* st = stage(s);
-    const int k0 = b * EB;
+    StepArgs a;
+    int lb;
+    prov.get(b, a, lb);
+    const int k0 = lb * EB;
     const uint32_t bo = (OPS_SMEM && with_ops) ? uint32_t(S::KD * Mpad * 4) : 0u;
     mbar_arrive_expect_tx(&bars[s], kStageBytes + bo);
     tma_bulk_g2s(st + P::sQ, a.q + size_t(k0) * Nf * Np, kQBytes, &bars[s]);
@@ -225,7 +289,10 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   // neighbour traces of block b that live outside it: 4-byte async copies
   // (cp.async) into trace buffer s, layout [Nf][4 Nfp][EBP], face node fastest
   auto issue_gathers = [&](int b, int s) {
-    const int k0 = b * EB;
+    StepArgs a;
+    int lb;
+    prov.get(b, a, lb);
+    const int k0 = lb * EB;
     const int4* nb_s = reinterpret_cast<const int4*>(stage(s) + P::sNbr);
     float* T = smem + (s ? P::oT1 : P::oT0);
     for (int i = tid; i < EB * NFN; i += NT) {
@@ -254,10 +321,10 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   }
   __syncthreads();
   if (tid == 0 && (int)blockIdx.x < nblk) issue_stage(blockIdx.x, 0, true);
-  for (int i = tid; i < 10 * Nfp; i += NT) sFtab[i] = a.ftab[i];
+  for (int i = tid; i < 10 * Nfp; i += NT) sFtab[i] = prov.ftab()[i];
   __syncthreads();
   if ((int)blockIdx.x < nblk) {
-    if (!__syncthreads_and(mbar_wait_bounded(&bars[0], 0u, a.err))) {
+    if (!__syncthreads_and(mbar_wait_bounded(&bars[0], 0u, err))) {
       mbar_wait_bounded(&bars[0], 0u, nullptr);
       return;
     }
@@ -267,8 +334,11 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   int it = 0;
   for (int b = blockIdx.x; b < nblk; b += G, ++it) {
     const int s = it & 1;
-    const int k0 = b * EB;
-    bool ok = mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), a.err);
+    StepArgs a;
+    int lb;
+    prov.get(b, a, lb);
+    const int k0 = lb * EB;
+    bool ok = mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), err);
     cp_async_wait_all();  // this block's neighbour traces
     if (!__syncthreads_and(ok)) {
       mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), nullptr);
@@ -281,7 +351,7 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
     const float* sT = smem + (s ? P::oT1 : P::oT0);
     if (tid == 0) {
       if (b + G < nblk) issue_stage(b + G, s ^ 1, false);
-      if (R_SMEM && a.mode == 0) {
+      if (R_SMEM && mode == 0) {
         if (it > 0) bulk_wait_read();  // the previous block's outputs have left sR
         mbar_arrive_expect_tx(&bars[2], 2 * kQBytes);
         tma_bulk_g2s(sR, a.r1 + size_t(k0) * Nf * Np, kQBytes, &bars[2]);
@@ -454,7 +524,7 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
     // the next block's stage was issued at the top of this block: once it has
     // landed, start its neighbour gathers so that they overlap the products
     if (b + G < nblk) {
-      if (mbar_wait_bounded(&bars[s ^ 1], uint32_t(((it + 1) >> 1) & 1), a.err)) issue_gathers(b + G, s ^ 1);
+      if (mbar_wait_bounded(&bars[s ^ 1], uint32_t(((it + 1) >> 1) & 1), err)) issue_gathers(b + G, s ^ 1);
     }
 
     // -------- register-tiled operator products (one tile of 4 nodes x TN elements per thread)
@@ -604,7 +674,7 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
       }
     }
 
-    if (a.mode != 0) {  // RHS only: straight to the caller's buffer
+    if (mode != 0) {  // RHS only: straight to the caller's buffer
 #pragma unroll
       for (int t = 0; t < TN; ++t) {
         const int k = k0 + e0 + t;
@@ -633,7 +703,7 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
             for (int c = 0; c < Nf; ++c) sRhs[(e0 + t) * Nf * Np + c * Np + i0 + v] = r[t][c][v];
     }
     bool okr = true;
-    if constexpr (R_SMEM) okr = mbar_wait_bounded(&bars[2], uint32_t(it & 1), a.err);  // history landed
+    if constexpr (R_SMEM) okr = mbar_wait_bounded(&bars[2], uint32_t(it & 1), err);  // history landed
     if (!__syncthreads_and(okr)) {
       if (R_SMEM) mbar_wait_bounded(&bars[2], uint32_t(it & 1), nullptr);
       return;
@@ -678,6 +748,21 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
     }
   }
   if (R_SMEM && tid == 0) bulk_wait_all();
+}
+
+// One solve per launch (dg_rhs / dg_step).
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM>
+__global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
+  SingleSolve p{a, EB};
+  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>(p);
+}
+
+// Every solve of a batch (same model and N) in one persistent launch; the
+// per-solve step index, AB3 phase and buffer parity are read from device memory.
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM>
+__global__ void __launch_bounds__(NT) dg_step_batched_kernel(const BatchArgs b) {
+  SolveBatch p{b};
+  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>(p);
 }
 
 }  // namespace dgk

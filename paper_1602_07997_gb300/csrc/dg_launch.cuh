@@ -23,6 +23,7 @@ KernelCfg make_cfg() {
   c.r_smem = R_SMEM;
   c.smem = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM>::bytes;
   c.fn = dg_step_kernel<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>;
+  c.fn_batched = dg_step_batched_kernel<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>;
   return c;
 }
 

@@ -1,0 +1,532 @@
+// Served solves with continuous batching (dg_server_* / dg_submit / dg_poll).
+//
+// One host thread per server owns a CUDA stream and runs the request loop:
+//   1. admission: queued requests are set up (mesh, operators, state) while
+//      free device memory minus a reserve, and the optional byte budget, cover
+//      them and fewer than max_batch solves are active;
+//   2. batching: active solves are grouped by (model, N); one tick advances
+//      every active solve by one AB3 step with one persistent batched launch
+//      per group plus one tiny launch that advances the per-solve step state
+//      on the device; the tick is captured once in a CUDA graph and replayed
+//      until the set of active solves changes;
+//   3. ticks run in chunks that end when the first active solve finishes (at
+//      most kMaxChunk ticks), so that requests that arrived meanwhile join at
+//      the next chunk boundary (continuous batching);
+//   4. a finished solve's q is copied to host memory owned by the server and
+//      its device memory is released before new requests are admitted.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "dg_args.h"
+#include "dg_handle.h"
+
+namespace dg {
+
+namespace {
+
+constexpr int kMaxChunk = 32;                  // ticks between admission points
+constexpr size_t kReserve = size_t(1) << 30;   // device memory kept free
+
+double now_s() {
+  using clk = std::chrono::steady_clock;
+  return std::chrono::duration<double>(clk::now().time_since_epoch()).count();
+}
+
+enum Status { kQueued = 0, kRunning = 1, kDone = 2, kCancelled = 3, kFailed = 4 };
+
+struct Request {
+  uint64_t id = 0;
+  std::vector<double> verts, coeffs, amp;
+  std::vector<int64_t> tets;
+  std::vector<float> q0;
+  int N = 0, model = 0, nsteps = 0;
+  dg_opts opts{};
+  bool has_src = false;
+  double xs[3] = {0, 0, 0}, dir[3] = {0, 0, 1};
+  double t_submit = 0, t_done = 0;
+  int status = kQueued;
+  bool cancel = false;
+  int error = DG_OK;
+  std::string message;
+  std::vector<float> q_out;
+};
+
+struct Active {
+  std::shared_ptr<Request> req;
+  dg_handle* h = nullptr;
+  float* d_amp = nullptr;
+  int steps_left = 0;
+};
+
+struct Group {
+  int model = 0, N = 0;
+  const dgk::KernelCfg* cfg = nullptr;
+  std::vector<Active*> members;
+  dgk::SolveDev* d_solves = nullptr;
+  int* d_block_start = nullptr;
+  int capacity = 0;
+};
+
+}  // namespace
+
+struct Server {
+  size_t budget = 0;
+  int max_batch = 64;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::thread thr;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  uint64_t next_id = 1;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::map<uint64_t, std::shared_ptr<Request>> all;
+  std::vector<std::unique_ptr<Active>> active;
+  std::map<std::pair<int, int>, Group> groups;
+  size_t active_bytes = 0;
+  std::atomic<int64_t> launches{0};
+  cudaGraphExec_t graph = nullptr;
+  bool dirty = true;
+  int* d_err = nullptr;
+
+  ~Server();
+  void loop();
+  bool admit_one(std::shared_ptr<Request> r);
+  int rebuild();
+  void retire(Active* a, int status);
+  void fail_request(const std::shared_ptr<Request>& r, int code, const std::string& msg);
+};
+
+static size_t estimate_bytes(const Request& r) {
+  const int Np = num_nodes(r.N), Nf = num_fields(r.model), Nfp = num_face_nodes(r.N);
+  const size_t K = r.tets.size() / 4 + 132;
+  const size_t Mpad = size_t((Np + 3) & ~3), KD = size_t(3 * Np + 4 * Nfp);
+  return 4 * K * Nf * Np * 4 + K * (25 * 4 + 16) + KD * Mpad * 4 + r.amp.size() * 4 + (size_t(1) << 20);
+}
+
+void Server::fail_request(const std::shared_ptr<Request>& r, int code, const std::string& msg) {
+  std::lock_guard<std::mutex> lock(mu);
+  r->status = kFailed;
+  r->error = code;
+  r->message = msg;
+  r->t_done = now_s();
+}
+
+bool Server::admit_one(std::shared_ptr<Request> r) {
+  const size_t need = estimate_bytes(*r);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return false;
+  const bool fits_mem = free_b > kReserve && free_b - kReserve >= need;
+  const bool fits_budget = budget == 0 || active_bytes + need <= budget;
+  if (!fits_mem || !fits_budget) {
+    if (active.empty()) {  // can never fit: refuse instead of waiting forever
+      fail_request(r, DG_ENOMEM, "request does not fit in device memory or the server budget");
+      std::lock_guard<std::mutex> lock(mu);
+      queue.pop_front();
+      return true;
+    }
+    return false;
+  }
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    queue.pop_front();
+    if (r->cancel) {
+      r->status = kCancelled;
+      r->t_done = now_s();
+      return true;
+    }
+    r->status = kRunning;
+  }
+  dg_mesh m{int64_t(r->verts.size() / 3), int64_t(r->tets.size() / 4), r->verts.data(), r->tets.data()};
+  dg_opts o = r->opts;
+  o.stream = stream;
+  o.block_elems = 0;
+  dg_handle* h = nullptr;
+  int rc = dg_setup(&m, r->coeffs.data(), r->N, r->model, &o, &h);
+  if (rc == DG_OK && !r->q0.empty()) rc = dg_set_state(h, r->q0.data(), nullptr, nullptr, 0, 0);
+  if (rc == DG_OK && r->has_src) rc = dg_set_source(h, r->xs, r->dir, r->amp.data(), int64_t(r->amp.size()));
+  auto a = std::make_unique<Active>();
+  if (rc == DG_OK && h->src_elem >= 0) {
+    std::vector<float> af(r->amp.begin(), r->amp.end());
+    if (cudaMalloc(&a->d_amp, af.size() * 4) != cudaSuccess ||
+        cudaMemcpyAsync(a->d_amp, af.data(), af.size() * 4, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+      rc = fail(DG_ECUDA, "source amplitudes");
+  }
+  if (rc != DG_OK) {
+    fail_request(r, rc, dg_last_error());
+    if (h) dg_destroy(h);
+    if (a->d_amp) cudaFree(a->d_amp);
+    return true;
+  }
+  a->req = r;
+  a->h = h;
+  a->steps_left = r->nsteps;
+  active_bytes += h->device_bytes;
+  Group& g = groups[{r->model, r->N}];
+  g.model = r->model;
+  g.N = r->N;
+  if (!g.cfg) g.cfg = h->cfg;
+  g.members.push_back(a.get());
+  active.push_back(std::move(a));
+  dirty = true;
+  return true;
+}
+
+// Device-side solve tables and the tick graph for the current active set.
+int Server::rebuild() {
+  if (graph) {
+    cudaGraphExecDestroy(graph);
+    graph = nullptr;
+  }
+  for (auto& kv : groups) {
+    Group& g = kv.second;
+    const int n = int(g.members.size());
+    if (n == 0) continue;
+    if (n > g.capacity) {
+      if (g.d_solves) cudaFree(g.d_solves);
+      if (g.d_block_start) cudaFree(g.d_block_start);
+      g.capacity = std::max(n, 8);
+      if (cudaMalloc(&g.d_solves, sizeof(dgk::SolveDev) * g.capacity) != cudaSuccess ||
+          cudaMalloc(&g.d_block_start, sizeof(int) * (g.capacity + 1)) != cudaSuccess)
+        return fail(DG_ENOMEM, "server tables");
+    }
+    std::vector<dgk::SolveDev> sd(n);
+    std::vector<int> bs(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      const Active* a = g.members[i];
+      const dg_handle* h = a->h;
+      dgk::SolveDev& d = sd[i];
+      std::memset(&d, 0, sizeof(d));
+      d.q[0] = h->d_q[0];
+      d.q[1] = h->d_q[1];
+      d.r[0] = h->d_r[0];
+      d.r[1] = h->d_r[1];
+      d.rec = h->d_geo;
+      d.nbr = reinterpret_cast<const int4*>(h->d_nbr);
+      d.srcvec = h->src_elem >= 0 ? h->d_src : nullptr;
+      d.amp = a->d_amp;
+      d.step = h->step;
+      d.namp = int(a->req->amp.size());
+      d.src_elem = h->src_elem;
+      d.K = int(h->K);
+      d.flux = h->opts.flux;
+      d.bc = (h->model == DG_ELASTIC && h->opts.bc == DG_BC_RIGID) ? 1 : 0;
+      d.dt = float(h->opts.dt);
+      d.have = h->have;
+      d.qcur = h->qcur;
+      d.r1slot = h->r1slot;
+      d.steps_left = a->steps_left;
+      bs[i + 1] = bs[i] + int((h->K + g.cfg->EB - 1) / g.cfg->EB);
+    }
+    if (cudaMemcpyAsync(g.d_solves, sd.data(), sizeof(dgk::SolveDev) * n, cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(g.d_block_start, bs.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess)
+      return fail(DG_ECUDA, "server tables upload");
+  }
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return fail(DG_ECUDA, "server sync");
+  // warm the kernels outside the capture (shared-memory opt-in, occupancy)
+  for (auto& kv : groups) {
+    Group& g = kv.second;
+    if (g.members.empty()) continue;
+    dgk::BatchArgs b{};
+    b.solves = g.d_solves;
+    b.block_start = g.d_block_start;
+    b.nsolves = 0;
+    b.total_blocks = 0;
+    b.ops = g.members[0]->h->d_ops;
+    b.ftab = g.members[0]->h->d_ftab;
+    b.err = d_err;
+    if (dgk::launch_step_batched(g.cfg, b, stream) != cudaSuccess) return fail(DG_ECUDA, "batched warm-up");
+  }
+  cudaGraph_t gr = nullptr;
+  if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(DG_ECUDA, "graph capture");
+  cudaError_t e = cudaSuccess;
+  for (auto& kv : groups) {
+    Group& g = kv.second;
+    const int n = int(g.members.size());
+    if (n == 0) continue;
+    dgk::BatchArgs b{};
+    b.solves = g.d_solves;
+    b.block_start = g.d_block_start;
+    b.nsolves = n;
+    int total = 0;
+    for (const Active* a : g.members) total += int((a->h->K + g.cfg->EB - 1) / g.cfg->EB);
+    b.total_blocks = total;
+    b.ops = g.members[0]->h->d_ops;
+    b.ftab = g.members[0]->h->d_ftab;
+    b.err = d_err;
+    if (e == cudaSuccess) e = dgk::launch_step_batched(g.cfg, b, stream);
+  }
+  for (auto& kv : groups) {
+    Group& g = kv.second;
+    if (!g.members.empty() && e == cudaSuccess) e = dgk::launch_advance(g.d_solves, int(g.members.size()), stream);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(stream, &gr);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    return fail(DG_ECUDA, "tick capture failed");
+  }
+  e = cudaGraphInstantiate(&graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return fail(DG_ECUDA, "graph instantiate");
+  dirty = false;
+  return DG_OK;
+}
+
+void Server::retire(Active* a, int status) {
+  dg_handle* h = a->h;
+  auto r = a->req;
+  std::vector<float> out;
+  if (status == kDone) {
+    out.resize(size_t(h->K) * h->Nf * h->Np);
+    if (cudaMemcpyAsync(out.data(), h->d_q[h->qcur], out.size() * 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      status = kFailed;
+  }
+  active_bytes -= std::min(active_bytes, h->device_bytes);
+  dg_destroy(h);
+  if (a->d_amp) cudaFree(a->d_amp);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    r->status = status;
+    if (status == kFailed) {
+      r->error = DG_ECUDA;
+      r->message = "result copy failed";
+    }
+    r->q_out.swap(out);
+    r->t_done = now_s();
+  }
+  for (auto& kv : groups) {
+    auto& m = kv.second.members;
+    m.erase(std::remove(m.begin(), m.end(), a), m.end());
+  }
+  active.erase(std::remove_if(active.begin(), active.end(), [a](const std::unique_ptr<Active>& p) { return p.get() == a; }),
+               active.end());
+  dirty = true;
+}
+
+void Server::loop() {
+  cudaSetDevice(device);
+  while (true) {
+    {
+      std::unique_lock<std::mutex> lock(mu);
+      if (stop) break;
+      if (queue.empty() && active.empty()) {
+        cv.wait_for(lock, std::chrono::milliseconds(20));
+        continue;
+      }
+    }
+    // admission (continuous batching: between chunks)
+    while (int(active.size()) < max_batch) {
+      std::shared_ptr<Request> r;
+      {
+        std::lock_guard<std::mutex> lock(mu);
+        if (queue.empty()) break;
+        r = queue.front();
+      }
+      if (!admit_one(r)) break;
+    }
+    // cancellations of running solves
+    std::vector<Active*> cancelled;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      for (auto& a : active)
+        if (a->req->cancel) cancelled.push_back(a.get());
+    }
+    for (Active* a : cancelled) retire(a, kCancelled);
+    if (active.empty()) continue;
+    if (dirty && rebuild() != DG_OK) {
+      std::string msg = dg_last_error();
+      std::vector<Active*> all_a;
+      for (auto& a : active) all_a.push_back(a.get());
+      for (Active* a : all_a) {
+        fail_request(a->req, DG_ECUDA, msg);
+        dg_destroy(a->h);
+        if (a->d_amp) cudaFree(a->d_amp);
+      }
+      active.clear();
+      for (auto& kv : groups) kv.second.members.clear();
+      active_bytes = 0;
+      dirty = true;
+      continue;
+    }
+    int chunk = kMaxChunk;
+    for (auto& a : active) chunk = std::min(chunk, a->steps_left);
+    bool ok = true;
+    for (int t = 0; t < chunk && ok; ++t) ok = cudaGraphLaunch(graph, stream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(stream) == cudaSuccess;
+    int err = 0;
+    if (ok) ok = cudaMemcpy(&err, d_err, 4, cudaMemcpyDeviceToHost) == cudaSuccess && err == 0;
+    int64_t nlaunch = 0;
+    for (auto& kv : groups)
+      if (!kv.second.members.empty()) nlaunch += 2;
+    launches += nlaunch * chunk;
+    // mirror the device-side step state on the host handles
+    for (auto& a : active) {
+      dg_handle* h = a->h;
+      if (chunk & 1) {
+        h->qcur ^= 1;
+        h->r1slot ^= 1;
+      }
+      h->step += chunk;
+      h->have = std::min(h->have + chunk, 2);
+      a->steps_left -= chunk;
+    }
+    std::vector<Active*> finished;
+    for (auto& a : active)
+      if (!ok || a->steps_left <= 0) finished.push_back(a.get());
+    for (Active* a : finished) retire(a, ok ? kDone : kFailed);
+  }
+}
+
+Server::~Server() {
+  for (auto& a : active) {
+    dg_destroy(a->h);
+    if (a->d_amp) cudaFree(a->d_amp);
+  }
+  for (auto& kv : groups) {
+    if (kv.second.d_solves) cudaFree(kv.second.d_solves);
+    if (kv.second.d_block_start) cudaFree(kv.second.d_block_start);
+  }
+  if (graph) cudaGraphExecDestroy(graph);
+  if (d_err) cudaFree(d_err);
+  if (stream) cudaStreamDestroy(stream);
+}
+
+}  // namespace dg
+
+struct dg_server : dg::Server {};
+
+using dg::fail;
+
+extern "C" {
+
+int dg_server_create(size_t hbm_budget_bytes, int max_batch, dg_server** out) {
+  if (!out) return fail(DG_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto* s = new (std::nothrow) dg_server();
+  if (!s) return fail(DG_ENOMEM, "host allocation failed");
+  s->budget = hbm_budget_bytes;
+  s->max_batch = max_batch > 0 ? max_batch : 64;
+  if (cudaGetDevice(&s->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&s->d_err, 4) != cudaSuccess || cudaMemset(s->d_err, 0, 4) != cudaSuccess) {
+    delete s;
+    return fail(DG_ECUDA, "server stream / error word");
+  }
+  s->thr = std::thread([s] { s->loop(); });
+  *out = s;
+  return DG_OK;
+}
+
+int dg_submit(dg_server* s, const dg_request* req, uint64_t* ticket) {
+  if (!s || !req || !ticket || !req->mesh || !req->coeffs) return fail(DG_EINVAL, "NULL argument");
+  if (req->N < 1 || req->N > 8) return fail(DG_EINVAL, "polynomial degree N must be in 1..8");
+  if (req->model != DG_ACOUSTIC && req->model != DG_ELASTIC) return fail(DG_EINVAL, "unknown model");
+  if (req->nsteps < 0) return fail(DG_EINVAL, "negative step count");
+  if (!(req->opts.dt > 0)) return fail(DG_EINVAL, "dt must be positive");
+  const dg_mesh* m = req->mesh;
+  if (!m->verts || !m->tets || m->ntets <= 0 || m->nverts < 4) return fail(DG_EINVAL, "empty mesh");
+  auto r = std::make_shared<dg::Request>();
+  r->verts.assign(m->verts, m->verts + 3 * m->nverts);
+  r->tets.assign(m->tets, m->tets + 4 * m->ntets);
+  const int nc = req->model == DG_ACOUSTIC ? 2 : 3;
+  r->coeffs.assign(req->coeffs, req->coeffs + nc * m->ntets);
+  r->N = req->N;
+  r->model = req->model;
+  r->nsteps = req->nsteps;
+  r->opts = req->opts;
+  if (req->q0) r->q0.assign(req->q0, req->q0 + size_t(m->ntets) * dg::num_fields(req->model) * dg::num_nodes(req->N));
+  if (req->src_xyz && req->src_amp && req->src_namp > 0) {
+    r->has_src = true;
+    std::memcpy(r->xs, req->src_xyz, sizeof(r->xs));
+    if (req->src_dir) std::memcpy(r->dir, req->src_dir, sizeof(r->dir));
+    r->amp.assign(req->src_amp, req->src_amp + req->src_namp);
+  }
+  r->t_submit = dg::now_s();
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    r->id = s->next_id++;
+    s->all[r->id] = r;
+    s->queue.push_back(r);
+  }
+  s->cv.notify_one();
+  *ticket = r->id;
+  return DG_OK;
+}
+
+int dg_poll(dg_server* s, uint64_t ticket, float* q_out, double* latency_s) {
+  if (!s) return fail(DG_EINVAL, "NULL server");
+  std::shared_ptr<dg::Request> r;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return fail(DG_ENOENT, "unknown ticket");
+    r = it->second;
+    if (r->status == dg::kQueued || r->status == dg::kRunning) return DG_EAGAIN;
+    s->all.erase(it);
+  }
+  if (latency_s) *latency_s = r->t_done - r->t_submit;
+  if (r->status == dg::kCancelled) return fail(DG_ECANCELED, "request cancelled");
+  if (r->status == dg::kFailed) return fail(r->error, r->message);
+  if (q_out) std::memcpy(q_out, r->q_out.data(), r->q_out.size() * 4);
+  return DG_OK;
+}
+
+int dg_cancel(dg_server* s, uint64_t ticket) {
+  if (!s) return fail(DG_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return fail(DG_ENOENT, "unknown ticket");
+  it->second->cancel = true;
+  if (it->second->status == dg::kQueued) {
+    auto& q = s->queue;
+    q.erase(std::remove(q.begin(), q.end(), it->second), q.end());
+    it->second->status = dg::kCancelled;
+    it->second->t_done = dg::now_s();
+  }
+  return DG_OK;
+}
+
+int dg_server_stats(dg_server* s, int64_t* queued, int64_t* running, int64_t* done, int64_t* launches) {
+  if (!s) return fail(DG_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  int64_t q = 0, r = 0, d = 0;
+  for (auto& kv : s->all) {
+    const int st = kv.second->status;
+    if (st == dg::kQueued) ++q;
+    else if (st == dg::kRunning) ++r;
+    else ++d;
+  }
+  if (queued) *queued = q;
+  if (running) *running = r;
+  if (done) *done = d;
+  if (launches) *launches = s->launches.load();
+  return DG_OK;
+}
+
+void dg_server_destroy(dg_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->thr.joinable()) s->thr.join();
+  delete s;
+}
+
+}  // extern "C"

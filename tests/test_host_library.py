@@ -1,0 +1,83 @@
+"""Host-side tests of libdg (no GPU): exports, reference element, dt helper, validation.
+
+The library's reference element is built by a different route (orthonormal
+Dubiner basis, V-based mass/lift, integer-lattice face tables) than the
+oracle's (Bernstein basis, quadrature, coordinate matching); agreement to
+round-off pins both set-up codes against each other.
+"""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.refelem import RefElement
+from oracle.dg import Solver as OSolver
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1602_07997_gb300 as P
+    from paper_1602_07997_gb300 import build as B
+    if not os.path.exists(B.LIB):
+        B.build()
+    P.lib()
+    return P
+
+
+def test_library_exports_every_declared_symbol(P):
+    src = open(os.path.join(ROOT, "include", "dg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(dg_[a-z_0-9]+)\s*\(", src))
+    assert len(names) >= 20
+    L = P.lib()
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+    assert names == set(P.EXPORTS)
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+def test_reference_element_matches_oracle(P, N):
+    L = P.reference_element(N)
+    R = RefElement(N)
+    assert np.abs(L["nodes"] - R.nodes).max() < 1e-13
+    for a, b in ((L["Dr"], R.Dr), (L["Ds"], R.Ds), (L["Dt"], R.Dt)):
+        assert np.abs(a - b).max() < 1e-12 * max(1.0, np.abs(b).max())
+    for f in range(4):
+        fm = L["fmask"][f]
+        assert sorted(fm) == sorted(R.Fmask[f])
+        col = [list(R.Fmask[f]).index(n) for n in fm]
+        A = L["LIFT"][:, f * R.Nfp:(f + 1) * R.Nfp]
+        B = R.LIFT[:, f * R.Nfp:(f + 1) * R.Nfp][:, col]
+        assert np.abs(A - B).max() < 1e-12 * np.abs(B).max()
+
+
+@pytest.mark.parametrize("model", ["acoustic", "elastic"])
+def test_suggest_dt_matches_oracle(P, model):
+    verts, tets = W.kuhn_cube_mesh(3, 0.1, seed=4)
+    K = tets.shape[0]
+    coeffs = (W.acoustic_coefficients(K, 1, 3, seed=1) if model == "acoustic"
+              else W.elastic_two_layer(verts, tets, seed=1))
+    for N in (1, 4, 8):
+        o = OSolver(model, N, verts, tets, coeffs)
+        assert abs(P.suggest_dt(verts, tets, coeffs, N, model, 0.4) - o.suggest_dt(0.4)) <= 1e-14 * o.suggest_dt(0.4)
+
+
+def test_host_validation_rejects_bad_input(P):
+    verts, tets = W.kuhn_cube_mesh(2, 0.1, seed=1)
+    K = tets.shape[0]
+    c = np.ones((K, 2))
+    bad = tets.copy()
+    bad[3, [1, 2]] = bad[3, [2, 1]]
+    for args in ((verts, bad, c, 2, "acoustic"),                          # inverted tet
+                 (verts, np.concatenate([tets, tets[:1]]), np.ones((K + 1, 2)), 2, "acoustic"),  # 3 tets on a face
+                 (verts, tets, c, 0, "acoustic"),                          # N out of range
+                 (verts, tets, -c, 2, "acoustic"),                         # negative coefficient
+                 (verts, np.where(tets == 0, 10 ** 6, tets), c, 2, "acoustic")):  # index out of range
+        with pytest.raises(P.DGError) as e:
+            P.suggest_dt(*args)
+        assert e.value.code == -1
