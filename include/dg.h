@@ -144,6 +144,28 @@ int dg_autotune(dg_handle *h, int reps, int *block_elems, double *ms_per_step, d
 int dg_kernel_info(const dg_handle *h, int *block_elems, int *threads, int64_t *smem_bytes,
                    int *variants, int *tile_elems);
 
+/* The paper has no counterpart to this entry point.  Same result as
+ * dg_rhs(h, r_out, 0) -- the RHS at the current state into the caller's host
+ * buffer r_out [K][Nf][Np] -- but without allocating device memory: dg_rhs
+ * stages the RHS in a device buffer it allocates per call, this function
+ * stages it in a fixed 16 MiB array (4 Mi floats) that the library holds on
+ * every device that loads it until the process exits.  It is meant for
+ * callers that cannot allocate device memory when they need the RHS, e.g.
+ * an application whose device memory is already committed to another
+ * allocator (a framework's caching allocator or a fixed memory budget),
+ * where a fresh allocation could fail or force a device synchronisation.
+ * dg_setup still allocates the handle's state once, beforehand.
+ *  - K*Nf*Np must not exceed 4194304; larger meshes get DG_EINVAL (use
+ *    dg_rhs).  The handle's device must be the current device.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.  The call synchronises the handle's stream.
+ *  - Every call shares the one array and leaves its contents behind; calls
+ *    whose work overlaps on the GPU (other host threads, other handles on the
+ *    same device) race on it and must be serialised by the caller.  Nothing
+ *    in it needs clearing: the RHS kernel overwrites every value read back.  */
+int dg_rhs_host_noalloc(dg_handle *h, float *r_out);
+
 /* Wait for the handle's stream; DG_ETIMEOUT if a device wait expired.       */
 int dg_sync(dg_handle *h);
 

@@ -23,7 +23,7 @@ BC = {None: 0, "default": 0, "rigid": 1, "free": 2}
 EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", "dg_rhs", "dg_step",
            "dg_set_dt", "dg_sync", "dg_autotune", "dg_kernel_info", "dg_node_coords", "dg_set_source", "dg_suggest_dt",
            "dg_reference_element", "dg_last_error", "dg_server_create", "dg_submit", "dg_poll",
-           "dg_cancel", "dg_server_stats", "dg_server_destroy")
+           "dg_cancel", "dg_server_stats", "dg_server_destroy", "dg_rhs_host_noalloc")
 
 
 class DGError(RuntimeError):
@@ -86,6 +86,7 @@ def lib():
         "dg_cancel": (i32, [vp, C.c_uint64]),
         "dg_server_stats": (i32, [vp, P(i64), P(i64), P(i64), P(i64)]),
         "dg_server_destroy": (None, [vp]),
+        "dg_rhs_host_noalloc": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -220,6 +221,17 @@ class Solver:
             out = np.empty(self.shape, dtype=np.float32)
         p, d, _ = _buf(out, np.float32, self.size, write=True)
         check(lib().dg_rhs(self.h, p, d))
+        return out if ret else None
+
+    def rhs_host_noalloc(self, out=None):
+        """RHS into host memory through the library's fixed scratch (no device allocation)."""
+        ret = out is None
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float32)
+        p, d, _ = _buf(out, np.float32, self.size, write=True)
+        if d:
+            raise ValueError("rhs_host_noalloc writes host memory")
+        check(lib().dg_rhs_host_noalloc(self.h, p))
         return out if ret else None
 
     def set_dt(self, dt):
