@@ -7,10 +7,15 @@ eight meshes (eight launches of the fused kernel).  value = sum over meshes
 of K*Np*Nf field updates / device time of the step.  The eight meshes hold
 ~1.3 GB, so consecutive steps on one mesh never find its state in L2.
 
-Extra keys: per_N (time, updates/s, algorithmic GB/s and GFLOP/s per
-degree), roofline (dominant kernel), cpu_baseline (FP64 oracle on the host),
-e2e (same metric through the C ABI with pinned host buffers, copies inside
-the timed region), clocks (nvidia-smi samples during the timed region).
+Before the timed region every mesh's kernel variant is autotuned.
+
+Extra keys: per_N (time, updates/s, algorithmic GB/s and GFLOP/s, kernel
+variant per degree), roofline (dominant kernel), cpu_baseline (FP64 oracle on
+the host), e2e (same metric through the C ABI with pinned host buffers,
+copies inside the timed region), served (64 acoustic shots, N in {3,5,7},
+500 steps, Poisson arrivals at 0.7 x the batched capacity: p50/p99 latency,
+against the same requests solved one at a time), clocks (nvidia-smi samples
+during the timed region).
 
 Multi-GPU: replicas only (the single-GPU path does not shard); each rank runs
 the whole sweep and value = sum of the ranks' updates / max rank time.
@@ -127,6 +132,100 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(t_local, updates, world):
+    """Job time = max over ranks, job updates = sum over ranks (replicas)."""
+    if world <= 1:
+        return t_local, float(updates)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def served_benchmark(P, count=64, steps=500, seed=1004, max_n=32):
+    """Served stream: acoustic shots with Poisson arrivals at 0.7 x the batched
+    capacity (measured first with every request submitted at once), p50/p99 of
+    submit -> result latency, against the same requests run one at a time."""
+    import workloads as W
+    from workloads.configs import request_mesh
+    reqs = W.config4_requests(count, seed=seed)
+    prepared = []
+    for r in reqs:
+        r = dict(r, n=min(r["n"], max_n), steps=steps)
+        verts, tets, coeffs = request_mesh(r)
+        dt = P.suggest_dt(verts, tets, coeffs, r["N"], "acoustic", 0.4)
+        amp = W.ricker(np.arange(steps) * dt, f0=4.0)
+        prepared.append((r, verts, tets, coeffs, dt, amp))
+    work = sum(t.shape[0] * (r["N"] + 1) * (r["N"] + 2) * (r["N"] + 3) // 6 * 4 * steps
+               for r, v, t, c, d, a in prepared)
+
+    def run_server(arrivals):
+        srv = P.Server()
+        t0 = time.perf_counter()
+        pending = {}
+        lat = []
+        i = 0
+        while i < len(prepared) or pending:
+            now = time.perf_counter() - t0
+            while i < len(prepared) and arrivals[i] <= now:
+                r, v, t, c, d, a = prepared[i]
+                pending[srv.submit(v, t, c, r["N"], dt=d, nsteps=steps, source=r["source"], amp=a)] = i
+                i += 1
+            for tk in list(pending):
+                res = srv.poll(tk)
+                if res is not None:
+                    lat.append(res[1])
+                    del pending[tk]
+            time.sleep(0.0005)
+        makespan = time.perf_counter() - t0
+        launches = srv.stats()["launches"]
+        srv.close()
+        return makespan, lat, launches
+
+    # capacity: everything at t = 0
+    mk0, _, _ = run_server([0.0] * len(prepared))
+    capacity = len(prepared) / mk0
+    rate = 0.7 * capacity
+    rng = np.random.default_rng(seed)
+    arr = np.cumsum(rng.exponential(1.0 / rate, size=len(prepared)))
+    mk, lat, launches = run_server(list(arr))
+    # plain: the same requests one at a time through dg_step, in arrival order
+    t0 = time.perf_counter()
+    plain_lat = []
+    for (r, v, t, c, d, a), ta in zip(prepared, arr):
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.0005)
+        g = P.Solver(v, t, c, r["N"], "acoustic", dt=d)
+        g.set_source(r["source"], a)
+        g.step(steps)
+        g.get_state()
+        g.close()
+        plain_lat.append(time.perf_counter() - t0 - ta)
+    mk_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for (r, v, t, c, d, a) in prepared:
+        g = P.Solver(v, t, c, r["N"], "acoustic", dt=d)
+        g.set_source(r["source"], a)
+        g.step(steps)
+        g.get_state()
+        g.close()
+    mk_plain0 = time.perf_counter() - t0
+    q = lambda x, p: float(np.percentile(np.asarray(x), p))
+    return {"requests": len(prepared), "steps": steps, "degrees": [3, 5, 7],
+            "mesh_tets": [int(p[2].shape[0]) for p in prepared],
+            "capacity_req_per_s": capacity, "arrival_rate_req_per_s": rate,
+            "p50_s": q(lat, 50), "p99_s": q(lat, 99), "makespan_s": mk,
+            "batched_all_at_once_makespan_s": mk0,
+            "batched_updates_per_s": work / mk0, "launches": launches,
+            "plain_p50_s": q(plain_lat, 50), "plain_p99_s": q(plain_lat, 99), "plain_makespan_s": mk_plain,
+            "plain_all_at_once_makespan_s": mk_plain0, "plain_updates_per_s": work / mk_plain0,
+            "note": "latency = submit to result in host memory (includes host set-up of the request)"}
+
+
 def build_meshes(model, Ns):
     import workloads as W
     out = []
@@ -209,6 +308,8 @@ def run(args, rank, world, local_rank):
                      stream=stream.cuda_stream)
         q = np.random.default_rng(N).uniform(-1, 1, size=g.shape).astype(np.float32)
         g.set_state(q)
+        if not args.no_tune:
+            g.autotune(5)
         solvers.append(g)
     torch.cuda.synchronize()
 
@@ -243,14 +344,7 @@ def run(args, rank, world, local_rank):
         g.sync()
     updates = sum(g.K * g.Np * g.Nf for g in solvers) * args.steps
     t_local = total_ms / 1e3
-    if world > 1:
-        tt = torch.tensor([t_local, float(updates)], device=dev, dtype=torch.float64)
-        tmax = tt.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        t_job, upd_job = float(tmax[0]), float(tt[1])
-    else:
-        t_job, upd_job = t_local, float(updates)
+    t_job, upd_job = aggregate(t_local, updates, world)
     value = upd_job / t_job
 
     pk = peaks()
@@ -264,7 +358,7 @@ def run(args, rank, world, local_rank):
         ridge = pk["fp32_tflops"] * 1e3 / pk["hbm_gbs"]
         bound = "hbm" if intensity < ridge else "alu"
         frac = gbs / pk["hbm_gbs"] if bound == "hbm" else gfl / (pk["fp32_tflops"] * 1e3)
-        per_N[str(g.N)] = {"K": g.K, "nodes": g.K * g.Np, "ms": round(ms, 5),
+        per_N[str(g.N)] = {"K": g.K, "nodes": g.K * g.Np, "ms": round(ms, 5), "kernel": g.kernel_info(),
                            "updates_per_s": g.K * g.Np * g.Nf / (ms * 1e-3),
                            "alg_GBs": round(gbs, 1), "alg_GFLOPs": round(gfl, 1),
                            "bound": bound, "roofline_frac": round(frac, 4)}
@@ -318,6 +412,10 @@ def run(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu and world == 1:
         cpu = cpu_baseline(model, Ns=(2, 4), steps=1)
 
+    served = None
+    if rank == 0 and not args.no_serve:
+        served = served_benchmark(P, count=args.serve_requests, steps=args.serve_steps)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps, "higher_is_better": True,
@@ -327,7 +425,7 @@ def run(args, rank, world, local_rank):
                            "l2": "inputs larger than L2: the 8 meshes hold ~1.3 GB, each ~130 MB",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "gpu_launches": nN * args.steps, "roofline": roof, "per_N": per_N,
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary()}
+                "cpu_baseline": cpu, "e2e": e2e, "served": served, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     for g in solvers:
         g.close()
@@ -354,6 +452,10 @@ def main():
     ap.add_argument("--degrees", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-steps", type=int, default=500)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

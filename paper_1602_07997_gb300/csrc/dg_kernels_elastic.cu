@@ -9,13 +9,13 @@ namespace dgk {
 const KernelCfg* kernel_variants_elastic(int N, int* count) {
   static const KernelCfg v1[] = {make_cfg<1, 1, 16, true, true>(), make_cfg<1, 1, 8, true, true>(),
                                  make_cfg<1, 1, 32, true, true>()};
-  static const KernelCfg v2[] = {make_cfg<1, 2, 16, true, true>(), make_cfg<1, 2, 4, true, true>(),
-                                 make_cfg<1, 2, 8, true, true>()};
+  static const KernelCfg v2[] = {make_cfg<1, 2, 8, true, true>(), make_cfg<1, 2, 4, true, true>(),
+                                 make_cfg<1, 2, 16, true, true>()};
   static const KernelCfg v3[] = {make_cfg<1, 3, 8, true, true>(), make_cfg<1, 3, 4, true, true>(),
                                  make_cfg<1, 3, 16, true, true>()};
   static const KernelCfg v4[] = {make_cfg<1, 4, 4, true, true>(), make_cfg<1, 4, 8, false, true>(),
                                  make_cfg<1, 4, 4, false, true>()};
-  static const KernelCfg v5[] = {make_cfg<1, 5, 4, false, false>(), make_cfg<1, 5, 4, false, true>()};
+  static const KernelCfg v5[] = {make_cfg<1, 5, 4, false, true>(), make_cfg<1, 5, 4, false, false>()};
   static const KernelCfg v6[] = {make_cfg<1, 6, 4, false, false>(), make_cfg<1, 6, 4, false, false, 2>()};
   static const KernelCfg v7[] = {make_cfg<1, 7, 4, false, false>(), make_cfg<1, 7, 4, false, false, 2>()};
   static const KernelCfg v8[] = {make_cfg<1, 8, 4, false, false>(), make_cfg<1, 8, 4, false, false, 2>()};

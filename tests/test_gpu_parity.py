@@ -162,3 +162,31 @@ def test_setup_rejects_bad_meshes(dg):
         dg.Solver(verts, dup, np.ones((K + 1, 2)), 2)
     with pytest.raises(dg.DGError):
         dg.Solver(verts, tets, coeffs, 9)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("model,N", [("acoustic", 3), ("elastic", 2)])
+def test_checkpoint_resume_is_bitwise(dg, model, N):
+    """50 steps, checkpoint (q, r^{m-1}, r^{m-2}, step) to host, restore into a
+    fresh handle, 50 more steps == 100 uninterrupted steps, bit for bit."""
+    verts, tets, coeffs = _mesh(model, 3, 90 + N)
+    o = OSolver(model, N, verts, tets, coeffs)
+    dt = o.suggest_dt(0.4)
+    q0 = np.zeros((o.K, o.Nf, o.ref.Np), np.float32)
+    q0[:, 0] = W.gaussian_pulse(o.mesh.x, width=0.25)
+    a = dg.Solver(verts, tets, coeffs, N, model, dt=dt)
+    a.set_state(q0)
+    a.step(100)
+    ref = a.get_state()
+    b = dg.Solver(verts, tets, coeffs, N, model, dt=dt)
+    b.set_state(q0)
+    b.step(50)
+    q = np.empty(b.shape, np.float32)
+    r1 = np.empty(b.shape, np.float32)
+    r2 = np.empty(b.shape, np.float32)
+    b.get_state(q, r1, r2)
+    assert b.step_index == 50 and b.history == 2
+    c = dg.Solver(verts, tets, coeffs, N, model, dt=dt)
+    c.set_state(q, r1, r2, step=50)
+    c.step(50)
+    assert np.array_equal(c.get_state(), ref)
