@@ -67,6 +67,7 @@ struct SolveDev {
 struct BatchArgs {
   SolveDev* solves;      // [nsolves]
   const int* block_start;  // [nsolves + 1] first global block of each solve
+  const int* block_solve;  // [total_blocks] solve of each global block
   int nsolves;
   int total_blocks;
   const float* ops;      // operators of the batch's (model, N)

@@ -205,12 +205,7 @@ struct SolveBatch {
   const BatchArgs& B;
   __device__ int nblocks() const { return B.total_blocks; }
   __device__ void get(int b, StepArgs& A, int& lb) const {
-    int lo = 0, hi = B.nsolves - 1;  // last solve whose first block is <= b
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (__ldg(B.block_start + mid) <= b) lo = mid;
-      else hi = mid - 1;
-    }
+    const int lo = __ldg(B.block_solve + b);  // solve of global block b
     const SolveDev& d = B.solves[lo];
     lb = b - __ldg(B.block_start + lo);
     const int qc = d.qcur, r1s = d.r1slot;
@@ -273,11 +268,8 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
   constexpr uint32_t kStageBytes = kQBytes + kRecBytes + uint32_t(EB * 16);
 
   auto stage = [&](int s) { return smem + (s ? P::oStage1 : P::oStage0); };
-  auto issue_stage = [&](int b, int s, bool with_ops) {
+  auto issue_stage = [&](const StepArgs& a, int lb, int s, bool with_ops) {
     float* st = stage(s);
-    StepArgs a;
-    int lb;
-    prov.get(b, a, lb);
     const int k0 = lb * EB;
     const uint32_t bo = (OPS_SMEM && with_ops) ? uint32_t(S::KD * Mpad * 4) : 0u;
     mbar_arrive_expect_tx(&bars[s], kStageBytes + bo);
@@ -288,10 +280,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
   };
   // neighbour traces of block b that live outside it: 4-byte async copies
   // (cp.async) into trace buffer s, layout [Nf][4 Nfp][EBP], face node fastest
-  auto issue_gathers = [&](int b, int s) {
-    StepArgs a;
-    int lb;
-    prov.get(b, a, lb);
+  auto issue_gathers = [&](const StepArgs& a, int lb, int s) {
     const int k0 = lb * EB;
     const int4* nb_s = reinterpret_cast<const int4*>(stage(s) + P::sNbr);
     float* T = smem + (s ? P::oT1 : P::oT0);
@@ -320,7 +309,11 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     fence_barrier_init();
   }
   __syncthreads();
-  if (tid == 0 && (int)blockIdx.x < nblk) issue_stage(blockIdx.x, 0, true);
+  // arguments of the block being processed (cur) and of the next one (nxt)
+  StepArgs nxt_a;
+  int nxt_lb = 0;
+  if ((int)blockIdx.x < nblk) prov.get(blockIdx.x, nxt_a, nxt_lb);
+  if (tid == 0 && (int)blockIdx.x < nblk) issue_stage(nxt_a, nxt_lb, 0, true);
   for (int i = tid; i < 10 * Nfp; i += NT) sFtab[i] = prov.ftab()[i];
   __syncthreads();
   if ((int)blockIdx.x < nblk) {
@@ -328,16 +321,16 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       mbar_wait_bounded(&bars[0], 0u, nullptr);
       return;
     }
-    issue_gathers(blockIdx.x, 0);
+    issue_gathers(nxt_a, nxt_lb, 0);
   }
 
   int it = 0;
   for (int b = blockIdx.x; b < nblk; b += G, ++it) {
     const int s = it & 1;
-    StepArgs a;
-    int lb;
-    prov.get(b, a, lb);
+    const StepArgs a = nxt_a;
+    const int lb = nxt_lb;
     const int k0 = lb * EB;
+    if (b + G < nblk) prov.get(b + G, nxt_a, nxt_lb);
     bool ok = mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), err);
     cp_async_wait_all();  // this block's neighbour traces
     if (!__syncthreads_and(ok)) {
@@ -350,7 +343,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     const int4* sNbr = reinterpret_cast<const int4*>(stage(s) + P::sNbr);
     const float* sT = smem + (s ? P::oT1 : P::oT0);
     if (tid == 0) {
-      if (b + G < nblk) issue_stage(b + G, s ^ 1, false);
+      if (b + G < nblk) issue_stage(nxt_a, nxt_lb, s ^ 1, false);
       if (R_SMEM && mode == 0) {
         if (it > 0) bulk_wait_read();  // the previous block's outputs have left sR
         mbar_arrive_expect_tx(&bars[2], 2 * kQBytes);
@@ -524,7 +517,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     // the next block's stage was issued at the top of this block: once it has
     // landed, start its neighbour gathers so that they overlap the products
     if (b + G < nblk) {
-      if (mbar_wait_bounded(&bars[s ^ 1], uint32_t(((it + 1) >> 1) & 1), err)) issue_gathers(b + G, s ^ 1);
+      if (mbar_wait_bounded(&bars[s ^ 1], uint32_t(((it + 1) >> 1) & 1), err)) issue_gathers(nxt_a, nxt_lb, s ^ 1);
     }
 
     // -------- register-tiled operator products (one tile of 4 nodes x TN elements per thread)

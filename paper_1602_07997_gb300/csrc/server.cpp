@@ -1,9 +1,10 @@
 // Served solves with continuous batching (dg_server_* / dg_submit / dg_poll).
 //
-// One host thread per server owns a CUDA stream and runs the request loop:
-//   1. admission: queued requests are set up (mesh, operators, state) while
-//      free device memory minus a reserve, and the optional byte budget, cover
-//      them and fewer than max_batch solves are active;
+// Two host threads per server, each with its own CUDA stream:
+//   1. admission (set-up thread): queued requests are set up (mesh, operators,
+//      state) while free device memory minus a reserve, and the optional byte
+//      budget, cover them and fewer than max_batch solves are admitted; the
+//      GPU keeps stepping the active solves meanwhile;
 //   2. batching: active solves are grouped by (model, N); one tick advances
 //      every active solve by one AB3 step with one persistent batched launch
 //      per group plus one tiny launch that advances the per-solve step state
@@ -75,7 +76,8 @@ struct Group {
   std::vector<Active*> members;
   dgk::SolveDev* d_solves = nullptr;
   int* d_block_start = nullptr;
-  int capacity = 0;
+  int* d_block_solve = nullptr;
+  int capacity = 0, block_capacity = 0;
 };
 
 }  // namespace
@@ -84,8 +86,9 @@ struct Server {
   size_t budget = 0;
   int max_batch = 64;
   int device = 0;
-  cudaStream_t stream = nullptr;
-  std::thread thr;
+  cudaStream_t stream = nullptr;       // steps
+  cudaStream_t prep_stream = nullptr;  // set-up of admitted requests
+  std::thread thr, prep_thr;
   std::mutex mu;
   std::condition_variable cv;
   bool stop = false;
@@ -93,8 +96,10 @@ struct Server {
   std::deque<std::shared_ptr<Request>> queue;
   std::map<uint64_t, std::shared_ptr<Request>> all;
   std::vector<std::unique_ptr<Active>> active;
+  std::vector<std::unique_ptr<Active>> ready;  // set up, waiting for the next chunk boundary
   std::map<std::pair<int, int>, Group> groups;
-  size_t active_bytes = 0;
+  size_t active_bytes = 0;  // admitted (ready + active)
+  int admitted = 0;
   std::atomic<int64_t> launches{0};
   cudaGraphExec_t graph = nullptr;
   bool dirty = true;
@@ -102,7 +107,9 @@ struct Server {
 
   ~Server();
   void loop();
+  void prep_loop();
   bool admit_one(std::shared_ptr<Request> r);
+  void activate_ready();
   int rebuild();
   void retire(Active* a, int status);
   void fail_request(const std::shared_ptr<Request>& r, int code, const std::string& msg);
@@ -127,19 +134,31 @@ bool Server::admit_one(std::shared_ptr<Request> r) {
   const size_t need = estimate_bytes(*r);
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return false;
+  bool nothing_admitted;
+  size_t admitted_bytes;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    nothing_admitted = admitted == 0;
+    admitted_bytes = active_bytes;
+  }
   const bool fits_mem = free_b > kReserve && free_b - kReserve >= need;
-  const bool fits_budget = budget == 0 || active_bytes + need <= budget;
+  const bool fits_budget = budget == 0 || admitted_bytes + need <= budget;
   if (!fits_mem || !fits_budget) {
-    if (active.empty()) {  // can never fit: refuse instead of waiting forever
-      fail_request(r, DG_ENOMEM, "request does not fit in device memory or the server budget");
+    if (nothing_admitted) {  // can never fit: refuse instead of waiting forever
       std::lock_guard<std::mutex> lock(mu);
+      if (queue.empty() || queue.front() != r) return true;  // cancelled meanwhile
       queue.pop_front();
+      r->status = kFailed;
+      r->error = DG_ENOMEM;
+      r->message = "request does not fit in device memory or the server budget";
+      r->t_done = now_s();
       return true;
     }
     return false;
   }
   {
     std::lock_guard<std::mutex> lock(mu);
+    if (queue.empty() || queue.front() != r) return true;  // cancelled meanwhile
     queue.pop_front();
     if (r->cancel) {
       r->status = kCancelled;
@@ -150,7 +169,7 @@ bool Server::admit_one(std::shared_ptr<Request> r) {
   }
   dg_mesh m{int64_t(r->verts.size() / 3), int64_t(r->tets.size() / 4), r->verts.data(), r->tets.data()};
   dg_opts o = r->opts;
-  o.stream = stream;
+  o.stream = prep_stream;
   o.block_elems = 0;
   dg_handle* h = nullptr;
   int rc = dg_setup(&m, r->coeffs.data(), r->N, r->model, &o, &h);
@@ -160,7 +179,8 @@ bool Server::admit_one(std::shared_ptr<Request> r) {
   if (rc == DG_OK && h->src_elem >= 0) {
     std::vector<float> af(r->amp.begin(), r->amp.end());
     if (cudaMalloc(&a->d_amp, af.size() * 4) != cudaSuccess ||
-        cudaMemcpyAsync(a->d_amp, af.data(), af.size() * 4, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        cudaMemcpyAsync(a->d_amp, af.data(), af.size() * 4, cudaMemcpyHostToDevice, prep_stream) != cudaSuccess ||
+        cudaStreamSynchronize(prep_stream) != cudaSuccess)
       rc = fail(DG_ECUDA, "source amplitudes");
   }
   if (rc != DG_OK) {
@@ -172,15 +192,54 @@ bool Server::admit_one(std::shared_ptr<Request> r) {
   a->req = r;
   a->h = h;
   a->steps_left = r->nsteps;
-  active_bytes += h->device_bytes;
-  Group& g = groups[{r->model, r->N}];
-  g.model = r->model;
-  g.N = r->N;
-  if (!g.cfg) g.cfg = h->cfg;
-  g.members.push_back(a.get());
-  active.push_back(std::move(a));
-  dirty = true;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    active_bytes += h->device_bytes;
+    ++admitted;
+    ready.push_back(std::move(a));
+  }
   return true;
+}
+
+// Tick thread, at a chunk boundary: ready solves join their (model, N) group.
+void Server::activate_ready() {
+  std::vector<std::unique_ptr<Active>> got;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    got.swap(ready);
+  }
+  for (auto& a : got) {
+    a->h->stream = stream;
+    Group& g = groups[{a->req->model, a->req->N}];
+    g.model = a->req->model;
+    g.N = a->req->N;
+    if (!g.cfg) g.cfg = a->h->cfg;
+    g.members.push_back(a.get());
+    active.push_back(std::move(a));
+    dirty = true;
+  }
+}
+
+// Set-up thread: admission and host/device set-up of queued requests.
+void Server::prep_loop() {
+  cudaSetDevice(device);
+  while (true) {
+    std::shared_ptr<Request> r;
+    {
+      std::unique_lock<std::mutex> lock(mu);
+      if (stop) break;
+      if (queue.empty() || admitted >= max_batch) {
+        cv.wait_for(lock, std::chrono::milliseconds(5));
+        continue;
+      }
+      r = queue.front();
+    }
+    if (!admit_one(r)) {  // does not fit yet: wait for a solve to finish
+      std::unique_lock<std::mutex> lock(mu);
+      cv.wait_for(lock, std::chrono::milliseconds(5));
+    }
+    cv.notify_all();
+  }
 }
 
 // Device-side solve tables and the tick graph for the current active set.
@@ -203,6 +262,7 @@ int Server::rebuild() {
     }
     std::vector<dgk::SolveDev> sd(n);
     std::vector<int> bs(n + 1, 0);
+    std::vector<int> bsolve;
     for (int i = 0; i < n; ++i) {
       const Active* a = g.members[i];
       const dg_handle* h = a->h;
@@ -228,7 +288,17 @@ int Server::rebuild() {
       d.r1slot = h->r1slot;
       d.steps_left = a->steps_left;
       bs[i + 1] = bs[i] + int((h->K + g.cfg->EB - 1) / g.cfg->EB);
+      bsolve.insert(bsolve.end(), size_t(bs[i + 1] - bs[i]), i);
     }
+    if (int(bsolve.size()) > g.block_capacity) {
+      if (g.d_block_solve) cudaFree(g.d_block_solve);
+      g.block_capacity = int(bsolve.size()) * 2;
+      if (cudaMalloc(&g.d_block_solve, sizeof(int) * g.block_capacity) != cudaSuccess)
+        return fail(DG_ENOMEM, "server block table");
+    }
+    if (cudaMemcpyAsync(g.d_block_solve, bsolve.data(), sizeof(int) * bsolve.size(), cudaMemcpyHostToDevice,
+                        stream) != cudaSuccess)
+      return fail(DG_ECUDA, "server block table upload");
     if (cudaMemcpyAsync(g.d_solves, sd.data(), sizeof(dgk::SolveDev) * n, cudaMemcpyHostToDevice, stream) !=
             cudaSuccess ||
         cudaMemcpyAsync(g.d_block_start, bs.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, stream) !=
@@ -243,6 +313,7 @@ int Server::rebuild() {
     dgk::BatchArgs b{};
     b.solves = g.d_solves;
     b.block_start = g.d_block_start;
+    b.block_solve = g.d_block_solve;
     b.nsolves = 0;
     b.total_blocks = 0;
     b.ops = g.members[0]->h->d_ops;
@@ -261,6 +332,7 @@ int Server::rebuild() {
     dgk::BatchArgs b{};
     b.solves = g.d_solves;
     b.block_start = g.d_block_start;
+    b.block_solve = g.d_block_solve;
     b.nsolves = n;
     int total = 0;
     for (const Active* a : g.members) total += int((a->h->K + g.cfg->EB - 1) / g.cfg->EB);
@@ -296,7 +368,12 @@ void Server::retire(Active* a, int status) {
         cudaStreamSynchronize(stream) != cudaSuccess)
       status = kFailed;
   }
-  active_bytes -= std::min(active_bytes, h->device_bytes);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    active_bytes -= std::min(active_bytes, h->device_bytes);
+    --admitted;
+  }
+  cv.notify_all();
   dg_destroy(h);
   if (a->d_amp) cudaFree(a->d_amp);
   {
@@ -324,21 +401,13 @@ void Server::loop() {
     {
       std::unique_lock<std::mutex> lock(mu);
       if (stop) break;
-      if (queue.empty() && active.empty()) {
-        cv.wait_for(lock, std::chrono::milliseconds(20));
+      if (ready.empty() && active.empty()) {
+        cv.wait_for(lock, std::chrono::milliseconds(2));
         continue;
       }
     }
-    // admission (continuous batching: between chunks)
-    while (int(active.size()) < max_batch) {
-      std::shared_ptr<Request> r;
-      {
-        std::lock_guard<std::mutex> lock(mu);
-        if (queue.empty()) break;
-        r = queue.front();
-      }
-      if (!admit_one(r)) break;
-    }
+    // continuous batching: solves set up meanwhile join at this chunk boundary
+    activate_ready();
     // cancellations of running solves
     std::vector<Active*> cancelled;
     {
@@ -357,9 +426,13 @@ void Server::loop() {
         dg_destroy(a->h);
         if (a->d_amp) cudaFree(a->d_amp);
       }
+      {
+        std::lock_guard<std::mutex> lock(mu);
+        admitted -= int(all_a.size());
+        active_bytes = 0;
+      }
       active.clear();
       for (auto& kv : groups) kv.second.members.clear();
-      active_bytes = 0;
       dirty = true;
       continue;
     }
@@ -393,17 +466,20 @@ void Server::loop() {
 }
 
 Server::~Server() {
-  for (auto& a : active) {
-    dg_destroy(a->h);
-    if (a->d_amp) cudaFree(a->d_amp);
-  }
+  for (auto* lst : {&active, &ready})
+    for (auto& a : *lst) {
+      dg_destroy(a->h);
+      if (a->d_amp) cudaFree(a->d_amp);
+    }
   for (auto& kv : groups) {
     if (kv.second.d_solves) cudaFree(kv.second.d_solves);
     if (kv.second.d_block_start) cudaFree(kv.second.d_block_start);
+    if (kv.second.d_block_solve) cudaFree(kv.second.d_block_solve);
   }
   if (graph) cudaGraphExecDestroy(graph);
   if (d_err) cudaFree(d_err);
   if (stream) cudaStreamDestroy(stream);
+  if (prep_stream) cudaStreamDestroy(prep_stream);
 }
 
 }  // namespace dg
@@ -423,11 +499,13 @@ int dg_server_create(size_t hbm_budget_bytes, int max_batch, dg_server** out) {
   s->max_batch = max_batch > 0 ? max_batch : 64;
   if (cudaGetDevice(&s->device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->prep_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&s->d_err, 4) != cudaSuccess || cudaMemset(s->d_err, 0, 4) != cudaSuccess) {
     delete s;
     return fail(DG_ECUDA, "server stream / error word");
   }
   s->thr = std::thread([s] { s->loop(); });
+  s->prep_thr = std::thread([s] { s->prep_loop(); });
   *out = s;
   return DG_OK;
 }
@@ -526,6 +604,7 @@ void dg_server_destroy(dg_server* s) {
   }
   s->cv.notify_all();
   if (s->thr.joinable()) s->thr.join();
+  if (s->prep_thr.joinable()) s->prep_thr.join();
   delete s;
 }
 
