@@ -140,9 +140,15 @@ int dg_set_dt(dg_handle *h, double dt);
 int dg_autotune(dg_handle *h, int reps, int *block_elems, double *ms_per_step, double *variant_ms);
 /* Launch configuration in use: elements per CTA, threads per CTA, dynamic
  * shared memory per CTA, number of compiled variants, elements per thread
- * tile.  Pointers may be NULL.                                              */
+ * tile, and whether it is a split variant (the operator products run as a
+ * separate GEMM over 32-64-element column tiles; used at high N, needs an
+ * extra device buffer of (4 Np + 4 (4 Nfp)) floats per element for the
+ * acoustic model, (12 Np + 9 (4 Nfp)) for the elastic one, allocated on
+ * first use).  Pointers may be NULL.                           */
 int dg_kernel_info(const dg_handle *h, int *block_elems, int *threads, int64_t *smem_bytes,
-                   int *variants, int *tile_elems);
+                   int *variants, int *tile_elems, int *split);
+/* Select compiled variant `index` (0 <= index < variants) for this handle.  */
+int dg_set_variant(dg_handle *h, int index);
 
 /* The paper has no counterpart to this entry point.  Same result as
  * dg_rhs(h, r_out, 0) -- the RHS at the current state into the caller's host

@@ -21,7 +21,7 @@ BC = {None: 0, "default": 0, "rigid": 1, "free": 2}
 
 # every symbol that include/dg.h declares
 EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", "dg_rhs", "dg_step",
-           "dg_set_dt", "dg_sync", "dg_autotune", "dg_kernel_info", "dg_node_coords", "dg_set_source", "dg_suggest_dt",
+           "dg_set_dt", "dg_sync", "dg_autotune", "dg_kernel_info", "dg_set_variant", "dg_node_coords", "dg_set_source", "dg_suggest_dt",
            "dg_reference_element", "dg_last_error", "dg_server_create", "dg_submit", "dg_poll",
            "dg_cancel", "dg_server_stats", "dg_server_destroy", "dg_rhs_host_noalloc")
 
@@ -74,7 +74,8 @@ def lib():
         "dg_set_dt": (i32, [vp, dbl]),
         "dg_sync": (i32, [vp]),
         "dg_autotune": (i32, [vp, i32, P(i32), P(dbl), P(dbl)]),
-        "dg_kernel_info": (i32, [vp, P(i32), P(i32), P(i64), P(i32), P(i32)]),
+        "dg_kernel_info": (i32, [vp, P(i32), P(i32), P(i64), P(i32), P(i32), P(i32)]),
+        "dg_set_variant": (i32, [vp, i32]),
         "dg_node_coords": (i32, [vp, P(dbl)]),
         "dg_set_source": (i32, [vp, P(dbl), P(dbl), P(dbl), i64]),
         "dg_suggest_dt": (i32, [P(Mesh), P(dbl), i32, i32, dbl, P(dbl)]),
@@ -254,10 +255,14 @@ class Solver:
         return eb.value, ms.value, list(vms)[:nv]
 
     def kernel_info(self):
-        eb, nt, sm, nv, tn = C.c_int(), C.c_int(), C.c_int64(), C.c_int(), C.c_int()
-        check(lib().dg_kernel_info(self.h, C.byref(eb), C.byref(nt), C.byref(sm), C.byref(nv), C.byref(tn)))
+        eb, nt, sm, nv, tn, sp = C.c_int(), C.c_int(), C.c_int64(), C.c_int(), C.c_int(), C.c_int()
+        check(lib().dg_kernel_info(self.h, C.byref(eb), C.byref(nt), C.byref(sm), C.byref(nv), C.byref(tn),
+                                   C.byref(sp)))
         return dict(block_elems=eb.value, threads=nt.value, smem_bytes=sm.value, variants=nv.value,
-                    tile_elems=tn.value)
+                    tile_elems=tn.value, split=bool(sp.value))
+
+    def set_variant(self, index):
+        check(lib().dg_set_variant(self.h, int(index)))
 
     def node_coords(self):
         x = np.empty((self.K, self.Np, 3))

@@ -234,6 +234,30 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
 
 Handle::~Handle() {
   if (d_base) cudaFree(d_base);
+  if (d_split) cudaFree(d_split);
+}
+
+// Buffers of the split step: X[tiles][KX][NE] and the operator blob with rows padded.
+int Handle::ensure_split(const dgk::KernelCfg* c) {
+  if (!c || !c->split || d_split) return DG_OK;
+  const size_t ntiles = size_t((Kpad + c->gemm_ne - 1) / c->gemm_ne);
+  const size_t xbytes = ntiles * c->gemm_kx * c->gemm_ne * 4;
+  const int KD = 3 * Np + 4 * Nfp, MP2 = c->gemm_mp2;
+  std::vector<float> ops2(size_t(KD) * MP2, 0.0f);
+  const std::vector<double>* D[3] = {&ref.Dr, &ref.Ds, &ref.Dt};
+  for (int d = 0; d < 3; ++d)
+    for (int j = 0; j < Np; ++j)
+      for (int i = 0; i < Np; ++i) ops2[size_t(d * Np + j) * MP2 + i] = float((*D[d])[size_t(i) * Np + j]);
+  for (int cc = 0; cc < 4 * Nfp; ++cc)
+    for (int i = 0; i < Np; ++i) ops2[size_t(3 * Np + cc) * MP2 + i] = float(ref.LIFT[size_t(i) * 4 * Nfp + cc]);
+  const size_t obytes = (ops2.size() * 4 + 255) & ~size_t(255);
+  DG_CUDA(cudaMalloc(&d_split, xbytes + obytes));
+  d_ops2 = static_cast<float*>(d_split);
+  d_x = reinterpret_cast<float*>(static_cast<char*>(d_split) + obytes);
+  DG_CUDA(cudaMemsetAsync(d_x, 0, xbytes, stream));
+  DG_CUDA(cudaMemcpyAsync(d_ops2, ops2.data(), ops2.size() * 4, cudaMemcpyHostToDevice, stream));
+  DG_CUDA(cudaStreamSynchronize(stream));
+  return DG_OK;
 }
 
 dgk::StepArgs Handle::args(int mode) const {
@@ -258,10 +282,14 @@ dgk::StepArgs Handle::args(int mode) const {
   else if (have == 1) { a.a1 = 1.5f; a.a2 = -0.5f; a.a3 = 0.0f; }
   else { a.a1 = float(23.0 / 12.0); a.a2 = float(-16.0 / 12.0); a.a3 = float(5.0 / 12.0); }
   a.err = d_err;
+  a.xg = d_x;
+  a.ops2 = d_ops2;
   return a;
 }
 
 int Handle::advance(int nsteps) {
+  int rc = ensure_split(cfg);
+  if (rc) return rc;
   for (int s = 0; s < nsteps; ++s) {
     dgk::StepArgs a = args(0);
     DG_CUDA(dgk::launch_step(cfg, a, stream));
@@ -344,6 +372,8 @@ int dg_get_state(dg_handle* h, float* q, float* r1, float* r2, int64_t* step, in
 
 int dg_rhs(dg_handle* h, float* r_out, int on_device) {
   if (!h || !r_out) return fail(DG_EINVAL, "NULL handle or output");
+  int rc0 = h->ensure_split(h->cfg);
+  if (rc0) return rc0;
   dgk::StepArgs a = h->args(1);
   float* tmp = nullptr;
   const size_t bytes = size_t(h->K) * h->Nf * h->Np * 4;
@@ -458,6 +488,10 @@ int dg_autotune(dg_handle* h, int reps, int* block_elems, double* ms_per_step, d
   if (!h || reps < 1) return fail(DG_EINVAL, "NULL handle or reps < 1");
   int n = 0;
   const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n);
+  for (int i = 0; i < n; ++i) {
+    int rs = h->ensure_split(&v[i]);
+    if (rs) return rs;
+  }
   // scratch copies of the state so that the handle's state and history stay untouched
   void* scratch = nullptr;
   DG_CUDA(cudaMallocAsync(&scratch, 4 * h->state_bytes, h->stream));
@@ -476,6 +510,8 @@ int dg_autotune(dg_handle* h, int reps, int* block_elems, double* ms_per_step, d
     DG_CUDA(cudaEventCreate(&e1));
     for (int i = 0; i < n; ++i) {
       dgk::StepArgs a = h->args(0);
+      a.xg = h->d_x;
+      a.ops2 = h->d_ops2;
       a.a1 = 1.0f;
       a.a2 = a.a3 = 0.0f;
       a.src_elem = -1;
@@ -529,9 +565,19 @@ int dg_autotune(dg_handle* h, int reps, int* block_elems, double* ms_per_step, d
   return DG_OK;
 }
 
+int dg_set_variant(dg_handle* h, int index) {
+  if (!h) return fail(DG_EINVAL, "NULL handle");
+  int n = 0;
+  const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n);
+  if (index < 0 || index >= n) return fail(DG_EINVAL, "variant index out of range");
+  h->cfg = &v[index];
+  return DG_OK;
+}
+
 int dg_kernel_info(const dg_handle* h, int* block_elems, int* threads, int64_t* smem_bytes, int* variants,
-                   int* tile_elems) {
+                   int* tile_elems, int* split) {
   if (!h || !h->cfg) return fail(DG_EINVAL, "NULL handle");
+  if (split) *split = h->cfg->split ? 1 : 0;
   if (tile_elems) *tile_elems = h->cfg->TN;
   if (block_elems) *block_elems = h->cfg->EB;
   if (threads) *threads = h->cfg->NT;

@@ -41,6 +41,8 @@ struct StepArgs {
   int bc;                // acoustic: rigid; elastic: 0 free, 1 rigid
   float dt, a1, a2, a3;
   int* err;              // device error word (bounded-wait expiry)
+  float* xg;             // split step: GEMM inputs X[tile][row][NE]
+  const float* ops2;     // split step: operator blob [3Np + 4Nfp][rows padded to 32]
 };
 
 // Per-solve device state of a batched launch (served mode).  The step index,
@@ -75,13 +77,18 @@ struct BatchArgs {
   int* err;
 };
 
-// Host-visible launch configuration of one (model, N) instantiation.
+// Host-visible launch configuration of one (model, N) instantiation.  A
+// split variant launches fn (front half, writes X) and then fn_gemm.
 struct KernelCfg {
   int EB, TN, NT;
   bool ops_smem, r_smem;
   size_t smem;
   void (*fn)(StepArgs);
   void (*fn_batched)(BatchArgs);
+  bool split;
+  void (*fn_gemm)(StepArgs);
+  size_t smem_gemm;
+  int gemm_threads, gemm_ne, gemm_mt, gemm_mtiles, gemm_kx, gemm_mp2;
 };
 
 // Compiled variants of one (model, N): different elements per block (EB) and

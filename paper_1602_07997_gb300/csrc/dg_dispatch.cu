@@ -51,6 +51,7 @@ cudaError_t prepare_fn(const KernelCfg* c, const void* fn, int* grid_cap) {
 
 cudaError_t launch_step(const KernelCfg* c, const StepArgs& args, cudaStream_t stream) {
   if (!c) return cudaErrorInvalidValue;
+  if (c->split && (!args.xg || !args.ops2)) return cudaErrorInvalidValue;
   int cap = 0;
   cudaError_t e = prepare_fn(c, reinterpret_cast<const void*>(c->fn), &cap);
   if (e != cudaSuccess) return e;
@@ -59,8 +60,25 @@ cudaError_t launch_step(const KernelCfg* c, const StepArgs& args, cudaStream_t s
   const int grid = nblk < cap ? nblk : cap;
   StepArgs a = args;
   void* params[] = {&a};
-  return cudaLaunchKernel(reinterpret_cast<const void*>(c->fn), dim3(grid), dim3(c->NT), params, c->smem,
-                          stream);
+  e = cudaLaunchKernel(reinterpret_cast<const void*>(c->fn), dim3(grid), dim3(c->NT), params, c->smem, stream);
+  if (e != cudaSuccess || !c->split) return e;
+  {
+    // the GEMM kernel: column tiles of gemm_ne elements x row tiles of gemm_mt
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto key = std::make_pair(dev, reinterpret_cast<const void*>(c->fn_gemm));
+    if (g_cap.find(key) == g_cap.end()) {
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(c->fn_gemm),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(c->smem_gemm));
+      if (e != cudaSuccess) return e;
+      g_cap[key] = 1;
+    }
+  }
+  const int ntiles = (args.K + c->gemm_ne - 1) / c->gemm_ne;
+  return cudaLaunchKernel(reinterpret_cast<const void*>(c->fn_gemm), dim3(unsigned(c->gemm_mtiles) * unsigned(ntiles)),
+                          dim3(c->gemm_threads), params, c->smem_gemm, stream);
 }
 
 __global__ void advance_kernel(SolveDev* s, int n) {
@@ -74,7 +92,7 @@ __global__ void advance_kernel(SolveDev* s, int n) {
 }
 
 cudaError_t launch_step_batched(const KernelCfg* c, const BatchArgs& args, cudaStream_t stream) {
-  if (!c || !c->fn_batched) return cudaErrorInvalidValue;
+  if (!c || !c->fn_batched || c->split) return cudaErrorInvalidValue;
   int cap = 0;
   cudaError_t e = prepare_fn(c, reinterpret_cast<const void*>(c->fn_batched), &cap);
   if (e != cudaSuccess) return e;

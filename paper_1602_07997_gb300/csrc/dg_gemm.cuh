@@ -1,0 +1,291 @@
+// Split step for high degree: operator products as a GEMM over element tiles.
+//
+// At high N the operator blob [Dr Ds Dt LIFT] no longer fits in shared
+// memory next to a block of elements, so the fused kernel must stream it
+// from L2 once per block of a few elements.  The split step instead
+//   kernel A (the fused kernel's front half, SPLIT = true): stages q, records
+//     and neighbour traces as usual, computes the volume inputs and the
+//     Fscale-weighted penalties, and writes them to a global buffer X laid
+//     out in column tiles of NE elements: X[tile][row][NE] (row = the input
+//     index of the operator products);
+//   kernel B (this file): a CTA owns MT output rows x NE elements; operator
+//     rows and X rows stream through shared memory in double-buffered K
+//     chunks (16-byte cp.async), every operator row chunk is reused by NE
+//     elements; one thread accumulates 4 rows x TN elements of every product
+//     (G_d = D_d p, R = sum_d D_d w_d + LIFT P_p, L_c = LIFT P_vc for the
+//     acoustic model; U_cd = D_d v_c, Rv_c = sum_d D_d s_cd + LIFT P_vc,
+//     LIFT P_sig for the elastic model) and does the geometric combination
+//     and the AB3 update (Eq. updateScheme) from registers.
+#pragma once
+
+#include "dg_kernels.cuh"
+
+namespace dgk {
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <int MODEL, int N>
+struct SplitShape {
+  using S = Sz<N>;
+  static constexpr int Nf = MODEL == 0 ? 4 : 9;
+  static constexpr int NV = MODEL == 0 ? 4 : 12;          // X rows per volume index j
+  static constexpr int KX = NV * S::Np + Nf * S::NFN;     // X rows per element
+  static constexpr int NE = MODEL == 0 ? 64 : 32;         // elements per column tile
+  static constexpr int TN = MODEL == 0 ? 2 : 1;           // elements per thread tile
+  static constexpr int MT = 32;                           // output rows per CTA
+  static constexpr int MP2 = (S::Np + MT - 1) / MT * MT;  // padded rows of the split operator blob
+  static constexpr int JC = 16;                           // volume indices per chunk
+  static constexpr int CC = 16;                           // face-node indices per chunk
+  static constexpr int NT = (MT / 4) * (NE / TN);         // threads per CTA
+  static constexpr int NVC = (S::Np + JC - 1) / JC;       // volume chunks
+  static constexpr int NLC = (S::NFN + CC - 1) / CC;      // lift chunks
+  // per buffer: A rows (3 JC volume, CC lift) x MT, X rows (NV JC, Nf CC) x NE
+  static constexpr int nA = (3 * JC > CC ? 3 * JC : CC) * MT;
+  static constexpr int nB = (NV * JC > Nf * CC ? NV * JC : Nf * CC) * NE;
+  static constexpr int NEP = NE + (TN == 2 ? 2 : 1);       // row stride of the staged RHS tile
+  static constexpr int nOut = Nf * MT * NEP;              // RHS tile [Nf][MT][NEP], reuses the B buffers
+  static constexpr int nBB = (2 * nB > nOut ? 2 * nB : nOut);
+  static constexpr size_t smem = size_t(2 * nA + nBB) * 4;
+  static constexpr size_t x_floats_per_tile = size_t(KX) * NE;
+};
+
+template <int MODEL, int N>
+__global__ void __launch_bounds__(SplitShape<MODEL, N>::NT) dg_split_gemm_kernel(const StepArgs a) {
+  using S = Sz<N>;
+  using SS = SplitShape<MODEL, N>;
+  constexpr int Np = S::Np, NFN = S::NFN, Nf = SS::Nf, NV = SS::NV, KX = SS::KX, NE = SS::NE, TN = SS::TN;
+  constexpr int MT = SS::MT, MP2 = SS::MP2, JC = SS::JC, CC = SS::CC, NT = SS::NT;
+  constexpr int NVC = SS::NVC, NLC = SS::NLC, NCH = NVC + NLC;
+  constexpr int REC = Rec<MODEL>::size;
+
+  extern __shared__ __align__(16) float smem[];
+  float* sA[2] = {smem, smem + SS::nA};
+  float* sB[2] = {smem + 2 * SS::nA, smem + 2 * SS::nA + SS::nB};
+
+  const int tid = threadIdx.x;
+  // row tiles fastest: the CTAs that share a column tile of X run together and
+  // read it from L2
+  constexpr int MTILES = MP2 / MT;
+  const int mtile = blockIdx.x % MTILES, ntile = blockIdx.x / MTILES;
+  const int row0 = mtile * MT;
+  const float* X = a.xg + size_t(ntile) * SS::x_floats_per_tile;
+  const float* OP = a.ops2;  // [3 Np + NFN][MP2]
+
+  // chunk c -> shared buffer (c & 1)
+  auto issue = [&](int c) {
+    float* A = sA[c & 1];
+    float* B = sB[c & 1];
+    if (c < NVC) {
+      const int j0 = c * JC;
+      const int nj = Np - j0 < JC ? Np - j0 : JC;
+      // A rows d*Np + j, j in [j0, j0+nj): MT columns from row0
+      for (int i = tid; i < 3 * nj * (MT / 4); i += NT) {
+        const int q4 = i % (MT / 4), rr = i / (MT / 4);
+        const int d = rr / nj, jj = rr - d * nj;
+        cp_async16(A + (d * JC + jj) * MT + 4 * q4, OP + size_t(d * Np + j0 + jj) * MP2 + row0 + 4 * q4);
+      }
+      // X rows f*Np + j for f < NV
+      for (int i = tid; i < NV * nj * (NE / 4); i += NT) {
+        const int q4 = i % (NE / 4), rr = i / (NE / 4);
+        const int f = rr / nj, jj = rr - f * nj;
+        cp_async16(B + (f * JC + jj) * NE + 4 * q4, X + size_t(f * Np + j0 + jj) * NE + 4 * q4);
+      }
+    } else {
+      const int c0 = (c - NVC) * CC;
+      const int nc = NFN - c0 < CC ? NFN - c0 : CC;
+      for (int i = tid; i < nc * (MT / 4); i += NT) {
+        const int q4 = i % (MT / 4), cc = i / (MT / 4);
+        cp_async16(A + cc * MT + 4 * q4, OP + size_t(3 * Np + c0 + cc) * MP2 + row0 + 4 * q4);
+      }
+      for (int i = tid; i < Nf * nc * (NE / 4); i += NT) {
+        const int q4 = i % (NE / 4), rr = i / (NE / 4);
+        const int f = rr / nc, cc = rr - f * nc;
+        cp_async16(B + (f * CC + cc) * NE + 4 * q4, X + size_t(NV * Np + f * NFN + c0 + cc) * NE + 4 * q4);
+      }
+    }
+    cp_async_commit();
+  };
+
+  // thread tile: rows i0..i0+3 of this CTA's slice, elements e0..e0+TN-1 of the column tile;
+  // lanes of a warp share the row tile (broadcast operator reads) and walk the elements
+  const int ct = tid % (NE / TN), rt = tid / (NE / TN);
+  const int il = 4 * rt, e0 = ct * TN;
+
+  constexpr int NACC = MODEL == 0 ? 7 : 12;  // acoustic G0..2, R, L0..2; elastic U00..U22, Rv0..2
+  float acc[NACC][TN][4];
+#pragma unroll
+  for (int x = 0; x < NACC; ++x)
+#pragma unroll
+    for (int t = 0; t < TN; ++t)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[x][t][v] = 0.f;
+  float accS[MODEL == 0 ? 1 : 6][TN][4];  // elastic LIFT P_sigma
+#pragma unroll
+  for (int x = 0; x < (MODEL == 0 ? 1 : 6); ++x)
+#pragma unroll
+    for (int t = 0; t < TN; ++t)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) accS[x][t][v] = 0.f;
+
+  issue(0);
+  for (int c = 0; c < NCH; ++c) {
+    if (c + 1 < NCH) {
+      issue(c + 1);
+      cp_async_wait_1();
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();
+    const float* A = sA[c & 1] + il;
+    const float* B = sB[c & 1] + e0;
+    if (c < NVC) {
+      const int j0 = c * JC;
+      const int nj = Np - j0 < JC ? Np - j0 : JC;
+#pragma unroll 4
+      for (int jj = 0; jj < nj; ++jj) {
+        const float4 a0 = *reinterpret_cast<const float4*>(A + (0 * JC + jj) * MT);
+        const float4 a1 = *reinterpret_cast<const float4*>(A + (1 * JC + jj) * MT);
+        const float4 a2 = *reinterpret_cast<const float4*>(A + (2 * JC + jj) * MT);
+        if constexpr (MODEL == 0) {
+          float xpv[TN], x0v[TN], x1v[TN], x2v[TN];
+          VecT<TN>::load(B + (0 * JC + jj) * NE, xpv);
+          VecT<TN>::load(B + (1 * JC + jj) * NE, x0v);
+          VecT<TN>::load(B + (2 * JC + jj) * NE, x1v);
+          VecT<TN>::load(B + (3 * JC + jj) * NE, x2v);
+#pragma unroll
+          for (int t = 0; t < TN; ++t) {
+            const float xp = xpv[t], x0 = x0v[t], x1 = x1v[t], x2 = x2v[t];
+            fma4(acc[0][t], a0, xp);
+            fma4(acc[1][t], a1, xp);
+            fma4(acc[2][t], a2, xp);
+            fma4(acc[3][t], a0, x0);
+            fma4(acc[3][t], a1, x1);
+            fma4(acc[3][t], a2, x2);
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < TN; ++t)
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+              const float xv = B[(cc * JC + jj) * NE + t];
+              fma4(acc[3 * cc + 0][t], a0, xv);
+              fma4(acc[3 * cc + 1][t], a1, xv);
+              fma4(acc[3 * cc + 2][t], a2, xv);
+              fma4(acc[9 + cc][t], a0, B[((3 + 3 * cc + 0) * JC + jj) * NE + t]);
+              fma4(acc[9 + cc][t], a1, B[((3 + 3 * cc + 1) * JC + jj) * NE + t]);
+              fma4(acc[9 + cc][t], a2, B[((3 + 3 * cc + 2) * JC + jj) * NE + t]);
+            }
+        }
+      }
+    } else {
+      const int c0 = (c - NVC) * CC;
+      const int nc = NFN - c0 < CC ? NFN - c0 : CC;
+#pragma unroll 4
+      for (int cc = 0; cc < nc; ++cc) {
+        const float4 l = *reinterpret_cast<const float4*>(A + cc * MT);
+        if constexpr (MODEL == 0) {
+          float p0[TN], p1[TN], p2[TN], p3[TN];
+          VecT<TN>::load(B + (0 * CC + cc) * NE, p0);
+          VecT<TN>::load(B + (1 * CC + cc) * NE, p1);
+          VecT<TN>::load(B + (2 * CC + cc) * NE, p2);
+          VecT<TN>::load(B + (3 * CC + cc) * NE, p3);
+#pragma unroll
+          for (int t = 0; t < TN; ++t) {
+            fma4(acc[3][t], l, p0[t]);
+            fma4(acc[4][t], l, p1[t]);
+            fma4(acc[5][t], l, p2[t]);
+            fma4(acc[6][t], l, p3[t]);
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < TN; ++t) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) fma4(acc[9 + f][t], l, B[(f * CC + cc) * NE + t]);
+#pragma unroll
+            for (int f = 0; f < 6; ++f) fma4(accS[f][t], l, B[((3 + f) * CC + cc) * NE + t]);
+          }
+        }
+      }
+    }
+    __syncthreads();  // buffer (c & 1) is refilled by chunk c + 2
+  }
+
+  // -------- epilogue, part 1: geometric combination and source in registers;
+  // the RHS tile goes to shared memory as [Nf][MT][NEP] (element fastest)
+  float* sOut = smem + 2 * SS::nA;
+  constexpr int NEP = SS::NEP;
+#pragma unroll
+  for (int t = 0; t < TN; ++t) {
+    const int k = ntile * NE + e0 + t;
+    const int kk = k < a.K ? k : a.K - 1;  // padding columns: any valid record
+    const float* gk = a.rec + size_t(kk) * REC;
+    float g[9];
+#pragma unroll
+    for (int x = 0; x < 9; ++x) g[x] = __ldg(gk + x);
+    const bool src = (k == a.src_elem) && a.srcvec;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = row0 + il + v;
+      float r[Nf];
+      if constexpr (MODEL == 0) {
+        const float rinv = __ldg(gk + 10);
+        r[0] = acc[3][t][v];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc)
+          r[1 + cc] = acc[4 + cc][t][v] -
+                      rinv * (g[3 * cc] * acc[0][t][v] + g[3 * cc + 1] * acc[1][t][v] + g[3 * cc + 2] * acc[2][t][v]);
+      } else {
+        const float lam = __ldg(gk + 9), mu = __ldg(gk + 10);
+        float gv[3][3];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+          for (int x = 0; x < 3; ++x)
+            gv[cc][x] = g[3 * x] * acc[3 * cc][t][v] + g[3 * x + 1] * acc[3 * cc + 1][t][v] +
+                        g[3 * x + 2] * acc[3 * cc + 2][t][v];
+        const float div = gv[0][0] + gv[1][1] + gv[2][2];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) r[cc] = acc[9 + cc][t][v];
+        r[3] = lam * div + 2.f * mu * gv[0][0] + accS[0][t][v];
+        r[4] = lam * div + 2.f * mu * gv[1][1] + accS[1][t][v];
+        r[5] = lam * div + 2.f * mu * gv[2][2] + accS[2][t][v];
+        r[6] = mu * (gv[0][1] + gv[1][0]) + accS[3][t][v];
+        r[7] = mu * (gv[0][2] + gv[2][0]) + accS[4][t][v];
+        r[8] = mu * (gv[1][2] + gv[2][1]) + accS[5][t][v];
+      }
+      if (src && i < Np) {
+#pragma unroll
+        for (int f = 0; f < Nf; ++f) r[f] = fmaf(a.src_amp, __ldg(a.srcvec + f * Np + i), r[f]);
+      }
+#pragma unroll
+      for (int f = 0; f < Nf; ++f) sOut[(f * MT + il + v) * NEP + e0 + t] = r[f];
+    }
+  }
+  __syncthreads();
+  // part 2: one warp per (element, field) row segment: coalesced AB3 update
+  const int warp = tid >> 5, lane = tid & 31;
+  constexpr int NWARP = NT / 32;
+  const int rows = (Np - row0) < MT ? (Np - row0) : MT;
+  for (int p = warp; p < NE * Nf; p += NWARP) {
+    const int e = p / Nf, f = p - e * Nf;
+    const int k = ntile * NE + e;
+    if (k >= a.K) continue;
+    const size_t base = size_t(k) * Nf * Np + size_t(f) * Np + row0;
+    for (int rr = lane; rr < rows; rr += 32) {
+      const float rv = sOut[(f * MT + rr) * NEP + e];
+      const size_t idx = base + rr;
+      if (a.mode == 0) {
+        const float accv = a.a1 * rv + a.a2 * __ldg(a.r1 + idx) + a.a3 * a.r2[idx];
+        a.qn[idx] = fmaf(a.dt, accv, __ldg(a.q + idx));
+        a.r2[idx] = rv;
+      } else {
+        a.rout[idx] = rv;
+      }
+    }
+  }
+}
+
+}  // namespace dgk

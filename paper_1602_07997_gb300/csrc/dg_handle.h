@@ -41,6 +41,10 @@ struct Handle {
   int* d_ftab = nullptr;
   float* d_src = nullptr;
   int* d_err = nullptr;
+  // split step (high N): GEMM inputs and the row-padded operator blob, allocated on first use
+  void* d_split = nullptr;
+  float* d_x = nullptr;
+  float* d_ops2 = nullptr;
 
   int qcur = 0;    // which q buffer holds q^m
   int r1slot = 0;  // which r buffer holds r^{m-1}; the other holds r^{m-2}
@@ -50,6 +54,7 @@ struct Handle {
   std::vector<double> src_amp;
 
   int init(const dg_mesh* mesh, const double* coeffs, int N, int model, const dg_opts* o);
+  int ensure_split(const dgk::KernelCfg* c);
   dgk::StepArgs args(int mode) const;
   int advance(int nsteps);
   ~Handle();

@@ -238,7 +238,7 @@ struct SolveBatch {
 };
 
 // ---------------------------------------------------------------- kernel body
-template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, class Prov>
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, bool SPLIT, class Prov>
 __device__ __forceinline__ void step_body(const Prov& prov) {
   using S = Sz<N>;
   using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM>;
@@ -520,6 +520,22 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       if (mbar_wait_bounded(&bars[s ^ 1], uint32_t(((it + 1) >> 1) & 1), err)) issue_gathers(nxt_a, nxt_lb, s ^ 1);
     }
 
+    if constexpr (SPLIT) {
+      // split step, front half: the GEMM inputs leave for the global buffer
+      // X[tile][row][NE] (row: volume inputs, then penalties), 4 elements per float4
+      constexpr int NV = MODEL == 0 ? 4 : 12;
+      constexpr int KX = NV * Np + Nf * NFN;
+      constexpr int NE = MODEL == 0 ? 64 : 32;
+      for (int i = tid; i < KX * (EB / 4); i += NT) {
+        const int e4 = i % (EB / 4), row = i / (EB / 4);
+        const float* src = row < NV * Np ? sXv + row * EBP : sXs + (row - NV * Np) * EBP;
+        const int k = k0 + 4 * e4;
+        const float4 v = make_float4(src[4 * e4], src[4 * e4 + 1], src[4 * e4 + 2], src[4 * e4 + 3]);
+        *reinterpret_cast<float4*>(a.xg + (size_t(k / NE) * KX + row) * NE + (k % NE)) = v;
+      }
+      continue;
+    }
+
     // -------- register-tiled operator products (one tile of 4 nodes x TN elements per thread)
     float r[TN][Nf][4];
     const bool has_tile = tid < NTILE;
@@ -743,11 +759,11 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
   if (R_SMEM && tid == 0) bulk_wait_all();
 }
 
-// One solve per launch (dg_rhs / dg_step).
-template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM>
+// One solve per launch (dg_rhs / dg_step); SPLIT = front half of the split step.
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, bool SPLIT = false>
 __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   SingleSolve p{a, EB};
-  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>(p);
+  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, SPLIT>(p);
 }
 
 // Every solve of a batch (same model and N) in one persistent launch; the
@@ -755,7 +771,7 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
 template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM>
 __global__ void __launch_bounds__(NT) dg_step_batched_kernel(const BatchArgs b) {
   SolveBatch p{b};
-  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>(p);
+  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, false>(p);
 }
 
 }  // namespace dgk

@@ -1,6 +1,6 @@
 // Launch helpers shared by the per-model instantiation units.
 #pragma once
-#include "dg_kernels.cuh"
+#include "dg_gemm.cuh"
 
 namespace dgk {
 
@@ -24,6 +24,38 @@ KernelCfg make_cfg() {
   c.smem = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM>::bytes;
   c.fn = dg_step_kernel<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>;
   c.fn_batched = dg_step_batched_kernel<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>;
+  c.split = false;
+  c.fn_gemm = nullptr;
+  c.smem_gemm = 0;
+  c.gemm_threads = c.gemm_ne = c.gemm_mt = c.gemm_mtiles = c.gemm_kx = c.gemm_mp2 = 0;
+  return c;
+}
+
+// Split variant: front half with EB elements per block, then the GEMM kernel.
+template <int MODEL, int N, int EB, int NT = threads_for<N, EB, 1>()>
+KernelCfg make_split_cfg() {
+  using SS = SplitShape<MODEL, N>;
+  static_assert(Plan<MODEL, N, EB, false, false>::bytes <= 227 * 1024, "shared memory budget");
+  static_assert(SS::smem <= 227 * 1024, "shared memory budget (GEMM)");
+  static_assert(SS::NE % EB == 0 || EB % SS::NE == 0, "element blocks inside column tiles");
+  KernelCfg c;
+  c.EB = EB;
+  c.TN = 1;
+  c.NT = NT;
+  c.ops_smem = false;
+  c.r_smem = false;
+  c.smem = Plan<MODEL, N, EB, false, false>::bytes;
+  c.fn = dg_step_kernel<MODEL, N, EB, 1, NT, false, false, true>;
+  c.fn_batched = nullptr;
+  c.split = true;
+  c.fn_gemm = dg_split_gemm_kernel<MODEL, N>;
+  c.smem_gemm = SS::smem;
+  c.gemm_threads = SS::NT;
+  c.gemm_ne = SS::NE;
+  c.gemm_mt = SS::MT;
+  c.gemm_mtiles = SS::MP2 / SS::MT;
+  c.gemm_kx = SS::KX;
+  c.gemm_mp2 = SS::MP2;
   return c;
 }
 

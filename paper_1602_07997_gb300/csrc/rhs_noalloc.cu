@@ -52,10 +52,13 @@ extern "C" int dg_rhs_host_noalloc(dg_handle* h, float* r_out) {
   float* scratch = nullptr;
   int rc = scratch_for_device(dev, &scratch);
   if (rc) return rc;
-  // the RHS kernel writes every value that is read back: nothing to clear
+  // the RHS kernel writes every value that is read back: nothing to clear.
+  // The fused default variant is used: a split variant would need its input
+  // buffer, which is allocated on first use.
+  const dgk::KernelCfg* cfg = h->cfg->split ? dgk::kernel_cfg(h->model, h->N) : h->cfg;
   dgk::StepArgs a = h->args(1);
   a.rout = scratch;
-  e = dgk::launch_step(h->cfg, a, h->stream);
+  e = dgk::launch_step(cfg, a, h->stream);
   if (e != cudaSuccess) return dg::cuda_fail(e, "launch");
   e = cudaMemcpyAsync(r_out, scratch, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return dg::cuda_fail(e, "copy to host");

@@ -173,6 +173,7 @@ bool Server::admit_one(std::shared_ptr<Request> r) {
   o.block_elems = 0;
   dg_handle* h = nullptr;
   int rc = dg_setup(&m, r->coeffs.data(), r->N, r->model, &o, &h);
+  if (rc == DG_OK) h->cfg = dgk::kernel_cfg(r->model, r->N);  // batched launches use the fused default
   if (rc == DG_OK && !r->q0.empty()) rc = dg_set_state(h, r->q0.data(), nullptr, nullptr, 0, 0);
   if (rc == DG_OK && r->has_src) rc = dg_set_source(h, r->xs, r->dir, r->amp.data(), int64_t(r->amp.size()));
   auto a = std::make_unique<Active>();

@@ -190,3 +190,32 @@ def test_checkpoint_resume_is_bitwise(dg, model, N):
     c.set_state(q, r1, r2, step=50)
     c.step(50)
     assert np.array_equal(c.get_state(), ref)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("model", ["acoustic", "elastic"])
+@pytest.mark.parametrize("N", range(1, 9))
+def test_every_kernel_variant_rhs_and_steps(dg, model, N):
+    """Every compiled variant (block sizes, tiles, split GEMM path) gives the
+    oracle's RHS and the same 20-step state as variant 0."""
+    n = 4 if N <= 3 else 3
+    verts, tets, coeffs = _mesh(model, n, 120 + N)
+    o = OSolver(model, N, verts, tets, coeffs)
+    dt = o.suggest_dt(0.4)
+    q = W.random_state(o.K, o.Nf, o.ref.Np, seed=N).astype(np.float32)
+    ro = o.rhs(q.astype(np.float64))
+    g = dg.Solver(verts, tets, coeffs, N, model, dt=dt)
+    nv = g.kernel_info()["variants"]
+    ref_state = None
+    for v in range(nv):
+        g.set_variant(v)
+        g.set_state(q)
+        assert rel_l2(model, g.rhs(), ro) <= RHS_TOL, (v, g.kernel_info())
+        g.step(20)
+        g.sync()
+        s = g.get_state()
+        if ref_state is None:
+            ref_state = s
+        else:
+            assert rel_l2(model, s, ref_state.astype(np.float64)) <= 1e-5, (v, g.kernel_info())
+    g.close()
