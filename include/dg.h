@@ -73,8 +73,19 @@ enum { DG_FLUX_UPWIND = 0, DG_FLUX_CENTERED = 1 };
  * Mirror ghost states: acoustic rigid p+ = p-, v+ = v- - 2 (v-.n) n;
  * elastic free v+ = v-, sigma+ = -sigma-; elastic rigid v+ = -v-, sigma+ = sigma-. */
 enum { DG_BC_DEFAULT = 0, DG_BC_RIGID = 1, DG_BC_FREE = 2 };
-/* arithmetic of the operator contractions; flux and AB3 are always float32 */
-enum { DG_FP32 = 0 };
+/* Arithmetic of the operator contractions (D_r, D_s, D_t and LIFT products,
+ * Section 3.2); flux, geometric combination and AB3 are always float32.
+ *   DG_FP32   FP32 FMAs on the CUDA cores.
+ *   DG_BF16X3 tensor cores (tcgen05, FP32 accumulation in TMEM); every operand
+ *             x is split into two BF16 pieces x0 + x1 and the three products
+ *             x0 y0 + x0 y1 + x1 y0 are summed: relative error of each product
+ *             about 2^-16 (the RHS of smooth fields at N >= 4 can miss 1e-5).
+ *   DG_BF16X6 tensor cores with three BF16 pieces per operand and the six
+ *             products of pieces (a, b) with a + b <= 2: float32-level error.
+ * The tensor-core modes run the split step (front half on the CUDA cores
+ * writing the contraction inputs to a device buffer, then the contraction and
+ * the AB3 epilogue on the tensor cores) at every N. */
+enum { DG_FP32 = 0, DG_BF16X3 = 1, DG_BF16X6 = 2 };
 
 typedef struct {
   int64_t nverts;
@@ -86,7 +97,7 @@ typedef struct {
 typedef struct {
   int flux;         /* DG_FLUX_*                                         */
   int bc;           /* DG_BC_*                                           */
-  int precision;    /* DG_FP32                                           */
+  int precision;    /* DG_FP32, DG_BF16X3 or DG_BF16X6                   */
   int block_elems;  /* elements per CTA of a compiled variant; 0 = the autotuned
                        choice for (model, N) if any, else the default variant */
   double dt;        /* time step used by dg_step (may be changed by dg_set_dt) */
@@ -139,12 +150,13 @@ int dg_set_dt(dg_handle *h, double dt);
  * Allocates and frees scratch device memory of 4 state sizes; synchronous. */
 int dg_autotune(dg_handle *h, int reps, int *block_elems, double *ms_per_step, double *variant_ms);
 /* Launch configuration in use: elements per CTA, threads per CTA, dynamic
- * shared memory per CTA, number of compiled variants, elements per thread
- * tile, and whether it is a split variant (the operator products run as a
- * separate GEMM over 32-64-element column tiles; used at high N, needs an
- * extra device buffer of (4 Np + 4 (4 Nfp)) floats per element for the
- * acoustic model, (12 Np + 9 (4 Nfp)) for the elastic one, allocated on
- * first use).  Pointers may be NULL.                           */
+ * shared memory per CTA, number of compiled variants (of the handle's
+ * precision mode), elements per thread tile, and the step's form in *split:
+ * 0 fused, 1 split with the FP32 CUDA-core GEMM, 2 split with the tensor-core
+ * GEMM (the operator products run as a separate GEMM over 16-64-element
+ * column tiles; needs an extra device buffer of (4 Np + 4 (4 Nfp)) floats per
+ * element for the acoustic model, (12 Np + 9 (4 Nfp)) for the elastic one,
+ * allocated on first use).  Pointers may be NULL.                           */
 int dg_kernel_info(const dg_handle *h, int *block_elems, int *threads, int64_t *smem_bytes,
                    int *variants, int *tile_elems, int *split);
 /* Select compiled variant `index` (0 <= index < variants) for this handle.  */
@@ -220,7 +232,9 @@ typedef struct {
   const double *coeffs;
   int N;
   int model;
-  dg_opts opts;          /* flux, bc, dt; block_elems and stream are ignored */
+  dg_opts opts;          /* flux, bc, dt; precision must be DG_FP32 (served
+                            solves run the batched FP32 kernels, else
+                            DG_EINVAL); block_elems and stream are ignored */
   const float *q0;       /* host [K][Nf][Np]; NULL = zero state              */
   const double *src_xyz; /* NULL = no source                                  */
   const double *src_dir; /* elastic only; NULL = (0,0,1)                      */

@@ -18,6 +18,7 @@ DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONFINITE, DG_ETIMEOUT, DG_EAGAIN, DG
 ACOUSTIC, ELASTIC = 0, 1
 FLUX = {"upwind": 0, "centered": 1, "centred": 1}
 BC = {None: 0, "default": 0, "rigid": 1, "free": 2}
+PRECISION = {"fp32": 0, "bf16x3": 1, "bf16x6": 2}
 
 # every symbol that include/dg.h declares
 EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", "dg_rhs", "dg_step",
@@ -168,10 +169,11 @@ class Solver:
     """One DG discretisation on the GPU (a dg_handle)."""
 
     def __init__(self, verts, tets, coeffs, N, model="acoustic", flux="upwind", bc=None, dt=0.0,
-                 stream=None, block_elems=0):
+                 stream=None, block_elems=0, precision="fp32"):
         m, keep = make_mesh(verts, tets)
         cf = np.ascontiguousarray(coeffs, dtype=np.float64)
-        o = Opts(FLUX[flux], BC[bc], 0, int(block_elems), float(dt), C.c_void_p(stream or 0))
+        o = Opts(FLUX[flux], BC[bc], PRECISION[precision], int(block_elems), float(dt),
+                 C.c_void_p(stream or 0))
         h = C.c_void_p()
         check(lib().dg_setup(C.byref(m), _dptr(cf), int(N), _model(model), C.byref(o), C.byref(h)))
         self.h = h
@@ -259,7 +261,7 @@ class Solver:
         check(lib().dg_kernel_info(self.h, C.byref(eb), C.byref(nt), C.byref(sm), C.byref(nv), C.byref(tn),
                                    C.byref(sp)))
         return dict(block_elems=eb.value, threads=nt.value, smem_bytes=sm.value, variants=nv.value,
-                    tile_elems=tn.value, split=bool(sp.value))
+                    tile_elems=tn.value, split=sp.value)
 
     def set_variant(self, index):
         check(lib().dg_set_variant(self.h, int(index)))

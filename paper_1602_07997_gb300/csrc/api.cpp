@@ -131,7 +131,7 @@ double suggest_dt(const HostMesh& m, const double* coeffs, int N, int model, dou
 // ---------------------------------------------------------------- variants
 // Autotuned choice per (device, model, N), shared by every handle of the process.
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int>, int> g_tuned;
+static std::map<std::tuple<int, int, int, int>, int> g_tuned;
 
 static int device_of_current() {
   int d = 0;
@@ -139,9 +139,9 @@ static int device_of_current() {
   return d;
 }
 
-const dgk::KernelCfg* select_variant(int model, int N, int block_elems, int device) {
+const dgk::KernelCfg* select_variant(int model, int N, int block_elems, int device, int precision) {
   int n = 0;
-  const dgk::KernelCfg* v = dgk::kernel_variants(model, N, &n);
+  const dgk::KernelCfg* v = dgk::kernel_variants(model, N, &n, precision);
   if (!v) return nullptr;
   if (block_elems > 0) {
     for (int i = 0; i < n; ++i)
@@ -149,7 +149,7 @@ const dgk::KernelCfg* select_variant(int model, int N, int block_elems, int devi
     return nullptr;
   }
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  auto it = g_tuned.find(std::make_tuple(device, model, N));
+  auto it = g_tuned.find(std::make_tuple(device, model, N, precision));
   return it != g_tuned.end() ? &v[it->second] : &v[0];
 }
 
@@ -164,7 +164,8 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
   if (opts.bc < DG_BC_DEFAULT || opts.bc > DG_BC_FREE) return fail(DG_EINVAL, "unknown boundary condition");
   if (model == DG_ACOUSTIC && opts.bc == DG_BC_FREE)
     return fail(DG_EINVAL, "acoustic model supports rigid walls only");
-  if (opts.precision != DG_FP32) return fail(DG_EINVAL, "unknown precision mode");
+  if (opts.precision != DG_FP32 && opts.precision != DG_BF16X3 && opts.precision != DG_BF16X6)
+    return fail(DG_EINVAL, "unknown precision mode");
   stream = static_cast<cudaStream_t>(opts.stream);
   int rc = ref.build(N);
   if (rc) return rc;
@@ -176,7 +177,7 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
   Nfp = ref.Nfp;
   Nf = num_fields(model);
   K = hm.K;
-  cfg = select_variant(model, N, opts.block_elems, device_of_current());
+  cfg = select_variant(model, N, opts.block_elems, device_of_current(), opts.precision);
   if (!cfg) return fail(DG_EINVAL, "no compiled kernel variant with block_elems = " + std::to_string(opts.block_elems));
   // every launch reads whole blocks of EB <= 128 elements with bulk copies:
   // pad the element arrays so that the last block stays inside the allocation
@@ -235,11 +236,79 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
 Handle::~Handle() {
   if (d_base) cudaFree(d_base);
   if (d_split) cudaFree(d_split);
+  if (d_tc) cudaFree(d_tc);
+}
+
+// BF16 rounding (nearest, ties to even) of a finite float, as raw bits.
+static uint16_t bf16_bits(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return uint16_t(u >> 16);
+}
+static double bf16_value(uint16_t b) {
+  const uint32_t u = uint32_t(b) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return double(f);
+}
+
+// Tensor-core split step: X[tiles + 1][KX][NE] (FP32; the extra tile keeps the
+// 16-row chunk copies of the last tile inside the allocation) and the operator
+// pieces.  For every 128-row tile of output nodes, chunk c of 16 input indices
+// holds D_r, D_s, D_t (volume chunks) or LIFT (lift chunks), each as nsplit BF16
+// pieces x = x_0 + x_1 (+ x_2) of the double-precision entry, every piece in
+// the no-swizzle K-major core-matrix layout [16 row groups][2 K halves][8 rows][8].
+static int pack_tc_ops(const RefElement& R, int nsplit, int mtiles, std::vector<uint16_t>& blob) {
+  const int Np = R.Np, NFN = 4 * R.Nfp;
+  const int NKD = (Np + 15) / 16, NKL = (NFN + 15) / 16;
+  const size_t piece = 128 * 16, a_d = 3 * size_t(nsplit) * piece, a_l = size_t(nsplit) * piece;
+  const size_t per_tile = NKD * a_d + NKL * a_l;
+  blob.assign(per_tile * mtiles, 0);
+  const std::vector<double>* D[3] = {&R.Dr, &R.Ds, &R.Dt};
+  auto put = [&](size_t base, int i_loc, int k_loc, double x) {
+    const size_t off = size_t(i_loc / 8) * 128 + size_t(k_loc / 8) * 64 + size_t(i_loc % 8) * 8 + (k_loc % 8);
+    double rem = x;
+    for (int h = 0; h < nsplit; ++h) {
+      const uint16_t b = bf16_bits(float(rem));
+      blob[base + h * piece + off] = b;
+      rem -= bf16_value(b);
+    }
+  };
+  for (int mt = 0; mt < mtiles; ++mt) {
+    const size_t t0 = mt * per_tile;
+    for (int il = 0; il < 128; ++il) {
+      const int i = mt * 128 + il;
+      if (i >= Np) break;
+      for (int j = 0; j < Np; ++j)
+        for (int d = 0; d < 3; ++d)
+          put(t0 + size_t(j / 16) * a_d + size_t(d) * nsplit * piece, il, j % 16, (*D[d])[size_t(i) * Np + j]);
+      for (int m = 0; m < NFN; ++m)
+        put(t0 + NKD * a_d + size_t(m / 16) * a_l, il, m % 16, R.LIFT[size_t(i) * NFN + m]);
+    }
+  }
+  return DG_OK;
 }
 
 // Buffers of the split step: X[tiles][KX][NE] and the operator blob with rows padded.
 int Handle::ensure_split(const dgk::KernelCfg* c) {
-  if (!c || !c->split || d_split) return DG_OK;
+  if (!c || !c->split) return DG_OK;
+  if (c->split == 2) {
+    if (d_tc) return DG_OK;
+    const size_t ntiles = size_t((Kpad + c->gemm_ne - 1) / c->gemm_ne) + 1;
+    const size_t xbytes = ntiles * c->gemm_kx * c->gemm_ne * 4;
+    std::vector<uint16_t> blob;
+    pack_tc_ops(ref, c->gemm_nsplit, c->gemm_mtiles, blob);
+    const size_t obytes = (blob.size() * 2 + 255) & ~size_t(255);
+    DG_CUDA(cudaMalloc(&d_tc, xbytes + obytes));
+    d_opstc = d_tc;
+    d_xtc = reinterpret_cast<float*>(static_cast<char*>(d_tc) + obytes);
+    DG_CUDA(cudaMemsetAsync(d_xtc, 0, xbytes, stream));
+    DG_CUDA(cudaMemcpyAsync(d_opstc, blob.data(), blob.size() * 2, cudaMemcpyHostToDevice, stream));
+    DG_CUDA(cudaStreamSynchronize(stream));
+    return DG_OK;
+  }
+  if (d_split) return DG_OK;
   const size_t ntiles = size_t((Kpad + c->gemm_ne - 1) / c->gemm_ne);
   const size_t xbytes = ntiles * c->gemm_kx * c->gemm_ne * 4;
   const int KD = 3 * Np + 4 * Nfp, MP2 = c->gemm_mp2;
@@ -282,9 +351,15 @@ dgk::StepArgs Handle::args(int mode) const {
   else if (have == 1) { a.a1 = 1.5f; a.a2 = -0.5f; a.a3 = 0.0f; }
   else { a.a1 = float(23.0 / 12.0); a.a2 = float(-16.0 / 12.0); a.a3 = float(5.0 / 12.0); }
   a.err = d_err;
-  a.xg = d_x;
-  a.ops2 = d_ops2;
+  split_ptrs(a, cfg);
   return a;
+}
+
+void Handle::split_ptrs(dgk::StepArgs& a, const dgk::KernelCfg* c) const {
+  const bool tc = c && c->split == 2;
+  a.xg = tc ? d_xtc : d_x;
+  a.ops2 = d_ops2;
+  a.opstc = d_opstc;
 }
 
 int Handle::advance(int nsteps) {
@@ -487,7 +562,7 @@ int dg_set_source(dg_handle* h, const double xs[3], const double dir[3], const d
 int dg_autotune(dg_handle* h, int reps, int* block_elems, double* ms_per_step, double* variant_ms) {
   if (!h || reps < 1) return fail(DG_EINVAL, "NULL handle or reps < 1");
   int n = 0;
-  const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n);
+  const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n, h->opts.precision);
   for (int i = 0; i < n; ++i) {
     int rs = h->ensure_split(&v[i]);
     if (rs) return rs;
@@ -510,8 +585,7 @@ int dg_autotune(dg_handle* h, int reps, int* block_elems, double* ms_per_step, d
     DG_CUDA(cudaEventCreate(&e1));
     for (int i = 0; i < n; ++i) {
       dgk::StepArgs a = h->args(0);
-      a.xg = h->d_x;
-      a.ops2 = h->d_ops2;
+      h->split_ptrs(a, &v[i]);
       a.a1 = 1.0f;
       a.a2 = a.a3 = 0.0f;
       a.src_elem = -1;
@@ -558,7 +632,7 @@ int dg_autotune(dg_handle* h, int reps, int* block_elems, double* ms_per_step, d
   h->cfg = &v[best];
   {
     std::lock_guard<std::mutex> lock(dg::g_tune_mu);
-    dg::g_tuned[std::make_tuple(h->device, h->model, h->N)] = best;
+    dg::g_tuned[std::make_tuple(h->device, h->model, h->N, h->opts.precision)] = best;
   }
   if (block_elems) *block_elems = v[best].EB;
   if (ms_per_step) *ms_per_step = best_ms;
@@ -568,7 +642,7 @@ int dg_autotune(dg_handle* h, int reps, int* block_elems, double* ms_per_step, d
 int dg_set_variant(dg_handle* h, int index) {
   if (!h) return fail(DG_EINVAL, "NULL handle");
   int n = 0;
-  const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n);
+  const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n, h->opts.precision);
   if (index < 0 || index >= n) return fail(DG_EINVAL, "variant index out of range");
   h->cfg = &v[index];
   return DG_OK;
@@ -577,12 +651,12 @@ int dg_set_variant(dg_handle* h, int index) {
 int dg_kernel_info(const dg_handle* h, int* block_elems, int* threads, int64_t* smem_bytes, int* variants,
                    int* tile_elems, int* split) {
   if (!h || !h->cfg) return fail(DG_EINVAL, "NULL handle");
-  if (split) *split = h->cfg->split ? 1 : 0;
+  if (split) *split = h->cfg->split;
   if (tile_elems) *tile_elems = h->cfg->TN;
   if (block_elems) *block_elems = h->cfg->EB;
   if (threads) *threads = h->cfg->NT;
   if (smem_bytes) *smem_bytes = int64_t(h->cfg->smem);
-  if (variants) dgk::kernel_variants(h->model, h->N, variants);
+  if (variants) dgk::kernel_variants(h->model, h->N, variants, h->opts.precision);
   return DG_OK;
 }
 

@@ -42,7 +42,8 @@ struct StepArgs {
   float dt, a1, a2, a3;
   int* err;              // device error word (bounded-wait expiry)
   float* xg;             // split step: GEMM inputs X[tile][row][NE]
-  const float* ops2;     // split step: operator blob [3Np + 4Nfp][rows padded to 32]
+  const float* ops2;     // split step (FP32): operator blob [3Np + 4Nfp][rows padded to 32]
+  const void* opstc;     // split step (tensor cores): BF16 operator pieces, core-matrix layout
 };
 
 // Per-solve device state of a batched launch (served mode).  The step index,
@@ -78,22 +79,25 @@ struct BatchArgs {
 };
 
 // Host-visible launch configuration of one (model, N) instantiation.  A
-// split variant launches fn (front half, writes X) and then fn_gemm.
+// split variant launches fn (front half, writes X) and then fn_gemm:
+// split = 1 FP32 CUDA-core GEMM, split = 2 tensor-core GEMM in split-BF16
+// arithmetic with gemm_nsplit pieces per operand.
 struct KernelCfg {
   int EB, TN, NT;
   bool ops_smem, r_smem;
   size_t smem;
   void (*fn)(StepArgs);
   void (*fn_batched)(BatchArgs);
-  bool split;
+  int split;
   void (*fn_gemm)(StepArgs);
   size_t smem_gemm;
-  int gemm_threads, gemm_ne, gemm_mt, gemm_mtiles, gemm_kx, gemm_mp2;
+  int gemm_threads, gemm_ne, gemm_mt, gemm_mtiles, gemm_kx, gemm_mp2, gemm_nsplit;
 };
 
 // Compiled variants of one (model, N): different elements per block (EB) and
-// threads per CTA.  Variant 0 is the default.
-const KernelCfg* kernel_variants(int model, int N, int* count);
+// threads per CTA.  Variant 0 is the default.  precision: 0 FP32 (fused and
+// FP32 split kernels), 1 bf16x3 and 2 bf16x6 tensor-core split kernels.
+const KernelCfg* kernel_variants(int model, int N, int* count, int precision = 0);
 const KernelCfg* kernel_cfg(int model, int N);
 
 // Launch the persistent step kernel on `stream` (grid = min(blocks, SMs x occupancy)).

@@ -8,10 +8,15 @@ namespace dgk {
 
 const KernelCfg* kernel_variants_acoustic(int N, int* count);
 const KernelCfg* kernel_variants_elastic(int N, int* count);
+const KernelCfg* kernel_variants_tc(int model, int N, int nsplit, int* count);
 
-const KernelCfg* kernel_variants(int model, int N, int* count) {
+const KernelCfg* kernel_variants(int model, int N, int* count, int precision) {
   int c = 0;
-  const KernelCfg* v = model == 0 ? kernel_variants_acoustic(N, &c) : kernel_variants_elastic(N, &c);
+  const KernelCfg* v = nullptr;
+  if (precision == 0)
+    v = model == 0 ? kernel_variants_acoustic(N, &c) : kernel_variants_elastic(N, &c);
+  else if (precision == 1 || precision == 2)
+    v = kernel_variants_tc(model, N, precision + 1, &c);
   if (count) *count = v ? c : 0;
   return v;
 }
@@ -51,7 +56,8 @@ cudaError_t prepare_fn(const KernelCfg* c, const void* fn, int* grid_cap) {
 
 cudaError_t launch_step(const KernelCfg* c, const StepArgs& args, cudaStream_t stream) {
   if (!c) return cudaErrorInvalidValue;
-  if (c->split && (!args.xg || !args.ops2)) return cudaErrorInvalidValue;
+  if (c->split == 1 && (!args.xg || !args.ops2)) return cudaErrorInvalidValue;
+  if (c->split == 2 && (!args.xg || !args.opstc)) return cudaErrorInvalidValue;
   int cap = 0;
   cudaError_t e = prepare_fn(c, reinterpret_cast<const void*>(c->fn), &cap);
   if (e != cudaSuccess) return e;

@@ -17,7 +17,7 @@ void pack_ops(const RefElement& R, std::vector<float>& ops, std::vector<int>& ft
 void pack_records(const HostMesh& hm, const double* coeffs, int model, int64_t Kpad, std::vector<float>& rec,
                   std::vector<int32_t>& nbr);
 double suggest_dt(const HostMesh& m, const double* coeffs, int N, int model, double cfl);
-const dgk::KernelCfg* select_variant(int model, int N, int block_elems, int device);
+const dgk::KernelCfg* select_variant(int model, int N, int block_elems, int device, int precision);
 
 struct Handle {
   int model = 0, N = 0, Np = 0, Nfp = 0, Nf = 0, device = 0;
@@ -45,6 +45,10 @@ struct Handle {
   void* d_split = nullptr;
   float* d_x = nullptr;
   float* d_ops2 = nullptr;
+  // tensor-core split step: FP32 GEMM inputs and the BF16 operator pieces, allocated on first use
+  void* d_tc = nullptr;
+  float* d_xtc = nullptr;
+  void* d_opstc = nullptr;
 
   int qcur = 0;    // which q buffer holds q^m
   int r1slot = 0;  // which r buffer holds r^{m-1}; the other holds r^{m-2}
@@ -55,6 +59,8 @@ struct Handle {
 
   int init(const dg_mesh* mesh, const double* coeffs, int N, int model, const dg_opts* o);
   int ensure_split(const dgk::KernelCfg* c);
+  // the split-step buffers of variant c (own, or those of the handle's variant)
+  void split_ptrs(dgk::StepArgs& a, const dgk::KernelCfg* c) const;
   dgk::StepArgs args(int mode) const;
   int advance(int nsteps);
   ~Handle();

@@ -238,7 +238,7 @@ struct SolveBatch {
 };
 
 // ---------------------------------------------------------------- kernel body
-template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, bool SPLIT, class Prov>
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT, class Prov>
 __device__ __forceinline__ void step_body(const Prov& prov) {
   using S = Sz<N>;
   using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM>;
@@ -520,12 +520,14 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       if (mbar_wait_bounded(&bars[s ^ 1], uint32_t(((it + 1) >> 1) & 1), err)) issue_gathers(nxt_a, nxt_lb, s ^ 1);
     }
 
-    if constexpr (SPLIT) {
+    if constexpr (SPLIT > 0) {
       // split step, front half: the GEMM inputs leave for the global buffer
-      // X[tile][row][NE] (row: volume inputs, then penalties), 4 elements per float4
+      // X[tile][row][NE] (row: volume inputs, then penalties; NE = SPLIT
+      // elements per tile), 4 elements per float4
       constexpr int NV = MODEL == 0 ? 4 : 12;
       constexpr int KX = NV * Np + Nf * NFN;
-      constexpr int NE = MODEL == 0 ? 64 : 32;
+      constexpr int NE = SPLIT;
+      static_assert(NE % 4 == 0 && (NE % EB == 0 || EB % NE == 0), "element blocks inside column tiles");
       for (int i = tid; i < KX * (EB / 4); i += NT) {
         const int e4 = i % (EB / 4), row = i / (EB / 4);
         const float* src = row < NV * Np ? sXv + row * EBP : sXs + (row - NV * Np) * EBP;
@@ -759,8 +761,9 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
   if (R_SMEM && tid == 0) bulk_wait_all();
 }
 
-// One solve per launch (dg_rhs / dg_step); SPLIT = front half of the split step.
-template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, bool SPLIT = false>
+// One solve per launch (dg_rhs / dg_step); SPLIT > 0: front half of the split
+// step writing X in column tiles of SPLIT elements.
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT = 0>
 __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   SingleSolve p{a, EB};
   step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, SPLIT>(p);
@@ -771,7 +774,7 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
 template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM>
 __global__ void __launch_bounds__(NT) dg_step_batched_kernel(const BatchArgs b) {
   SolveBatch p{b};
-  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, false>(p);
+  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, 0>(p);
 }
 
 }  // namespace dgk

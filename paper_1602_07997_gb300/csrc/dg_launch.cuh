@@ -1,6 +1,7 @@
 // Launch helpers shared by the per-model instantiation units.
 #pragma once
 #include "dg_gemm.cuh"
+#include "dg_tc.cuh"
 
 namespace dgk {
 
@@ -24,10 +25,10 @@ KernelCfg make_cfg() {
   c.smem = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM>::bytes;
   c.fn = dg_step_kernel<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>;
   c.fn_batched = dg_step_batched_kernel<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>;
-  c.split = false;
+  c.split = 0;
   c.fn_gemm = nullptr;
   c.smem_gemm = 0;
-  c.gemm_threads = c.gemm_ne = c.gemm_mt = c.gemm_mtiles = c.gemm_kx = c.gemm_mp2 = 0;
+  c.gemm_threads = c.gemm_ne = c.gemm_mt = c.gemm_mtiles = c.gemm_kx = c.gemm_mp2 = c.gemm_nsplit = 0;
   return c;
 }
 
@@ -37,7 +38,7 @@ KernelCfg make_split_cfg() {
   using SS = SplitShape<MODEL, N>;
   static_assert(Plan<MODEL, N, EB, false, false>::bytes <= 227 * 1024, "shared memory budget");
   static_assert(SS::smem <= 227 * 1024, "shared memory budget (GEMM)");
-  static_assert(SS::NE % EB == 0 || EB % SS::NE == 0, "element blocks inside column tiles");
+
   KernelCfg c;
   c.EB = EB;
   c.TN = 1;
@@ -45,9 +46,9 @@ KernelCfg make_split_cfg() {
   c.ops_smem = false;
   c.r_smem = false;
   c.smem = Plan<MODEL, N, EB, false, false>::bytes;
-  c.fn = dg_step_kernel<MODEL, N, EB, 1, NT, false, false, true>;
+  c.fn = dg_step_kernel<MODEL, N, EB, 1, NT, false, false, SS::NE>;
   c.fn_batched = nullptr;
-  c.split = true;
+  c.split = 1;
   c.fn_gemm = dg_split_gemm_kernel<MODEL, N>;
   c.smem_gemm = SS::smem;
   c.gemm_threads = SS::NT;
@@ -56,6 +57,37 @@ KernelCfg make_split_cfg() {
   c.gemm_mtiles = SS::MP2 / SS::MT;
   c.gemm_kx = SS::KX;
   c.gemm_mp2 = SS::MP2;
+  c.gemm_nsplit = 0;
+  return c;
+}
+
+// Tensor-core split variant: front half with EB elements per block writing X
+// in tiles of the tensor-core kernel's NE, then the tcgen05 kernel with
+// NSPLIT BF16 pieces per operand.
+template <int MODEL, int N, int EB, int NSPLIT, int NT = threads_for<N, EB, 1>()>
+KernelCfg make_tc_cfg() {
+  using TS = TcShape<MODEL, N, NSPLIT>;
+  static_assert(Plan<MODEL, N, EB, false, false>::bytes <= 227 * 1024, "shared memory budget");
+  static_assert(TS::smem <= 227 * 1024, "shared memory budget (tensor-core kernel)");
+  KernelCfg c;
+  c.EB = EB;
+  c.TN = 1;
+  c.NT = NT;
+  c.ops_smem = false;
+  c.r_smem = false;
+  c.smem = Plan<MODEL, N, EB, false, false>::bytes;
+  c.fn = dg_step_kernel<MODEL, N, EB, 1, NT, false, false, TS::NE>;
+  c.fn_batched = nullptr;
+  c.split = 2;
+  c.fn_gemm = dg_tc_gemm_kernel<MODEL, N, NSPLIT>;
+  c.smem_gemm = TS::smem;
+  c.gemm_threads = TS::NT;
+  c.gemm_ne = TS::NE;
+  c.gemm_mt = TS::MT;
+  c.gemm_mtiles = TS::MTILES;
+  c.gemm_kx = TS::KX;
+  c.gemm_mp2 = TS::MTILES * TS::MT;
+  c.gemm_nsplit = NSPLIT;
   return c;
 }
 
