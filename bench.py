@@ -10,7 +10,10 @@ of K*Np*Nf field updates / device time of the step.  The eight meshes hold
 Before the timed region every mesh's kernel variant is autotuned.
 
 Extra keys: per_N (time, updates/s, algorithmic GB/s and GFLOP/s, kernel
-variant per degree), roofline (dominant kernel), cpu_baseline (FP64 oracle on
+variant per degree), sweeps (the same per-degree table for the acoustic
+bf16x6 tensor-core mode and for the elastic model in FP32 and bf16x6, each
+timed over --sweep-steps steps; bf16x6 results are compared with the FP32
+path on the same meshes), roofline (dominant kernel), cpu_baseline (FP64 oracle on
 the host), e2e (same metric through the C ABI with pinned host buffers,
 copies inside the timed region), served (64 acoustic shots, N in {3,5,7},
 500 steps, Poisson arrivals at 0.7 x the batched capacity: p50/p99 latency,
@@ -290,6 +293,102 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def make_solvers(P, cfgs, model, precision, stream, tune):
+    solvers = []
+    for cfg in cfgs:
+        N = cfg["N"]
+        dt = P.suggest_dt(cfg["verts"], cfg["tets"], cfg["coeffs"], N, model, 0.4)
+        g = P.Solver(cfg["verts"], cfg["tets"], cfg["coeffs"], N, model, dt=dt,
+                     stream=stream.cuda_stream, precision=precision)
+        q = np.random.default_rng(N).uniform(-1, 1, size=g.shape).astype(np.float32)
+        g.set_state(q)
+        if tune:
+            g.autotune(5)
+        solvers.append(g)
+    return solvers
+
+
+def launches_per_step(g):
+    return 2 if g.kernel_info()["split"] else 1
+
+
+def per_degree(model, g, ms, pk, tensor=False):
+    """One row of the per-degree table: algorithmic bytes and FLOPs over the
+    measured time, and the roofline that bounds the path (tensor-core modes:
+    the contraction ceiling is far above the FP32 one, so HBM)."""
+    byt, flop = algorithmic(model, g.N, g.K)
+    gbs = byt / (ms * 1e-3) / 1e9
+    gfl = flop / (ms * 1e-3) / 1e9
+    ridge = pk["fp32_tflops"] * 1e3 / pk["hbm_gbs"]
+    bound = "hbm" if (tensor or flop / byt < ridge) else "alu"
+    frac = gbs / pk["hbm_gbs"] if bound == "hbm" else gfl / (pk["fp32_tflops"] * 1e3)
+    return {"K": g.K, "nodes": g.K * g.Np, "ms": round(ms, 5), "kernel": g.kernel_info(),
+            "updates_per_s": g.K * g.Np * g.Nf / (ms * 1e-3),
+            "alg_GBs": round(gbs, 1), "alg_GFLOPs": round(gfl, 1),
+            "bound": bound, "roofline_frac": round(frac, 4)}
+
+
+def time_sweep(solvers, steps, stream):
+    """Per-degree mean step time (CUDA events on the solvers' stream)."""
+    import torch
+    for g in solvers:
+        g.step(2)
+    torch.cuda.synchronize()
+    out = []
+    for g in solvers:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        g.sync()
+        out.append(e0.elapsed_time(e1) / steps)
+    return out
+
+
+def extra_sweeps(P, args, acoustic_cfgs, stream, pk):
+    """Acoustic bf16x6 on the headline meshes; elastic FP32 and bf16x6 on the
+    elastic sweep meshes (lambda, mu, rho ~ U[1,3] with a two-layer jump).
+    For each bf16x6 mesh the state after --sweep-steps steps is compared with
+    the FP32 path's (relative L2)."""
+    Ns = [cfg["N"] for cfg in acoustic_cfgs]
+    res = {}
+    for model, cfgs in (("acoustic", acoustic_cfgs), ("elastic", None)):
+        if cfgs is None:
+            cfgs = build_meshes(model, Ns)
+        precs = ("bf16x6",) if model == "acoustic" else ("fp32", "bf16x6")
+        ref_states = {}
+        if model == "acoustic":
+            ref = make_solvers(P, cfgs, model, "fp32", stream, False)
+            for g in ref:
+                g.step(2 + args.sweep_steps)  # as many steps as time_sweep takes
+                g.sync()
+                ref_states[g.N] = g.get_state()
+                g.close()
+        for prec in precs:
+            solvers = make_solvers(P, cfgs, model, prec, stream, not args.no_tune)
+            ms = time_sweep(solvers, args.sweep_steps, stream)
+            rows = {}
+            for g, t in zip(solvers, ms):
+                rows[str(g.N)] = per_degree(model, g, t, pk, tensor=prec != "fp32")
+            if prec != "fp32" or model == "elastic":
+                # states after 2 + sweep_steps steps from the same initial state
+                for g in solvers:
+                    if prec == "fp32":
+                        ref_states[g.N] = g.get_state()
+                    elif g.N in ref_states:
+                        a = g.get_state().astype(np.float64)
+                        b = ref_states[g.N].astype(np.float64)
+                        rows[str(g.N)]["rel_l2_vs_fp32"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+            tot = sum(ms)
+            upd = sum(g.K * g.Np * g.Nf for g in solvers)
+            res["%s_%s" % (model, prec)] = {"per_N": rows, "ms_per_sweep_step": round(tot, 4),
+                                            "updates_per_s": upd / (tot * 1e-3), "steps": args.sweep_steps}
+            for g in solvers:
+                g.close()
+    return res
+
+
 def run(args, rank, world, local_rank):
     import torch
     import paper_1602_07997_gb300 as P
@@ -300,17 +399,7 @@ def run(args, rank, world, local_rank):
     Ns = [int(x) for x in args.degrees.split(",")]
     stream = torch.cuda.Stream(device=dev)
     cfgs = build_meshes(model, Ns)
-    solvers = []
-    for cfg in cfgs:
-        N = cfg["N"]
-        dt = P.suggest_dt(cfg["verts"], cfg["tets"], cfg["coeffs"], N, model, 0.4)
-        g = P.Solver(cfg["verts"], cfg["tets"], cfg["coeffs"], N, model, dt=dt,
-                     stream=stream.cuda_stream)
-        q = np.random.default_rng(N).uniform(-1, 1, size=g.shape).astype(np.float32)
-        g.set_state(q)
-        if not args.no_tune:
-            g.autotune(5)
-        solvers.append(g)
+    solvers = make_solvers(P, cfgs, model, "fp32", stream, not args.no_tune)
     torch.cuda.synchronize()
 
     def barrier():
@@ -351,19 +440,12 @@ def run(args, rank, world, local_rank):
     per_N = {}
     dom = None
     for g, ms in zip(solvers, per_ms):
-        byt, flop = algorithmic(model, g.N, g.K)
-        gbs = byt / (ms * 1e-3) / 1e9
-        gfl = flop / (ms * 1e-3) / 1e9
-        intensity = flop / byt
-        ridge = pk["fp32_tflops"] * 1e3 / pk["hbm_gbs"]
-        bound = "hbm" if intensity < ridge else "alu"
-        frac = gbs / pk["hbm_gbs"] if bound == "hbm" else gfl / (pk["fp32_tflops"] * 1e3)
-        per_N[str(g.N)] = {"K": g.K, "nodes": g.K * g.Np, "ms": round(ms, 5), "kernel": g.kernel_info(),
-                           "updates_per_s": g.K * g.Np * g.Nf / (ms * 1e-3),
-                           "alg_GBs": round(gbs, 1), "alg_GFLOPs": round(gfl, 1),
-                           "bound": bound, "roofline_frac": round(frac, 4)}
+        row = per_degree(model, g, ms, pk)
+        per_N[str(g.N)] = row
         if dom is None or ms > dom[1]:
-            dom = (g, ms, byt, flop, bound)
+            byt, flop = algorithmic(model, g.N, g.K)
+            dom = (g, ms, byt, flop, row["bound"])
+    launches = sum(launches_per_step(g) for g in solvers) * args.steps
     g, ms, byt, flop, bound = dom
     traffic = None
     try:
@@ -408,6 +490,12 @@ def run(args, rank, world, local_rank):
                "d2h_bytes_per_step": nbytes, "steps": e_steps,
                "note": "per step and mesh: dg_set_state(pinned host q) + dg_step(1) + dg_get_state(pinned host)"}
 
+    for s in solvers:
+        s.close()
+    sweeps = None
+    if rank == 0 and not args.no_sweeps:
+        sweeps = extra_sweeps(P, args, cfgs, stream, pk)
+
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         cpu = cpu_baseline(model, Ns=(2, 4), steps=1)
@@ -424,11 +512,9 @@ def run(args, rank, world, local_rank):
                            "meshes": {str(g.N): g.K for g in solvers},
                            "l2": "inputs larger than L2: the 8 meshes hold ~1.3 GB, each ~130 MB",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "gpu_launches": nN * args.steps, "roofline": roof, "per_N": per_N,
+                "gpu_launches": launches, "roofline": roof, "per_N": per_N, "sweeps": sweeps,
                 "cpu_baseline": cpu, "e2e": e2e, "served": served, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
-    for g in solvers:
-        g.close()
 
 
 def kernel_rev():
@@ -456,6 +542,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-steps", type=int, default=500)
+    ap.add_argument("--no-sweeps", action="store_true")
+    ap.add_argument("--sweep-steps", type=int, default=50)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -159,7 +159,11 @@ int dg_autotune(dg_handle *h, int reps, int *block_elems, double *ms_per_step, d
  * allocated on first use).  Pointers may be NULL.                           */
 int dg_kernel_info(const dg_handle *h, int *block_elems, int *threads, int64_t *smem_bytes,
                    int *variants, int *tile_elems, int *split);
-/* Select compiled variant `index` (0 <= index < variants) for this handle.  */
+/* Select compiled variant `index` (0 <= index < variants of the handle's
+ * precision mode) for this handle and, like dg_autotune, for handles created
+ * later in the process on the same device, model, N and precision (servers
+ * fix their variant per (model, N) at the first admission).  DG_EINVAL for
+ * an index out of range.                                                    */
 int dg_set_variant(dg_handle *h, int index);
 
 /* The paper has no counterpart to this entry point.  Same result as

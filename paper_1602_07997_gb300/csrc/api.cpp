@@ -301,6 +301,7 @@ int Handle::ensure_split(const dgk::KernelCfg* c) {
     pack_tc_ops(ref, c->gemm_nsplit, c->gemm_mtiles, blob);
     const size_t obytes = (blob.size() * 2 + 255) & ~size_t(255);
     DG_CUDA(cudaMalloc(&d_tc, xbytes + obytes));
+    split_bytes += xbytes + obytes;
     d_opstc = d_tc;
     d_xtc = reinterpret_cast<float*>(static_cast<char*>(d_tc) + obytes);
     DG_CUDA(cudaMemsetAsync(d_xtc, 0, xbytes, stream));
@@ -321,6 +322,7 @@ int Handle::ensure_split(const dgk::KernelCfg* c) {
     for (int i = 0; i < Np; ++i) ops2[size_t(3 * Np + cc) * MP2 + i] = float(ref.LIFT[size_t(i) * 4 * Nfp + cc]);
   const size_t obytes = (ops2.size() * 4 + 255) & ~size_t(255);
   DG_CUDA(cudaMalloc(&d_split, xbytes + obytes));
+  split_bytes += xbytes + obytes;
   d_ops2 = static_cast<float*>(d_split);
   d_x = reinterpret_cast<float*>(static_cast<char*>(d_split) + obytes);
   DG_CUDA(cudaMemsetAsync(d_x, 0, xbytes, stream));
@@ -645,6 +647,10 @@ int dg_set_variant(dg_handle* h, int index) {
   const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n, h->opts.precision);
   if (index < 0 || index >= n) return fail(DG_EINVAL, "variant index out of range");
   h->cfg = &v[index];
+  {
+    std::lock_guard<std::mutex> lock(dg::g_tune_mu);
+    dg::g_tuned[std::make_tuple(h->device, h->model, h->N, h->opts.precision)] = index;
+  }
   return DG_OK;
 }
 

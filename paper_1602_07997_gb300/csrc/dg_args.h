@@ -65,6 +65,7 @@ struct SolveDev {
   int qcur;              // q[qcur] holds q^m
   int r1slot;            // r[r1slot] holds r^{m-1}
   int steps_left;        // the advance kernel stops moving a solve at 0
+  float* xg;             // split step: the solve's GEMM input buffer
 };
 
 struct BatchArgs {
@@ -76,6 +77,11 @@ struct BatchArgs {
   const float* ops;      // operators of the batch's (model, N)
   const int* ftab;
   int* err;
+  // split step: row-padded operators and the GEMM tiles of every solve
+  const float* ops2;
+  const int* tile_start;   // [nsolves + 1] first global tile of each solve
+  const int* tile_solve;   // [total_tiles] solve of each global tile
+  int total_tiles;
 };
 
 // Host-visible launch configuration of one (model, N) instantiation.  A
@@ -90,8 +96,10 @@ struct KernelCfg {
   void (*fn_batched)(BatchArgs);
   int split;
   void (*fn_gemm)(StepArgs);
+  void (*fn_gemm_batched)(BatchArgs);  // split step of a batch (FP32 GEMM only)
   size_t smem_gemm;
   int gemm_threads, gemm_ne, gemm_mt, gemm_mtiles, gemm_kx, gemm_mp2, gemm_nsplit;
+  bool gemm_persistent;  // grid = min(tiles, SMs x resident CTAs) instead of one CTA per tile
 };
 
 // Compiled variants of one (model, N): different elements per block (EB) and
@@ -102,7 +110,8 @@ const KernelCfg* kernel_cfg(int model, int N);
 
 // Launch the persistent step kernel on `stream` (grid = min(blocks, SMs x occupancy)).
 cudaError_t launch_step(const KernelCfg* cfg, const StepArgs& args, cudaStream_t stream);
-// One batched step over every solve of `args` (same model and N).
+// One batched step over every solve of `args` (same model and N); a split
+// variant launches the batched front half and then the batched GEMM.
 cudaError_t launch_step_batched(const KernelCfg* cfg, const BatchArgs& args, cudaStream_t stream);
 // Advance the device-side step state of the solves (one thread per solve).
 cudaError_t launch_advance(SolveDev* solves, int nsolves, cudaStream_t stream);

@@ -68,23 +68,17 @@ cudaError_t launch_step(const KernelCfg* c, const StepArgs& args, cudaStream_t s
   void* params[] = {&a};
   e = cudaLaunchKernel(reinterpret_cast<const void*>(c->fn), dim3(grid), dim3(c->NT), params, c->smem, stream);
   if (e != cudaSuccess || !c->split) return e;
-  {
-    // the GEMM kernel: column tiles of gemm_ne elements x row tiles of gemm_mt
-    int dev = 0;
-    e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lock(g_mu);
-    auto key = std::make_pair(dev, reinterpret_cast<const void*>(c->fn_gemm));
-    if (g_cap.find(key) == g_cap.end()) {
-      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(c->fn_gemm),
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(c->smem_gemm));
-      if (e != cudaSuccess) return e;
-      g_cap[key] = 1;
-    }
-  }
-  const int ntiles = (args.K + c->gemm_ne - 1) / c->gemm_ne;
-  return cudaLaunchKernel(reinterpret_cast<const void*>(c->fn_gemm), dim3(unsigned(c->gemm_mtiles) * unsigned(ntiles)),
-                          dim3(c->gemm_threads), params, c->smem_gemm, stream);
+  // the GEMM kernel: column tiles of gemm_ne elements x row tiles of gemm_mt
+  KernelCfg g = *c;
+  g.NT = c->gemm_threads;
+  g.smem = c->smem_gemm;
+  int gcap = 0;
+  e = prepare_fn(&g, reinterpret_cast<const void*>(c->fn_gemm), &gcap);
+  if (e != cudaSuccess) return e;
+  const unsigned tiles = unsigned(c->gemm_mtiles) * unsigned((args.K + c->gemm_ne - 1) / c->gemm_ne);
+  const unsigned ggrid = c->gemm_persistent && tiles > unsigned(gcap) ? unsigned(gcap) : tiles;
+  return cudaLaunchKernel(reinterpret_cast<const void*>(c->fn_gemm), dim3(ggrid), dim3(c->gemm_threads), params,
+                          c->smem_gemm, stream);
 }
 
 __global__ void advance_kernel(SolveDev* s, int n) {
@@ -98,16 +92,29 @@ __global__ void advance_kernel(SolveDev* s, int n) {
 }
 
 cudaError_t launch_step_batched(const KernelCfg* c, const BatchArgs& args, cudaStream_t stream) {
-  if (!c || !c->fn_batched || c->split) return cudaErrorInvalidValue;
+  if (!c || !c->fn_batched) return cudaErrorInvalidValue;
+  if (c->split && (!c->fn_gemm_batched || (args.total_blocks > 0 && (!args.ops2 || !args.tile_solve))))
+    return cudaErrorInvalidValue;
   int cap = 0;
   cudaError_t e = prepare_fn(c, reinterpret_cast<const void*>(c->fn_batched), &cap);
   if (e != cudaSuccess) return e;
+  int gcap = 0;
+  if (c->split) {
+    KernelCfg g = *c;
+    g.NT = c->gemm_threads;
+    g.smem = c->smem_gemm;
+    e = prepare_fn(&g, reinterpret_cast<const void*>(c->fn_gemm_batched), &gcap);
+    if (e != cudaSuccess) return e;
+  }
   if (args.total_blocks == 0) return cudaSuccess;
   const int grid = args.total_blocks < cap ? args.total_blocks : cap;
   BatchArgs a = args;
   void* params[] = {&a};
-  return cudaLaunchKernel(reinterpret_cast<const void*>(c->fn_batched), dim3(grid), dim3(c->NT), params,
-                          c->smem, stream);
+  e = cudaLaunchKernel(reinterpret_cast<const void*>(c->fn_batched), dim3(grid), dim3(c->NT), params, c->smem,
+                       stream);
+  if (e != cudaSuccess || !c->split || args.total_tiles == 0) return e;
+  return cudaLaunchKernel(reinterpret_cast<const void*>(c->fn_gemm_batched), dim3(unsigned(args.total_tiles)),
+                          dim3(c->gemm_threads), params, c->smem_gemm, stream);
 }
 
 cudaError_t launch_advance(SolveDev* solves, int nsolves, cudaStream_t stream) {

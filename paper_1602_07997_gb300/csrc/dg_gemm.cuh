@@ -53,7 +53,7 @@ struct SplitShape {
 };
 
 template <int MODEL, int N>
-__global__ void __launch_bounds__(SplitShape<MODEL, N>::NT) dg_split_gemm_kernel(const StepArgs a) {
+__device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mtile, const int ntile) {
   using S = Sz<N>;
   using SS = SplitShape<MODEL, N>;
   constexpr int Np = S::Np, NFN = S::NFN, Nf = SS::Nf, NV = SS::NV, KX = SS::KX, NE = SS::NE, TN = SS::TN;
@@ -66,10 +66,6 @@ __global__ void __launch_bounds__(SplitShape<MODEL, N>::NT) dg_split_gemm_kernel
   float* sB[2] = {smem + 2 * SS::nA, smem + 2 * SS::nA + SS::nB};
 
   const int tid = threadIdx.x;
-  // row tiles fastest: the CTAs that share a column tile of X run together and
-  // read it from L2
-  constexpr int MTILES = MP2 / MT;
-  const int mtile = blockIdx.x % MTILES, ntile = blockIdx.x / MTILES;
   const int row0 = mtile * MT;
   const float* X = a.xg + size_t(ntile) * SS::x_floats_per_tile;
   const float* OP = a.ops2;  // [3 Np + NFN][MP2]
@@ -286,6 +282,26 @@ __global__ void __launch_bounds__(SplitShape<MODEL, N>::NT) dg_split_gemm_kernel
       }
     }
   }
+}
+
+// One solve: row tiles fastest, so that the CTAs that share a column tile of
+// X run together and read it from L2.
+template <int MODEL, int N>
+__global__ void __launch_bounds__(SplitShape<MODEL, N>::NT) dg_split_gemm_kernel(const StepArgs a) {
+  constexpr int MTILES = SplitShape<MODEL, N>::MP2 / SplitShape<MODEL, N>::MT;
+  split_gemm_body<MODEL, N>(a, int(blockIdx.x) % MTILES, int(blockIdx.x) / MTILES);
+}
+
+// Every solve of a batch: global tile -> (solve, local tile) through the
+// batch's tile tables, the solve's arguments from its device-side state.
+template <int MODEL, int N>
+__global__ void __launch_bounds__(SplitShape<MODEL, N>::NT) dg_split_gemm_batched_kernel(const BatchArgs b) {
+  constexpr int MTILES = SplitShape<MODEL, N>::MP2 / SplitShape<MODEL, N>::MT;
+  const int so = __ldg(b.tile_solve + blockIdx.x);
+  const int lt = int(blockIdx.x) - __ldg(b.tile_start + so);
+  StepArgs a;
+  solve_args(b, b.solves[so], a);
+  split_gemm_body<MODEL, N>(a, lt % MTILES, lt / MTILES);
 }
 
 }  // namespace dgk

@@ -33,6 +33,7 @@ struct Handle {
   // device memory: one allocation carved into the pieces below
   void* d_base = nullptr;
   size_t device_bytes = 0, state_bytes = 0;
+  size_t split_bytes = 0;  // split-step buffers allocated on first use
   float* d_q[2] = {nullptr, nullptr};  // ping-pong q^m / q^{m+1}
   float* d_r[2] = {nullptr, nullptr};  // AB3 history slots
   float* d_geo = nullptr;  // element records, dgk::Rec layout

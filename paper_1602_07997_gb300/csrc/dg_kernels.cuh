@@ -201,13 +201,9 @@ struct SingleSolve {
   __device__ int mode() const { return a.mode; }
 };
 
-struct SolveBatch {
-  const BatchArgs& B;
-  __device__ int nblocks() const { return B.total_blocks; }
-  __device__ void get(int b, StepArgs& A, int& lb) const {
-    const int lo = __ldg(B.block_solve + b);  // solve of global block b
-    const SolveDev& d = B.solves[lo];
-    lb = b - __ldg(B.block_start + lo);
+// Step arguments of one solve of a batch, from its device-side state.
+__device__ __forceinline__ void solve_args(const BatchArgs& B, const SolveDev& d, StepArgs& A) {
+  {
     const int qc = d.qcur, r1s = d.r1slot;
     A.q = d.q[qc];
     A.qn = d.q[1 - qc];
@@ -230,6 +226,19 @@ struct SolveBatch {
     else if (d.have == 1) { A.a1 = 1.5f; A.a2 = -0.5f; A.a3 = 0.f; }
     else { A.a1 = 23.f / 12.f; A.a2 = -16.f / 12.f; A.a3 = 5.f / 12.f; }
     A.err = B.err;
+    A.xg = d.xg;
+    A.ops2 = B.ops2;
+    A.opstc = nullptr;
+  }
+}
+
+struct SolveBatch {
+  const BatchArgs& B;
+  __device__ int nblocks() const { return B.total_blocks; }
+  __device__ void get(int b, StepArgs& A, int& lb) const {
+    const int lo = __ldg(B.block_solve + b);  // solve of global block b
+    lb = b - __ldg(B.block_start + lo);
+    solve_args(B, B.solves[lo], A);
   }
   __device__ const float* ops() const { return B.ops; }
   __device__ const int* ftab() const { return B.ftab; }
@@ -770,11 +779,12 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
 }
 
 // Every solve of a batch (same model and N) in one persistent launch; the
-// per-solve step index, AB3 phase and buffer parity are read from device memory.
-template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM>
+// per-solve step index, AB3 phase and buffer parity are read from device
+// memory.  SPLIT > 0: front half of the batch's split step.
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT = 0>
 __global__ void __launch_bounds__(NT) dg_step_batched_kernel(const BatchArgs b) {
   SolveBatch p{b};
-  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, 0>(p);
+  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, SPLIT>(p);
 }
 
 }  // namespace dgk

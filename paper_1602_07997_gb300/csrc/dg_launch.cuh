@@ -27,8 +27,10 @@ KernelCfg make_cfg() {
   c.fn_batched = dg_step_batched_kernel<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>;
   c.split = 0;
   c.fn_gemm = nullptr;
+  c.fn_gemm_batched = nullptr;
   c.smem_gemm = 0;
   c.gemm_threads = c.gemm_ne = c.gemm_mt = c.gemm_mtiles = c.gemm_kx = c.gemm_mp2 = c.gemm_nsplit = 0;
+  c.gemm_persistent = false;
   return c;
 }
 
@@ -47,9 +49,10 @@ KernelCfg make_split_cfg() {
   c.r_smem = false;
   c.smem = Plan<MODEL, N, EB, false, false>::bytes;
   c.fn = dg_step_kernel<MODEL, N, EB, 1, NT, false, false, SS::NE>;
-  c.fn_batched = nullptr;
+  c.fn_batched = dg_step_batched_kernel<MODEL, N, EB, 1, NT, false, false, SS::NE>;
   c.split = 1;
   c.fn_gemm = dg_split_gemm_kernel<MODEL, N>;
+  c.fn_gemm_batched = dg_split_gemm_batched_kernel<MODEL, N>;
   c.smem_gemm = SS::smem;
   c.gemm_threads = SS::NT;
   c.gemm_ne = SS::NE;
@@ -58,6 +61,7 @@ KernelCfg make_split_cfg() {
   c.gemm_kx = SS::KX;
   c.gemm_mp2 = SS::MP2;
   c.gemm_nsplit = 0;
+  c.gemm_persistent = false;
   return c;
 }
 
@@ -80,6 +84,7 @@ KernelCfg make_tc_cfg() {
   c.fn_batched = nullptr;
   c.split = 2;
   c.fn_gemm = dg_tc_gemm_kernel<MODEL, N, NSPLIT>;
+  c.fn_gemm_batched = nullptr;
   c.smem_gemm = TS::smem;
   c.gemm_threads = TS::NT;
   c.gemm_ne = TS::NE;
@@ -88,6 +93,7 @@ KernelCfg make_tc_cfg() {
   c.gemm_kx = TS::KX;
   c.gemm_mp2 = TS::MTILES * TS::MT;
   c.gemm_nsplit = NSPLIT;
+  c.gemm_persistent = true;
   return c;
 }
 

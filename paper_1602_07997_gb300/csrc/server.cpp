@@ -77,7 +77,10 @@ struct Group {
   dgk::SolveDev* d_solves = nullptr;
   int* d_block_start = nullptr;
   int* d_block_solve = nullptr;
-  int capacity = 0, block_capacity = 0;
+  int* d_tile_start = nullptr;  // split step: GEMM tiles of each solve
+  int* d_tile_solve = nullptr;
+  int capacity = 0, block_capacity = 0, tile_capacity = 0;
+  int total_blocks = 0, total_tiles = 0;
 };
 
 }  // namespace
@@ -98,6 +101,9 @@ struct Server {
   std::vector<std::unique_ptr<Active>> active;
   std::vector<std::unique_ptr<Active>> ready;  // set up, waiting for the next chunk boundary
   std::map<std::pair<int, int>, Group> groups;
+  // kernel variant of each (model, N): the autotuned FP32 choice of the
+  // process when it has a batched form, fixed at the first admission
+  std::map<std::pair<int, int>, const dgk::KernelCfg*> cfg_of;
   size_t active_bytes = 0;  // admitted (ready + active)
   int admitted = 0;
   std::atomic<int64_t> launches{0};
@@ -115,11 +121,14 @@ struct Server {
   void fail_request(const std::shared_ptr<Request>& r, int code, const std::string& msg);
 };
 
-static size_t estimate_bytes(const Request& r) {
+static size_t estimate_bytes(const Request& r, const dgk::KernelCfg* cfg) {
   const int Np = num_nodes(r.N), Nf = num_fields(r.model), Nfp = num_face_nodes(r.N);
   const size_t K = r.tets.size() / 4 + 132;
   const size_t Mpad = size_t((Np + 3) & ~3), KD = size_t(3 * Np + 4 * Nfp);
-  return 4 * K * Nf * Np * 4 + K * (25 * 4 + 16) + KD * Mpad * 4 + r.amp.size() * 4 + (size_t(1) << 20);
+  size_t b = 4 * K * Nf * Np * 4 + K * (25 * 4 + 16) + KD * Mpad * 4 + r.amp.size() * 4 + (size_t(1) << 20);
+  if (cfg && cfg->split)  // GEMM inputs and the row-padded operators
+    b += (K / cfg->gemm_ne + 2) * size_t(cfg->gemm_kx) * cfg->gemm_ne * 4 + KD * size_t(cfg->gemm_mp2) * 4;
+  return b;
 }
 
 void Server::fail_request(const std::shared_ptr<Request>& r, int code, const std::string& msg) {
@@ -131,7 +140,20 @@ void Server::fail_request(const std::shared_ptr<Request>& r, int code, const std
 }
 
 bool Server::admit_one(std::shared_ptr<Request> r) {
-  const size_t need = estimate_bytes(*r);
+  const dgk::KernelCfg* cfg = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(r->model, r->N);
+    auto it = cfg_of.find(key);
+    if (it != cfg_of.end()) {
+      cfg = it->second;
+    } else {
+      cfg = dg::select_variant(r->model, r->N, 0, device, DG_FP32);
+      if (!cfg || !cfg->fn_batched) cfg = dgk::kernel_cfg(r->model, r->N);
+      cfg_of[key] = cfg;
+    }
+  }
+  const size_t need = estimate_bytes(*r, cfg);
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return false;
   bool nothing_admitted;
@@ -173,7 +195,10 @@ bool Server::admit_one(std::shared_ptr<Request> r) {
   o.block_elems = 0;
   dg_handle* h = nullptr;
   int rc = dg_setup(&m, r->coeffs.data(), r->N, r->model, &o, &h);
-  if (rc == DG_OK) h->cfg = dgk::kernel_cfg(r->model, r->N);  // batched launches use the fused default
+  if (rc == DG_OK) {
+    h->cfg = cfg;  // the group's batched variant
+    rc = h->ensure_split(cfg);
+  }
   if (rc == DG_OK && !r->q0.empty()) rc = dg_set_state(h, r->q0.data(), nullptr, nullptr, 0, 0);
   if (rc == DG_OK && r->has_src) rc = dg_set_source(h, r->xs, r->dir, r->amp.data(), int64_t(r->amp.size()));
   auto a = std::make_unique<Active>();
@@ -195,7 +220,7 @@ bool Server::admit_one(std::shared_ptr<Request> r) {
   a->steps_left = r->nsteps;
   {
     std::lock_guard<std::mutex> lock(mu);
-    active_bytes += h->device_bytes;
+    active_bytes += h->device_bytes + h->split_bytes;
     ++admitted;
     ready.push_back(std::move(a));
   }
@@ -243,6 +268,24 @@ void Server::prep_loop() {
   }
 }
 
+// Launch arguments of a group's batched step (tables built by rebuild).
+static dgk::BatchArgs batch_args(const Group& g, int* d_err) {
+  dgk::BatchArgs b{};
+  b.solves = g.d_solves;
+  b.block_start = g.d_block_start;
+  b.block_solve = g.d_block_solve;
+  b.nsolves = int(g.members.size());
+  b.total_blocks = g.total_blocks;
+  b.ops = g.members[0]->h->d_ops;
+  b.ftab = g.members[0]->h->d_ftab;
+  b.err = d_err;
+  b.ops2 = g.members[0]->h->d_ops2;
+  b.tile_start = g.d_tile_start;
+  b.tile_solve = g.d_tile_solve;
+  b.total_tiles = g.total_tiles;
+  return b;
+}
+
 // Device-side solve tables and the tick graph for the current active set.
 int Server::rebuild() {
   if (graph) {
@@ -256,14 +299,16 @@ int Server::rebuild() {
     if (n > g.capacity) {
       if (g.d_solves) cudaFree(g.d_solves);
       if (g.d_block_start) cudaFree(g.d_block_start);
+      if (g.d_tile_start) cudaFree(g.d_tile_start);
       g.capacity = std::max(n, 8);
       if (cudaMalloc(&g.d_solves, sizeof(dgk::SolveDev) * g.capacity) != cudaSuccess ||
-          cudaMalloc(&g.d_block_start, sizeof(int) * (g.capacity + 1)) != cudaSuccess)
+          cudaMalloc(&g.d_block_start, sizeof(int) * (g.capacity + 1)) != cudaSuccess ||
+          cudaMalloc(&g.d_tile_start, sizeof(int) * (g.capacity + 1)) != cudaSuccess)
         return fail(DG_ENOMEM, "server tables");
     }
     std::vector<dgk::SolveDev> sd(n);
-    std::vector<int> bs(n + 1, 0);
-    std::vector<int> bsolve;
+    std::vector<int> bs(n + 1, 0), ts(n + 1, 0);
+    std::vector<int> bsolve, tsolve;
     for (int i = 0; i < n; ++i) {
       const Active* a = g.members[i];
       const dg_handle* h = a->h;
@@ -288,9 +333,26 @@ int Server::rebuild() {
       d.qcur = h->qcur;
       d.r1slot = h->r1slot;
       d.steps_left = a->steps_left;
+      d.xg = h->d_x;
       bs[i + 1] = bs[i] + int((h->K + g.cfg->EB - 1) / g.cfg->EB);
       bsolve.insert(bsolve.end(), size_t(bs[i + 1] - bs[i]), i);
+      ts[i + 1] = ts[i] + (g.cfg->split ? g.cfg->gemm_mtiles * int((h->K + g.cfg->gemm_ne - 1) / g.cfg->gemm_ne) : 0);
+      tsolve.insert(tsolve.end(), size_t(ts[i + 1] - ts[i]), i);
     }
+    g.total_blocks = bs[n];
+    g.total_tiles = ts[n];
+    if (int(tsolve.size()) > g.tile_capacity) {
+      if (g.d_tile_solve) cudaFree(g.d_tile_solve);
+      g.tile_capacity = int(tsolve.size()) * 2;
+      if (cudaMalloc(&g.d_tile_solve, sizeof(int) * g.tile_capacity) != cudaSuccess)
+        return fail(DG_ENOMEM, "server tile table");
+    }
+    if (!tsolve.empty() && cudaMemcpyAsync(g.d_tile_solve, tsolve.data(), sizeof(int) * tsolve.size(),
+                                           cudaMemcpyHostToDevice, stream) != cudaSuccess)
+      return fail(DG_ECUDA, "server tile table upload");
+    if (cudaMemcpyAsync(g.d_tile_start, ts.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, stream) !=
+        cudaSuccess)
+      return fail(DG_ECUDA, "server tile table upload");
     if (int(bsolve.size()) > g.block_capacity) {
       if (g.d_block_solve) cudaFree(g.d_block_solve);
       g.block_capacity = int(bsolve.size()) * 2;
@@ -311,15 +373,10 @@ int Server::rebuild() {
   for (auto& kv : groups) {
     Group& g = kv.second;
     if (g.members.empty()) continue;
-    dgk::BatchArgs b{};
-    b.solves = g.d_solves;
-    b.block_start = g.d_block_start;
-    b.block_solve = g.d_block_solve;
+    dgk::BatchArgs b = batch_args(g, d_err);
     b.nsolves = 0;
     b.total_blocks = 0;
-    b.ops = g.members[0]->h->d_ops;
-    b.ftab = g.members[0]->h->d_ftab;
-    b.err = d_err;
+    b.total_tiles = 0;
     if (dgk::launch_step_batched(g.cfg, b, stream) != cudaSuccess) return fail(DG_ECUDA, "batched warm-up");
   }
   cudaGraph_t gr = nullptr;
@@ -330,17 +387,7 @@ int Server::rebuild() {
     Group& g = kv.second;
     const int n = int(g.members.size());
     if (n == 0) continue;
-    dgk::BatchArgs b{};
-    b.solves = g.d_solves;
-    b.block_start = g.d_block_start;
-    b.block_solve = g.d_block_solve;
-    b.nsolves = n;
-    int total = 0;
-    for (const Active* a : g.members) total += int((a->h->K + g.cfg->EB - 1) / g.cfg->EB);
-    b.total_blocks = total;
-    b.ops = g.members[0]->h->d_ops;
-    b.ftab = g.members[0]->h->d_ftab;
-    b.err = d_err;
+    dgk::BatchArgs b = batch_args(g, d_err);
     if (e == cudaSuccess) e = dgk::launch_step_batched(g.cfg, b, stream);
   }
   for (auto& kv : groups) {
@@ -371,7 +418,7 @@ void Server::retire(Active* a, int status) {
   }
   {
     std::lock_guard<std::mutex> lock(mu);
-    active_bytes -= std::min(active_bytes, h->device_bytes);
+    active_bytes -= std::min(active_bytes, h->device_bytes + h->split_bytes);
     --admitted;
   }
   cv.notify_all();
@@ -476,6 +523,8 @@ Server::~Server() {
     if (kv.second.d_solves) cudaFree(kv.second.d_solves);
     if (kv.second.d_block_start) cudaFree(kv.second.d_block_start);
     if (kv.second.d_block_solve) cudaFree(kv.second.d_block_solve);
+    if (kv.second.d_tile_start) cudaFree(kv.second.d_tile_start);
+    if (kv.second.d_tile_solve) cudaFree(kv.second.d_tile_solve);
   }
   if (graph) cudaGraphExecDestroy(graph);
   if (d_err) cudaFree(d_err);

@@ -139,3 +139,35 @@ def test_requests_join_a_running_batch(P):
     assert srv.poll(t_long) is None    # the long solve is still running
     srv.wait(t_long)
     srv.close()
+
+
+@pytest.mark.gpu
+def test_batched_split_step_equals_solo_runs(P):
+    """A server whose (model, N) variant is the split step (batched front half +
+    batched operator GEMM) gives every request the bits of its solo run."""
+    N = 5
+    probe = _req(50, N, 2, 1, with_src=False)
+    g = P.Solver(probe["verts"], probe["tets"], probe["coeffs"], N, "acoustic", dt=1e-3)
+    split = [i for i in range(g.kernel_info()["variants"]) if (g.set_variant(i) or g.kernel_info()["split"])]
+    assert split, "no split variant compiled for this degree"
+    g.set_variant(split[0])  # recorded for later handles and servers of the process
+    g.close()
+    try:
+        reqs = [_req(51, N, 3, 30), _req(52, N, 2, 45), _req(53, N, 4, 12, with_src=False)]
+        srv = P.Server()
+        tickets, expect = [], []
+        for r in reqs:
+            dt = P.suggest_dt(r["verts"], r["tets"], r["coeffs"], N, "acoustic")
+            amp = W.ricker(np.arange(r["steps"]) * dt, f0=4.0, t0=0.05)
+            q0, out = _alone(P, r, dt, amp)
+            expect.append(out)
+            tickets.append(srv.submit(r["verts"], r["tets"], r["coeffs"], N, q0=q0, dt=dt,
+                                      nsteps=r["steps"], source=r["src"], amp=amp))
+        for t, e in zip(tickets, expect):
+            q, _ = srv.wait(t)
+            assert np.array_equal(q, e)
+        srv.close()
+    finally:
+        g = P.Solver(probe["verts"], probe["tets"], probe["coeffs"], N, "acoustic", dt=1e-3)
+        g.set_variant(0)
+        g.close()
