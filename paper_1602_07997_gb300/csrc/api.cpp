@@ -253,10 +253,10 @@ static double bf16_value(uint16_t b) {
   return double(f);
 }
 
-// Tensor-core split step: X[tiles + 1][KX][NE] (FP32; the extra tile keeps the
-// 16-row chunk copies of the last tile inside the allocation) and the operator
-// pieces.  For every 128-row tile of output nodes, chunk c of 16 input indices
-// holds D_r, D_s, D_t (volume chunks) or LIFT (lift chunks), each as nsplit BF16
+// Tensor-core split step: the front half's BF16 input pieces (one block per
+// column tile of gemm_ne elements, one spare tile) and the operator pieces.
+// For every 128-row tile of output nodes, chunk c of 16 input indices holds
+// D_r, D_s, D_t (volume chunks) or LIFT (lift chunks), each as nsplit BF16
 // pieces x = x_0 + x_1 (+ x_2) of the double-precision entry, every piece in
 // the no-swizzle K-major core-matrix layout [16 row groups][2 K halves][8 rows][8].
 static int pack_tc_ops(const RefElement& R, int nsplit, int mtiles, std::vector<uint16_t>& blob) {
@@ -296,7 +296,7 @@ int Handle::ensure_split(const dgk::KernelCfg* c) {
   if (c->split == 2) {
     if (d_tc) return DG_OK;
     const size_t ntiles = size_t((Kpad + c->gemm_ne - 1) / c->gemm_ne) + 1;
-    const size_t xbytes = ntiles * c->gemm_kx * c->gemm_ne * 4;
+    const size_t xbytes = ntiles * c->gemm_xtile;
     std::vector<uint16_t> blob;
     pack_tc_ops(ref, c->gemm_nsplit, c->gemm_mtiles, blob);
     const size_t obytes = (blob.size() * 2 + 255) & ~size_t(255);

@@ -99,6 +99,7 @@ struct KernelCfg {
   void (*fn_gemm_batched)(BatchArgs);  // split step of a batch (FP32 GEMM only)
   size_t smem_gemm;
   int gemm_threads, gemm_ne, gemm_mt, gemm_mtiles, gemm_kx, gemm_mp2, gemm_nsplit;
+  size_t gemm_xtile;     // bytes of X per column tile of gemm_ne elements
   bool gemm_persistent;  // grid = min(tiles, SMs x resident CTAs) instead of one CTA per tile
 };
 

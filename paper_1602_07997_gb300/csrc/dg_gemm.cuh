@@ -56,7 +56,7 @@ template <int MODEL, int N>
 __device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mtile, const int ntile) {
   using S = Sz<N>;
   using SS = SplitShape<MODEL, N>;
-  constexpr int Np = S::Np, NFN = S::NFN, Nf = SS::Nf, NV = SS::NV, KX = SS::KX, NE = SS::NE, TN = SS::TN;
+  constexpr int Np = S::Np, NFN = S::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NE, TN = SS::TN;
   constexpr int MT = SS::MT, MP2 = SS::MP2, JC = SS::JC, CC = SS::CC, NT = SS::NT;
   constexpr int NVC = SS::NVC, NLC = SS::NLC, NCH = NVC + NLC;
   constexpr int REC = Rec<MODEL>::size;

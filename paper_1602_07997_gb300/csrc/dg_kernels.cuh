@@ -36,6 +36,7 @@
 // with the penalty terms of Section 2.1.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -183,6 +184,56 @@ struct Plan {
   static_assert(nXvol >= nQ, "the RHS of a block is staged in the volume-input buffer");
 };
 
+// Split step for the tensor cores: the front half leaves its GEMM inputs as
+// NSPLIT BF16 pieces, already in the tcgen05 operand layout.  Per column tile
+// of NE elements, chunk c of 16 input indices (volume chunks c < NKD: the NV
+// volume input vectors at nodes 16c..16c+15; lift chunks: the Nf penalty
+// vectors at face nodes 16(c - NKD)..) is one contiguous block
+// [piece][vector][NE/8 element groups][2 K halves][8 elements][8 values]
+// (no-swizzle K-major core matrices of 8 rows x 16 bytes), zero beyond Np or
+// 4 Nfp, so that one bulk copy moves a chunk.
+template <int MODEL, int N, int NSPLIT>
+struct TcX {
+  using S = Sz<N>;
+  static constexpr int Np = S::Np, NFN = S::NFN;
+  static constexpr int Nf = MODEL == 0 ? 4 : 9;
+  static constexpr int NV = MODEL == 0 ? 4 : 12;
+  static constexpr int NE = MODEL == 0 ? 32 : 16;  // elements per column tile (the MMA N)
+  static constexpr int NKD = (Np + 15) / 16, NKL = (NFN + 15) / 16;
+  static constexpr int BV = NE * 16 * 2;           // one piece of one vector of one chunk
+  static constexpr int CD = NSPLIT * NV * BV;      // bytes of a volume chunk
+  static constexpr int CL = NSPLIT * Nf * BV;      // bytes of a lift chunk
+  static constexpr size_t TILE = size_t(NKD) * CD + size_t(NKL) * CL;
+  __host__ __device__ static constexpr size_t chunk_off(int c) {
+    return c < NKD ? size_t(c) * CD : size_t(NKD) * CD + size_t(c - NKD) * CL;
+  }
+};
+
+// BF16 pieces of 8 values, two at a time: x_0 = bf16(x), x_1 = bf16(x - x_0),
+// x_2 = bf16(x - x_0 - x_1) (round to nearest even; the remainders are exact
+// in FP32); out[h] holds piece h of the 8 values, value 0 in the low half.
+template <int NSPLIT>
+__device__ __forceinline__ void bf16_pieces8(const float* x, uint4* out) {
+  float r[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) r[t] = x[t];
+#pragma unroll
+  for (int h = 0; h < NSPLIT; ++h) {
+    uint32_t w[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const __nv_bfloat162 b = __floats2bfloat162_rn(r[2 * p], r[2 * p + 1]);
+      w[p] = *reinterpret_cast<const uint32_t*>(&b);
+      if (h + 1 < NSPLIT) {
+        const float2 f = __bfloat1622float2(b);
+        r[2 * p] -= f.x;
+        r[2 * p + 1] -= f.y;
+      }
+    }
+    out[h] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
 // ---------------------------------------------------------------- block providers
 // A provider maps a global block index to the arguments of the solve it
 // belongs to and to its local block index; operators, face tables, error word
@@ -247,7 +298,7 @@ struct SolveBatch {
 };
 
 // ---------------------------------------------------------------- kernel body
-template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT, class Prov>
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT, int XP, class Prov>
 __device__ __forceinline__ void step_body(const Prov& prov) {
   using S = Sz<N>;
   using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM>;
@@ -529,7 +580,40 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       if (mbar_wait_bounded(&bars[s ^ 1], uint32_t(((it + 1) >> 1) & 1), err)) issue_gathers(nxt_a, nxt_lb, s ^ 1);
     }
 
-    if constexpr (SPLIT > 0) {
+    if constexpr (SPLIT > 0 && XP > 0) {
+      // split step for the tensor cores, front half: every 8 input indices of
+      // one element become XP BF16 pieces of 16 bytes in the chunk layout of TcX
+      using TX = TcX<MODEL, N, XP>;
+      static_assert(TX::NE == SPLIT, "column tile of the tensor-core kernel");
+      constexpr int NV = TX::NV, NKD = TX::NKD, NKL = TX::NKL, NE = TX::NE;
+      constexpr int NRG = 2 * (NV * NKD + Nf * NKL);  // groups of 8 input indices per element
+      uint8_t* xb = reinterpret_cast<uint8_t*>(a.xg);
+      for (int i = tid; i < EB * NRG; i += NT) {
+        const int e = i % EB, rg = i / EB;
+        const bool vol = rg < 2 * NV * NKD;
+        const int r2 = vol ? rg : rg - 2 * NV * NKD;
+        const int per = vol ? 2 * NKD : 2 * NKL;
+        const int vv = r2 / per, w = r2 - vv * per;
+        const int cl = w >> 1, kh = w & 1;  // chunk within its kind, K half
+        const int i0 = cl * 16 + kh * 8;    // first node (volume) or face node (lift)
+        const int lim = vol ? Np : NFN;
+        const float* src = vol ? sXv + (vv * Np) * EBP + e : sXs + (vv * NFN) * EBP + e;
+        float x[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[t] = (i0 + t < lim) ? src[(i0 + t) * EBP] : 0.f;
+        uint4 pc[XP];
+        bf16_pieces8<XP>(x, pc);
+        const int k = k0 + e;
+        const int el = k % NE;
+        const int nvs = vol ? NV : Nf;
+        uint8_t* dst = xb + size_t(k / NE) * TX::TILE + TX::chunk_off(vol ? cl : NKD + cl) +
+                       size_t(vv * (NE / 8) + (el >> 3)) * 256 + kh * 128 + (el & 7) * 16;
+#pragma unroll
+        for (int h = 0; h < XP; ++h)
+          *reinterpret_cast<uint4*>(dst + size_t(h) * nvs * TX::BV) = pc[h];
+      }
+      continue;
+    } else if constexpr (SPLIT > 0) {
       // split step, front half: the GEMM inputs leave for the global buffer
       // X[tile][row][NE] (row: volume inputs, then penalties; NE = SPLIT
       // elements per tile), 4 elements per float4
@@ -771,11 +855,12 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
 }
 
 // One solve per launch (dg_rhs / dg_step); SPLIT > 0: front half of the split
-// step writing X in column tiles of SPLIT elements.
-template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT = 0>
+// step writing X in column tiles of SPLIT elements (FP32 rows, or XP BF16
+// pieces in the tensor-core chunk layout when XP > 0).
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT = 0, int XP = 0>
 __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   SingleSolve p{a, EB};
-  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, SPLIT>(p);
+  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, SPLIT, XP>(p);
 }
 
 // Every solve of a batch (same model and N) in one persistent launch; the
@@ -784,7 +869,7 @@ __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
 template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT = 0>
 __global__ void __launch_bounds__(NT) dg_step_batched_kernel(const BatchArgs b) {
   SolveBatch p{b};
-  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, SPLIT>(p);
+  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, SPLIT, 0>(p);
 }
 
 }  // namespace dgk

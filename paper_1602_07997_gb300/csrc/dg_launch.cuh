@@ -30,6 +30,7 @@ KernelCfg make_cfg() {
   c.fn_gemm_batched = nullptr;
   c.smem_gemm = 0;
   c.gemm_threads = c.gemm_ne = c.gemm_mt = c.gemm_mtiles = c.gemm_kx = c.gemm_mp2 = c.gemm_nsplit = 0;
+  c.gemm_xtile = 0;
   c.gemm_persistent = false;
   return c;
 }
@@ -61,13 +62,14 @@ KernelCfg make_split_cfg() {
   c.gemm_kx = SS::KX;
   c.gemm_mp2 = SS::MP2;
   c.gemm_nsplit = 0;
+  c.gemm_xtile = size_t(SS::KX) * SS::NE * 4;
   c.gemm_persistent = false;
   return c;
 }
 
-// Tensor-core split variant: front half with EB elements per block writing X
-// in tiles of the tensor-core kernel's NE, then the tcgen05 kernel with
-// NSPLIT BF16 pieces per operand.
+// Tensor-core split variant: front half with EB elements per block writing
+// the NSPLIT BF16 pieces of its GEMM inputs in the tensor-core chunk layout,
+// then the tcgen05 kernel.
 template <int MODEL, int N, int EB, int NSPLIT, int NT = threads_for<N, EB, 1>()>
 KernelCfg make_tc_cfg() {
   using TS = TcShape<MODEL, N, NSPLIT>;
@@ -80,7 +82,7 @@ KernelCfg make_tc_cfg() {
   c.ops_smem = false;
   c.r_smem = false;
   c.smem = Plan<MODEL, N, EB, false, false>::bytes;
-  c.fn = dg_step_kernel<MODEL, N, EB, 1, NT, false, false, TS::NE>;
+  c.fn = dg_step_kernel<MODEL, N, EB, 1, NT, false, false, TS::NE, NSPLIT>;
   c.fn_batched = nullptr;
   c.split = 2;
   c.fn_gemm = dg_tc_gemm_kernel<MODEL, N, NSPLIT>;
@@ -90,9 +92,10 @@ KernelCfg make_tc_cfg() {
   c.gemm_ne = TS::NE;
   c.gemm_mt = TS::MT;
   c.gemm_mtiles = TS::MTILES;
-  c.gemm_kx = TS::KX;
+  c.gemm_kx = 0;
   c.gemm_mp2 = TS::MTILES * TS::MT;
   c.gemm_nsplit = NSPLIT;
+  c.gemm_xtile = TS::TX::TILE;
   c.gemm_persistent = true;
   return c;
 }

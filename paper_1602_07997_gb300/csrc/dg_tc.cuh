@@ -1,31 +1,28 @@
 // Split step, tensor-core back half: operator products on the 5th-generation
 // tensor cores (tcgen05) in split-BF16 arithmetic, FP32 accumulation in TMEM.
 //
-// The front half (the fused kernel with SPLIT = NE) leaves the GEMM inputs of
-// every element in X[tile][row][NE] (FP32, row = input index: the volume
-// inputs, then the Fscale-weighted penalty terms; NE elements per tile,
-// element fastest).  A tile of this kernel is 128 output rows x NE elements;
-// persistent CTAs (one per SM) walk the tiles t = blockIdx.x + j gridDim.x
-// with warp-specialised roles:
-//   - warp 0 (one lane), producer: per tile the element records, then per
-//     chunk of 16 input indices (the K of one MMA) the chunk's operator pieces
-//     [D_r D_s D_t] or LIFT, pre-split on the host into NSPLIT BF16 pieces in
-//     the no-swizzle K-major core-matrix layout, and the chunk's FP32 input
-//     rows: 1-D TMA bulk copies into an NS-stage ring (mbarrier tx counts);
-//   - warps 2-3, converters: split every FP32 input x into BF16 pieces
-//     x = x_0 + x_1 (+ x_2) (round to nearest, each piece the rounding of the
-//     remainder) stored in the same core-matrix layout;
+// The front half (the fused kernel with SPLIT = NE, XP = NSPLIT) leaves the
+// GEMM inputs of every element already split into NSPLIT BF16 pieces in the
+// tcgen05 operand layout (TcX: one contiguous block per column tile of NE
+// elements and chunk of 16 input indices).  A tile of this kernel is 128
+// output rows x NE elements; persistent CTAs (one per SM) walk the tiles
+// t = blockIdx.x + j gridDim.x with warp-specialised roles:
+//   - warp 0 (one lane), producer: per tile the element records (and an L2
+//     prefetch of the tile's AB3 inputs), then per chunk the operator pieces
+//     [D_r D_s D_t] or LIFT (pre-split on the host, same core-matrix layout)
+//     and the chunk's input pieces: two 1-D TMA bulk copies into an NS-stage
+//     ring (mbarrier transaction counts);
 //   - warp 1 (one lane), MMA issuer: tcgen05.mma (M = 128, N = NE, K = 16) for
 //     every product and every piece pair (a, b) with a + b < NSPLIT into the
 //     tile's TMEM accumulator (two accumulators alternate when they fit in the
 //     512 TMEM columns, so that a tile's products run while the previous
 //     tile's epilogue drains): NSPLIT = 2 gives the three products of bf16x3,
 //     NSPLIT = 3 the six products that leave only terms of relative size 2^-24;
-//   - warps 4-7, epilogue: each reads its 32 TMEM lanes (its output rows) and
-//     does the geometric combination, the point source and the AB3 update
-//     (Eq. updateScheme) as in the fused kernel, rows across lanes: global
-//     accesses are coalesced; the AB3 inputs of a group of elements are all in
-//     flight before the first store.
+//   - warps 2-5, epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its
+//     output rows) and does the geometric combination, the point source and
+//     the AB3 update (Eq. updateScheme) as in the fused kernel, rows across
+//     lanes: global accesses are coalesced; the AB3 inputs of a group of
+//     elements are all in flight before the first store.
 // Products (TMEM column blocks of NE):
 //   acoustic: G_d = D_d p (0..2), R = sum_d D_d w_d + LIFT P_p (3),
 //             L_c = LIFT P_v,c (4..6)
@@ -38,41 +35,37 @@
 
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "dg_kernels.cuh"
 
 namespace dgk {
 
 template <int MODEL, int N, int NSPLIT>
 struct TcShape {
-  using S = Sz<N>;
-  static constexpr int Np = S::Np, NFN = S::NFN;
-  static constexpr int Nf = MODEL == 0 ? 4 : 9;
-  static constexpr int NV = MODEL == 0 ? 4 : 12;  // volume input vectors
-  static constexpr int KX = NV * Np + Nf * NFN;   // X rows per element
-  static constexpr int NE = MODEL == 0 ? 32 : 16; // elements per tile (MMA N)
+  using TX = TcX<MODEL, N, NSPLIT>;
+  static constexpr int Np = TX::Np, NFN = TX::NFN, Nf = TX::Nf, NV = TX::NV, NE = TX::NE;
   static constexpr int MT = 128;                  // output rows per tile (MMA M)
   static constexpr int MTILES = (Np + MT - 1) / MT;
-  static constexpr int NKD = (Np + 15) / 16;      // K chunks of the volume products
-  static constexpr int NKL = (NFN + 15) / 16;     // K chunks of the LIFT products
-  static constexpr int NCH = NKD + NKL;
+  static constexpr int NKD = TX::NKD, NKL = TX::NKL, NCH = NKD + NKL;
   static constexpr int NACC = MODEL == 0 ? 7 : 18;
   static constexpr int TCOLS = NACC * NE;         // TMEM columns of one accumulator
   static constexpr int NBUF = 2 * TCOLS <= 512 ? 2 : 1;
   static constexpr int TNEED = NBUF * TCOLS;
   static constexpr int TALLOC = TNEED <= 32 ? 32 : TNEED <= 64 ? 64 : TNEED <= 128 ? 128 : TNEED <= 256 ? 256 : 512;
-  static constexpr int NB = NV > Nf ? NV : Nf;    // input vectors of one chunk, at most
   static constexpr int PIECE = MT * 16 * 2;       // one BF16 operator piece of one chunk
   static constexpr int A_D = 3 * NSPLIT * PIECE;  // volume chunk: D_r, D_s, D_t pieces
   static constexpr int A_L = NSPLIT * PIECE;      // LIFT chunk
-  static constexpr int B32 = NB * 16 * NE * 4;    // FP32 input rows of one chunk
-  static constexpr int BV = NE * 16 * 2;          // one BF16 piece of one input vector
-  static constexpr int B16 = NSPLIT * NB * BV;
-  static constexpr int STAGE = A_D + B32 + B16;
-  static constexpr int NS = 3;                    // pipeline stages
+  static constexpr int B16 = TX::CD > TX::CL ? TX::CD : TX::CL;
+  static constexpr int STAGE = A_D + B16;
   static constexpr int RECB = NE * Rec<MODEL>::size * 4;  // element records of one tile
-  static constexpr int NT = 256;                  // 8 warps: producer, MMA, 2 converters, 4 epilogue
+  static constexpr int NT = 192;                  // 6 warps: producer, MMA, 4 epilogue
   static constexpr size_t OPS_PER_MTILE = size_t(NKD) * A_D + size_t(NKL) * A_L;
-  static constexpr size_t smem = size_t(NS) * STAGE + 2 * RECB + 256;
+  static constexpr size_t FIXED = 2 * RECB + 256;
+  static constexpr int NSF = int((225 * 1024 - FIXED) / STAGE);
+  static constexpr int NS = NSF > 6 ? 6 : NSF;    // pipeline stages
+  static constexpr size_t smem = size_t(NS) * STAGE + FIXED;
+  static_assert(NS >= 2, "pipeline stages");
   static_assert(TCOLS <= 512, "TMEM columns");
   static_assert(NE % 16 == 0 && NE <= 256, "MMA N for M = 128");
   static_assert(RECB % 16 == 0, "record copies are whole 16-byte pieces");
@@ -135,36 +128,55 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float* v) {
 #pragma unroll
   for (int t = 0; t < 8; ++t) v[t] = __uint_as_float(r[t]);
 }
+// Compile-time loop: f(std::integral_constant<int, i>) for i = I .. END - 1.
+template <int I, int END>
+struct StaticFor {
+  template <class F>
+  __device__ __forceinline__ static void run(F&& f) {
+    if constexpr (I < END) {
+      f(std::integral_constant<int, I>{});
+      StaticFor<I + 1, END>::run(f);
+    }
+  }
+};
+
+// The MMAs of one product: every piece pair (ha, hb) with ha + hb < NSPLIT,
+// operator slot OP against input vector V of the stage (NVS vectors per piece;
+// compile-time, so the
+// descriptor offsets are immediates added to the stage's base descriptors
+// a0 / b0; the 14-bit address field cannot carry below 256 KB); first = 1
+// if this product starts its accumulator.
+template <int NSPLIT, int NVS, int PIECE, int BV, int OP, int V>
+__device__ __forceinline__ void tc_prod(uint32_t tcol, uint64_t a0, uint64_t b0, uint32_t idesc, uint32_t first) {
+#pragma unroll
+  for (int ha = 0; ha < NSPLIT; ++ha)
+#pragma unroll
+    for (int hb = 0; hb < NSPLIT - ha; ++hb)
+      tc_mma(tcol, a0 + uint64_t(((OP * NSPLIT + ha) * PIECE) >> 4), b0 + uint64_t(((hb * NVS + V) * BV) >> 4), idesc,
+             (ha == 0 && hb == 0) ? (first ^ 1u) : 1u);
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// pieces of x: x_0 = bf16(x), x_1 = bf16(x - x_0), x_2 = bf16(x - x_0 - x_1);
-// the remainders are exact in FP32
-template <int NSPLIT>
-__device__ __forceinline__ void bf16_pieces(float x, uint16_t* out) {
-  float r = x;
-#pragma unroll
-  for (int h = 0; h < NSPLIT; ++h) {
-    const __nv_bfloat16 b = __float2bfloat16_rn(r);
-    out[h] = __bfloat16_as_ushort(b);
-    r -= __bfloat162float(b);
-  }
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 template <int MODEL, int N, int NSPLIT>
-__global__ void __launch_bounds__(256, 1) dg_tc_gemm_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(192, 1) dg_tc_gemm_kernel(const StepArgs a) {
   using TS = TcShape<MODEL, N, NSPLIT>;
-  constexpr int Np = TS::Np, NFN = TS::NFN, Nf = TS::Nf, NV = TS::NV, KX = TS::KX, NE = TS::NE;
-  constexpr int NKD = TS::NKD, NCH = TS::NCH, NS = TS::NS, NB = TS::NB, NBUF = TS::NBUF, MTILES = TS::MTILES;
+  using TX = typename TS::TX;
+  constexpr int Np = TS::Np, Nf = TS::Nf, NV = TS::NV, NE = TS::NE;
+  constexpr int NKD = TS::NKD, NCH = TS::NCH, NS = TS::NS, NBUF = TS::NBUF, MTILES = TS::MTILES;
   constexpr int REC = Rec<MODEL>::size;
   constexpr uint32_t IDESC = tc_idesc_bf16(128, NE);
 
   extern __shared__ __align__(1024) uint8_t tsm[];
   float* recs = reinterpret_cast<float*>(tsm + NS * TS::STAGE);  // [2][NE][REC]
   uint64_t* full = reinterpret_cast<uint64_t*>(tsm + NS * TS::STAGE + 2 * TS::RECB);
-  uint64_t* conv = full + NS;
-  uint64_t* empty = conv + NS;
+  uint64_t* empty = full + NS;
   uint64_t* tfull = empty + NS;   // accumulator b holds a finished tile
   uint64_t* tempty = tfull + 2;   // accumulator b has been read out
   uint64_t* rfull = tempty + 2;   // records of tile buffer r landed
@@ -179,7 +191,6 @@ __global__ void __launch_bounds__(256, 1) dg_tc_gemm_kernel(const StepArgs a) {
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 64);
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -204,6 +215,7 @@ __global__ void __launch_bounds__(256, 1) dg_tc_gemm_kernel(const StepArgs a) {
   int issued = 0, rissued = 0;  // producer: chunks / tile records whose copies were issued
   if (warp == 0) {
     if (lane == 0) {
+      // -------- producer
       int g = 0;
       for (int j = 0; j < nmine && ok; ++j) {
         const int t = int(blockIdx.x) + j * int(gridDim.x);
@@ -216,8 +228,17 @@ __global__ void __launch_bounds__(256, 1) dg_tc_gemm_kernel(const StepArgs a) {
         mbar_arrive_expect_tx(&rfull[rb], TS::RECB);
         tma_bulk_g2s(recs + rb * NE * REC, a.rec + size_t(ntile) * NE * REC, TS::RECB, &rfull[rb]);
         rissued = j + 1;
-        const float* X = a.xg + size_t(ntile) * KX * NE;
+        if (a.mode == 0 && mtile == 0) {
+          // the epilogue's AB3 inputs of this tile: into L2 while the products run
+          // (q, r^{m-1}, r^{m-2} are padded past K: whole tiles stay in bounds)
+          const size_t e0 = size_t(ntile) * NE * Nf * Np;
+          constexpr uint32_t bytes = uint32_t(NE * Nf * Np * 4);
+          prefetch_l2(a.q + e0, bytes);
+          prefetch_l2(a.r1 + e0, bytes);
+          prefetch_l2(a.r2 + e0, bytes);
+        }
         const uint8_t* OPS = reinterpret_cast<const uint8_t*>(a.opstc) + size_t(mtile) * TS::OPS_PER_MTILE;
+        const uint8_t* XT = reinterpret_cast<const uint8_t*>(a.xg) + size_t(ntile) * TX::TILE;
         for (int c = 0; c < NCH; ++c, ++g) {
           const int s = g % NS;
           if (g >= NS && !mbar_wait_bounded(&empty[s], uint32_t(((g / NS) - 1) & 1), a.err)) {
@@ -225,18 +246,13 @@ __global__ void __launch_bounds__(256, 1) dg_tc_gemm_kernel(const StepArgs a) {
             break;
           }
           uint8_t* st = tsm + s * TS::STAGE;
-          float* b32 = reinterpret_cast<float*>(st + TS::A_D);
           const bool vol = c < NKD;
-          const int nvec = vol ? NV : Nf;
           const uint32_t abytes = vol ? TS::A_D : TS::A_L;
-          const uint32_t rbytes = 16u * NE * 4u;
-          mbar_arrive_expect_tx(&full[s], abytes + uint32_t(nvec) * rbytes);
-          const uint8_t* asrc = OPS + (vol ? size_t(c) * TS::A_D : size_t(NKD) * TS::A_D + size_t(c - NKD) * TS::A_L);
-          tma_bulk_g2s(st, asrc, abytes, &full[s]);
-          for (int v = 0; v < nvec; ++v) {
-            const int row = vol ? v * Np + c * 16 : NV * Np + v * NFN + (c - NKD) * 16;
-            tma_bulk_g2s(b32 + v * 16 * NE, X + size_t(row) * NE, rbytes, &full[s]);
-          }
+          const uint32_t xbytes = vol ? TX::CD : TX::CL;
+          mbar_arrive_expect_tx(&full[s], abytes + xbytes);
+          tma_bulk_g2s(st, OPS + (vol ? size_t(c) * TS::A_D : size_t(NKD) * TS::A_D + size_t(c - NKD) * TS::A_L),
+                       abytes, &full[s]);
+          tma_bulk_g2s(st + TS::A_D, XT + TX::chunk_off(c), xbytes, &full[s]);
           issued = g + 1;
         }
       }
@@ -257,44 +273,58 @@ __global__ void __launch_bounds__(256, 1) dg_tc_gemm_kernel(const StepArgs a) {
         const uint32_t tacc = tmem + uint32_t(b * TS::TCOLS);
         for (int c = 0; c < NCH; ++c, ++g) {
           const int s = g % NS;
-          if (!mbar_wait_bounded(&conv[s], uint32_t((g / NS) & 1), a.err)) {
+          if (!mbar_wait_bounded(&full[s], uint32_t((g / NS) & 1), a.err)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t sa = smem_addr(tsm + s * TS::STAGE);
-          const uint32_t sb = sa + TS::A_D + TS::B32;
-          auto adesc = [&](int op, int h) { return tc_sdesc(sa + (op * NSPLIT + h) * TS::PIECE, 128, 256); };
-          auto bdesc = [&](int v, int h) { return tc_sdesc(sb + (h * NB + v) * TS::BV, 128, 256); };
-          // acc: column block; op: operator slot; v: input vector; first:
-          // this chunk starts the accumulator
-          auto prod = [&](int acc, int op, int v, bool first) {
-#pragma unroll
-            for (int ha = 0; ha < NSPLIT; ++ha)
-#pragma unroll
-              for (int hb = 0; hb < NSPLIT - ha; ++hb)
-                tc_mma(tacc + uint32_t(acc * NE), adesc(op, ha), bdesc(v, hb), IDESC,
-                       (first && ha == 0 && hb == 0) ? 0u : 1u);
-          };
+          const uint64_t a0 = tc_sdesc(sa, 128, 256);           // operator pieces of the stage
+          const uint64_t b0 = tc_sdesc(sa + TS::A_D, 128, 256);  // BF16 input pieces of the stage
+          constexpr int PC = TS::PIECE, BV = TX::BV;
           if (c < NKD) {
-            const bool c0 = c == 0;
+            const uint32_t c0 = c == 0 ? 1u : 0u;
             if constexpr (MODEL == 0) {
-              for (int d = 0; d < 3; ++d) prod(d, d, 0, c0);
-              for (int d = 0; d < 3; ++d) prod(3, d, 1 + d, c0 && d == 0);
+              // G_d = D_d p; R = sum_d D_d w_d
+              StaticFor<0, 3>::run([&](auto ic) {
+                constexpr int d = decltype(ic)::value;
+                tc_prod<NSPLIT, NV, PC, BV, d, 0>(tacc + uint32_t(d * NE), a0, b0, IDESC, c0);
+              });
+              StaticFor<0, 3>::run([&](auto ic) {
+                constexpr int d = decltype(ic)::value;
+                tc_prod<NSPLIT, NV, PC, BV, d, 1 + d>(tacc + uint32_t(3 * NE), a0, b0, IDESC, d == 0 ? c0 : 0u);
+              });
             } else {
-              for (int cc = 0; cc < 3; ++cc)
-                for (int d = 0; d < 3; ++d) prod(3 * cc + d, d, cc, c0);
-              for (int cc = 0; cc < 3; ++cc)
-                for (int d = 0; d < 3; ++d) prod(9 + cc, d, 3 + 3 * cc + d, c0 && d == 0);
+              // U_cd = D_d v_c; Rv_c = sum_d D_d s_cd
+              StaticFor<0, 9>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value, cc = i / 3, d = i % 3;
+                tc_prod<NSPLIT, NV, PC, BV, d, cc>(tacc + uint32_t(i * NE), a0, b0, IDESC, c0);
+              });
+              StaticFor<0, 9>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value, cc = i / 3, d = i % 3;
+                tc_prod<NSPLIT, NV, PC, BV, d, 3 + i>(tacc + uint32_t((9 + cc) * NE), a0, b0, IDESC,
+                                                      d == 0 ? c0 : 0u);
+              });
             }
           } else {
-            const bool l0 = c == NKD;
+            const uint32_t l0 = c == NKD ? 1u : 0u;
             if constexpr (MODEL == 0) {
-              prod(3, 0, 0, false);
-              for (int cc = 0; cc < 3; ++cc) prod(4 + cc, 0, 1 + cc, l0);
+              // R += LIFT P_p; L_c = LIFT P_v,c
+              tc_prod<NSPLIT, Nf, PC, BV, 0, 0>(tacc + uint32_t(3 * NE), a0, b0, IDESC, 0u);
+              StaticFor<0, 3>::run([&](auto ic) {
+                constexpr int cc = decltype(ic)::value;
+                tc_prod<NSPLIT, Nf, PC, BV, 0, 1 + cc>(tacc + uint32_t((4 + cc) * NE), a0, b0, IDESC, l0);
+              });
             } else {
-              for (int cc = 0; cc < 3; ++cc) prod(9 + cc, 0, cc, false);
-              for (int x = 0; x < 6; ++x) prod(12 + x, 0, 3 + x, l0);
+              // Rv_c += LIFT P_v,c; S_x = LIFT P_sig,x
+              StaticFor<0, 3>::run([&](auto ic) {
+                constexpr int cc = decltype(ic)::value;
+                tc_prod<NSPLIT, Nf, PC, BV, 0, cc>(tacc + uint32_t((9 + cc) * NE), a0, b0, IDESC, 0u);
+              });
+              StaticFor<0, 6>::run([&](auto ic) {
+                constexpr int x = decltype(ic)::value;
+                tc_prod<NSPLIT, Nf, PC, BV, 0, 3 + x>(tacc + uint32_t((12 + x) * NE), a0, b0, IDESC, l0);
+              });
             }
           }
           tc_commit(&empty[s]);
@@ -305,53 +335,9 @@ __global__ void __launch_bounds__(256, 1) dg_tc_gemm_kernel(const StepArgs a) {
       if (!mbar_wait_bounded(done, 0u, a.err)) ok = false;
     }
     __syncwarp();
-  } else if (warp < 4) {
-    // -------- converters: FP32 input rows -> BF16 pieces, core-matrix layout
-    const int ct = tid - 64;
-    int g = 0;
-    for (int j = 0; j < nmine && ok; ++j) {
-      for (int c = 0; c < NCH; ++c, ++g) {
-        const int s = g % NS;
-        if (!mbar_wait_bounded(&full[s], uint32_t((g / NS) & 1), a.err)) {
-          ok = false;
-          break;
-        }
-        uint8_t* st = tsm + s * TS::STAGE;
-        const float* b32 = reinterpret_cast<const float*>(st + TS::A_D);
-        uint8_t* b16 = st + TS::A_D + TS::B32;
-        const bool vol = c < NKD;
-        const int nvec = vol ? NV : Nf;
-        const int k0 = vol ? c * 16 : (c - NKD) * 16;
-        const int klim = vol ? Np : NFN;
-        for (int u = ct; u < nvec * 2 * NE; u += 64) {
-          const int e = u % NE, kh = (u / NE) & 1, v = u / (2 * NE);
-          uint16_t pc[NSPLIT][8];
-#pragma unroll
-          for (int tt = 0; tt < 8; ++tt) {
-            const int kk = kh * 8 + tt;
-            const float x = (k0 + kk < klim) ? b32[(v * 16 + kk) * NE + e] : 0.f;
-            uint16_t hp[NSPLIT];
-            bf16_pieces<NSPLIT>(x, hp);
-#pragma unroll
-            for (int h = 0; h < NSPLIT; ++h) pc[h][tt] = hp[h];
-          }
-#pragma unroll
-          for (int h = 0; h < NSPLIT; ++h) {
-            uint4 w;
-            w.x = uint32_t(pc[h][0]) | (uint32_t(pc[h][1]) << 16);
-            w.y = uint32_t(pc[h][2]) | (uint32_t(pc[h][3]) << 16);
-            w.z = uint32_t(pc[h][4]) | (uint32_t(pc[h][5]) << 16);
-            w.w = uint32_t(pc[h][6]) | (uint32_t(pc[h][7]) << 16);
-            *reinterpret_cast<uint4*>(b16 + (h * NB + v) * TS::BV + (e >> 3) * 256 + kh * 128 + (e & 7) * 16) = w;
-          }
-        }
-        fence_proxy_async_smem();
-        mbar_arrive(&conv[s]);
-      }
-    }
   } else {
-    // -------- epilogue: warp 4 + q reads TMEM lanes 32 q .. 32 q + 31
-    const int quarter = warp - 4;
+    // -------- epilogue: warp w reads TMEM lanes 32 (w mod 4) .. 32 (w mod 4) + 31
+    const int quarter = warp & 3;
     constexpr int EC = MODEL == 0 ? 8 : 4;  // elements per group: TMEM loads and AB3 inputs in flight together
     for (int j = 0; j < nmine; ++j) {
       const int t = int(blockIdx.x) + j * int(gridDim.x);
