@@ -293,16 +293,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def make_solvers(P, cfgs, model, precision, stream, tune):
+def make_solvers(P, cfgs, model, precision, stream, tune, variants=None):
     solvers = []
-    for cfg in cfgs:
+    for i, cfg in enumerate(cfgs):
         N = cfg["N"]
         dt = P.suggest_dt(cfg["verts"], cfg["tets"], cfg["coeffs"], N, model, 0.4)
         g = P.Solver(cfg["verts"], cfg["tets"], cfg["coeffs"], N, model, dt=dt,
                      stream=stream.cuda_stream, precision=precision)
         q = np.random.default_rng(N).uniform(-1, 1, size=g.shape).astype(np.float32)
         g.set_state(q)
-        if tune:
+        if variants is not None:
+            g.set_variant(variants[i])
+        elif tune:
             g.autotune(5)
         solvers.append(g)
     return solvers
@@ -399,7 +401,10 @@ def run(args, rank, world, local_rank):
     Ns = [int(x) for x in args.degrees.split(",")]
     stream = torch.cuda.Stream(device=dev)
     cfgs = build_meshes(model, Ns)
-    solvers = make_solvers(P, cfgs, model, "fp32", stream, not args.no_tune)
+    variants = [int(x) for x in args.variants.split(",")] if args.variants else None
+    if variants is not None and len(variants) != len(Ns):
+        raise SystemExit("--variants needs one index per degree")
+    solvers = make_solvers(P, cfgs, model, args.precision, stream, not args.no_tune, variants)
     torch.cuda.synchronize()
 
     def barrier():
@@ -440,7 +445,7 @@ def run(args, rank, world, local_rank):
     per_N = {}
     dom = None
     for g, ms in zip(solvers, per_ms):
-        row = per_degree(model, g, ms, pk)
+        row = per_degree(model, g, ms, pk, tensor=args.precision != "fp32")
         per_N[str(g.N)] = row
         if dom is None or ms > dom[1]:
             byt, flop = algorithmic(model, g.N, g.K)
@@ -451,7 +456,7 @@ def run(args, rank, world, local_rank):
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
-        ent = tr.get("%s_N%d" % (model, g.N))
+        ent = tr.get("%s_N%d_%s_v%d" % (model, g.N, args.precision, g.kernel_info()["variant"]))
         if ent and ent.get("kernel_rev") == kernel_rev():
             traffic = ent["dram_bytes_per_launch"]
     except Exception:
@@ -463,7 +468,11 @@ def run(args, rank, world, local_rank):
                 "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = traffic
-    roof["kernel"] = "dg_step_kernel<acoustic, N=%d>" % g.N
+    ki = g.kernel_info()
+    roof["kernel"] = ("dg_step_kernel<acoustic, N=%d, EB=%d, TN=%d> (variant %d)"
+                      % (g.N, ki["block_elems"], ki["tile_elems"], ki["variant"]) if not ki["split"] else
+                      "split step, acoustic N=%d (front half + %s GEMM, variant %d)"
+                      % (g.N, "tcgen05" if ki["split"] == 2 else "FP32", ki["variant"]))
     roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs (burst copy)" if bound == "hbm"
                            else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz")
 
@@ -507,7 +516,9 @@ def run(args, rank, world, local_rank):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "fp32" else args.precision + " (f32 accumulate)",
+                "data": "synthetic",
                 "config": {"workload": WORKLOAD, "degrees": Ns,
                            "meshes": {str(g.N): g.K for g in solvers},
                            "l2": "inputs larger than L2: the 8 meshes hold ~1.3 GB, each ~130 MB",
@@ -543,6 +554,10 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-steps", type=int, default=500)
     ap.add_argument("--no-sweeps", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16x6"],
+                    help="arithmetic of the timed sweep's operator contractions (default FP32)")
+    ap.add_argument("--variants", default="",
+                    help="kernel variant index per degree instead of autotuning (e.g. to replay a run's choice)")
     ap.add_argument("--sweep-steps", type=int, default=50)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -156,9 +156,10 @@ int dg_autotune(dg_handle *h, int reps, int *block_elems, double *ms_per_step, d
  * GEMM (the operator products run as a separate GEMM over 16-64-element
  * column tiles; needs an extra device buffer of (4 Np + 4 (4 Nfp)) floats per
  * element for the acoustic model, (12 Np + 9 (4 Nfp)) for the elastic one,
- * allocated on first use).  Pointers may be NULL.                           */
+ * allocated on first use), and the index of the variant in use (as taken by
+ * dg_set_variant).  Pointers may be NULL.                                   */
 int dg_kernel_info(const dg_handle *h, int *block_elems, int *threads, int64_t *smem_bytes,
-                   int *variants, int *tile_elems, int *split);
+                   int *variants, int *tile_elems, int *split, int *variant);
 /* Select compiled variant `index` (0 <= index < variants of the handle's
  * precision mode) for this handle and, like dg_autotune, for handles created
  * later in the process on the same device, model, N and precision (servers

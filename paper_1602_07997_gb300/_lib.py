@@ -258,10 +258,11 @@ class Solver:
 
     def kernel_info(self):
         eb, nt, sm, nv, tn, sp = C.c_int(), C.c_int(), C.c_int64(), C.c_int(), C.c_int(), C.c_int()
+        vi = C.c_int()
         check(lib().dg_kernel_info(self.h, C.byref(eb), C.byref(nt), C.byref(sm), C.byref(nv), C.byref(tn),
-                                   C.byref(sp)))
+                                   C.byref(sp), C.byref(vi)))
         return dict(block_elems=eb.value, threads=nt.value, smem_bytes=sm.value, variants=nv.value,
-                    tile_elems=tn.value, split=sp.value)
+                    tile_elems=tn.value, split=sp.value, variant=vi.value)
 
     def set_variant(self, index):
         check(lib().dg_set_variant(self.h, int(index)))

@@ -655,8 +655,13 @@ int dg_set_variant(dg_handle* h, int index) {
 }
 
 int dg_kernel_info(const dg_handle* h, int* block_elems, int* threads, int64_t* smem_bytes, int* variants,
-                   int* tile_elems, int* split) {
+                   int* tile_elems, int* split, int* variant) {
   if (!h || !h->cfg) return fail(DG_EINVAL, "NULL handle");
+  if (variant) {
+    int n = 0;
+    const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n, h->opts.precision);
+    *variant = (v && h->cfg >= v && h->cfg < v + n) ? int(h->cfg - v) : -1;
+  }
   if (split) *split = h->cfg->split;
   if (tile_elems) *tile_elems = h->cfg->TN;
   if (block_elems) *block_elems = h->cfg->EB;

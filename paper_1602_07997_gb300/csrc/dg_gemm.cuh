@@ -11,7 +11,7 @@
 //   kernel B (this file): a CTA owns MT output rows x NE elements; operator
 //     rows and X rows stream through shared memory in double-buffered K
 //     chunks (16-byte cp.async), every operator row chunk is reused by NE
-//     elements; one thread accumulates 4 rows x TN elements of every product
+//     elements; one thread accumulates 4 RQ rows x TN elements of every product
 //     (G_d = D_d p, R = sum_d D_d w_d + LIFT P_p, L_c = LIFT P_vc for the
 //     acoustic model; U_cd = D_d v_c, Rv_c = sum_d D_d s_cd + LIFT P_vc,
 //     LIFT P_sig for the elastic model) and does the geometric combination
@@ -35,11 +35,12 @@ struct SplitShape {
   static constexpr int KX = NV * S::Np + Nf * S::NFN;     // X rows per element
   static constexpr int NE = MODEL == 0 ? 64 : 32;         // elements per column tile
   static constexpr int TN = MODEL == 0 ? 2 : 1;           // elements per thread tile
+  static constexpr int RQ = MODEL == 0 ? 1 : 2;           // row quads per thread tile (4 or 8 rows)
   static constexpr int MT = 32;                           // output rows per CTA
   static constexpr int MP2 = (S::Np + MT - 1) / MT * MT;  // padded rows of the split operator blob
   static constexpr int JC = 16;                           // volume indices per chunk
   static constexpr int CC = 16;                           // face-node indices per chunk
-  static constexpr int NT = (MT / 4) * (NE / TN);         // threads per CTA
+  static constexpr int NT = (MT / (4 * RQ)) * (NE / TN);  // threads per CTA
   static constexpr int NVC = (S::Np + JC - 1) / JC;       // volume chunks
   static constexpr int NLC = (S::NFN + CC - 1) / CC;      // lift chunks
   // per buffer: A rows (3 JC volume, CC lift) x MT, X rows (NV JC, Nf CC) x NE
@@ -56,7 +57,8 @@ template <int MODEL, int N>
 __device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mtile, const int ntile) {
   using S = Sz<N>;
   using SS = SplitShape<MODEL, N>;
-  constexpr int Np = S::Np, NFN = S::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NE, TN = SS::TN;
+  constexpr int Np = S::Np, NFN = S::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NE, TN = SS::TN, RQ = SS::RQ;
+  constexpr int RV = 4 * RQ;  // rows per thread
   constexpr int MT = SS::MT, MP2 = SS::MP2, JC = SS::JC, CC = SS::CC, NT = SS::NT;
   constexpr int NVC = SS::NVC, NLC = SS::NLC, NCH = NVC + NLC;
   constexpr int REC = Rec<MODEL>::size;
@@ -105,26 +107,27 @@ __device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mti
     cp_async_commit();
   };
 
-  // thread tile: rows i0..i0+3 of this CTA's slice, elements e0..e0+TN-1 of the column tile;
-  // lanes of a warp share the row tile (broadcast operator reads) and walk the elements
+  // thread tile: rows il..il+RV-1 of this CTA's slice, elements e0..e0+TN-1 of the
+  // column tile; lanes of a warp share the row tile (broadcast operator reads)
+  // and walk the elements
   const int ct = tid % (NE / TN), rt = tid / (NE / TN);
-  const int il = 4 * rt, e0 = ct * TN;
+  const int il = RV * rt, e0 = ct * TN;
 
   constexpr int NACC = MODEL == 0 ? 7 : 12;  // acoustic G0..2, R, L0..2; elastic U00..U22, Rv0..2
-  float acc[NACC][TN][4];
+  float acc[NACC][TN][RV];
 #pragma unroll
   for (int x = 0; x < NACC; ++x)
 #pragma unroll
     for (int t = 0; t < TN; ++t)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[x][t][v] = 0.f;
-  float accS[MODEL == 0 ? 1 : 6][TN][4];  // elastic LIFT P_sigma
+      for (int v = 0; v < RV; ++v) acc[x][t][v] = 0.f;
+  float accS[MODEL == 0 ? 1 : 6][TN][RV];  // elastic LIFT P_sigma
 #pragma unroll
   for (int x = 0; x < (MODEL == 0 ? 1 : 6); ++x)
 #pragma unroll
     for (int t = 0; t < TN; ++t)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) accS[x][t][v] = 0.f;
+      for (int v = 0; v < RV; ++v) accS[x][t][v] = 0.f;
 
   issue(0);
   for (int c = 0; c < NCH; ++c) {
@@ -140,11 +143,13 @@ __device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mti
     if (c < NVC) {
       const int j0 = c * JC;
       const int nj = Np - j0 < JC ? Np - j0 : JC;
-#pragma unroll 4
+#pragma unroll 2
       for (int jj = 0; jj < nj; ++jj) {
-        const float4 a0 = *reinterpret_cast<const float4*>(A + (0 * JC + jj) * MT);
-        const float4 a1 = *reinterpret_cast<const float4*>(A + (1 * JC + jj) * MT);
-        const float4 a2 = *reinterpret_cast<const float4*>(A + (2 * JC + jj) * MT);
+        float4 ad[3][RQ];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int q = 0; q < RQ; ++q) ad[d][q] = *reinterpret_cast<const float4*>(A + (d * JC + jj) * MT + 4 * q);
         if constexpr (MODEL == 0) {
           float xpv[TN], x0v[TN], x1v[TN], x2v[TN];
           VecT<TN>::load(B + (0 * JC + jj) * NE, xpv);
@@ -152,36 +157,46 @@ __device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mti
           VecT<TN>::load(B + (2 * JC + jj) * NE, x1v);
           VecT<TN>::load(B + (3 * JC + jj) * NE, x2v);
 #pragma unroll
-          for (int t = 0; t < TN; ++t) {
-            const float xp = xpv[t], x0 = x0v[t], x1 = x1v[t], x2 = x2v[t];
-            fma4(acc[0][t], a0, xp);
-            fma4(acc[1][t], a1, xp);
-            fma4(acc[2][t], a2, xp);
-            fma4(acc[3][t], a0, x0);
-            fma4(acc[3][t], a1, x1);
-            fma4(acc[3][t], a2, x2);
-          }
+          for (int t = 0; t < TN; ++t)
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {
+              const float xp = xpv[t], x0 = x0v[t], x1 = x1v[t], x2 = x2v[t];
+              fma4(&acc[0][t][4 * q], ad[0][q], xp);
+              fma4(&acc[1][t][4 * q], ad[1][q], xp);
+              fma4(&acc[2][t][4 * q], ad[2][q], xp);
+              fma4(&acc[3][t][4 * q], ad[0][q], x0);
+              fma4(&acc[3][t][4 * q], ad[1][q], x1);
+              fma4(&acc[3][t][4 * q], ad[2][q], x2);
+            }
         } else {
 #pragma unroll
           for (int t = 0; t < TN; ++t)
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) {
               const float xv = B[(cc * JC + jj) * NE + t];
-              fma4(acc[3 * cc + 0][t], a0, xv);
-              fma4(acc[3 * cc + 1][t], a1, xv);
-              fma4(acc[3 * cc + 2][t], a2, xv);
-              fma4(acc[9 + cc][t], a0, B[((3 + 3 * cc + 0) * JC + jj) * NE + t]);
-              fma4(acc[9 + cc][t], a1, B[((3 + 3 * cc + 1) * JC + jj) * NE + t]);
-              fma4(acc[9 + cc][t], a2, B[((3 + 3 * cc + 2) * JC + jj) * NE + t]);
+              const float s0 = B[((3 + 3 * cc + 0) * JC + jj) * NE + t];
+              const float s1 = B[((3 + 3 * cc + 1) * JC + jj) * NE + t];
+              const float s2 = B[((3 + 3 * cc + 2) * JC + jj) * NE + t];
+#pragma unroll
+              for (int q = 0; q < RQ; ++q) {
+                fma4(&acc[3 * cc + 0][t][4 * q], ad[0][q], xv);
+                fma4(&acc[3 * cc + 1][t][4 * q], ad[1][q], xv);
+                fma4(&acc[3 * cc + 2][t][4 * q], ad[2][q], xv);
+                fma4(&acc[9 + cc][t][4 * q], ad[0][q], s0);
+                fma4(&acc[9 + cc][t][4 * q], ad[1][q], s1);
+                fma4(&acc[9 + cc][t][4 * q], ad[2][q], s2);
+              }
             }
         }
       }
     } else {
       const int c0 = (c - NVC) * CC;
       const int nc = NFN - c0 < CC ? NFN - c0 : CC;
-#pragma unroll 4
+#pragma unroll 2
       for (int cc = 0; cc < nc; ++cc) {
-        const float4 l = *reinterpret_cast<const float4*>(A + cc * MT);
+        float4 l[RQ];
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) l[q] = *reinterpret_cast<const float4*>(A + cc * MT + 4 * q);
         if constexpr (MODEL == 0) {
           float p0[TN], p1[TN], p2[TN], p3[TN];
           VecT<TN>::load(B + (0 * CC + cc) * NE, p0);
@@ -189,19 +204,29 @@ __device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mti
           VecT<TN>::load(B + (2 * CC + cc) * NE, p2);
           VecT<TN>::load(B + (3 * CC + cc) * NE, p3);
 #pragma unroll
-          for (int t = 0; t < TN; ++t) {
-            fma4(acc[3][t], l, p0[t]);
-            fma4(acc[4][t], l, p1[t]);
-            fma4(acc[5][t], l, p2[t]);
-            fma4(acc[6][t], l, p3[t]);
-          }
+          for (int t = 0; t < TN; ++t)
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {
+              fma4(&acc[3][t][4 * q], l[q], p0[t]);
+              fma4(&acc[4][t][4 * q], l[q], p1[t]);
+              fma4(&acc[5][t][4 * q], l[q], p2[t]);
+              fma4(&acc[6][t][4 * q], l[q], p3[t]);
+            }
         } else {
 #pragma unroll
           for (int t = 0; t < TN; ++t) {
 #pragma unroll
-            for (int f = 0; f < 3; ++f) fma4(acc[9 + f][t], l, B[(f * CC + cc) * NE + t]);
+            for (int f = 0; f < 3; ++f) {
+              const float p = B[(f * CC + cc) * NE + t];
 #pragma unroll
-            for (int f = 0; f < 6; ++f) fma4(accS[f][t], l, B[((3 + f) * CC + cc) * NE + t]);
+              for (int q = 0; q < RQ; ++q) fma4(&acc[9 + f][t][4 * q], l[q], p);
+            }
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+              const float p = B[((3 + f) * CC + cc) * NE + t];
+#pragma unroll
+              for (int q = 0; q < RQ; ++q) fma4(&accS[f][t][4 * q], l[q], p);
+            }
           }
         }
       }
@@ -223,7 +248,7 @@ __device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mti
     for (int x = 0; x < 9; ++x) g[x] = __ldg(gk + x);
     const bool src = (k == a.src_elem) && a.srcvec;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < RV; ++v) {
       const int i = row0 + il + v;
       float r[Nf];
       if constexpr (MODEL == 0) {
