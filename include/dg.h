@@ -85,7 +85,25 @@ enum { DG_BC_DEFAULT = 0, DG_BC_RIGID = 1, DG_BC_FREE = 2 };
  * The tensor-core modes run the split step (front half on the CUDA cores
  * writing the contraction inputs to a device buffer, then the contraction and
  * the AB3 epilogue on the tensor cores) at every N. */
-enum { DG_FP32 = 0, DG_BF16X3 = 1, DG_BF16X6 = 2 };
+enum { DG_FP32 = 0, DG_BF16X3 = 1, DG_BF16X6 = 2, DG_TF32 = 3 };
+
+/* Step strategy (the paper's Section 3 compares several ways of organising
+ * the same computation):
+ *   DG_STRATEGY_FUSED   this library's step: one fused kernel per step (or
+ *                       the split step at high N / in the tensor-core modes);
+ *                       every precision mode except DG_TF32.
+ *   DG_STRATEGY_LIBRARY the library route of Section 3.3: the fused kernel's
+ *                       front half writes the operator-product inputs, cuBLAS
+ *                       strided-batched SGEMMs compute the D_r/D_s/D_t and LIFT
+ *                       products (7 GEMMs per step acoustic, 21 elastic), a
+ *                       streaming kernel does the geometric combination and
+ *                       AB3.  Precision DG_FP32 (SGEMM) or DG_TF32 (cuBLAS TF32
+ *                       tensor-core math; its error is far above 1e-5).
+ *   DG_STRATEGY_PLAIN   the one-node-per-thread multi-kernel route of Section
+ *                       3.2: volume, surface and AB3 update kernels with the
+ *                       partial RHS in device memory between them; DG_FP32.
+ * Autotuning and kernel variants apply to DG_STRATEGY_FUSED only. */
+enum { DG_STRATEGY_FUSED = 0, DG_STRATEGY_LIBRARY = 1, DG_STRATEGY_PLAIN = 2 };
 
 typedef struct {
   int64_t nverts;
@@ -97,11 +115,13 @@ typedef struct {
 typedef struct {
   int flux;         /* DG_FLUX_*                                         */
   int bc;           /* DG_BC_*                                           */
-  int precision;    /* DG_FP32, DG_BF16X3 or DG_BF16X6                   */
+  int precision;    /* DG_FP32, DG_BF16X3, DG_BF16X6 (fused strategy) or
+                       DG_TF32 (library strategy)                        */
   int block_elems;  /* elements per CTA of a compiled variant; 0 = the autotuned
                        choice for (model, N) if any, else the default variant */
   double dt;        /* time step used by dg_step (may be changed by dg_set_dt) */
   void *stream;     /* cudaStream_t; NULL = legacy default stream        */
+  int strategy;     /* DG_STRATEGY_* (0 = fused)                         */
 } dg_opts;
 
 typedef struct dg_handle dg_handle;
@@ -237,9 +257,10 @@ typedef struct {
   const double *coeffs;
   int N;
   int model;
-  dg_opts opts;          /* flux, bc, dt; precision must be DG_FP32 (served
-                            solves run the batched FP32 kernels, else
-                            DG_EINVAL); block_elems and stream are ignored */
+  dg_opts opts;          /* flux, bc, dt; precision must be DG_FP32 and
+                            strategy DG_STRATEGY_FUSED (served solves run
+                            the batched FP32 kernels, else DG_EINVAL);
+                            block_elems and stream are ignored */
   const float *q0;       /* host [K][Nf][Np]; NULL = zero state              */
   const double *src_xyz; /* NULL = no source                                  */
   const double *src_dir; /* elastic only; NULL = (0,0,1)                      */

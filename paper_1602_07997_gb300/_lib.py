@@ -18,7 +18,8 @@ DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONFINITE, DG_ETIMEOUT, DG_EAGAIN, DG
 ACOUSTIC, ELASTIC = 0, 1
 FLUX = {"upwind": 0, "centered": 1, "centred": 1}
 BC = {None: 0, "default": 0, "rigid": 1, "free": 2}
-PRECISION = {"fp32": 0, "bf16x3": 1, "bf16x6": 2}
+PRECISION = {"fp32": 0, "bf16x3": 1, "bf16x6": 2, "tf32": 3}
+STRATEGY = {"fused": 0, "library": 1, "plain": 2}
 
 # every symbol that include/dg.h declares
 EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", "dg_rhs", "dg_step",
@@ -40,7 +41,7 @@ class Mesh(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("flux", C.c_int), ("bc", C.c_int), ("precision", C.c_int),
-                ("block_elems", C.c_int), ("dt", C.c_double), ("stream", C.c_void_p)]
+                ("block_elems", C.c_int), ("dt", C.c_double), ("stream", C.c_void_p), ("strategy", C.c_int)]
 
 
 class Request(C.Structure):
@@ -169,11 +170,11 @@ class Solver:
     """One DG discretisation on the GPU (a dg_handle)."""
 
     def __init__(self, verts, tets, coeffs, N, model="acoustic", flux="upwind", bc=None, dt=0.0,
-                 stream=None, block_elems=0, precision="fp32"):
+                 stream=None, block_elems=0, precision="fp32", strategy="fused"):
         m, keep = make_mesh(verts, tets)
         cf = np.ascontiguousarray(coeffs, dtype=np.float64)
         o = Opts(FLUX[flux], BC[bc], PRECISION[precision], int(block_elems), float(dt),
-                 C.c_void_p(stream or 0))
+                 C.c_void_p(stream or 0), STRATEGY[strategy])
         h = C.c_void_p()
         check(lib().dg_setup(C.byref(m), _dptr(cf), int(N), _model(model), C.byref(o), C.byref(h)))
         self.h = h

@@ -16,7 +16,7 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["dg_kernels_acoustic.cu", "dg_kernels_elastic.cu", "dg_kernels_tc_acoustic.cu",
+CU_SOURCES = ["dg_kernels_acoustic.cu", "dg_kernels_elastic.cu", "dg_kernels_tc_acoustic.cu", "dg_strategies.cu",
               "dg_kernels_tc_elastic.cu", "dg_dispatch.cu", "rhs_noalloc.cu"]
 CPP_SOURCES = ["api.cpp", "refelem.cpp", "mesh.cpp", "server.cpp"]
 
@@ -63,7 +63,7 @@ def build(verbose=False, force=False, ptxas_info=False):
                 print(o)
     objs = [os.path.join(OUT, f + ".o") for f in CU_SOURCES + CPP_SOURCES]
     if force or jobs or not os.path.exists(LIB):
-        _run([NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs, "-lpthread",
+        _run([NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs, "-lcublas", "-lpthread",
               "-Xlinker", "-rpath=" + os.path.join(CUDA, "lib64")])
     return LIB
 

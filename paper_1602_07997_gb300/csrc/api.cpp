@@ -8,9 +8,11 @@
 #include <tuple>
 #include <vector>
 
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include "dg_args.h"
+#include "dg_strategies.h"
 #include "dg_internal.h"
 #include "dg_handle.h"
 
@@ -164,8 +166,14 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
   if (opts.bc < DG_BC_DEFAULT || opts.bc > DG_BC_FREE) return fail(DG_EINVAL, "unknown boundary condition");
   if (model == DG_ACOUSTIC && opts.bc == DG_BC_FREE)
     return fail(DG_EINVAL, "acoustic model supports rigid walls only");
-  if (opts.precision != DG_FP32 && opts.precision != DG_BF16X3 && opts.precision != DG_BF16X6)
-    return fail(DG_EINVAL, "unknown precision mode");
+  if (opts.strategy < DG_STRATEGY_FUSED || opts.strategy > DG_STRATEGY_PLAIN) return fail(DG_EINVAL, "unknown strategy");
+  if (opts.strategy == DG_STRATEGY_FUSED && opts.precision != DG_FP32 && opts.precision != DG_BF16X3 &&
+      opts.precision != DG_BF16X6)
+    return fail(DG_EINVAL, "the fused strategy supports DG_FP32, DG_BF16X3 and DG_BF16X6");
+  if (opts.strategy == DG_STRATEGY_LIBRARY && opts.precision != DG_FP32 && opts.precision != DG_TF32)
+    return fail(DG_EINVAL, "the library strategy supports DG_FP32 and DG_TF32");
+  if (opts.strategy == DG_STRATEGY_PLAIN && opts.precision != DG_FP32)
+    return fail(DG_EINVAL, "the plain strategy supports DG_FP32");
   stream = static_cast<cudaStream_t>(opts.stream);
   int rc = ref.build(N);
   if (rc) return rc;
@@ -177,7 +185,8 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
   Nfp = ref.Nfp;
   Nf = num_fields(model);
   K = hm.K;
-  cfg = select_variant(model, N, opts.block_elems, device_of_current(), opts.precision);
+  cfg = select_variant(model, N, opts.block_elems, device_of_current(),
+                       opts.strategy == DG_STRATEGY_FUSED ? opts.precision : DG_FP32);
   if (!cfg) return fail(DG_EINVAL, "no compiled kernel variant with block_elems = " + std::to_string(opts.block_elems));
   // every launch reads whole blocks of EB <= 128 elements with bulk copies:
   // pad the element arrays so that the last block stays inside the allocation
@@ -237,6 +246,72 @@ Handle::~Handle() {
   if (d_base) cudaFree(d_base);
   if (d_split) cudaFree(d_split);
   if (d_tc) cudaFree(d_tc);
+  if (d_lib) cudaFree(d_lib);
+  if (d_r0) cudaFree(d_r0);
+  if (cublas) cublasDestroy(static_cast<cublasHandle_t>(cublas));
+}
+
+// Buffers of the comparison strategies, on first use.
+int Handle::ensure_strategy() {
+  if (opts.strategy == DG_STRATEGY_PLAIN && !d_r0) {
+    DG_CUDA(cudaMalloc(reinterpret_cast<void**>(&d_r0), state_bytes));
+    split_bytes += state_bytes;
+  }
+  if (opts.strategy == DG_STRATEGY_LIBRARY && !d_lib) {
+    const dgk::KernelCfg* f = dgk::front_cfg(model, N);
+    if (!f) return fail(DG_EINVAL, "no library-route front half for this degree");
+    const size_t nt = size_t((Kpad + f->gemm_ne - 1) / f->gemm_ne) + 1;
+    const size_t xbytes = (nt * f->gemm_xtile + 255) & ~size_t(255);
+    const int KD = 3 * Np + 4 * Nfp, MP2 = f->gemm_mp2;
+    std::vector<float> ops2(size_t(KD) * MP2, 0.0f);
+    const std::vector<double>* D[3] = {&ref.Dr, &ref.Ds, &ref.Dt};
+    for (int d = 0; d < 3; ++d)
+      for (int j = 0; j < Np; ++j)
+        for (int i = 0; i < Np; ++i) ops2[size_t(d * Np + j) * MP2 + i] = float((*D[d])[size_t(i) * Np + j]);
+    for (int cc = 0; cc < 4 * Nfp; ++cc)
+      for (int i = 0; i < Np; ++i) ops2[size_t(3 * Np + cc) * MP2 + i] = float(ref.LIFT[size_t(i) * 4 * Nfp + cc]);
+    const size_t obytes = (ops2.size() * 4 + 255) & ~size_t(255);
+    libyprod = nt * size_t(f->gemm_ne) * Np;
+    const size_t ybytes = size_t(dgk::library_products(model)) * libyprod * 4;
+    DG_CUDA(cudaMalloc(&d_lib, xbytes + obytes + ybytes));
+    split_bytes += xbytes + obytes + ybytes;
+    d_libx = static_cast<float*>(d_lib);
+    d_libops = reinterpret_cast<float*>(static_cast<char*>(d_lib) + xbytes);
+    d_liby = reinterpret_cast<float*>(static_cast<char*>(d_lib) + xbytes + obytes);
+    DG_CUDA(cudaMemsetAsync(d_libx, 0, xbytes, stream));
+    DG_CUDA(cudaMemcpyAsync(d_libops, ops2.data(), ops2.size() * 4, cudaMemcpyHostToDevice, stream));
+    DG_CUDA(cudaStreamSynchronize(stream));
+    cublasHandle_t hb = nullptr;
+    if (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) return fail(DG_ECUDA, "cublasCreate failed");
+    cublas = hb;
+    if (cublasSetMathMode(hb, opts.precision == DG_TF32 ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_DEFAULT_MATH) !=
+        CUBLAS_STATUS_SUCCESS)
+      return fail(DG_ECUDA, "cublasSetMathMode failed");
+  }
+  return DG_OK;
+}
+
+int Handle::launch(dgk::StepArgs a) {
+  if (opts.strategy == DG_STRATEGY_FUSED) {
+    DG_CUDA(dgk::launch_step(cfg, a, stream));
+    return DG_OK;
+  }
+  int rc = ensure_strategy();
+  if (rc) return rc;
+  if (opts.strategy == DG_STRATEGY_PLAIN) {
+    DG_CUDA(dgk::launch_plain_step(model, N, a, d_r0, stream));
+    return DG_OK;
+  }
+  // library route: front half, GEMMs, epilogue
+  a.xg = d_libx;
+  a.ops2 = d_libops;
+  DG_CUDA(dgk::launch_step(dgk::front_cfg(model, N), a, stream));
+  cublasHandle_t hb = static_cast<cublasHandle_t>(cublas);
+  if (cublasSetStream(hb, stream) != CUBLAS_STATUS_SUCCESS) return fail(DG_ECUDA, "cublasSetStream failed");
+  const int st = dgk::library_gemms(cublas, model, N, a, d_liby, libyprod);
+  if (st != 0) return fail(DG_ECUDA, "cuBLAS SGEMM failed with status " + std::to_string(st));
+  DG_CUDA(dgk::launch_library_epilogue(model, N, a, d_liby, libyprod, stream));
+  return DG_OK;
 }
 
 // BF16 rounding (nearest, ties to even) of a finite float, as raw bits.
@@ -292,7 +367,7 @@ static int pack_tc_ops(const RefElement& R, int nsplit, int mtiles, std::vector<
 
 // Buffers of the split step: X[tiles][KX][NE] and the operator blob with rows padded.
 int Handle::ensure_split(const dgk::KernelCfg* c) {
-  if (!c || !c->split) return DG_OK;
+  if (!c || !c->split || opts.strategy != DG_STRATEGY_FUSED) return DG_OK;
   if (c->split == 2) {
     if (d_tc) return DG_OK;
     const size_t ntiles = size_t((Kpad + c->gemm_ne - 1) / c->gemm_ne) + 1;
@@ -369,7 +444,8 @@ int Handle::advance(int nsteps) {
   if (rc) return rc;
   for (int s = 0; s < nsteps; ++s) {
     dgk::StepArgs a = args(0);
-    DG_CUDA(dgk::launch_step(cfg, a, stream));
+    int lr = launch(a);
+    if (lr) return lr;
     qcur ^= 1;
     r1slot ^= 1;  // r^m was written into the r^{m-2} slot
     ++step;
@@ -460,10 +536,10 @@ int dg_rhs(dg_handle* h, float* r_out, int on_device) {
     DG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&tmp), bytes, h->stream));
     a.rout = tmp;
   }
-  cudaError_t e = dgk::launch_step(h->cfg, a, h->stream);
-  if (e != cudaSuccess) {
+  const int lr = h->launch(a);
+  if (lr) {
     if (tmp) cudaFreeAsync(tmp, h->stream);
-    return dg::cuda_fail(e, "launch");
+    return lr;
   }
   if (!on_device) {
     DG_CUDA(cudaMemcpyAsync(r_out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -563,6 +639,7 @@ int dg_set_source(dg_handle* h, const double xs[3], const double dir[3], const d
 
 int dg_autotune(dg_handle* h, int reps, int* block_elems, double* ms_per_step, double* variant_ms) {
   if (!h || reps < 1) return fail(DG_EINVAL, "NULL handle or reps < 1");
+  if (h->opts.strategy != DG_STRATEGY_FUSED) return fail(DG_EINVAL, "kernel variants apply to the fused strategy");
   int n = 0;
   const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n, h->opts.precision);
   for (int i = 0; i < n; ++i) {
@@ -643,6 +720,7 @@ int dg_autotune(dg_handle* h, int reps, int* block_elems, double* ms_per_step, d
 
 int dg_set_variant(dg_handle* h, int index) {
   if (!h) return fail(DG_EINVAL, "NULL handle");
+  if (h->opts.strategy != DG_STRATEGY_FUSED) return fail(DG_EINVAL, "kernel variants apply to the fused strategy");
   int n = 0;
   const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n, h->opts.precision);
   if (index < 0 || index >= n) return fail(DG_EINVAL, "variant index out of range");

@@ -50,6 +50,15 @@ struct Handle {
   void* d_tc = nullptr;
   float* d_xtc = nullptr;
   void* d_opstc = nullptr;
+  // comparison strategies (allocated on first use): library route X, operator
+  // blob and GEMM products; plain route partial RHS
+  void* cublas = nullptr;
+  void* d_lib = nullptr;
+  float* d_libx = nullptr;
+  float* d_libops = nullptr;
+  float* d_liby = nullptr;
+  size_t libyprod = 0;
+  float* d_r0 = nullptr;
 
   int qcur = 0;    // which q buffer holds q^m
   int r1slot = 0;  // which r buffer holds r^{m-1}; the other holds r^{m-2}
@@ -60,6 +69,9 @@ struct Handle {
 
   int init(const dg_mesh* mesh, const double* coeffs, int N, int model, const dg_opts* o);
   int ensure_split(const dgk::KernelCfg* c);
+  int ensure_strategy();
+  // one step (a.mode 0) or RHS (mode 1) with the handle's strategy
+  int launch(dgk::StepArgs a);
   // the split-step buffers of variant c (own, or those of the handle's variant)
   void split_ptrs(dgk::StepArgs& a, const dgk::KernelCfg* c) const;
   dgk::StepArgs args(int mode) const;

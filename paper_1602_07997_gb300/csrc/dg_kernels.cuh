@@ -234,6 +234,116 @@ __device__ __forceinline__ void bf16_pieces8(const float* x, uint4* out) {
   }
 }
 
+// Outward unit normal and Fscale = |g N_f| of face f of an element with
+// inverse metric g (row-major g[c][d] = dr_d/dx_c): n = g N_f / |g N_f|.
+__device__ __forceinline__ float4 face_normal(const float* g, int f) {
+  float nv[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    nv[c] = g[3 * c] * ref_normal(f, 0) + g[3 * c + 1] * ref_normal(f, 1) + g[3 * c + 2] * ref_normal(f, 2);
+  const float fs = sqrtf(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+  const float inv = 1.0f / fs;
+  return make_float4(nv[0] * inv, nv[1] * inv, nv[2] * inv, fs);
+}
+
+// Fscale-weighted penalty terms at one face node (Section 2.1): the numerical
+// flux across the face minus the own trace's flux, for the upwind (flux = 0)
+// or centred (flux = 1) flux, with the mirror ghost state on the outer
+// boundary (acoustic rigid wall; elastic bc = 0 traction-free, 1 rigid).
+//   gM: the element's record; f: its face; qM, qP: own and neighbour traces
+//   (qP unused on the boundary); fn = (n_x, n_y, n_z, Fscale) of the face.
+//   pen[Nf]: acoustic (dp, dv_x, dv_y, dv_z), elastic (p_v[3], P_sigma[6]).
+template <int MODEL>
+__device__ __forceinline__ void face_penalty(const float* gM, int f, bool bnd, const float* qM, const float* qPv,
+                                             const float4 fn, int flux, int bc, float* pen) {
+  const float nx = fn.x, ny = fn.y, nz = fn.z, fs = fn.w;
+  if constexpr (MODEL == 0) {
+    const float kap = gM[9], rinv = gM[10], ZM = gM[11], zP = gM[12 + f];
+    float pP, vP0, vP1, vP2;
+    if (bnd) {  // rigid wall: p+ = p-, v+ = v- - 2 (v-.n) n
+      const float vn = qM[1] * nx + qM[2] * ny + qM[3] * nz;
+      pP = qM[0];
+      vP0 = qM[1] - 2.f * vn * nx;
+      vP1 = qM[2] - 2.f * vn * ny;
+      vP2 = qM[3] - 2.f * vn * nz;
+    } else {
+      pP = qPv[0]; vP0 = qPv[1]; vP1 = qPv[2]; vP2 = qPv[3];
+    }
+    const float jp = 0.5f * (pP - qM[0]);
+    const float jvn = 0.5f * ((vP0 - qM[1]) * nx + (vP1 - qM[2]) * ny + (vP2 - qM[3]) * nz);
+    float dp, sv;  // dv = sv * n
+    if (flux == 0) {
+      const float kc = 2.f / (ZM + zP);
+      const float ac = jp - zP * jvn;
+      dp = kap * kc * ac;
+      sv = -(ZM * rinv) * kc * ac;  // c^- = Z^- / rho^-
+    } else {
+      dp = -kap * jvn;
+      sv = -rinv * jp;
+    }
+    pen[0] = fs * dp;
+    pen[1] = fs * sv * nx;
+    pen[2] = fs * sv * ny;
+    pen[3] = fs * sv * nz;
+  } else {
+    const float lam = gM[9], mu = gM[10], rinv = gM[11], ZpM = gM[12], ZsM = gM[13], cpM = gM[14],
+                csM = gM[15], zP0 = gM[16 + f], zP1 = gM[20 + f];
+    float vP[3], sPd[6];
+    if (bnd) {
+      const float sv = (bc == 0) ? 1.f : -1.f;  // free: v+ = v-, sigma+ = -sigma-
+#pragma unroll
+      for (int c = 0; c < 3; ++c) vP[c] = sv * qM[c];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sPd[c] = -sv * qM[3 + c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) vP[c] = qPv[c];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sPd[c] = qPv[3 + c];
+    }
+    const float n[3] = {nx, ny, nz};
+    float ds[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) ds[c] = sPd[c] - qM[3 + c];
+    float jt[3], jv[3];  // [[sigma n]], [[v]]  (sxx syy szz sxy sxz syz)
+    jt[0] = 0.5f * (ds[0] * nx + ds[3] * ny + ds[4] * nz);
+    jt[1] = 0.5f * (ds[3] * nx + ds[1] * ny + ds[5] * nz);
+    jt[2] = 0.5f * (ds[4] * nx + ds[5] * ny + ds[2] * nz);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) jv[c] = 0.5f * (vP[c] - qM[c]);
+    float pv[3], dv[3];  // p_v and the velocity jump with P_sigma = C:sym(n (x) dv)
+    if (flux == 0) {
+      const float jsnn = jt[0] * nx + jt[1] * ny + jt[2] * nz;
+      const float jvn = jv[0] * nx + jv[1] * ny + jv[2] * nz;
+      const float ap = jsnn + zP0 * jvn;
+      const float as = jsnn + zP1 * jvn;
+      const float kp = 2.f / (ZpM + zP0), ks = 2.f / (ZsM + zP1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float tang = (jt[c] + zP1 * jv[c]) - as * n[c];
+        dv[c] = kp * ap * n[c] + ks * tang;
+        pv[c] = kp * ap * cpM * n[c] + ks * csM * tang;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dv[c] = jv[c];
+        pv[c] = rinv * jt[c];
+      }
+    }
+    const float ndv = nx * dv[0] + ny * dv[1] + nz * dv[2];
+    pen[0] = fs * pv[0];
+    pen[1] = fs * pv[1];
+    pen[2] = fs * pv[2];
+    pen[3] = fs * (lam * ndv + 2.f * mu * nx * dv[0]);
+    pen[4] = fs * (lam * ndv + 2.f * mu * ny * dv[1]);
+    pen[5] = fs * (lam * ndv + 2.f * mu * nz * dv[2]);
+    pen[6] = fs * (mu * (nx * dv[1] + ny * dv[0]));
+    pen[7] = fs * (mu * (nx * dv[2] + nz * dv[0]));
+    pen[8] = fs * (mu * (ny * dv[2] + nz * dv[1]));
+  }
+}
+
 // ---------------------------------------------------------------- block providers
 // A provider maps a global block index to the arguments of the solve it
 // belongs to and to its local block index; operators, face tables, error word
@@ -415,14 +525,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     // -------- face normals and Fscale (n = g N_f / |g N_f|)
     for (int i = tid; i < EB * 4; i += NT) {
       const int e = i >> 2, f = i & 3;
-      const float* gk = sRec + e * REC;
-      float nv[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        nv[c] = gk[3 * c] * ref_normal(f, 0) + gk[3 * c + 1] * ref_normal(f, 1) + gk[3 * c + 2] * ref_normal(f, 2);
-      const float fs = sqrtf(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
-      const float inv = 1.0f / fs;
-      *reinterpret_cast<float4*>(sFn + i * 4) = make_float4(nv[0] * inv, nv[1] * inv, nv[2] * inv, fs);
+      *reinterpret_cast<float4*>(sFn + i * 4) = face_normal(sRec + e * REC, f);
     }
     // -------- volume inputs (node index fastest: conflict-free reads of q)
     for (int i = tid; i < EB * Np; i += NT) {
@@ -480,98 +583,16 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       }
       const float* qe = sQ + e * Nf * Np;
       const float4 fn = *reinterpret_cast<const float4*>(sFn + (e * 4 + f) * 4);
-      const float nx = fn.x, ny = fn.y, nz = fn.z, fs = fn.w;
       const float* gM = sRec + e * REC;
       float qM[Nf];
 #pragma unroll
       for (int c = 0; c < Nf; ++c) qM[c] = qe[c * Np + nM];
       float* X = sXs + fm * EBP + e;
       constexpr int XS = NFN * EBP;
-      if constexpr (MODEL == 0) {
-        const float kap = gM[9], rinv = gM[10], ZM = gM[11], zP = gM[12 + f];
-        float pP, vP0, vP1, vP2;
-        if (bnd) {  // rigid wall: p+ = p-, v+ = v- - 2 (v-.n) n
-          const float vn = qM[1] * nx + qM[2] * ny + qM[3] * nz;
-          pP = qM[0];
-          vP0 = qM[1] - 2.f * vn * nx;
-          vP1 = qM[2] - 2.f * vn * ny;
-          vP2 = qM[3] - 2.f * vn * nz;
-        } else {
-          pP = qPv[0]; vP0 = qPv[1]; vP1 = qPv[2]; vP2 = qPv[3];
-        }
-        const float jp = 0.5f * (pP - qM[0]);
-        const float jvn = 0.5f * ((vP0 - qM[1]) * nx + (vP1 - qM[2]) * ny + (vP2 - qM[3]) * nz);
-        float dp, sv;  // dv = sv * n
-        if (a.flux == 0) {
-          const float kc = 2.f / (ZM + zP);
-          const float ac = jp - zP * jvn;
-          dp = kap * kc * ac;
-          sv = -(ZM * rinv) * kc * ac;  // c^- = Z^- / rho^-
-        } else {
-          dp = -kap * jvn;
-          sv = -rinv * jp;
-        }
-        X[0] = fs * dp;
-        X[XS] = fs * sv * nx;
-        X[2 * XS] = fs * sv * ny;
-        X[3 * XS] = fs * sv * nz;
-      } else {
-        const float lam = gM[9], mu = gM[10], rinv = gM[11], ZpM = gM[12], ZsM = gM[13], cpM = gM[14],
-                    csM = gM[15], zP0 = gM[16 + f], zP1 = gM[20 + f];
-        float vP[3], sPd[6];
-        if (bnd) {
-          const float sv = (a.bc == 0) ? 1.f : -1.f;  // free: v+ = v-, sigma+ = -sigma-
+      float pen[Nf];
+      face_penalty<MODEL>(gM, f, bnd, qM, qPv, fn, a.flux, a.bc, pen);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) vP[c] = sv * qM[c];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) sPd[c] = -sv * qM[3 + c];
-        } else {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) vP[c] = qPv[c];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) sPd[c] = qPv[3 + c];
-        }
-        const float n[3] = {nx, ny, nz};
-        float ds[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) ds[c] = sPd[c] - qM[3 + c];
-        float jt[3], jv[3];  // [[sigma n]], [[v]]  (sxx syy szz sxy sxz syz)
-        jt[0] = 0.5f * (ds[0] * nx + ds[3] * ny + ds[4] * nz);
-        jt[1] = 0.5f * (ds[3] * nx + ds[1] * ny + ds[5] * nz);
-        jt[2] = 0.5f * (ds[4] * nx + ds[5] * ny + ds[2] * nz);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) jv[c] = 0.5f * (vP[c] - qM[c]);
-        float pv[3], dv[3];  // p_v and the velocity jump with P_sigma = C:sym(n (x) dv)
-        if (a.flux == 0) {
-          const float jsnn = jt[0] * nx + jt[1] * ny + jt[2] * nz;
-          const float jvn = jv[0] * nx + jv[1] * ny + jv[2] * nz;
-          const float ap = jsnn + zP0 * jvn;
-          const float as = jsnn + zP1 * jvn;
-          const float kp = 2.f / (ZpM + zP0), ks = 2.f / (ZsM + zP1);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float tang = (jt[c] + zP1 * jv[c]) - as * n[c];
-            dv[c] = kp * ap * n[c] + ks * tang;
-            pv[c] = kp * ap * cpM * n[c] + ks * csM * tang;
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            dv[c] = jv[c];
-            pv[c] = rinv * jt[c];
-          }
-        }
-        const float ndv = nx * dv[0] + ny * dv[1] + nz * dv[2];
-        X[0 * XS] = fs * pv[0];
-        X[1 * XS] = fs * pv[1];
-        X[2 * XS] = fs * pv[2];
-        X[3 * XS] = fs * (lam * ndv + 2.f * mu * nx * dv[0]);
-        X[4 * XS] = fs * (lam * ndv + 2.f * mu * ny * dv[1]);
-        X[5 * XS] = fs * (lam * ndv + 2.f * mu * nz * dv[2]);
-        X[6 * XS] = fs * (mu * (nx * dv[1] + ny * dv[0]));
-        X[7 * XS] = fs * (mu * (nx * dv[2] + nz * dv[0]));
-        X[8 * XS] = fs * (mu * (ny * dv[2] + nz * dv[1]));
-      }
+      for (int c = 0; c < Nf; ++c) X[c * XS] = pen[c];
     }
     __syncthreads();
     // the next block's stage was issued at the top of this block: once it has

@@ -566,8 +566,9 @@ int dg_submit(dg_server* s, const dg_request* req, uint64_t* ticket) {
   if (req->model != DG_ACOUSTIC && req->model != DG_ELASTIC) return fail(DG_EINVAL, "unknown model");
   if (req->nsteps < 0) return fail(DG_EINVAL, "negative step count");
   if (!(req->opts.dt > 0)) return fail(DG_EINVAL, "dt must be positive");
-  if (req->opts.precision != DG_FP32)
-    return fail(DG_EINVAL, "served solves run the batched FP32 kernels: precision must be DG_FP32");
+  if (req->opts.precision != DG_FP32 || req->opts.strategy != DG_STRATEGY_FUSED)
+    return fail(DG_EINVAL, "served solves run the batched FP32 fused kernels: precision must be DG_FP32 and "
+                           "strategy DG_STRATEGY_FUSED");
   const dg_mesh* m = req->mesh;
   if (!m->verts || !m->tets || m->ntets <= 0 || m->nverts < 4) return fail(DG_EINVAL, "empty mesh");
   auto r = std::make_shared<dg::Request>();

@@ -81,3 +81,15 @@ def test_host_validation_rejects_bad_input(P):
         with pytest.raises(P.DGError) as e:
             P.suggest_dt(*args)
         assert e.value.code == -1
+
+
+def test_strategy_and_precision_combinations_checked_before_device_use(P):
+    """Each strategy takes only its precision modes (DG_EINVAL otherwise), and
+    the check comes before any device allocation."""
+    verts, tets = W.kuhn_cube_mesh(2, 0.1, seed=1)
+    c = np.ones((tets.shape[0], 2))
+    for strategy, precision in (("plain", "bf16x6"), ("plain", "tf32"), ("fused", "tf32"),
+                                ("library", "bf16x3"), ("library", "bf16x6")):
+        with pytest.raises(P.DGError) as e:
+            P.Solver(verts, tets, c, 2, "acoustic", strategy=strategy, precision=precision)
+        assert e.value.code == -1, (strategy, precision)
