@@ -293,16 +293,17 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def make_solvers(P, cfgs, model, precision, stream, tune, variants=None):
+def make_solvers(P, cfgs, model, precision, stream, tune, variants=None, strategy="fused"):
     solvers = []
+    tune = tune and strategy == "fused"
     for i, cfg in enumerate(cfgs):
         N = cfg["N"]
         dt = P.suggest_dt(cfg["verts"], cfg["tets"], cfg["coeffs"], N, model, 0.4)
         g = P.Solver(cfg["verts"], cfg["tets"], cfg["coeffs"], N, model, dt=dt,
-                     stream=stream.cuda_stream, precision=precision)
+                     stream=stream.cuda_stream, precision=precision, strategy=strategy)
         q = np.random.default_rng(N).uniform(-1, 1, size=g.shape).astype(np.float32)
         g.set_state(q)
-        if variants is not None:
+        if variants is not None and strategy == "fused":
             g.set_variant(variants[i])
         elif tune:
             g.autotune(5)
@@ -310,7 +311,12 @@ def make_solvers(P, cfgs, model, precision, stream, tune, variants=None):
     return solvers
 
 
-def launches_per_step(g):
+def launches_per_step(g, strategy="fused"):
+    """Kernels of this library launched per step (cuBLAS GEMMs not counted)."""
+    if strategy == "library":
+        return 2  # front half + epilogue
+    if strategy == "plain":
+        return 3  # volume, surface, update
     return 2 if g.kernel_info()["split"] else 1
 
 
@@ -349,16 +355,18 @@ def time_sweep(solvers, steps, stream):
 
 
 def extra_sweeps(P, args, acoustic_cfgs, stream, pk):
-    """Acoustic bf16x6 on the headline meshes; elastic FP32 and bf16x6 on the
-    elastic sweep meshes (lambda, mu, rho ~ U[1,3] with a two-layer jump).
-    For each bf16x6 mesh the state after --sweep-steps steps is compared with
-    the FP32 path's (relative L2)."""
+    """Acoustic bf16x6, library route and plain route on the headline meshes;
+    elastic FP32, bf16x6, library and plain routes on the elastic sweep meshes
+    (lambda, mu, rho ~ U[1,3] with a two-layer jump).  The state after
+    --sweep-steps steps of every non-reference sweep is compared with the
+    fused FP32 path's (relative L2)."""
     Ns = [cfg["N"] for cfg in acoustic_cfgs]
     res = {}
     for model, cfgs in (("acoustic", acoustic_cfgs), ("elastic", None)):
         if cfgs is None:
             cfgs = build_meshes(model, Ns)
-        precs = ("bf16x6",) if model == "acoustic" else ("fp32", "bf16x6")
+        precs = (("bf16x6", "fused"), ("fp32", "library"), ("fp32", "plain")) if model == "acoustic" else \
+            (("fp32", "fused"), ("bf16x6", "fused"), ("fp32", "library"), ("fp32", "plain"))
         ref_states = {}
         if model == "acoustic":
             ref = make_solvers(P, cfgs, model, "fp32", stream, False)
@@ -367,16 +375,19 @@ def extra_sweeps(P, args, acoustic_cfgs, stream, pk):
                 g.sync()
                 ref_states[g.N] = g.get_state()
                 g.close()
-        for prec in precs:
-            solvers = make_solvers(P, cfgs, model, prec, stream, not args.no_tune)
+        for prec, strat in precs:
+            solvers = make_solvers(P, cfgs, model, prec, stream, not args.no_tune, strategy=strat)
             ms = time_sweep(solvers, args.sweep_steps, stream)
             rows = {}
             for g, t in zip(solvers, ms):
                 rows[str(g.N)] = per_degree(model, g, t, pk, tensor=prec != "fp32")
-            if prec != "fp32" or model == "elastic":
+                rows[str(g.N)]["strategy"] = strat
+                if strat != "fused":
+                    del rows[str(g.N)]["kernel"]
+            if prec != "fp32" or model == "elastic" or strat != "fused":
                 # states after 2 + sweep_steps steps from the same initial state
                 for g in solvers:
-                    if prec == "fp32":
+                    if prec == "fp32" and strat == "fused":
                         ref_states[g.N] = g.get_state()
                     elif g.N in ref_states:
                         a = g.get_state().astype(np.float64)
@@ -384,7 +395,8 @@ def extra_sweeps(P, args, acoustic_cfgs, stream, pk):
                         rows[str(g.N)]["rel_l2_vs_fp32"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
             tot = sum(ms)
             upd = sum(g.K * g.Np * g.Nf for g in solvers)
-            res["%s_%s" % (model, prec)] = {"per_N": rows, "ms_per_sweep_step": round(tot, 4),
+            key = "%s_%s" % (model, prec) if strat == "fused" else "%s_%s_%s" % (model, strat, prec)
+            res[key] = {"per_N": rows, "ms_per_sweep_step": round(tot, 4),
                                             "updates_per_s": upd / (tot * 1e-3), "steps": args.sweep_steps}
             for g in solvers:
                 g.close()
@@ -404,7 +416,7 @@ def run(args, rank, world, local_rank):
     variants = [int(x) for x in args.variants.split(",")] if args.variants else None
     if variants is not None and len(variants) != len(Ns):
         raise SystemExit("--variants needs one index per degree")
-    solvers = make_solvers(P, cfgs, model, args.precision, stream, not args.no_tune, variants)
+    solvers = make_solvers(P, cfgs, model, args.precision, stream, not args.no_tune, variants, args.strategy)
     torch.cuda.synchronize()
 
     def barrier():
@@ -450,7 +462,7 @@ def run(args, rank, world, local_rank):
         if dom is None or ms > dom[1]:
             byt, flop = algorithmic(model, g.N, g.K)
             dom = (g, ms, byt, flop, row["bound"])
-    launches = sum(launches_per_step(g) for g in solvers) * args.steps
+    launches = sum(launches_per_step(g, args.strategy) for g in solvers) * args.steps
     g, ms, byt, flop, bound = dom
     traffic = None
     try:
@@ -554,7 +566,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-steps", type=int, default=500)
     ap.add_argument("--no-sweeps", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16x6"],
+    ap.add_argument("--strategy", default="fused", choices=["fused", "library", "plain"],
+                    help="step strategy of the timed sweep (default: the fused step)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16x6", "tf32"],
                     help="arithmetic of the timed sweep's operator contractions (default FP32)")
     ap.add_argument("--variants", default="",
                     help="kernel variant index per degree instead of autotuning (e.g. to replay a run's choice)")

@@ -1,21 +1,37 @@
-// Split step for high degree: operator products as a GEMM over element tiles.
+// Split step, FP32 back half: operator products as a register-tiled GEMM over
+// column tiles of elements.
 //
 // At high N the operator blob [Dr Ds Dt LIFT] no longer fits in shared
 // memory next to a block of elements, so the fused kernel must stream it
 // from L2 once per block of a few elements.  The split step instead
-//   kernel A (the fused kernel's front half, SPLIT = true): stages q, records
+//   kernel A (the fused kernel's front half, SPLIT = NE): stages q, records
 //     and neighbour traces as usual, computes the volume inputs and the
 //     Fscale-weighted penalties, and writes them to a global buffer X laid
 //     out in column tiles of NE elements: X[tile][row][NE] (row = the input
 //     index of the operator products);
-//   kernel B (this file): a CTA owns MT output rows x NE elements; operator
-//     rows and X rows stream through shared memory in double-buffered K
-//     chunks (16-byte cp.async), every operator row chunk is reused by NE
-//     elements; one thread accumulates 4 RQ rows x TN elements of every product
-//     (G_d = D_d p, R = sum_d D_d w_d + LIFT P_p, L_c = LIFT P_vc for the
-//     acoustic model; U_cd = D_d v_c, Rv_c = sum_d D_d s_cd + LIFT P_vc,
-//     LIFT P_sig for the elastic model) and does the geometric combination
-//     and the AB3 update (Eq. updateScheme) from registers.
+//   kernel B (this file, two designs; the autotuner times both):
+//   design A: a CTA owns 32 output rows x NE elements, one thread 4 (or 8)
+//     rows x TN elements of every one of the 7 (acoustic) / 18 (elastic)
+//     products, double-buffered 16-deep K chunks, and the combination and
+//     AB3 update in the epilogue;
+//   design B: a CTA owns MT output rows x NE elements; operator
+//     rows and X rows stream through shared memory in 16-deep K chunks
+//     (16-byte cp.async, NS-stage ring), every operator row is reused by NE
+//     elements and every X row by MT rows.  One thread accumulates TM rows x
+//     TE elements.  The K loop runs the volume chunks (D_r, D_s, D_t) and then
+//     the LIFT chunks; at the boundary the accumulators of the pure derivative
+//     products are combined with the element's geometric factors into the
+//     RHS components, and the LIFT products accumulate straight onto them:
+//       acoustic: G_d = D_d p and R = sum_d D_d w_d over the volume chunks;
+//                 then T_c = -(1/rho) sum_d g_cd G_d, and over the LIFT
+//                 chunks r_v,c = T_c + LIFT P_v,c, r_p = R + LIFT P_p
+//                 (4 accumulators per output instead of 7);
+//       elastic:  U_cd = D_d v_c and Rv_c = sum_d D_d s_cd over the volume
+//                 chunks; then the stress parts S (lambda div v + 2 mu dv_i/dx_i,
+//                 mu (dv_i/dx_j + dv_j/dx_i)) from U, and over the LIFT chunks
+//                 r_sig = S + LIFT P_sig, r_v,c = Rv_c + LIFT P_v,c.
+//   The epilogue stages one field at a time in shared memory and runs the
+//   point source and the AB3 update (Eq. updateScheme) with coalesced accesses.
 #pragma once
 
 #include "dg_kernels.cuh"
@@ -25,10 +41,29 @@ namespace dgk {
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait_n() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
+}
 
+// Layout shared by the front half, both GEMM designs and the library route:
+// X[tile][row][NE] (KX rows per element) and the operator blob
+// [3 Np + 4 Nfp][OPP] (row = input index, column = output node, OPP = Np
+// rounded up to 32, enough for every design's row tiles).
 template <int MODEL, int N>
 struct SplitShape {
+  using S = Sz<N>;
+  static constexpr int Np = S::Np, NFN = S::NFN;
+  static constexpr int Nf = MODEL == 0 ? 4 : 9;
+  static constexpr int NV = MODEL == 0 ? 4 : 12;       // X rows per volume index j
+  static constexpr int KX = NV * Np + Nf * NFN;        // X rows per element
+  static constexpr int NE = MODEL == 0 ? 64 : 32;      // elements per column tile
+  static constexpr int OPP = (Np + 31) / 32 * 32;      // row pitch of the operator blob
+  static constexpr size_t x_floats_per_tile = size_t(KX) * NE;
+};
+
+template <int MODEL, int N>
+struct GemmA {
   using S = Sz<N>;
   static constexpr int Nf = MODEL == 0 ? 4 : 9;
   static constexpr int NV = MODEL == 0 ? 4 : 12;          // X rows per volume index j
@@ -54,12 +89,12 @@ struct SplitShape {
 };
 
 template <int MODEL, int N>
-__device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mtile, const int ntile) {
+__device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, const int ntile) {
   using S = Sz<N>;
-  using SS = SplitShape<MODEL, N>;
+  using SS = GemmA<MODEL, N>;
   constexpr int Np = S::Np, NFN = S::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NE, TN = SS::TN, RQ = SS::RQ;
   constexpr int RV = 4 * RQ;  // rows per thread
-  constexpr int MT = SS::MT, MP2 = SS::MP2, JC = SS::JC, CC = SS::CC, NT = SS::NT;
+  constexpr int MT = SS::MT, MP2 = SplitShape<MODEL, N>::OPP, JC = SS::JC, CC = SS::CC, NT = SS::NT;
   constexpr int NVC = SS::NVC, NLC = SS::NLC, NCH = NVC + NLC;
   constexpr int REC = Rec<MODEL>::size;
 
@@ -69,7 +104,7 @@ __device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mti
 
   const int tid = threadIdx.x;
   const int row0 = mtile * MT;
-  const float* X = a.xg + size_t(ntile) * SS::x_floats_per_tile;
+  const float* X = a.xg + size_t(ntile) * SplitShape<MODEL, N>::x_floats_per_tile;
   const float* OP = a.ops2;  // [3 Np + NFN][MP2]
 
   // chunk c -> shared buffer (c & 1)
@@ -133,7 +168,7 @@ __device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mti
   for (int c = 0; c < NCH; ++c) {
     if (c + 1 < NCH) {
       issue(c + 1);
-      cp_async_wait_1();
+      cp_async_wait_n<1>();
     } else {
       cp_async_wait_all();
     }
@@ -309,24 +344,327 @@ __device__ __forceinline__ void split_gemm_body(const StepArgs& a, const int mti
   }
 }
 
-// One solve: row tiles fastest, so that the CTAs that share a column tile of
-// X run together and read it from L2.
 template <int MODEL, int N>
-__global__ void __launch_bounds__(SplitShape<MODEL, N>::NT) dg_split_gemm_kernel(const StepArgs a) {
-  constexpr int MTILES = SplitShape<MODEL, N>::MP2 / SplitShape<MODEL, N>::MT;
-  split_gemm_body<MODEL, N>(a, int(blockIdx.x) % MTILES, int(blockIdx.x) / MTILES);
+struct GemmB {
+  using S = Sz<N>;
+  static constexpr int Np = S::Np, NFN = S::NFN;
+  static constexpr int Nf = MODEL == 0 ? 4 : 9;
+  static constexpr int NV = MODEL == 0 ? 4 : 12;          // X rows per volume index j
+  static constexpr int KX = NV * Np + Nf * NFN;           // X rows per element
+  static constexpr int NE = MODEL == 0 ? 64 : 32;         // elements per column tile
+  static constexpr int TM = MODEL == 0 ? 8 : 4;           // rows per thread tile
+  static constexpr int TE = MODEL == 0 ? 4 : 2;           // elements per thread tile
+  // output rows per CTA (MT / TM even, so that the CTA is whole warps)
+  static constexpr int MT =
+      MODEL == 0 ? (N <= 2 ? 16 : N == 3 ? 32 : N == 4 ? 48 : N == 5 ? 64 : N == 6 ? 96 : N == 7 ? 128 : 96)
+                 : (N <= 3 ? 24 : N == 4 ? 40 : N == 5 ? 56 : N == 6 ? 48 : N == 7 ? 64 : 56);
+  static constexpr int MP2 = (Np + MT - 1) / MT * MT;     // padded rows of the split operator blob
+  static constexpr int KC = 16;                           // K chunk (volume indices or face nodes)
+  static constexpr int NS = 3;                            // cp.async stages
+  static constexpr int NT = (MT / TM) * (NE / TE);        // threads per CTA
+  static constexpr int NVC = (Np + KC - 1) / KC;          // volume chunks
+  static constexpr int NLC = (NFN + KC - 1) / KC;         // lift chunks
+  static constexpr int NB = NV > Nf ? NV : Nf;            // X vectors of one chunk, at most
+  static constexpr int nA = 3 * KC * MT;                  // operator rows of one stage
+  static constexpr int nB = NB * KC * NE;                 // X rows of one stage
+  static constexpr int NEP = NE + 1;                      // row stride of the staged RHS field
+  static constexpr int nOut = MT * NEP;
+  static constexpr int nStage = nA + nB;
+  static constexpr size_t smem = size_t(NS * nStage > nOut ? NS * nStage : nOut) * 4;
+  static constexpr size_t x_floats_per_tile = size_t(KX) * NE;
+  static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
+  static_assert(MT % 4 == 0 && NE % 4 == 0 && TM % 4 == 0, "16-byte copies and loads");
+};
+
+template <int MODEL, int N>
+__device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, const int ntile) {
+  using SS = GemmB<MODEL, N>;
+  constexpr int Np = SS::Np, NFN = SS::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NE, TM = SS::TM, TE = SS::TE;
+  constexpr int MT = SS::MT, MP2 = SplitShape<MODEL, N>::OPP, KC = SS::KC, NT = SS::NT, NS = SS::NS;
+  constexpr int NVC = SS::NVC, NLC = SS::NLC, NCH = NVC + NLC;
+  constexpr int REC = Rec<MODEL>::size;
+  constexpr int NACC = MODEL == 0 ? 4 : 12;
+
+  extern __shared__ __align__(16) float smem[];
+  auto sA = [&](int s) { return smem + s * SS::nStage; };
+  auto sB = [&](int s) { return smem + s * SS::nStage + SS::nA; };
+
+  const int tid = threadIdx.x;
+  const int row0 = mtile * MT;
+  const float* X = a.xg + size_t(ntile) * SplitShape<MODEL, N>::x_floats_per_tile;
+  const float* OP = a.ops2;  // [3 Np + NFN][MP2]
+
+  // chunk c -> stage c % NS: operator rows [KC][MT] (3 of them for a volume
+  // chunk), X rows [vector][KC][NE]; rows past Np / 4 Nfp are neither copied
+  // nor read
+  auto issue = [&](int c) {
+    if (c < NCH) {
+      float* A = sA(c % NS);
+      float* B = sB(c % NS);
+      if (c < NVC) {
+        const int j0 = c * KC;
+        const int nj = Np - j0 < KC ? Np - j0 : KC;
+        for (int i = tid; i < 3 * nj * (MT / 4); i += NT) {
+          const int q4 = i % (MT / 4), rr = i / (MT / 4);
+          const int d = rr / nj, jj = rr - d * nj;
+          cp_async16(A + (d * KC + jj) * MT + 4 * q4, OP + size_t(d * Np + j0 + jj) * MP2 + row0 + 4 * q4);
+        }
+        for (int i = tid; i < NV * nj * (NE / 4); i += NT) {
+          const int q4 = i % (NE / 4), rr = i / (NE / 4);
+          const int f = rr / nj, jj = rr - f * nj;
+          cp_async16(B + (f * KC + jj) * NE + 4 * q4, X + size_t(f * Np + j0 + jj) * NE + 4 * q4);
+        }
+      } else {
+        const int c0 = (c - NVC) * KC;
+        const int nc = NFN - c0 < KC ? NFN - c0 : KC;
+        for (int i = tid; i < nc * (MT / 4); i += NT) {
+          const int q4 = i % (MT / 4), cc = i / (MT / 4);
+          cp_async16(A + cc * MT + 4 * q4, OP + size_t(3 * Np + c0 + cc) * MP2 + row0 + 4 * q4);
+        }
+        for (int i = tid; i < Nf * nc * (NE / 4); i += NT) {
+          const int q4 = i % (NE / 4), rr = i / (NE / 4);
+          const int f = rr / nc, cc = rr - f * nc;
+          cp_async16(B + (f * KC + cc) * NE + 4 * q4, X + size_t(NV * Np + f * NFN + c0 + cc) * NE + 4 * q4);
+        }
+      }
+    }
+    cp_async_commit();  // an empty group past the last chunk keeps the wait count uniform
+  };
+
+  // thread tile: rows il..il+TM-1 of the CTA's slice, elements e0..e0+TE-1;
+  // the lanes of a warp span the elements (two row groups per warp)
+  constexpr int CT = NE / TE;
+  const int ct = tid % CT, rt = tid / CT;
+  const int il = TM * rt, e0 = TE * ct;
+
+  float acc[NACC][TE][TM];
+#pragma unroll
+  for (int x = 0; x < NACC; ++x)
+#pragma unroll
+    for (int t = 0; t < TE; ++t)
+#pragma unroll
+      for (int v = 0; v < TM; ++v) acc[x][t][v] = 0.f;
+
+  auto ldA = [&](const float* p, float* o) {  // TM consecutive rows, as float4s
+#pragma unroll
+    for (int q = 0; q < TM / 4; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(p + 4 * q);
+      o[4 * q] = v.x;
+      o[4 * q + 1] = v.y;
+      o[4 * q + 2] = v.z;
+      o[4 * q + 3] = v.w;
+    }
+  };
+  auto ldB = [&](const float* p, float* o) {  // TE consecutive elements
+    if constexpr (TE == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p);
+      o[0] = v.x;
+      o[1] = v.y;
+      o[2] = v.z;
+      o[3] = v.w;
+    } else {
+      const float2 v = *reinterpret_cast<const float2*>(p);
+      o[0] = v.x;
+      o[1] = v.y;
+    }
+  };
+
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) issue(s);
+  for (int c = 0; c < NCH; ++c) {
+    issue(c + NS - 1);
+    cp_async_wait_n<NS - 1>();  // chunk c has landed
+    __syncthreads();
+    const float* A = sA(c % NS) + il;
+    const float* B = sB(c % NS) + e0;
+    if (c < NVC) {
+      const int nj = Np - c * KC < KC ? Np - c * KC : KC;
+#pragma unroll 2
+      for (int jj = 0; jj < nj; ++jj) {
+        float ad[3][TM];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ldA(A + (d * KC + jj) * MT, ad[d]);
+        if constexpr (MODEL == 0) {
+          float xp[TE], xw[3][TE];
+          ldB(B + (0 * KC + jj) * NE, xp);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) ldB(B + ((1 + d) * KC + jj) * NE, xw[d]);
+#pragma unroll
+          for (int t = 0; t < TE; ++t)
+#pragma unroll
+            for (int v = 0; v < TM; ++v) {
+              acc[0][t][v] = fmaf(ad[0][v], xp[t], acc[0][t][v]);
+              acc[1][t][v] = fmaf(ad[1][v], xp[t], acc[1][t][v]);
+              acc[2][t][v] = fmaf(ad[2][v], xp[t], acc[2][t][v]);
+              acc[3][t][v] = fmaf(ad[0][v], xw[0][t], acc[3][t][v]);
+              acc[3][t][v] = fmaf(ad[1][v], xw[1][t], acc[3][t][v]);
+              acc[3][t][v] = fmaf(ad[2][v], xw[2][t], acc[3][t][v]);
+            }
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) {
+            float xv[TE], xs[3][TE];
+            ldB(B + (cc * KC + jj) * NE, xv);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) ldB(B + ((3 + 3 * cc + d) * KC + jj) * NE, xs[d]);
+#pragma unroll
+            for (int t = 0; t < TE; ++t)
+#pragma unroll
+              for (int v = 0; v < TM; ++v) {
+                acc[3 * cc + 0][t][v] = fmaf(ad[0][v], xv[t], acc[3 * cc + 0][t][v]);
+                acc[3 * cc + 1][t][v] = fmaf(ad[1][v], xv[t], acc[3 * cc + 1][t][v]);
+                acc[3 * cc + 2][t][v] = fmaf(ad[2][v], xv[t], acc[3 * cc + 2][t][v]);
+                acc[9 + cc][t][v] = fmaf(ad[0][v], xs[0][t], acc[9 + cc][t][v]);
+                acc[9 + cc][t][v] = fmaf(ad[1][v], xs[1][t], acc[9 + cc][t][v]);
+                acc[9 + cc][t][v] = fmaf(ad[2][v], xs[2][t], acc[9 + cc][t][v]);
+              }
+          }
+        }
+      }
+      if (c == NVC - 1) {
+        // boundary: derivative products -> RHS components (per element column)
+#pragma unroll
+        for (int t = 0; t < TE; ++t) {
+          const int k = ntile * NE + e0 + t;
+          const int kk = k < a.K ? k : a.K - 1;  // padding columns: any valid record
+          const float* gk = a.rec + size_t(kk) * REC;
+          float g[9];
+#pragma unroll
+          for (int x = 0; x < 9; ++x) g[x] = __ldg(gk + x);
+          if constexpr (MODEL == 0) {
+            const float rinv = __ldg(gk + 10);
+#pragma unroll
+            for (int v = 0; v < TM; ++v) {
+              const float G0 = acc[0][t][v], G1 = acc[1][t][v], G2 = acc[2][t][v];
+#pragma unroll
+              for (int cc = 0; cc < 3; ++cc)
+                acc[cc][t][v] = -rinv * (g[3 * cc] * G0 + g[3 * cc + 1] * G1 + g[3 * cc + 2] * G2);
+            }
+          } else {
+            const float lam = __ldg(gk + 9), mu = __ldg(gk + 10);
+#pragma unroll
+            for (int v = 0; v < TM; ++v) {
+              float gv[3][3];
+#pragma unroll
+              for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+                for (int x = 0; x < 3; ++x)
+                  gv[cc][x] = g[3 * x] * acc[3 * cc][t][v] + g[3 * x + 1] * acc[3 * cc + 1][t][v] +
+                              g[3 * x + 2] * acc[3 * cc + 2][t][v];
+              const float div = gv[0][0] + gv[1][1] + gv[2][2];
+              acc[0][t][v] = lam * div + 2.f * mu * gv[0][0];
+              acc[1][t][v] = lam * div + 2.f * mu * gv[1][1];
+              acc[2][t][v] = lam * div + 2.f * mu * gv[2][2];
+              acc[3][t][v] = mu * (gv[0][1] + gv[1][0]);
+              acc[4][t][v] = mu * (gv[0][2] + gv[2][0]);
+              acc[5][t][v] = mu * (gv[1][2] + gv[2][1]);
+            }
+          }
+        }
+      }
+    } else {
+      const int nc = NFN - (c - NVC) * KC < KC ? NFN - (c - NVC) * KC : KC;
+#pragma unroll 2
+      for (int cc = 0; cc < nc; ++cc) {
+        float l[TM];
+        ldA(A + cc * MT, l);
+        if constexpr (MODEL == 0) {
+          float pp[4][TE];
+#pragma unroll
+          for (int f = 0; f < 4; ++f) ldB(B + (f * KC + cc) * NE, pp[f]);
+#pragma unroll
+          for (int t = 0; t < TE; ++t)
+#pragma unroll
+            for (int v = 0; v < TM; ++v) {
+              acc[3][t][v] = fmaf(l[v], pp[0][t], acc[3][t][v]);
+              acc[0][t][v] = fmaf(l[v], pp[1][t], acc[0][t][v]);
+              acc[1][t][v] = fmaf(l[v], pp[2][t], acc[1][t][v]);
+              acc[2][t][v] = fmaf(l[v], pp[3][t], acc[2][t][v]);
+            }
+        } else {
+#pragma unroll
+          for (int f = 0; f < 9; ++f) {
+            float pf[TE];
+            ldB(B + (f * KC + cc) * NE, pf);
+            // P_v,c onto Rv_c (accumulators 9..11), P_sig,x onto S_x (0..5)
+            const int slot = f < 3 ? 9 + f : f - 3;
+#pragma unroll
+            for (int t = 0; t < TE; ++t)
+#pragma unroll
+              for (int v = 0; v < TM; ++v) acc[slot][t][v] = fmaf(l[v], pf[t], acc[slot][t][v]);
+          }
+        }
+      }
+    }
+    __syncthreads();  // stage c % NS is refilled by chunk c + NS
+  }
+  cp_async_wait_n<0>();
+  __syncthreads();
+
+  // -------- epilogue: one field at a time through shared memory [MT][NEP]
+  float* sOut = smem;
+  constexpr int NEP = SS::NEP;
+  const int rows = (Np - row0) < MT ? (Np - row0) : MT;
+#pragma unroll
+  for (int f = 0; f < Nf; ++f) {
+    const int slot = MODEL == 0 ? (f == 0 ? 3 : f - 1) : (f < 3 ? 9 + f : f - 3);  // accumulator of field f
+#pragma unroll
+    for (int t = 0; t < TE; ++t)
+#pragma unroll
+      for (int v = 0; v < TM; ++v) sOut[(il + v) * NEP + e0 + t] = acc[slot][t][v];
+    __syncthreads();
+    for (int p = tid; p < NE * MT; p += NT) {
+      const int e = p / MT, rr = p - e * MT;
+      const int k = ntile * NE + e;
+      if (k >= a.K || rr >= rows) continue;
+      const int i = row0 + rr;
+      float rv = sOut[rr * NEP + e];
+      if (k == a.src_elem && a.srcvec) rv = fmaf(a.src_amp, __ldg(a.srcvec + f * Np + i), rv);
+      const size_t idx = size_t(k) * Nf * Np + size_t(f) * Np + i;
+      if (a.mode == 0) {
+        const float accv = a.a1 * rv + a.a2 * __ldg(a.r1 + idx) + a.a3 * a.r2[idx];
+        a.qn[idx] = fmaf(a.dt, accv, __ldg(a.q + idx));
+        a.r2[idx] = rv;
+      } else {
+        a.rout[idx] = rv;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Design V of the FP32 GEMM (V = 2: design B, otherwise design A).
+template <int MODEL, int N, int V>
+struct GemmOf {
+  using T = GemmA<MODEL, N>;
+  __device__ static void body(const StepArgs& a, int mtile, int ntile) { gemm_a_body<MODEL, N>(a, mtile, ntile); }
+};
+template <int MODEL, int N>
+struct GemmOf<MODEL, N, 2> {
+  using T = GemmB<MODEL, N>;
+  __device__ static void body(const StepArgs& a, int mtile, int ntile) { gemm_b_body<MODEL, N>(a, mtile, ntile); }
+};
+
+// One solve: row tiles fastest, so that the CTAs that share a column tile of
+// X run together and read it from L2.  V selects the design (1 = A, 2 = B).
+template <int MODEL, int N, int V>
+__global__ void __launch_bounds__(GemmOf<MODEL, N, V>::T::NT) dg_split_gemm_kernel(const StepArgs a) {
+  using G = typename GemmOf<MODEL, N, V>::T;
+  constexpr int MTILES = (Sz<N>::Np + G::MT - 1) / G::MT;
+  GemmOf<MODEL, N, V>::body(a, int(blockIdx.x) % MTILES, int(blockIdx.x) / MTILES);
 }
 
 // Every solve of a batch: global tile -> (solve, local tile) through the
 // batch's tile tables, the solve's arguments from its device-side state.
-template <int MODEL, int N>
-__global__ void __launch_bounds__(SplitShape<MODEL, N>::NT) dg_split_gemm_batched_kernel(const BatchArgs b) {
-  constexpr int MTILES = SplitShape<MODEL, N>::MP2 / SplitShape<MODEL, N>::MT;
+template <int MODEL, int N, int V>
+__global__ void __launch_bounds__(GemmOf<MODEL, N, V>::T::NT) dg_split_gemm_batched_kernel(const BatchArgs b) {
+  using G = typename GemmOf<MODEL, N, V>::T;
+  constexpr int MTILES = (Sz<N>::Np + G::MT - 1) / G::MT;
   const int so = __ldg(b.tile_solve + blockIdx.x);
   const int lt = int(blockIdx.x) - __ldg(b.tile_start + so);
   StepArgs a;
   solve_args(b, b.solves[so], a);
-  split_gemm_body<MODEL, N>(a, lt % MTILES, lt / MTILES);
+  GemmOf<MODEL, N, V>::body(a, lt % MTILES, lt / MTILES);
 }
 
 }  // namespace dgk

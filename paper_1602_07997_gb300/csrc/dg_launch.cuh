@@ -35,12 +35,17 @@ KernelCfg make_cfg() {
   return c;
 }
 
-// Split variant: front half with EB elements per block, then the GEMM kernel.
-template <int MODEL, int N, int EB, int NT = threads_for<N, EB, 1>()>
+// Split variant: front half with EB elements per block, then the FP32 GEMM
+// kernel of design V (1 = one thread per 4 rows x TN elements of every
+// product, 2 = geometric combination at the volume/LIFT boundary and larger
+// register tiles).
+template <int MODEL, int N, int EB, int V = 1, int NT = threads_for<N, EB, 1>()>
 KernelCfg make_split_cfg() {
   using SS = SplitShape<MODEL, N>;
+  using G = typename GemmOf<MODEL, N, V>::T;
   static_assert(Plan<MODEL, N, EB, false, false>::bytes <= 227 * 1024, "shared memory budget");
-  static_assert(SS::smem <= 227 * 1024, "shared memory budget (GEMM)");
+  static_assert(G::smem <= 227 * 1024, "shared memory budget (GEMM)");
+  static_assert((Sz<N>::Np + G::MT - 1) / G::MT * G::MT <= SS::OPP, "row tiles inside the operator pitch");
 
   KernelCfg c;
   c.EB = EB;
@@ -52,15 +57,15 @@ KernelCfg make_split_cfg() {
   c.fn = dg_step_kernel<MODEL, N, EB, 1, NT, false, false, SS::NE>;
   c.fn_batched = dg_step_batched_kernel<MODEL, N, EB, 1, NT, false, false, SS::NE>;
   c.split = 1;
-  c.fn_gemm = dg_split_gemm_kernel<MODEL, N>;
-  c.fn_gemm_batched = dg_split_gemm_batched_kernel<MODEL, N>;
-  c.smem_gemm = SS::smem;
-  c.gemm_threads = SS::NT;
+  c.fn_gemm = dg_split_gemm_kernel<MODEL, N, V>;
+  c.fn_gemm_batched = dg_split_gemm_batched_kernel<MODEL, N, V>;
+  c.smem_gemm = G::smem;
+  c.gemm_threads = G::NT;
   c.gemm_ne = SS::NE;
-  c.gemm_mt = SS::MT;
-  c.gemm_mtiles = SS::MP2 / SS::MT;
+  c.gemm_mt = G::MT;
+  c.gemm_mtiles = (Sz<N>::Np + G::MT - 1) / G::MT;
   c.gemm_kx = SS::KX;
-  c.gemm_mp2 = SS::MP2;
+  c.gemm_mp2 = SS::OPP;
   c.gemm_nsplit = 0;
   c.gemm_xtile = size_t(SS::KX) * SS::NE * 4;
   c.gemm_persistent = false;

@@ -45,7 +45,7 @@ KernelCfg make_front_cfg() {
   c.split = 0;
   c.gemm_ne = SS::NE;
   c.gemm_kx = SS::KX;
-  c.gemm_mp2 = SS::MP2;
+  c.gemm_mp2 = SS::OPP;
   c.gemm_xtile = size_t(SS::KX) * SS::NE * 4;
   return c;
 }
