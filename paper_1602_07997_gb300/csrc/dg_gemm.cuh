@@ -46,6 +46,43 @@ __device__ __forceinline__ void cp_async_wait_n() {
   asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
 }
 
+// AB3 update (a.mode 0) or RHS store (mode 1) of U values: every load of the
+// batch is issued before the first store, so that their latencies overlap.
+template <int U>
+__device__ __forceinline__ void ab3_batch(const StepArgs& a, const size_t* idx, const float* rv, const bool* on) {
+  if (a.mode == 0) {
+    float q[U], r1[U], r2[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      q[u] = on[u] ? __ldg(a.q + idx[u]) : 0.f;
+      r1[u] = on[u] ? __ldg(a.r1 + idx[u]) : 0.f;
+      r2[u] = on[u] ? a.r2[idx[u]] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (on[u]) {
+        const float accv = a.a1 * rv[u] + a.a2 * r1[u] + a.a3 * r2[u];
+        a.qn[idx[u]] = fmaf(a.dt, accv, q[u]);
+        a.r2[idx[u]] = rv[u];
+      }
+  } else {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (on[u]) a.rout[idx[u]] = rv[u];
+  }
+}
+
+// The AB3 inputs of a column tile into L2 while its products run (q, r^{m-1},
+// r^{m-2} are padded past K: a whole tile stays inside the allocation).
+template <int Nf, int Np, int NE>
+__device__ __forceinline__ void prefetch_tile_l2(const StepArgs& a, int ntile) {
+  const size_t e0 = size_t(ntile) * NE * Nf * Np;
+  constexpr uint32_t bytes = uint32_t(NE * Nf * Np * 4);
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.q + e0), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.r1 + e0), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.r2 + e0), "r"(bytes) : "memory");
+}
+
 // Layout shared by the front half, both GEMM designs and the library route:
 // X[tile][row][NE] (KX rows per element) and the operator blob
 // [3 Np + 4 Nfp][OPP] (row = input index, column = output node, OPP = Np
@@ -106,6 +143,7 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
   const int row0 = mtile * MT;
   const float* X = a.xg + size_t(ntile) * SplitShape<MODEL, N>::x_floats_per_tile;
   const float* OP = a.ops2;  // [3 Np + NFN][MP2]
+  if (tid == 0 && mtile == 0 && a.mode == 0) prefetch_tile_l2<Nf, Np, NE>(a, ntile);
 
   // chunk c -> shared buffer (c & 1)
   auto issue = [&](int c) {
@@ -321,26 +359,26 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
     }
   }
   __syncthreads();
-  // part 2: one warp per (element, field) row segment: coalesced AB3 update
-  const int warp = tid >> 5, lane = tid & 31;
-  constexpr int NWARP = NT / 32;
+  // part 2: coalesced AB3 update over (element, field, row), rows fastest,
+  // 8 values per thread in flight
   const int rows = (Np - row0) < MT ? (Np - row0) : MT;
-  for (int p = warp; p < NE * Nf; p += NWARP) {
-    const int e = p / Nf, f = p - e * Nf;
-    const int k = ntile * NE + e;
-    if (k >= a.K) continue;
-    const size_t base = size_t(k) * Nf * Np + size_t(f) * Np + row0;
-    for (int rr = lane; rr < rows; rr += 32) {
-      const float rv = sOut[(f * MT + rr) * NEP + e];
-      const size_t idx = base + rr;
-      if (a.mode == 0) {
-        const float accv = a.a1 * rv + a.a2 * __ldg(a.r1 + idx) + a.a3 * a.r2[idx];
-        a.qn[idx] = fmaf(a.dt, accv, __ldg(a.q + idx));
-        a.r2[idx] = rv;
-      } else {
-        a.rout[idx] = rv;
-      }
+  const int total = NE * Nf * rows;
+  constexpr int U = 8;
+  for (int v0 = tid; v0 < total; v0 += NT * U) {
+    size_t idx[U];
+    float rv[U];
+    bool on[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int v = v0 + u * NT;
+      const int rr = v % rows, ef = v / rows;
+      const int e = ef / Nf, f = ef - e * Nf;
+      const int k = ntile * NE + e;
+      on[u] = v < total && k < a.K;
+      idx[u] = on[u] ? size_t(k) * Nf * Np + size_t(f) * Np + row0 + rr : 0;
+      rv[u] = on[u] ? sOut[(f * MT + rr) * NEP + e] : 0.f;
     }
+    ab3_batch<U>(a, idx, rv, on);
   }
 }
 
@@ -393,6 +431,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
   const int row0 = mtile * MT;
   const float* X = a.xg + size_t(ntile) * SplitShape<MODEL, N>::x_floats_per_tile;
   const float* OP = a.ops2;  // [3 Np + NFN][MP2]
+  if (tid == 0 && mtile == 0 && a.mode == 0) prefetch_tile_l2<Nf, Np, NE>(a, ntile);
 
   // chunk c -> stage c % NS: operator rows [KC][MT] (3 of them for a volume
   // chunk), X rows [vector][KC][NE]; rows past Np / 4 Nfp are neither copied
@@ -613,21 +652,24 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
 #pragma unroll
       for (int v = 0; v < TM; ++v) sOut[(il + v) * NEP + e0 + t] = acc[slot][t][v];
     __syncthreads();
-    for (int p = tid; p < NE * MT; p += NT) {
-      const int e = p / MT, rr = p - e * MT;
-      const int k = ntile * NE + e;
-      if (k >= a.K || rr >= rows) continue;
-      const int i = row0 + rr;
-      float rv = sOut[rr * NEP + e];
-      if (k == a.src_elem && a.srcvec) rv = fmaf(a.src_amp, __ldg(a.srcvec + f * Np + i), rv);
-      const size_t idx = size_t(k) * Nf * Np + size_t(f) * Np + i;
-      if (a.mode == 0) {
-        const float accv = a.a1 * rv + a.a2 * __ldg(a.r1 + idx) + a.a3 * a.r2[idx];
-        a.qn[idx] = fmaf(a.dt, accv, __ldg(a.q + idx));
-        a.r2[idx] = rv;
-      } else {
-        a.rout[idx] = rv;
+    constexpr int U = 8;  // values per thread in flight
+    for (int p0 = tid; p0 < NE * MT; p0 += NT * U) {
+      size_t idx[U];
+      float rv[U];
+      bool on[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int p = p0 + u * NT;
+        const int e = p / MT, rr = p - e * MT;
+        const int k = ntile * NE + e;
+        on[u] = p < NE * MT && k < a.K && rr < rows;
+        const int i = row0 + rr;
+        float r = on[u] ? sOut[rr * NEP + e] : 0.f;
+        if (on[u] && k == a.src_elem && a.srcvec) r = fmaf(a.src_amp, __ldg(a.srcvec + f * Np + i), r);
+        rv[u] = r;
+        idx[u] = on[u] ? size_t(k) * Nf * Np + size_t(f) * Np + i : 0;
       }
+      ab3_batch<U>(a, idx, rv, on);
     }
     __syncthreads();
   }
