@@ -447,6 +447,13 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     tma_bulk_g2s(st + P::sRec, a.rec + size_t(k0) * REC, kRecBytes, &bars[s]);
     tma_bulk_g2s(st + P::sNbr, a.nbr + k0, uint32_t(EB * 16), &bars[s]);
     if (OPS_SMEM && with_ops) tma_bulk_g2s(smem + P::oOps, a.ops, bo, &bars[s]);
+    if (!R_SMEM && SPLIT == 0 && a.mode == 0) {
+      // the block's AB3 history into L2 (it is read from global memory in the update pass)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.r1 + size_t(k0) * Nf * Np), "r"(kQBytes)
+                   : "memory");
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.r2 + size_t(k0) * Nf * Np), "r"(kQBytes)
+                   : "memory");
+    }
   };
   // neighbour traces of block b that live outside it: 4-byte async copies
   // (cp.async) into trace buffer s, layout [Nf][4 Nfp][EBP], face node fastest
@@ -856,19 +863,36 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
         bulk_commit();
       }
     } else {
+      // history from global memory (prefetched into L2 with the block's
+      // stage): UB float4 per thread in flight, loads before stores
       const size_t g0 = size_t(k0) * Nf * Np / 4;
       const float4* gr1 = reinterpret_cast<const float4*>(a.r1) + g0;
       float4* gr2 = reinterpret_cast<float4*>(a.r2) + g0;
       float4* gqn = reinterpret_cast<float4*>(a.qn) + g0;
-      for (int i = tid; i < P::nQ / 4; i += NT) {
-        const float4 q4 = reinterpret_cast<const float4*>(sQ)[i];
-        const float4 r4 = reinterpret_cast<const float4*>(sRhs)[i];
-        const float4 p1 = __ldg(gr1 + i), p2 = gr2[i];
-        gqn[i] = make_float4(fmaf(dt, a1 * r4.x + a2 * p1.x + a3 * p2.x, q4.x),
-                             fmaf(dt, a1 * r4.y + a2 * p1.y + a3 * p2.y, q4.y),
-                             fmaf(dt, a1 * r4.z + a2 * p1.z + a3 * p2.z, q4.z),
-                             fmaf(dt, a1 * r4.w + a2 * p1.w + a3 * p2.w, q4.w));
-        gr2[i] = r4;
+      constexpr int UB = 4;
+      for (int i0 = tid; i0 < P::nQ / 4; i0 += NT * UB) {
+        float4 p1[UB], p2[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+          const int i = i0 + u * NT;
+          if (i < P::nQ / 4) {
+            p1[u] = __ldg(gr1 + i);
+            p2[u] = gr2[i];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+          const int i = i0 + u * NT;
+          if (i < P::nQ / 4) {
+            const float4 q4 = reinterpret_cast<const float4*>(sQ)[i];
+            const float4 r4 = reinterpret_cast<const float4*>(sRhs)[i];
+            gqn[i] = make_float4(fmaf(dt, a1 * r4.x + a2 * p1[u].x + a3 * p2[u].x, q4.x),
+                                 fmaf(dt, a1 * r4.y + a2 * p1[u].y + a3 * p2[u].y, q4.y),
+                                 fmaf(dt, a1 * r4.z + a2 * p1[u].z + a3 * p2[u].z, q4.z),
+                                 fmaf(dt, a1 * r4.w + a2 * p1[u].w + a3 * p2[u].w, q4.w));
+            gr2[i] = r4;
+          }
+        }
       }
     }
   }
