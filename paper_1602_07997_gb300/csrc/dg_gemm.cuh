@@ -382,7 +382,8 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
   }
 }
 
-template <int MODEL, int N>
+// NARROW: elements per thread halved (fewer registers, two CTAs per SM).
+template <int MODEL, int N, bool NARROW = false>
 struct GemmB {
   using S = Sz<N>;
   static constexpr int Np = S::Np, NFN = S::NFN;
@@ -391,7 +392,7 @@ struct GemmB {
   static constexpr int KX = NV * Np + Nf * NFN;           // X rows per element
   static constexpr int NE = MODEL == 0 ? 64 : 32;         // elements per column tile
   static constexpr int TM = MODEL == 0 ? 8 : 4;           // rows per thread tile
-  static constexpr int TE = MODEL == 0 ? 4 : 2;           // elements per thread tile
+  static constexpr int TE = (MODEL == 0 ? 4 : 2) / (NARROW ? 2 : 1);  // elements per thread tile
   // output rows per CTA (MT / TM even, so that the CTA is whole warps)
   static constexpr int MT =
       MODEL == 0 ? (N <= 2 ? 16 : N == 3 ? 32 : N == 4 ? 48 : N == 5 ? 64 : N == 6 ? 96 : N == 7 ? 128 : 96)
@@ -414,9 +415,9 @@ struct GemmB {
   static_assert(MT % 4 == 0 && NE % 4 == 0 && TM % 4 == 0, "16-byte copies and loads");
 };
 
-template <int MODEL, int N>
+template <int MODEL, int N, bool NARROW = false>
 __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, const int ntile) {
-  using SS = GemmB<MODEL, N>;
+  using SS = GemmB<MODEL, N, NARROW>;
   constexpr int Np = SS::Np, NFN = SS::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NE, TM = SS::TM, TE = SS::TE;
   constexpr int MT = SS::MT, MP2 = SplitShape<MODEL, N>::OPP, KC = SS::KC, NT = SS::NT, NS = SS::NS;
   constexpr int NVC = SS::NVC, NLC = SS::NLC, NCH = NVC + NLC;
@@ -501,10 +502,12 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
       o[1] = v.y;
       o[2] = v.z;
       o[3] = v.w;
-    } else {
+    } else if constexpr (TE == 2) {
       const float2 v = *reinterpret_cast<const float2*>(p);
       o[0] = v.x;
       o[1] = v.y;
+    } else {
+      o[0] = *p;
     }
   };
 
@@ -675,7 +678,8 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
   }
 }
 
-// Design V of the FP32 GEMM (V = 2: design B, otherwise design A).
+// Design V of the FP32 GEMM (V = 2: design B, V = 3: design B with half the
+// elements per thread, otherwise design A).
 template <int MODEL, int N, int V>
 struct GemmOf {
   using T = GemmA<MODEL, N>;
@@ -685,6 +689,11 @@ template <int MODEL, int N>
 struct GemmOf<MODEL, N, 2> {
   using T = GemmB<MODEL, N>;
   __device__ static void body(const StepArgs& a, int mtile, int ntile) { gemm_b_body<MODEL, N>(a, mtile, ntile); }
+};
+template <int MODEL, int N>
+struct GemmOf<MODEL, N, 3> {
+  using T = GemmB<MODEL, N, true>;
+  __device__ static void body(const StepArgs& a, int mtile, int ntile) { gemm_b_body<MODEL, N, true>(a, mtile, ntile); }
 };
 
 // One solve: row tiles fastest, so that the CTAs that share a column tile of

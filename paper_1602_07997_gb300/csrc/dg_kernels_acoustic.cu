@@ -22,15 +22,15 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_split_cfg<0, 5, 8>(), make_split_cfg<0, 5, 8, 2>()};
   static const KernelCfg v6[] = {make_cfg<0, 6, 8, false, true>(), make_cfg<0, 6, 4, false, true>(),
                                  make_cfg<0, 6, 8, false, true, 2>(), make_cfg<0, 6, 4, false, true, 2>(),
-                                 make_split_cfg<0, 6, 8>(), make_split_cfg<0, 6, 4>(), make_split_cfg<0, 6, 8, 2>()};
+                                 make_split_cfg<0, 6, 8>(), make_split_cfg<0, 6, 4>(), make_split_cfg<0, 6, 8, 2>(), make_split_cfg<0, 6, 8, 3>()};
   static const KernelCfg v7[] = {make_cfg<0, 7, 4, false, true>(), make_cfg<0, 7, 4, false, true, 2>(),
                                  make_cfg<0, 7, 8, false, true, 2>(), make_cfg<0, 7, 4, false, true, 4>(),
-                                 make_split_cfg<0, 7, 8>(), make_split_cfg<0, 7, 4>(), make_split_cfg<0, 7, 8, 2>()};
+                                 make_split_cfg<0, 7, 8>(), make_split_cfg<0, 7, 4>(), make_split_cfg<0, 7, 8, 2>(), make_split_cfg<0, 7, 8, 3>()};
   static const KernelCfg v8[] = {make_cfg<0, 8, 4, false, true>(), make_cfg<0, 8, 4, false, true, 2>(),
                                  make_cfg<0, 8, 4, false, true, 4>(), make_cfg<0, 8, 8, false, true, 2>(),
-                                 make_split_cfg<0, 8, 4>(), make_split_cfg<0, 8, 8>(), make_split_cfg<0, 8, 8, 2>()};
+                                 make_split_cfg<0, 8, 4>(), make_split_cfg<0, 8, 8>(), make_split_cfg<0, 8, 8, 2>(), make_split_cfg<0, 8, 8, 3>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
-  static const int cnt[8] = {4, 4, 4, 4, 6, 7, 7, 7};
+  static const int cnt[8] = {4, 4, 4, 4, 6, 8, 8, 8};
   if (N < 1 || N > 8) return nullptr;
   *count = cnt[N - 1];
   return tab[N - 1];

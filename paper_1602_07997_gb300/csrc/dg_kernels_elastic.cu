@@ -16,15 +16,15 @@ const KernelCfg* kernel_variants_elastic(int N, int* count) {
   static const KernelCfg v4[] = {make_cfg<1, 4, 4, true, true>(), make_cfg<1, 4, 8, false, true>(),
                                  make_cfg<1, 4, 4, false, true>(), make_split_cfg<1, 4, 8>(), make_split_cfg<1, 4, 8, 2>()};
   static const KernelCfg v5[] = {make_cfg<1, 5, 4, false, true>(), make_cfg<1, 5, 4, false, false>(),
-                                 make_split_cfg<1, 5, 4>(), make_split_cfg<1, 5, 4, 2>()};
+                                 make_split_cfg<1, 5, 4>(), make_split_cfg<1, 5, 4, 2>(), make_split_cfg<1, 5, 4, 3>()};
   static const KernelCfg v6[] = {make_cfg<1, 6, 4, false, false>(), make_cfg<1, 6, 4, false, false, 2>(),
-                                 make_split_cfg<1, 6, 4>(), make_split_cfg<1, 6, 4, 2>()};
+                                 make_split_cfg<1, 6, 4>(), make_split_cfg<1, 6, 4, 2>(), make_split_cfg<1, 6, 4, 3>()};
   static const KernelCfg v7[] = {make_cfg<1, 7, 4, false, false>(), make_cfg<1, 7, 4, false, false, 2>(),
-                                 make_split_cfg<1, 7, 4>(), make_split_cfg<1, 7, 4, 2>()};
+                                 make_split_cfg<1, 7, 4>(), make_split_cfg<1, 7, 4, 2>(), make_split_cfg<1, 7, 4, 3>()};
   static const KernelCfg v8[] = {make_cfg<1, 8, 4, false, false>(), make_cfg<1, 8, 4, false, false, 2>(),
-                                 make_split_cfg<1, 8, 4>(), make_split_cfg<1, 8, 4, 2>()};
+                                 make_split_cfg<1, 8, 4>(), make_split_cfg<1, 8, 4, 2>(), make_split_cfg<1, 8, 4, 3>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
-  static const int cnt[8] = {3, 3, 3, 5, 4, 4, 4, 4};
+  static const int cnt[8] = {3, 3, 3, 5, 5, 5, 5, 5};
   if (N < 1 || N > 8) return nullptr;
   *count = cnt[N - 1];
   return tab[N - 1];
