@@ -9,28 +9,39 @@
 namespace dgk {
 
 const KernelCfg* kernel_variants_acoustic(int N, int* count) {
-  static const KernelCfg v1[] = {make_cfg<0, 1, 16, true, true>(), make_cfg<0, 1, 64, true, true>(),
-                                 make_cfg<0, 1, 32, true, true>(), make_cfg<0, 1, 128, true, true>()};
-  static const KernelCfg v2[] = {make_cfg<0, 2, 8, true, true>(), make_cfg<0, 2, 32, true, true>(),
-                                 make_cfg<0, 2, 16, true, true>(), make_cfg<0, 2, 64, true, true>()};
-  static const KernelCfg v3[] = {make_cfg<0, 3, 8, true, true>(), make_cfg<0, 3, 4, true, true>(),
-                                 make_cfg<0, 3, 16, true, true>(), make_cfg<0, 3, 32, true, true>()};
-  static const KernelCfg v4[] = {make_cfg<0, 4, 12, true, true>(), make_cfg<0, 4, 4, true, true>(),
-                                 make_cfg<0, 4, 8, true, true, 2>(), make_cfg<0, 4, 8, true, true>()};
-  static const KernelCfg v5[] = {make_cfg<0, 5, 8, false, true>(), make_cfg<0, 5, 8, false, true, 2>(),
+  static const KernelCfg v1[] = {make_cfg<0, 1, 32, true, true, 1, 128>(), make_cfg<0, 1, 64, true, true>(),
+                                 make_cfg<0, 1, 32, true, true>(), make_cfg<0, 1, 128, true, true>(),
+                                 make_cfg<0, 1, 16, true, true>(), make_cfg<0, 1, 64, true, true, 1, 256>(),
+                                 make_cfg<0, 1, 32, true, true, 1, 256>(), make_cfg<0, 1, 64, true, true, 1, 512>()};
+  static const KernelCfg v2[] = {make_cfg<0, 2, 32, true, true, 1, 256>(), make_cfg<0, 2, 32, true, true>(),
+                                 make_cfg<0, 2, 16, true, true>(), make_cfg<0, 2, 64, true, true>(),
+                                 make_cfg<0, 2, 16, true, true, 1, 128>(), make_cfg<0, 2, 8, true, true>(),
+                                 make_cfg<0, 2, 16, true, true, 1, 256>(), make_cfg<0, 2, 32, true, true, 1, 512>()};
+  static const KernelCfg v3[] = {make_cfg<0, 3, 16, true, true, 1, 256>(), make_cfg<0, 3, 4, true, true>(),
+                                 make_cfg<0, 3, 16, true, true>(), make_cfg<0, 3, 32, true, true>(),
+                                 make_cfg<0, 3, 16, true, true, 1, 128>(), make_cfg<0, 3, 8, true, true>(),
+                                 make_cfg<0, 3, 32, true, true, 1, 256>(), make_cfg<0, 3, 32, true, true, 1, 512>()};
+  static const KernelCfg v4[] = {make_cfg<0, 4, 8, true, true, 1, 256>(), make_cfg<0, 4, 4, true, true>(),
+                                 make_cfg<0, 4, 8, true, true, 2>(), make_cfg<0, 4, 8, true, true>(),
+                                 make_cfg<0, 4, 8, true, true, 1, 128>(), make_cfg<0, 4, 16, true, true, 1, 256>(),
+                                 make_cfg<0, 4, 12, true, true>(), make_cfg<0, 4, 12, true, true, 1, 256>()};
+  static const KernelCfg v5[] = {make_split_cfg<0, 5, 8, 2>(), make_cfg<0, 5, 8, false, true, 2>(),
                                  make_cfg<0, 5, 4, true, true>(), make_cfg<0, 5, 12, false, true, 2>(),
-                                 make_split_cfg<0, 5, 8>(), make_split_cfg<0, 5, 8, 2>()};
-  static const KernelCfg v6[] = {make_cfg<0, 6, 8, false, true>(), make_cfg<0, 6, 4, false, true>(),
+                                 make_split_cfg<0, 5, 8>(), make_cfg<0, 5, 8, false, true>()};
+  static const KernelCfg v6[] = {make_split_cfg<0, 6, 8>(), make_cfg<0, 6, 4, false, true>(),
                                  make_cfg<0, 6, 8, false, true, 2>(), make_cfg<0, 6, 4, false, true, 2>(),
-                                 make_split_cfg<0, 6, 8>(), make_split_cfg<0, 6, 4>(), make_split_cfg<0, 6, 8, 2>(), make_split_cfg<0, 6, 8, 3>()};
-  static const KernelCfg v7[] = {make_cfg<0, 7, 4, false, true>(), make_cfg<0, 7, 4, false, true, 2>(),
+                                 make_cfg<0, 6, 8, false, true>(), make_split_cfg<0, 6, 4>(),
+                                 make_split_cfg<0, 6, 8, 2>(), make_split_cfg<0, 6, 8, 3>()};
+  static const KernelCfg v7[] = {make_split_cfg<0, 7, 8, 3>(), make_cfg<0, 7, 4, false, true, 2>(),
                                  make_cfg<0, 7, 8, false, true, 2>(), make_cfg<0, 7, 4, false, true, 4>(),
-                                 make_split_cfg<0, 7, 8>(), make_split_cfg<0, 7, 4>(), make_split_cfg<0, 7, 8, 2>(), make_split_cfg<0, 7, 8, 3>()};
-  static const KernelCfg v8[] = {make_cfg<0, 8, 4, false, true>(), make_cfg<0, 8, 4, false, true, 2>(),
+                                 make_split_cfg<0, 7, 8>(), make_split_cfg<0, 7, 4>(),
+                                 make_split_cfg<0, 7, 8, 2>(), make_cfg<0, 7, 4, false, true>()};
+  static const KernelCfg v8[] = {make_split_cfg<0, 8, 8, 3>(), make_cfg<0, 8, 4, false, true, 2>(),
                                  make_cfg<0, 8, 4, false, true, 4>(), make_cfg<0, 8, 8, false, true, 2>(),
-                                 make_split_cfg<0, 8, 4>(), make_split_cfg<0, 8, 8>(), make_split_cfg<0, 8, 8, 2>(), make_split_cfg<0, 8, 8, 3>()};
+                                 make_split_cfg<0, 8, 4>(), make_split_cfg<0, 8, 8>(),
+                                 make_split_cfg<0, 8, 8, 2>(), make_cfg<0, 8, 4, false, true>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
-  static const int cnt[8] = {4, 4, 4, 4, 6, 8, 8, 8};
+  static const int cnt[8] = {8, 8, 8, 8, 6, 8, 8, 8};
   if (N < 1 || N > 8) return nullptr;
   *count = cnt[N - 1];
   return tab[N - 1];

@@ -53,9 +53,17 @@ extern "C" int dg_rhs_host_noalloc(dg_handle* h, float* r_out) {
   int rc = scratch_for_device(dev, &scratch);
   if (rc) return rc;
   // the RHS kernel writes every value that is read back: nothing to clear.
-  // The fused default variant is used: a split variant would need its input
-  // buffer, which is allocated on first use.
-  const dgk::KernelCfg* cfg = h->cfg->split ? dgk::kernel_cfg(h->model, h->N) : h->cfg;
+  // A fused FP32 variant is used (the handle's own if it is one): a split
+  // variant would need its input buffer, which is allocated on first use.
+  const dgk::KernelCfg* cfg = h->cfg;
+  if (cfg->split || h->opts.strategy != DG_STRATEGY_FUSED) {
+    int n = 0;
+    const dgk::KernelCfg* v = dgk::kernel_variants(h->model, h->N, &n, 0);
+    cfg = nullptr;
+    for (int i = 0; i < n && !cfg; ++i)
+      if (!v[i].split) cfg = &v[i];
+    if (!cfg) return dg::fail(DG_EINVAL, "no fused variant for this degree");
+  }
   dgk::StepArgs a = h->args(1);
   a.rout = scratch;
   e = dgk::launch_step(cfg, a, h->stream);
