@@ -187,6 +187,23 @@ int dg_kernel_info(const dg_handle *h, int *block_elems, int *threads, int64_t *
  * an index out of range.                                                    */
 int dg_set_variant(dg_handle *h, int index);
 
+/* Receivers (seismogram sampling).  The paper samples no point values; the
+ * method's nodal polynomial fixes them: the field at a point x in element k
+ * is sum_i q_k[f][i] l_i(r(x)) with l_i the Lagrange basis of the element's
+ * nodes (Section 2.2) and r(x) the reference coordinates of x.
+ * dg_set_receivers places nrec receivers at xyz [nrec][3] (host, borrowed
+ * for the call; each in the element whose smallest barycentric coordinate of
+ * the point is largest, DG_EINVAL for a point outside the mesh) and clears
+ * the recorded traces; nrec = 0 removes them.  After every step of dg_step
+ * the fields at the receivers are recorded on the device (one sample =
+ * [nrec][Nf] floats, the state q^{m+1} just computed).
+ * dg_get_traces copies the samples recorded since dg_set_receivers into out
+ * [nsamples][nrec][Nf] (host, or device memory if on_device; NULL to query
+ * *nsamples only).  Samples are kept on the device; dg_step grows the buffer
+ * as needed (DG_ENOMEM if it cannot).                                     */
+int dg_set_receivers(dg_handle *h, const double *xyz, int nrec);
+int dg_get_traces(dg_handle *h, float *out, int64_t *nsamples, int on_device);
+
 /* The paper has no counterpart to this entry point.  Same result as
  * dg_rhs(h, r_out, 0) -- the RHS at the current state into the caller's host
  * buffer r_out [K][Nf][Np] -- but without allocating device memory: dg_rhs

@@ -273,6 +273,28 @@ class Solver:
         return r + self._lift(corr)
 
     # ------------------------------------------------------------------
+    def locate(self, xs):
+        """Element whose smallest barycentric coordinate of xs is largest, and
+        the reference coordinates of xs in it (affine map of Section 2.2)."""
+        m = self.mesh
+        xs = np.asarray(xs, dtype=np.float64)
+        x1 = m.verts[m.tets[:, 0]]
+        rst = np.einsum("kij,kj->ki", np.linalg.inv(m.A), xs[None, :] - x1) - 1.0
+        lam = np.stack([-(1 + rst.sum(axis=1)) / 2.0, (1 + rst[:, 0]) / 2.0,
+                        (1 + rst[:, 1]) / 2.0, (1 + rst[:, 2]) / 2.0], axis=1)
+        k = int(np.argmax(lam.min(axis=1)))
+        return k, rst[k]
+
+    def point_values(self, q, pts):
+        """[npts, Nf]: the nodal polynomial of the containing element evaluated
+        at each point, sum_i q_k[f][i] l_i(r(x)) (Section 2.2)."""
+        out = np.empty((len(pts), self.Nf))
+        for p, x in enumerate(pts):
+            k, rst = self.locate(x)
+            ell = self.ref.lag.eval(rst[None, :])[0]
+            out[p] = np.asarray(q[k], dtype=np.float64) @ ell
+        return out
+
     def set_source(self, xs, amp, direction=(0.0, 0.0, 1.0)):
         m, R = self.mesh, self.ref
         xs = np.asarray(xs, dtype=np.float64)

@@ -25,7 +25,8 @@ STRATEGY = {"fused": 0, "library": 1, "plain": 2}
 EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", "dg_rhs", "dg_step",
            "dg_set_dt", "dg_sync", "dg_autotune", "dg_kernel_info", "dg_set_variant", "dg_node_coords", "dg_set_source", "dg_suggest_dt",
            "dg_reference_element", "dg_last_error", "dg_server_create", "dg_submit", "dg_poll",
-           "dg_cancel", "dg_server_stats", "dg_server_destroy", "dg_rhs_host_noalloc")
+           "dg_cancel", "dg_server_stats", "dg_server_destroy", "dg_rhs_host_noalloc", "dg_set_receivers",
+           "dg_get_traces")
 
 
 class DGError(RuntimeError):
@@ -76,7 +77,7 @@ def lib():
         "dg_set_dt": (i32, [vp, dbl]),
         "dg_sync": (i32, [vp]),
         "dg_autotune": (i32, [vp, i32, P(i32), P(dbl), P(dbl)]),
-        "dg_kernel_info": (i32, [vp, P(i32), P(i32), P(i64), P(i32), P(i32), P(i32)]),
+        "dg_kernel_info": (i32, [vp, P(i32), P(i32), P(i64), P(i32), P(i32), P(i32), P(i32)]),
         "dg_set_variant": (i32, [vp, i32]),
         "dg_node_coords": (i32, [vp, P(dbl)]),
         "dg_set_source": (i32, [vp, P(dbl), P(dbl), P(dbl), i64]),
@@ -90,6 +91,8 @@ def lib():
         "dg_server_stats": (i32, [vp, P(i64), P(i64), P(i64), P(i64)]),
         "dg_server_destroy": (None, [vp]),
         "dg_rhs_host_noalloc": (i32, [vp, vp]),
+        "dg_set_receivers": (i32, [vp, P(dbl), i32]),
+        "dg_get_traces": (i32, [vp, vp, P(i64), i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -281,6 +284,22 @@ class Solver:
         d = np.ascontiguousarray(direction, dtype=np.float64)
         a = np.ascontiguousarray(amp, dtype=np.float64)
         check(lib().dg_set_source(self.h, _dptr(xs), _dptr(d), _dptr(a), a.size))
+
+
+    def set_receivers(self, xyz):
+        """Receivers at xyz [nrec][3]: the fields there are recorded after every step."""
+        x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        self.nrec = x.shape[0]
+        check(lib().dg_set_receivers(self.h, _dptr(x) if x.size else None, int(self.nrec)))
+
+    def traces(self):
+        """Recorded receiver samples, [nsamples][nrec][Nf] float32."""
+        n = C.c_int64()
+        check(lib().dg_get_traces(self.h, None, C.byref(n), 0))
+        out = np.empty((n.value, getattr(self, "nrec", 0), self.Nf), np.float32)
+        if out.size:
+            check(lib().dg_get_traces(self.h, out.ctypes.data_as(C.c_void_p), C.byref(n), 0))
+        return out
 
 
 class Server:

@@ -248,6 +248,8 @@ Handle::~Handle() {
   if (d_tc) cudaFree(d_tc);
   if (d_lib) cudaFree(d_lib);
   if (d_r0) cudaFree(d_r0);
+  if (d_recel) cudaFree(d_recel);
+  if (d_traces) cudaFree(d_traces);
   if (cublas) cublasDestroy(static_cast<cublasHandle_t>(cublas));
 }
 
@@ -442,6 +444,21 @@ void Handle::split_ptrs(dgk::StepArgs& a, const dgk::KernelCfg* c) const {
 int Handle::advance(int nsteps) {
   int rc = ensure_split(cfg);
   if (rc) return rc;
+  if (nrec > 0 && nsamples + nsteps > trace_cap) {
+    // grow the trace buffer (keep what was recorded)
+    const int64_t cap = std::max<int64_t>(nsamples + nsteps, 2 * trace_cap);
+    float* nb = nullptr;
+    const size_t per = size_t(nrec) * Nf * sizeof(float);
+    if (cudaMalloc(reinterpret_cast<void**>(&nb), size_t(cap) * per) != cudaSuccess)
+      return fail(DG_ENOMEM, "receiver trace buffer");
+    if (nsamples > 0) DG_CUDA(cudaMemcpyAsync(nb, d_traces, size_t(nsamples) * per, cudaMemcpyDeviceToDevice, stream));
+    if (d_traces) {
+      DG_CUDA(cudaStreamSynchronize(stream));
+      cudaFree(d_traces);
+    }
+    d_traces = nb;
+    trace_cap = cap;
+  }
   for (int s = 0; s < nsteps; ++s) {
     dgk::StepArgs a = args(0);
     int lr = launch(a);
@@ -450,8 +467,34 @@ int Handle::advance(int nsteps) {
     r1slot ^= 1;  // r^m was written into the r^{m-2} slot
     ++step;
     have = std::min(have + 1, 2);
+    if (nrec > 0) {
+      DG_CUDA(dgk::launch_sample(d_q[qcur], d_recel, d_recvec, nrec, Nf, Np,
+                                 d_traces + size_t(nsamples) * nrec * Nf, stream));
+      ++nsamples;
+    }
   }
   return DG_OK;
+}
+
+int64_t Handle::locate(const double x[3], double rst_out[3]) const {
+  int64_t best = -1;
+  double bestmin = -1e300;
+  for (int64_t k = 0; k < K; ++k) {
+    const double* x1 = &verts[3 * tets[4 * k]];
+    const double* gk = &hm.g[9 * k];
+    const double d[3] = {x[0] - x1[0], x[1] - x1[1], x[2] - x1[2]};
+    double rst[3];
+    for (int j = 0; j < 3; ++j) rst[j] = gk[j] * d[0] + gk[3 + j] * d[1] + gk[6 + j] * d[2] - 1.0;
+    const double lam[4] = {-(1 + rst[0] + rst[1] + rst[2]) / 2, (1 + rst[0]) / 2, (1 + rst[1]) / 2,
+                           (1 + rst[2]) / 2};
+    const double mn = std::min(std::min(lam[0], lam[1]), std::min(lam[2], lam[3]));
+    if (mn > bestmin) {
+      bestmin = mn;
+      best = k;
+      std::memcpy(rst_out, rst, sizeof(rst));
+    }
+  }
+  return (best < 0 || bestmin < -1e-9) ? -1 : best;
 }
 
 }  // namespace dg
@@ -593,24 +636,9 @@ int dg_set_source(dg_handle* h, const double xs[3], const double dir[3], const d
     return DG_OK;
   }
   if (!xs) return fail(DG_EINVAL, "source position is NULL");
-  // element whose smallest barycentric coordinate of xs is largest
-  int64_t best = -1;
-  double bestmin = -1e300, brst[3] = {0, 0, 0};
-  for (int64_t k = 0; k < h->K; ++k) {
-    const double* x1 = &h->verts[3 * h->tets[4 * k]];
-    const double* gk = &h->hm.g[9 * k];
-    double d[3] = {xs[0] - x1[0], xs[1] - x1[1], xs[2] - x1[2]};
-    double rst[3];
-    for (int j = 0; j < 3; ++j) rst[j] = gk[j] * d[0] + gk[3 + j] * d[1] + gk[6 + j] * d[2] - 1.0;
-    double lam[4] = {-(1 + rst[0] + rst[1] + rst[2]) / 2, (1 + rst[0]) / 2, (1 + rst[1]) / 2, (1 + rst[2]) / 2};
-    double mn = std::min(std::min(lam[0], lam[1]), std::min(lam[2], lam[3]));
-    if (mn > bestmin) {
-      bestmin = mn;
-      best = k;
-      std::memcpy(brst, rst, sizeof(brst));
-    }
-  }
-  if (best < 0 || bestmin < -1e-9) return fail(DG_EINVAL, "source position outside the mesh");
+  double brst[3] = {0, 0, 0};
+  const int64_t best = h->locate(xs, brst);
+  if (best < 0) return fail(DG_EINVAL, "source position outside the mesh");
   // M_k^{-1} l(x_s) = V psi(x_s) / J_k  (V orthonormal Vandermonde)
   const auto& R = h->ref;
   std::vector<double> psi(R.Np), b(R.Np, 0.0);
@@ -634,6 +662,88 @@ int dg_set_source(dg_handle* h, const double xs[3], const double dir[3], const d
   DG_CUDA(cudaStreamSynchronize(h->stream));
   h->src_elem = int(best);
   h->src_amp.assign(amp, amp + namp);
+  return DG_OK;
+}
+
+// Gauss-Jordan inverse with partial pivoting of an n x n row-major matrix.
+static bool invert(std::vector<double> a, int n, std::vector<double>& inv) {
+  inv.assign(size_t(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[size_t(i) * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[size_t(r) * n + c]) > std::fabs(a[size_t(p) * n + c])) p = r;
+    if (a[size_t(p) * n + c] == 0.0) return false;
+    if (p != c)
+      for (int j = 0; j < n; ++j) {
+        std::swap(a[size_t(p) * n + j], a[size_t(c) * n + j]);
+        std::swap(inv[size_t(p) * n + j], inv[size_t(c) * n + j]);
+      }
+    const double d = 1.0 / a[size_t(c) * n + c];
+    for (int j = 0; j < n; ++j) {
+      a[size_t(c) * n + j] *= d;
+      inv[size_t(c) * n + j] *= d;
+    }
+    for (int r = 0; r < n; ++r)
+      if (r != c && a[size_t(r) * n + c] != 0.0) {
+        const double f = a[size_t(r) * n + c];
+        for (int j = 0; j < n; ++j) {
+          a[size_t(r) * n + j] -= f * a[size_t(c) * n + j];
+          inv[size_t(r) * n + j] -= f * inv[size_t(c) * n + j];
+        }
+      }
+  }
+  return true;
+}
+
+int dg_set_receivers(dg_handle* h, const double* xyz, int nrec) {
+  if (!h || nrec < 0 || (nrec > 0 && !xyz)) return fail(DG_EINVAL, "NULL handle, negative count or NULL points");
+  const auto& R = h->ref;
+  std::vector<int> el(size_t(std::max(nrec, 0)));
+  std::vector<float> vec(size_t(std::max(nrec, 0)) * R.Np);
+  if (nrec > 0 && h->Vinv.empty() && !invert(R.V, R.Np, h->Vinv))
+    return fail(DG_EINVAL, "singular Vandermonde matrix");
+  std::vector<double> psi(R.Np);
+  for (int r = 0; r < nrec; ++r) {
+    double rst[3];
+    const int64_t k = h->locate(xyz + 3 * r, rst);
+    if (k < 0) return fail(DG_EINVAL, "receiver " + std::to_string(r) + " outside the mesh");
+    el[r] = int(k);
+    // l_i(x) = sum_m psi_m(r(x)) (V^{-1})_{m i}
+    R.basis(rst[0], rst[1], rst[2], psi.data());
+    for (int i = 0; i < R.Np; ++i) {
+      double acc = 0.0;
+      for (int m = 0; m < R.Np; ++m) acc += psi[m] * h->Vinv[size_t(m) * R.Np + i];
+      vec[size_t(r) * R.Np + i] = float(acc);
+    }
+  }
+  DG_CUDA(cudaStreamSynchronize(h->stream));
+  if (h->d_recel) cudaFree(h->d_recel);
+  if (h->d_traces) cudaFree(h->d_traces);
+  h->d_recel = nullptr;
+  h->d_recvec = nullptr;
+  h->d_traces = nullptr;
+  h->trace_cap = h->nsamples = 0;
+  h->nrec = 0;
+  if (nrec == 0) return DG_OK;
+  const size_t eb = (size_t(nrec) * 4 + 255) & ~size_t(255);
+  DG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->d_recel), eb + vec.size() * 4));
+  h->d_recvec = reinterpret_cast<float*>(reinterpret_cast<char*>(h->d_recel) + eb);
+  DG_CUDA(cudaMemcpyAsync(h->d_recel, el.data(), el.size() * 4, cudaMemcpyHostToDevice, h->stream));
+  DG_CUDA(cudaMemcpyAsync(h->d_recvec, vec.data(), vec.size() * 4, cudaMemcpyHostToDevice, h->stream));
+  DG_CUDA(cudaStreamSynchronize(h->stream));
+  h->nrec = nrec;
+  return DG_OK;
+}
+
+int dg_get_traces(dg_handle* h, float* out, int64_t* nsamples, int on_device) {
+  if (!h) return fail(DG_EINVAL, "NULL handle");
+  if (nsamples) *nsamples = h->nsamples;
+  if (!out || h->nsamples == 0 || h->nrec == 0) return DG_OK;
+  const size_t bytes = size_t(h->nsamples) * h->nrec * h->Nf * 4;
+  DG_CUDA(cudaMemcpyAsync(out, h->d_traces, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          h->stream));
+  DG_CUDA(cudaStreamSynchronize(h->stream));
   return DG_OK;
 }
 

@@ -116,5 +116,8 @@ cudaError_t launch_step(const KernelCfg* cfg, const StepArgs& args, cudaStream_t
 cudaError_t launch_step_batched(const KernelCfg* cfg, const BatchArgs& args, cudaStream_t stream);
 // Advance the device-side step state of the solves (one thread per solve).
 cudaError_t launch_advance(SolveDev* solves, int nsolves, cudaStream_t stream);
+// Receiver sample: out[r][f] = sum_i vec[r][i] q[elem[r]][f][i].
+cudaError_t launch_sample(const float* q, const int* elem, const float* vec, int nrec, int Nf, int Np, float* out,
+                          cudaStream_t stream);
 
 }  // namespace dgk

@@ -81,6 +81,29 @@ cudaError_t launch_step(const KernelCfg* c, const StepArgs& args, cudaStream_t s
                           c->smem_gemm, stream);
 }
 
+// one warp per (receiver, field): lanes over the nodes, then a warp sum
+__global__ void sample_kernel(const float* __restrict__ q, const int* __restrict__ elem,
+                              const float* __restrict__ vec, int nrec, int Nf, int Np, float* __restrict__ out) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= nrec * Nf) return;
+  const int r = w / Nf, f = w - r * Nf;
+  const float* qk = q + (size_t(elem[r]) * Nf + f) * Np;
+  const float* l = vec + size_t(r) * Np;
+  float acc = 0.f;
+  for (int i = lane; i < Np; i += 32) acc = fmaf(l[i], qk[i], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[w] = acc;
+}
+
+cudaError_t launch_sample(const float* q, const int* elem, const float* vec, int nrec, int Nf, int Np, float* out,
+                          cudaStream_t stream) {
+  if (nrec <= 0) return cudaSuccess;
+  const int warps = nrec * Nf;
+  sample_kernel<<<(warps * 32 + 255) / 256, 256, 0, stream>>>(q, elem, vec, nrec, Nf, Np, out);
+  return cudaGetLastError();
+}
+
 __global__ void advance_kernel(SolveDev* s, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || s[i].steps_left <= 0) return;

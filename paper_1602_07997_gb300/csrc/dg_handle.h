@@ -66,8 +66,18 @@ struct Handle {
   int have = 0;    // stored RHS levels (0, 1, 2)
   int src_elem = -1;
   std::vector<double> src_amp;
+  // receivers: element and interpolation vector per receiver (device), traces
+  int nrec = 0;
+  int* d_recel = nullptr;
+  float* d_recvec = nullptr;  // [nrec][Np]
+  float* d_traces = nullptr;  // [trace_cap][nrec][Nf]
+  int64_t trace_cap = 0, nsamples = 0;
+  std::vector<double> Vinv;   // inverse Vandermonde, on first use
 
   int init(const dg_mesh* mesh, const double* coeffs, int N, int model, const dg_opts* o);
+  // element whose smallest barycentric coordinate of x is largest, and the
+  // reference coordinates of x in it; -1 if x is outside the mesh
+  int64_t locate(const double x[3], double rst[3]) const;
   int ensure_split(const dgk::KernelCfg* c);
   int ensure_strategy();
   // one step (a.mode 0) or RHS (mode 1) with the handle's strategy

@@ -390,3 +390,31 @@ def test_suggested_dt_is_ab3_stable(model, N):
         E.append(S.energy(st.q))
     E = np.array(E)
     assert np.all(np.diff(E[2:]) <= 1e-13 * E[0]), np.max(np.diff(E[2:]))
+
+
+@pytest.mark.parametrize("N", [1, 3, 6])
+def test_point_values_reproduce_polynomials(N):
+    """Point evaluation of the nodal polynomial (receivers) is exact for fields
+    that are polynomials of degree <= N, at interior points and at points on
+    faces shared by two elements."""
+    verts, tets = W.kuhn_cube_mesh(2, 0.1, seed=11)
+    K = tets.shape[0]
+    S = Solver("acoustic", N, verts, tets, np.ones((K, 2)))
+    rng = np.random.default_rng(N)
+    # random polynomial of total degree N per field, evaluated at the nodes
+    expo = [(a, b, c) for a in range(N + 1) for b in range(N + 1 - a) for c in range(N + 1 - a - b)]
+    coef = rng.uniform(-1, 1, size=(S.Nf, len(expo)))
+
+    def poly(x):
+        x = np.atleast_2d(x)
+        mon = np.stack([x[:, 0] ** a * x[:, 1] ** b * x[:, 2] ** c for a, b, c in expo], axis=1)
+        return mon @ coef.T
+
+    X = S.mesh.x.reshape(-1, 3)
+    q = poly(X).reshape(K, S.ref.Np, S.Nf).transpose(0, 2, 1)
+    pts = rng.uniform(0.05, 0.95, size=(20, 3))
+    # a point on an interior face: the centroid of a face shared by two tets
+    k0 = int(np.argmax(S.mesh.EToE[:, 0] != np.arange(K)))
+    fv = verts[tets[k0][[0, 1, 2]]]
+    pts = np.vstack([pts, fv.mean(axis=0)])
+    assert np.abs(S.point_values(q, pts) - poly(pts)).max() < 1e-10
