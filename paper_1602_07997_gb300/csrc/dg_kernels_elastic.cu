@@ -13,26 +13,33 @@ const KernelCfg* kernel_variants_elastic(int N, int* count) {
   static const KernelCfg v2[] = {make_cfg<1, 2, 8, true, true, 1, 128>(), make_cfg<1, 2, 4, true, true>(),
                                  make_cfg<1, 2, 16, true, true>(), make_cfg<1, 2, 8, true, true>(),
                                  make_cfg<1, 2, 16, true, true, 1, 256>()};
-  static const KernelCfg v3[] = {make_cfg<1, 3, 8, true, true, 1, 256>(), make_cfg<1, 3, 4, true, true>(),
+  static const KernelCfg v3[] = {make_split_cfg<1, 3, 8, 3, 256>(), make_cfg<1, 3, 4, true, true>(),
                                  make_cfg<1, 3, 16, true, true>(), make_cfg<1, 3, 8, true, true, 1, 128>(),
-                                 make_cfg<1, 3, 8, true, true>()};
-  static const KernelCfg v4[] = {make_cfg<1, 4, 4, true, true>(), make_cfg<1, 4, 8, false, true>(),
+                                 make_cfg<1, 3, 8, true, true>(), make_cfg<1, 3, 8, true, true, 1, 256>(),
+                                 make_split_cfg<1, 3, 8, 2, 256>()};
+  static const KernelCfg v4[] = {make_split_cfg<1, 4, 8, 3, 256>(), make_cfg<1, 4, 8, false, true>(),
                                  make_cfg<1, 4, 4, false, true>(), make_split_cfg<1, 4, 8>(),
-                                 make_split_cfg<1, 4, 8, 2>()};
-  static const KernelCfg v5[] = {make_split_cfg<1, 5, 4, 3>(), make_cfg<1, 5, 4, false, false>(),
+                                 make_split_cfg<1, 4, 8, 2>(), make_cfg<1, 4, 4, true, true, 1, 128>(),
+                                 make_cfg<1, 4, 4, true, true, 1, 256>(), make_split_cfg<1, 4, 4, 3, 256>(),
+                                 make_cfg<1, 4, 4, true, true>()};
+  static const KernelCfg v5[] = {make_split_cfg<1, 5, 4, 3, 512>(), make_cfg<1, 5, 4, false, false>(),
                                  make_split_cfg<1, 5, 4>(), make_split_cfg<1, 5, 4, 2>(),
-                                 make_cfg<1, 5, 4, false, true>()};
-  static const KernelCfg v6[] = {make_split_cfg<1, 6, 4, 3>(), make_cfg<1, 6, 4, false, false, 2>(),
+                                 make_cfg<1, 5, 4, false, true>(), make_split_cfg<1, 5, 4, 3, 256>(),
+                                 make_split_cfg<1, 5, 4, 3, 384>(), make_split_cfg<1, 5, 4, 3>()};
+  static const KernelCfg v6[] = {make_split_cfg<1, 6, 4, 3, 512>(), make_cfg<1, 6, 4, false, false, 2>(),
                                  make_split_cfg<1, 6, 4>(), make_split_cfg<1, 6, 4, 2>(),
-                                 make_cfg<1, 6, 4, false, false>()};
-  static const KernelCfg v7[] = {make_split_cfg<1, 7, 4, 3>(), make_cfg<1, 7, 4, false, false, 2>(),
+                                 make_cfg<1, 6, 4, false, false>(), make_split_cfg<1, 6, 4, 3, 256>(),
+                                 make_split_cfg<1, 6, 4, 3, 384>(), make_split_cfg<1, 6, 4, 3>()};
+  static const KernelCfg v7[] = {make_split_cfg<1, 7, 4, 3, 512>(), make_cfg<1, 7, 4, false, false, 2>(),
                                  make_split_cfg<1, 7, 4>(), make_split_cfg<1, 7, 4, 2>(),
-                                 make_cfg<1, 7, 4, false, false>()};
-  static const KernelCfg v8[] = {make_split_cfg<1, 8, 4, 2>(), make_cfg<1, 8, 4, false, false, 2>(),
+                                 make_cfg<1, 7, 4, false, false>(), make_split_cfg<1, 7, 4, 3, 256>(),
+                                 make_split_cfg<1, 7, 4, 3, 384>(), make_split_cfg<1, 7, 4, 3>()};
+  static const KernelCfg v8[] = {make_split_cfg<1, 8, 4, 2, 384>(), make_cfg<1, 8, 4, false, false, 2>(),
                                  make_split_cfg<1, 8, 4>(), make_cfg<1, 8, 4, false, false>(),
-                                 make_split_cfg<1, 8, 4, 3>()};
+                                 make_split_cfg<1, 8, 4, 3>(), make_split_cfg<1, 8, 4, 3, 256>(),
+                                 make_split_cfg<1, 8, 4, 3, 384>(), make_split_cfg<1, 8, 4, 2>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
-  static const int cnt[8] = {5, 5, 5, 5, 5, 5, 5, 5};
+  static const int cnt[8] = {5, 5, 7, 9, 8, 8, 8, 8};
   if (N < 1 || N > 8) return nullptr;
   *count = cnt[N - 1];
   return tab[N - 1];
