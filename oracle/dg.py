@@ -163,16 +163,18 @@ class Solver:
         return cfl * float(np.min(1.0 / (self.cmax[:, None] * m.Fscale * nf)))
 
     # ------------------------------------------------------------------
-    def _traces(self, q):
-        """Interior (-) and exterior (+) traces, [K, Nf, 4, Nfp] each."""
+    # E selects the elements whose RHS is computed (all of them when E is a
+    # full slice); the traces still read the neighbours' states from q.
+    def _traces(self, q, E):
+        """Interior (-) and exterior (+) traces, [len(E), Nf, 4, Nfp] each."""
         m = self.mesh
         qf = q.transpose(1, 0, 2).reshape(self.Nf, -1)
-        return qf[:, m.vmapM].transpose(1, 0, 2, 3), qf[:, m.vmapP].transpose(1, 0, 2, 3)
+        return qf[:, m.vmapM[E]].transpose(1, 0, 2, 3), qf[:, m.vmapP[E]].transpose(1, 0, 2, 3)
 
-    def _lift(self, corr):
-        """sum_f Fscale_f L_f corr_f for corr [K, Nf, 4, Nfp]."""
+    def _lift(self, corr, E):
+        """sum_f Fscale_f L_f corr_f for corr [len(E), Nf, 4, Nfp]."""
         m = self.mesh
-        c = corr * m.Fscale[:, None, :, None]
+        c = corr * m.Fscale[E][:, None, :, None]
         K = c.shape[0]
         return np.einsum("ij,kfj->kfi", self.ref.LIFT, c.reshape(K, self.Nf, -1))
 
@@ -181,80 +183,89 @@ class Solver:
         R = self.ref
         return np.stack([np.einsum("ij,kfj->kfi", D, u) for D in (R.Dr, R.Ds, R.Dt)], axis=2)
 
-    def _phys_grad(self, u):
-        """[K, F, 3(i), Np]: d u / d x_i = sum_j g_ij D_j u."""
-        return np.einsum("kij,kfjn->kfin", self.mesh.g, self._ref_grad(u))
+    def _phys_grad(self, u, E=slice(None)):
+        """[K, F, 3(i), Np]: d u / d x_i = sum_j g_ij D_j u (u of the elements E)."""
+        return np.einsum("kij,kfjn->kfin", self.mesh.g[E], self._ref_grad(u))
 
     # ------------------------------------------------------------------
-    def rhs(self, q, step=None):
+    def rhs(self, q, step=None, elems=None):
+        """The semi-discrete RHS (Eq. dgLocalRhs) for the full state q; of
+        every element, or only of the elements listed in elems (sampled
+        checks of large meshes: the same formulas on those elements' rows)."""
         q = np.asarray(q, dtype=np.float64)
-        r = self._rhs_acoustic(q) if self.model == ACOUSTIC else self._rhs_elastic(q)
+        E = slice(None) if elems is None else np.asarray(elems, dtype=np.int64)
+        r = self._rhs_acoustic(q, E) if self.model == ACOUSTIC else self._rhs_elastic(q, E)
         if self.src is not None and step is not None:
             k, b, amp, d = self.src
             a = amp[step] if step < len(amp) else 0.0
-            if self.model == ACOUSTIC:
-                r[k, 0] += a * b
-            else:
-                for i in range(3):
-                    r[k, i] += a * d[i] / self.rho[k] * b
+            rows = [k] if elems is None else list(np.nonzero(np.asarray(elems) == k)[0])
+            for row in rows:
+                if self.model == ACOUSTIC:
+                    r[row, 0] += a * b
+                else:
+                    for i in range(3):
+                        r[row, i] += a * d[i] / self.rho[k] * b
         return r
 
-    def _rhs_acoustic(self, q):
+    def _rhs_acoustic(self, q, E):
         m = self.mesh
-        K = self.K
-        p, v = q[:, 0:1], q[:, 1:4]
-        gp = self._phys_grad(p)[:, 0]                   # [K, 3, Np]
-        gv = self._phys_grad(v)                         # [K, 3(comp), 3(dir), Np]
+        qE = q[E]
+        K = qE.shape[0]
+        kappa, rho, c, Z = self.kappa[E], self.rho[E], self.c[E], self.Z[E]
+        p, v = qE[:, 0:1], qE[:, 1:4]
+        gp = self._phys_grad(p, E)[:, 0]                # [K, 3, Np]
+        gv = self._phys_grad(v, E)                      # [K, 3(comp), 3(dir), Np]
         divv = np.einsum("kiin->kn", gv)
-        r = np.empty_like(q)
-        r[:, 0] = -self.kappa[:, None] * divv
-        r[:, 1:4] = -(1.0 / self.rho)[:, None, None] * gp
+        r = np.empty_like(qE)
+        r[:, 0] = -kappa[:, None] * divv
+        r[:, 1:4] = -(1.0 / rho)[:, None, None] * gp
 
-        qM, qP = self._traces(q)
-        n = m.n[:, :, None, :]                          # [K, 4, 1, 3]
+        qM, qP = self._traces(q, E)
+        n = m.n[E][:, :, None, :]                       # [K, 4, 1, 3]
         pM, pP = qM[:, 0], qP[:, 0]
         vM = np.moveaxis(qM[:, 1:4], 1, -1)             # [K, 4, Nfp, 3]
         vP = np.moveaxis(qP[:, 1:4], 1, -1)
-        bnd = m.boundary[:, :, None]
+        bnd = m.boundary[E][:, :, None]
         vnM = np.sum(vM * n, axis=-1)
         # rigid-wall mirror ghost
         pP = np.where(bnd, pM, pP)
         vP = np.where(bnd[..., None], vM - 2.0 * vnM[..., None] * n, vP)
-        ZP = np.where(bnd, self.Z[:, None, None], self.Z[m.EToE][:, :, None])
-        dp, dv = acoustic_penalty(pM, pP, vM, vP, n, self.kappa[:, None, None],
-                                  self.rho[:, None, None], self.c[:, None, None], ZP,
+        ZP = np.where(bnd, Z[:, None, None], self.Z[m.EToE[E]][:, :, None])
+        dp, dv = acoustic_penalty(pM, pP, vM, vP, n, kappa[:, None, None],
+                                  rho[:, None, None], c[:, None, None], ZP,
                                   self.flux)
         corr = np.empty((K, 4, 4, self.ref.Nfp))
         corr[:, 0] = dp
         corr[:, 1:4] = np.moveaxis(dv, -1, 1)
-        return r + self._lift(corr)
+        return r + self._lift(corr, E)
 
-    def _rhs_elastic(self, q):
+    def _rhs_elastic(self, q, E):
         m = self.mesh
-        K = self.K
-        lam, mu, rho = self.lam, self.mu, self.rho
-        v = q[:, 0:3]
-        gv = self._phys_grad(v)                          # [K, i(comp), j(dir), Np]
+        qE = q[E]
+        K = qE.shape[0]
+        lam, mu, rho = self.lam[E], self.mu[E], self.rho[E]
+        v = qE[:, 0:3]
+        gv = self._phys_grad(v, E)                       # [K, i(comp), j(dir), Np]
         divv = np.einsum("kiin->kn", gv)
-        r = np.empty_like(q)
+        r = np.empty_like(qE)
         for i in range(3):
             for j in range(i, 3):
                 val = mu[:, None] * (gv[:, i, j] + gv[:, j, i])
                 if i == j:
                     val = val + lam[:, None] * divv
                 r[:, SIG[i, j]] = val
-        sig = q[:, SIG.ravel()].reshape(K, 3, 3, -1)      # sigma_ij
-        gs = self._phys_grad(sig.reshape(K, 9, -1)).reshape(K, 3, 3, 3, -1)  # d_k sigma_ij
+        sig = qE[:, SIG.ravel()].reshape(K, 3, 3, -1)     # sigma_ij
+        gs = self._phys_grad(sig.reshape(K, 9, -1), E).reshape(K, 3, 3, 3, -1)  # d_k sigma_ij
         divs = np.einsum("kijjn->kin", gs)
         r[:, 0:3] = divs / rho[:, None, None]
 
-        qM, qP = self._traces(q)
-        n = m.n[:, :, None, :]                           # [K, 4, 1, 3]
+        qM, qP = self._traces(q, E)
+        n = m.n[E][:, :, None, :]                        # [K, 4, 1, 3]
         vM = np.moveaxis(qM[:, 0:3], 1, -1)              # [K, 4, Nfp, 3]
         vP = np.moveaxis(qP[:, 0:3], 1, -1)
         sM = np.moveaxis(qM[:, SIG.ravel()], 1, -1).reshape(qM.shape[0], 4, -1, 3, 3)
         sP = np.moveaxis(qP[:, SIG.ravel()], 1, -1).reshape(qP.shape[0], 4, -1, 3, 3)
-        bnd = m.boundary[:, :, None]
+        bnd = m.boundary[E][:, :, None]
         if self.bc == "free":
             vP = np.where(bnd[..., None], vM, vP)
             sP = np.where(bnd[..., None, None], -sM, sP)
@@ -262,7 +273,7 @@ class Solver:
             vP = np.where(bnd[..., None], -vM, vP)
             sP = np.where(bnd[..., None, None], sM, sP)
         def nb(x):
-            return np.where(bnd, x[:, None, None], x[m.EToE][:, :, None])
+            return np.where(bnd, x[E][:, None, None], x[m.EToE[E]][:, :, None])
         Psig, pv = elastic_penalty(vM, vP, sM, sP, n, lam[:, None, None], mu[:, None, None],
                                    rho[:, None, None], nb(self.Zp), nb(self.Zs), self.flux)
         corr = np.empty((K, 9, 4, self.ref.Nfp))
@@ -270,7 +281,7 @@ class Solver:
         for i in range(3):
             for j in range(i, 3):
                 corr[:, SIG[i, j]] = Psig[..., i, j]
-        return r + self._lift(corr)
+        return r + self._lift(corr, E)
 
     # ------------------------------------------------------------------
     def locate(self, xs):

@@ -91,3 +91,25 @@ def test_full_size_ab3_steps(dg):
     err = rel_l2(model, g.get_state(), st.q)
     g.close()
     assert err <= STEP_TOL, err
+
+
+@pytest.mark.gpu
+def test_large_elastic_rhs_sampled(dg):
+    """The large elastic configuration (N = 7, 131 712 tets, 15.8 M nodes, 2.3 GB
+    of state) in the autotuned launch configuration, against the oracle's RHS
+    on 400 sampled elements (the same formulas on those elements' rows)."""
+    from workloads.configs import config5_elastic_large
+    cfg = config5_elastic_large()
+    model, N = "elastic", cfg["N"]
+    o = OSolver(model, N, cfg["verts"], cfg["tets"], cfg["coeffs"])
+    g = dg.Solver(cfg["verts"], cfg["tets"], cfg["coeffs"], N, model, dt=1e-6)
+    q = W.random_state(o.K, o.Nf, o.ref.Np, seed=5).astype(np.float32)
+    g.set_state(q)
+    g.autotune(2)
+    r = g.rhs()
+    g.close()
+    sample = np.sort(np.random.default_rng(5).choice(o.K, size=400, replace=False))
+    ro = o.rhs(q, elems=sample)
+    err = rel_l2(model, r[sample], ro)
+    print(f"large elastic N=7 K={o.K} sampled rel-L2 {err:.2e}")
+    assert err <= RHS_TOL, err

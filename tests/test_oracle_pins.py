@@ -418,3 +418,19 @@ def test_point_values_reproduce_polynomials(N):
     fv = verts[tets[k0][[0, 1, 2]]]
     pts = np.vstack([pts, fv.mean(axis=0)])
     assert np.abs(S.point_values(q, pts) - poly(pts)).max() < 1e-10
+
+
+@pytest.mark.parametrize("model", ["acoustic", "elastic"])
+def test_rhs_on_element_subset_equals_full_rows(model):
+    """The oracle's RHS restricted to sampled elements (used for the largest
+    meshes) is exactly the corresponding rows of the full RHS, source included."""
+    verts, tets = W.kuhn_cube_mesh(3, 0.1, seed=17)
+    K = tets.shape[0]
+    coeffs = (W.acoustic_coefficients(K, 1, 3, seed=18) if model == "acoustic"
+              else W.elastic_two_layer(verts, tets, seed=18))
+    S = Solver(model, 3, verts, tets, coeffs)
+    ks = S.set_source((0.47, 0.52, 0.44), np.array([0.7, -0.3]))
+    q = W.random_state(K, S.Nf, S.ref.Np, seed=4)
+    full = S.rhs(q, step=0)
+    sample = np.array(sorted({0, 5, K - 1, ks} | set(np.random.default_rng(1).integers(0, K, 20).tolist())))
+    assert np.array_equal(S.rhs(q, step=0, elems=sample), full[sample])
