@@ -154,7 +154,11 @@ __device__ __forceinline__ constexpr float ref_normal(int f, int i) {
 // ---------------------------------------------------------------- smem plan
 constexpr int round4(int x) { return (x + 3) & ~3; }
 
-template <int MODEL, int N, int EB, bool OPS_SMEM, bool R_SMEM>
+// FACT (acoustic, fused step): the surface inputs are two streams per face
+// node, the pressure penalty and the magnitude psi of the velocity penalty
+// psi n_f (n_f is constant on a face of a straight-sided tetrahedron), plus
+// per-face penalty coefficients and neighbour sources.
+template <int MODEL, int N, int EB, bool OPS_SMEM, bool R_SMEM, bool FACT = false>
 struct Plan {
   using S = Sz<N>;
   static constexpr int Nf = MODEL == 0 ? 4 : 9;
@@ -165,7 +169,7 @@ struct Plan {
   static constexpr int sQ = 0, sRec = nQ, sNbr = round4(nQ + EB * REC);
   static constexpr int nR = R_SMEM ? 2 * nQ : 0;
   static constexpr int nXvol = (MODEL == 0 ? 4 : 12) * S::Np * EBP;
-  static constexpr int nXsur = Nf * S::NFN * EBP;
+  static constexpr int nXsur = (FACT ? 2 : Nf) * S::NFN * EBP;
   static constexpr int nT = Nf * S::NFN * EBP;             // neighbour traces [Nf][4Nfp][EBP]
   static constexpr int nOps = OPS_SMEM ? S::KD * S::Mpad : 0;
   static constexpr int oStage0 = 0;
@@ -177,8 +181,11 @@ struct Plan {
   static constexpr int oT1 = round4(oT0 + nT);
   static constexpr int oOps = round4(oT1 + nT);
   static constexpr int oFn = round4(oOps + nOps);          // [EB][4] float4: n, Fscale
-  static constexpr int oFtab = oFn + EB * 16;              // int [10][Nfp]
-  static constexpr int oBar = round4(oFtab + 10 * S::Nfp);
+  static constexpr int oCo = oFn + EB * 16;                // [EB][4] float4: penalty coefficients (FACT)
+  static constexpr int oFi = oCo + (FACT ? EB * 16 : 0);   // [EB][4] int2: neighbour source (FACT)
+  static constexpr int oFtab = oFi + (FACT ? EB * 8 : 0);  // int [10][Nfp]
+  static constexpr int oPtab = oFtab + 10 * S::Nfp;        // int [4][6][Nfp]: neighbour node (FACT)
+  static constexpr int oBar = round4(oPtab + (FACT ? 24 * S::Nfp : 0));
   static constexpr int nFloats = oBar + 8;                 // 3 mbarriers
   static constexpr size_t bytes = size_t(nFloats) * 4;
   static_assert(nXvol >= nQ, "the RHS of a block is staged in the volume-input buffer");
@@ -411,7 +418,8 @@ struct SolveBatch {
 template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT, int XP, class Prov>
 __device__ __forceinline__ void step_body(const Prov& prov) {
   using S = Sz<N>;
-  using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM>;
+  constexpr bool FACT = MODEL == 0 && SPLIT == 0;
+  using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM, FACT>;
   constexpr int Np = S::Np, Nfp = S::Nfp, NFN = S::NFN, Mpad = S::Mpad, RT = S::RT;
   constexpr int Nf = P::Nf, REC = P::REC, EBP = P::EBP;
   constexpr int NTILE = RT * (EB / TN);  // tiles of 4 output nodes x TN elements
@@ -428,6 +436,9 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
   const int mode = prov.mode();
   float* sFn = smem + P::oFn;
   int* sFtab = reinterpret_cast<int*>(smem + P::oFtab);
+  float4* sCo = reinterpret_cast<float4*>(smem + P::oCo);
+  int2* sFi = reinterpret_cast<int2*>(smem + P::oFi);
+  int* sPtab = reinterpret_cast<int*>(smem + P::oPtab);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P::oBar);
 
   const int tid = threadIdx.x;
@@ -493,6 +504,14 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
   if (tid == 0 && (int)blockIdx.x < nblk) issue_stage(nxt_a, nxt_lb, 0, true);
   for (int i = tid; i < 10 * Nfp; i += NT) sFtab[i] = prov.ftab()[i];
   __syncthreads();
+  if constexpr (FACT) {
+    // neighbour volume node of own face node m across a face seen as the
+    // neighbour's face f2 under rotation rot: ptab[(f2 * 6 + rot) Nfp + m]
+    for (int i = tid; i < 24 * Nfp; i += NT) {
+      const int m = i % Nfp, fr = i / Nfp;
+      sPtab[i] = sFtab[(fr / 6) * Nfp + sFtab[4 * Nfp + (fr % 6) * Nfp + m]];
+    }
+  }
   if ((int)blockIdx.x < nblk) {
     if (!__syncthreads_and(mbar_wait_bounded(&bars[0], 0u, err))) {
       mbar_wait_bounded(&bars[0], 0u, nullptr);
@@ -532,7 +551,36 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     // -------- face normals and Fscale (n = g N_f / |g N_f|)
     for (int i = tid; i < EB * 4; i += NT) {
       const int e = i >> 2, f = i & 3;
-      *reinterpret_cast<float4*>(sFn + i * 4) = face_normal(sRec + e * REC, f);
+      const float4 fn = face_normal(sRec + e * REC, f);
+      *reinterpret_cast<float4*>(sFn + i * 4) = fn;
+      if constexpr (FACT) {
+        // penalty coefficients of the face, pen_p = A jp + B jvn and
+        // psi = C jp + D jvn with jp = [[p]]/2, jvn = [[v]].n/2 (Fscale folded
+        // in), and where the neighbour trace comes from: -1 outer boundary,
+        // >= 0 the neighbour's fields in this block, -2 the gathered traces
+        const float* gk = sRec + e * REC;
+        const float fs = fn.w, kap = gk[9], rinv = gk[10], ZM = gk[11], zP = gk[12 + f];
+        float4 co;
+        if (a.flux == 0) {
+          const float kc = 2.f / (ZM + zP);
+          co.x = fs * kap * kc;
+          co.y = -co.x * zP;
+          co.z = -fs * (ZM * rinv) * kc;
+          co.w = -co.z * zP;
+        } else {
+          co = make_float4(0.f, -fs * kap, -fs * rinv, 0.f);
+        }
+        sCo[i] = co;
+        const int4 nb = sNbr[e];
+        const int w = (f == 0) ? nb.x : (f == 1) ? nb.y : (f == 2) ? nb.z : nb.w;
+        int2 fi = make_int2(-1, 0);
+        if (w >= 0) {
+          const int le = (w >> kNbrShift) - k0;
+          fi.x = (le >= 0 && le < EB) ? le * Nf * Np : -2;
+          fi.y = ((w & 3) * 6 + ((w >> 2) & 7)) * Nfp;
+        }
+        sFi[i] = fi;
+      }
     }
     // -------- volume inputs (node index fastest: conflict-free reads of q)
     for (int i = tid; i < EB * Np; i += NT) {
@@ -566,6 +614,39 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     __syncthreads();  // sFn ready
 
     // -------- traces and penalty terms at the 4 Nfp face nodes (face node fastest)
+    if constexpr (FACT) {
+      constexpr int XS = NFN * EBP;
+      for (int i = tid; i < EB * NFN; i += NT) {
+        const int fm = i % NFN, e = i / NFN;
+        const int f = fm / Nfp, m = fm - f * Nfp;
+        const int fi = e * 4 + f;
+        const int2 src = sFi[fi];
+        const float4 fn = *reinterpret_cast<const float4*>(sFn + fi * 4);
+        const float4 co = sCo[fi];
+        const int nM = sFtab[f * Nfp + m];
+        const float* qe = sQ + e * Nf * Np + nM;
+        const float pM = qe[0], vM0 = qe[Np], vM1 = qe[2 * Np], vM2 = qe[3 * Np];
+        float jp, jvn;
+        if (src.x == -1) {  // rigid wall: p+ = p-, v+ = v- - 2 (v-.n) n
+          jp = 0.f;
+          jvn = -(vM0 * fn.x + vM1 * fn.y + vM2 * fn.z);
+        } else {
+          float pP, vP0, vP1, vP2;
+          if (src.x >= 0) {
+            const float* qn = sQ + src.x + sPtab[src.y + m];
+            pP = qn[0]; vP0 = qn[Np]; vP1 = qn[2 * Np]; vP2 = qn[3 * Np];
+          } else {
+            const float* T = sT + fm * EBP + e;
+            pP = T[0]; vP0 = T[XS]; vP1 = T[2 * XS]; vP2 = T[3 * XS];
+          }
+          jp = 0.5f * (pP - pM);
+          jvn = 0.5f * ((vP0 - vM0) * fn.x + (vP1 - vM1) * fn.y + (vP2 - vM2) * fn.z);
+        }
+        float* X = sXs + fm * EBP + e;
+        X[0] = co.x * jp + co.y * jvn;
+        X[XS] = co.z * jp + co.w * jvn;
+      }
+    } else
     for (int i = tid; i < EB * NFN; i += NT) {
       const int fm = i % NFN, e = i / NFN;
       const int f = fm / Nfp, m = fm - f * Nfp;
@@ -670,14 +751,19 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     if (has_tile) {
       const float* A = sOps + i0;
       if constexpr (MODEL == 0) {
-        float G3[3][TN][4], R[TN][4], L[3][TN][4];
+        // L: LIFT of the three velocity penalties (split step) or, FACT, of
+        // psi face by face (L[f]; the velocity lift is sum_f n_f L[f])
+        constexpr int NL = FACT ? 4 : 3;
+        float G3[3][TN][4], R[TN][4], L[NL][TN][4];
 #pragma unroll
         for (int t = 0; t < TN; ++t)
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             R[t][v] = 0.f;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) G3[d][t][v] = L[d][t][v] = 0.f;
+            for (int d = 0; d < 3; ++d) G3[d][t][v] = 0.f;
+#pragma unroll
+            for (int d = 0; d < NL; ++d) L[d][t][v] = 0.f;
           }
 #pragma unroll 4
         for (int j = 0; j < Np; ++j) {
@@ -698,28 +784,60 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
             fma4(R[t], a2, x2);
           }
         }
-#pragma unroll 4
-        for (int c = 0; c < NFN; ++c) {
-          const float4 l = load_op<OPS_SMEM>(A + (3 * Np + c) * Mpad);
+        if constexpr (FACT) {
 #pragma unroll
-          for (int t = 0; t < TN; ++t) {
-            fma4(R[t], l, sXs[(0 * NFN + c) * EBP + e0 + t]);
-            fma4(L[0][t], l, sXs[(1 * NFN + c) * EBP + e0 + t]);
-            fma4(L[1][t], l, sXs[(2 * NFN + c) * EBP + e0 + t]);
-            fma4(L[2][t], l, sXs[(3 * NFN + c) * EBP + e0 + t]);
+          for (int f = 0; f < 4; ++f) {
+#pragma unroll 4
+            for (int m = 0; m < Nfp; ++m) {
+              const int c = f * Nfp + m;
+              const float4 l = load_op<OPS_SMEM>(A + (3 * Np + c) * Mpad);
+#pragma unroll
+              for (int t = 0; t < TN; ++t) {
+                fma4(R[t], l, sXs[c * EBP + e0 + t]);
+                fma4(L[f][t], l, sXs[(NFN + c) * EBP + e0 + t]);
+              }
+            }
+          }
+        } else {
+#pragma unroll 4
+          for (int c = 0; c < NFN; ++c) {
+            const float4 l = load_op<OPS_SMEM>(A + (3 * Np + c) * Mpad);
+#pragma unroll
+            for (int t = 0; t < TN; ++t) {
+              fma4(R[t], l, sXs[(0 * NFN + c) * EBP + e0 + t]);
+              fma4(L[0][t], l, sXs[(1 * NFN + c) * EBP + e0 + t]);
+              fma4(L[1][t], l, sXs[(2 * NFN + c) * EBP + e0 + t]);
+              fma4(L[2][t], l, sXs[(3 * NFN + c) * EBP + e0 + t]);
+            }
           }
         }
 #pragma unroll
         for (int t = 0; t < TN; ++t) {
           const float* gk = sRec + (e0 + t) * REC;
           const float rinv = gk[10];
+          float lv[3][4];
+          if constexpr (FACT) {
+            const float4* nf = reinterpret_cast<const float4*>(sFn) + (e0 + t) * 4;
+            const float4 n0 = nf[0], n1 = nf[1], n2 = nf[2], n3 = nf[3];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              lv[0][v] = n0.x * L[0][t][v] + n1.x * L[1][t][v] + n2.x * L[2][t][v] + n3.x * L[NL - 1][t][v];
+              lv[1][v] = n0.y * L[0][t][v] + n1.y * L[1][t][v] + n2.y * L[2][t][v] + n3.y * L[NL - 1][t][v];
+              lv[2][v] = n0.z * L[0][t][v] + n1.z * L[1][t][v] + n2.z * L[2][t][v] + n3.z * L[NL - 1][t][v];
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) lv[c][v] = L[c][t][v];
+          }
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             r[t][0][v] = R[t][v];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-              r[t][1 + c][v] = L[c][t][v] - rinv * (gk[3 * c] * G3[0][t][v] + gk[3 * c + 1] * G3[1][t][v] +
-                                                    gk[3 * c + 2] * G3[2][t][v]);
+              r[t][1 + c][v] = lv[c][v] - rinv * (gk[3 * c] * G3[0][t][v] + gk[3 * c + 1] * G3[1][t][v] +
+                                                  gk[3 * c + 2] * G3[2][t][v]);
           }
         }
       } else {

@@ -62,6 +62,7 @@ def test_rhs_parity_random_state(dg, model, N):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("model,N,flux,bc", [("acoustic", 3, "centered", None),
+                                              ("acoustic", 1, "centered", None),
                                               ("elastic", 3, "centered", None),
                                               ("elastic", 2, "upwind", "rigid"),
                                               ("elastic", 4, "centered", "rigid")])
