@@ -84,7 +84,7 @@ __device__ __forceinline__ void prefetch_tile_l2(const StepArgs& a, int ntile) {
 }
 
 // Layout shared by the front half, both GEMM designs and the library route:
-// X[tile][row][NE] (KX rows per element) and the operator blob
+// X[tile][row][NE] (the KX rows of XRows per element) and the operator blob
 // [3 Np + 4 Nfp][OPP] (row = input index, column = output node, OPP = Np
 // rounded up to 32, enough for every design's row tiles).
 template <int MODEL, int N>
@@ -92,8 +92,8 @@ struct SplitShape {
   using S = Sz<N>;
   static constexpr int Np = S::Np, NFN = S::NFN;
   static constexpr int Nf = MODEL == 0 ? 4 : 9;
-  static constexpr int NV = MODEL == 0 ? 4 : 12;       // X rows per volume index j
-  static constexpr int KX = NV * Np + Nf * NFN;        // X rows per element
+  static constexpr int NV = XRows<MODEL, N>::NV;      // X rows per volume index j
+  static constexpr int KX = XRows<MODEL, N>::KX;      // X rows per element
   static constexpr int NE = MODEL == 0 ? 64 : 32;      // elements per column tile
   static constexpr int OPP = (Np + 31) / 32 * 32;      // row pitch of the operator blob
   static constexpr size_t x_floats_per_tile = size_t(KX) * NE;
@@ -103,8 +103,8 @@ template <int MODEL, int N>
 struct GemmA {
   using S = Sz<N>;
   static constexpr int Nf = MODEL == 0 ? 4 : 9;
-  static constexpr int NV = MODEL == 0 ? 4 : 12;          // X rows per volume index j
-  static constexpr int KX = NV * S::Np + Nf * S::NFN;     // X rows per element
+  static constexpr int NV = XRows<MODEL, N>::NV;          // X rows per volume index j
+  static constexpr int KX = XRows<MODEL, N>::KX;          // X rows per element
   static constexpr int NE = MODEL == 0 ? 64 : 32;         // elements per column tile
   static constexpr int TN = MODEL == 0 ? 2 : 1;           // elements per thread tile
   static constexpr int RQ = MODEL == 0 ? 1 : 2;           // row quads per thread tile (4 or 8 rows)
@@ -115,9 +115,11 @@ struct GemmA {
   static constexpr int NT = (MT / (4 * RQ)) * (NE / TN);  // threads per CTA
   static constexpr int NVC = (S::Np + JC - 1) / JC;       // volume chunks
   static constexpr int NLC = (S::NFN + CC - 1) / CC;      // lift chunks
-  // per buffer: A rows (3 JC volume, CC lift) x MT, X rows (NV JC, Nf CC) x NE
+  // per buffer: A rows (3 JC volume, CC lift) x MT, X rows (NV JC volume;
+  // lift: 2 CC streams + 12 normal rows acoustic, Nf CC elastic) x NE
   static constexpr int nA = (3 * JC > CC ? 3 * JC : CC) * MT;
-  static constexpr int nB = (NV * JC > Nf * CC ? NV * JC : Nf * CC) * NE;
+  static constexpr int LB = MODEL == 0 ? 2 * CC + 12 : Nf * CC;
+  static constexpr int nB = (NV * JC > LB ? NV * JC : LB) * NE;
   static constexpr int NEP = NE + (TN == 2 ? 2 : 1);       // row stride of the staged RHS tile
   static constexpr int nOut = Nf * MT * NEP;              // RHS tile [Nf][MT][NEP], reuses the B buffers
   static constexpr int nBB = (2 * nB > nOut ? 2 * nB : nOut);
@@ -130,6 +132,7 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
   using S = Sz<N>;
   using SS = GemmA<MODEL, N>;
   constexpr int Np = S::Np, NFN = S::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NE, TN = SS::TN, RQ = SS::RQ;
+  constexpr int Nfp = S::Nfp, NXS = XRows<MODEL, N>::NXS, KXM = XRows<MODEL, N>::KXM;
   constexpr int RV = 4 * RQ;  // rows per thread
   constexpr int MT = SS::MT, MP2 = SplitShape<MODEL, N>::OPP, JC = SS::JC, CC = SS::CC, NT = SS::NT;
   constexpr int NVC = SS::NVC, NLC = SS::NLC, NCH = NVC + NLC;
@@ -171,10 +174,16 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
         const int q4 = i % (MT / 4), cc = i / (MT / 4);
         cp_async16(A + cc * MT + 4 * q4, OP + size_t(3 * Np + c0 + cc) * MP2 + row0 + 4 * q4);
       }
-      for (int i = tid; i < Nf * nc * (NE / 4); i += NT) {
+      for (int i = tid; i < NXS * nc * (NE / 4); i += NT) {
         const int q4 = i % (NE / 4), rr = i / (NE / 4);
         const int f = rr / nc, cc = rr - f * nc;
         cp_async16(B + (f * CC + cc) * NE + 4 * q4, X + size_t(NV * Np + f * NFN + c0 + cc) * NE + 4 * q4);
+      }
+      if constexpr (MODEL == 0) {  // the face normals, after the two streams
+        for (int i = tid; i < 12 * (NE / 4); i += NT) {
+          const int q4 = i % (NE / 4), r = i / (NE / 4);
+          cp_async16(B + (2 * CC + r) * NE + 4 * q4, X + size_t(KXM + r) * NE + 4 * q4);
+        }
       }
     }
     cp_async_commit();
@@ -188,6 +197,11 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
 
   constexpr int NACC = MODEL == 0 ? 7 : 12;  // acoustic G0..2, R, L0..2; elastic U00..U22, Rv0..2
   float acc[NACC][TN][RV];
+  float lf[TN][RV];  // acoustic: LIFT_f psi of the current face f
+#pragma unroll
+  for (int t = 0; t < TN; ++t)
+#pragma unroll
+    for (int v = 0; v < RV; ++v) lf[t][v] = 0.f;
 #pragma unroll
   for (int x = 0; x < NACC; ++x)
 #pragma unroll
@@ -265,27 +279,52 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
     } else {
       const int c0 = (c - NVC) * CC;
       const int nc = NFN - c0 < CC ? NFN - c0 : CC;
+      if constexpr (MODEL == 0) {
+        // P_p onto R; psi face by face onto lf, which joins the velocity
+        // accumulators L_c as n_f,c lf once face f is complete
+        int cc = 0;
+        while (cc < nc) {
+          const int f = (c0 + cc) / Nfp;
+          const int fe = (f + 1) * Nfp - c0;  // end of face f, chunk-relative
+          const int ce = fe < nc ? fe : nc;
 #pragma unroll 2
-      for (int cc = 0; cc < nc; ++cc) {
-        float4 l[RQ];
+          for (; cc < ce; ++cc) {
+            float4 l[RQ];
 #pragma unroll
-        for (int q = 0; q < RQ; ++q) l[q] = *reinterpret_cast<const float4*>(A + cc * MT + 4 * q);
-        if constexpr (MODEL == 0) {
-          float p0[TN], p1[TN], p2[TN], p3[TN];
-          VecT<TN>::load(B + (0 * CC + cc) * NE, p0);
-          VecT<TN>::load(B + (1 * CC + cc) * NE, p1);
-          VecT<TN>::load(B + (2 * CC + cc) * NE, p2);
-          VecT<TN>::load(B + (3 * CC + cc) * NE, p3);
+            for (int q = 0; q < RQ; ++q) l[q] = *reinterpret_cast<const float4*>(A + cc * MT + 4 * q);
+            float p0[TN], p1[TN];
+            VecT<TN>::load(B + (0 * CC + cc) * NE, p0);
+            VecT<TN>::load(B + (1 * CC + cc) * NE, p1);
 #pragma unroll
-          for (int t = 0; t < TN; ++t)
+            for (int t = 0; t < TN; ++t)
 #pragma unroll
-            for (int q = 0; q < RQ; ++q) {
-              fma4(&acc[3][t][4 * q], l[q], p0[t]);
-              fma4(&acc[4][t][4 * q], l[q], p1[t]);
-              fma4(&acc[5][t][4 * q], l[q], p2[t]);
-              fma4(&acc[6][t][4 * q], l[q], p3[t]);
+              for (int q = 0; q < RQ; ++q) {
+                fma4(&acc[3][t][4 * q], l[q], p0[t]);
+                fma4(&lf[t][4 * q], l[q], p1[t]);
+              }
+          }
+          if (cc == fe) {
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+              float nv[TN];
+              VecT<TN>::load(B + (2 * CC + 3 * f + x) * NE, nv);
+#pragma unroll
+              for (int t = 0; t < TN; ++t)
+#pragma unroll
+                for (int v = 0; v < RV; ++v) acc[4 + x][t][v] = fmaf(nv[t], lf[t][v], acc[4 + x][t][v]);
             }
-        } else {
+#pragma unroll
+            for (int t = 0; t < TN; ++t)
+#pragma unroll
+              for (int v = 0; v < RV; ++v) lf[t][v] = 0.f;
+          }
+        }
+      } else {
+#pragma unroll 2
+        for (int cc = 0; cc < nc; ++cc) {
+          float4 l[RQ];
+#pragma unroll
+          for (int q = 0; q < RQ; ++q) l[q] = *reinterpret_cast<const float4*>(A + cc * MT + 4 * q);
 #pragma unroll
           for (int t = 0; t < TN; ++t) {
 #pragma unroll
@@ -388,8 +427,8 @@ struct GemmB {
   using S = Sz<N>;
   static constexpr int Np = S::Np, NFN = S::NFN;
   static constexpr int Nf = MODEL == 0 ? 4 : 9;
-  static constexpr int NV = MODEL == 0 ? 4 : 12;          // X rows per volume index j
-  static constexpr int KX = NV * Np + Nf * NFN;           // X rows per element
+  static constexpr int NV = XRows<MODEL, N>::NV;          // X rows per volume index j
+  static constexpr int KX = XRows<MODEL, N>::KX;          // X rows per element
   static constexpr int NE = MODEL == 0 ? 64 : 32;         // elements per column tile
   static constexpr int TM = MODEL == 0 ? 8 : 4;           // rows per thread tile
   static constexpr int TE = (MODEL == 0 ? 4 : 2) / (NARROW ? 2 : 1);  // elements per thread tile
@@ -403,9 +442,11 @@ struct GemmB {
   static constexpr int NT = (MT / TM) * (NE / TE);        // threads per CTA
   static constexpr int NVC = (Np + KC - 1) / KC;          // volume chunks
   static constexpr int NLC = (NFN + KC - 1) / KC;         // lift chunks
-  static constexpr int NB = NV > Nf ? NV : Nf;            // X vectors of one chunk, at most
+  // X rows of one chunk: NV KC (volume); lift: 2 KC streams + 12 normal
+  // rows (acoustic), Nf KC (elastic)
+  static constexpr int LB = MODEL == 0 ? 2 * KC + 12 : Nf * KC;
   static constexpr int nA = 3 * KC * MT;                  // operator rows of one stage
-  static constexpr int nB = NB * KC * NE;                 // X rows of one stage
+  static constexpr int nB = (NV * KC > LB ? NV * KC : LB) * NE;  // X rows of one stage
   static constexpr int NEP = NE + 1;                      // row stride of the staged RHS field
   static constexpr int nOut = MT * NEP;
   static constexpr int nStage = nA + nB;
@@ -419,6 +460,7 @@ template <int MODEL, int N, bool NARROW = false>
 __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, const int ntile) {
   using SS = GemmB<MODEL, N, NARROW>;
   constexpr int Np = SS::Np, NFN = SS::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NE, TM = SS::TM, TE = SS::TE;
+  constexpr int Nfp = Sz<N>::Nfp, NXS = XRows<MODEL, N>::NXS, KXM = XRows<MODEL, N>::KXM;
   constexpr int MT = SS::MT, MP2 = SplitShape<MODEL, N>::OPP, KC = SS::KC, NT = SS::NT, NS = SS::NS;
   constexpr int NVC = SS::NVC, NLC = SS::NLC, NCH = NVC + NLC;
   constexpr int REC = Rec<MODEL>::size;
@@ -461,10 +503,16 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
           const int q4 = i % (MT / 4), cc = i / (MT / 4);
           cp_async16(A + cc * MT + 4 * q4, OP + size_t(3 * Np + c0 + cc) * MP2 + row0 + 4 * q4);
         }
-        for (int i = tid; i < Nf * nc * (NE / 4); i += NT) {
+        for (int i = tid; i < NXS * nc * (NE / 4); i += NT) {
           const int q4 = i % (NE / 4), rr = i / (NE / 4);
           const int f = rr / nc, cc = rr - f * nc;
           cp_async16(B + (f * KC + cc) * NE + 4 * q4, X + size_t(NV * Np + f * NFN + c0 + cc) * NE + 4 * q4);
+        }
+        if constexpr (MODEL == 0) {  // the face normals, after the two streams
+          for (int i = tid; i < 12 * (NE / 4); i += NT) {
+            const int q4 = i % (NE / 4), r = i / (NE / 4);
+            cp_async16(B + (2 * KC + r) * NE + 4 * q4, X + size_t(KXM + r) * NE + 4 * q4);
+          }
         }
       }
     }
@@ -484,6 +532,11 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
     for (int t = 0; t < TE; ++t)
 #pragma unroll
       for (int v = 0; v < TM; ++v) acc[x][t][v] = 0.f;
+  float lf[MODEL == 0 ? TE : 1][TM];  // acoustic: LIFT_f psi of the current face f
+#pragma unroll
+  for (int t = 0; t < (MODEL == 0 ? TE : 1); ++t)
+#pragma unroll
+    for (int v = 0; v < TM; ++v) lf[t][v] = 0.f;
 
   auto ldA = [&](const float* p, float* o) {  // TM consecutive rows, as float4s
 #pragma unroll
@@ -605,25 +658,51 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
         }
       }
     } else {
-      const int nc = NFN - (c - NVC) * KC < KC ? NFN - (c - NVC) * KC : KC;
+      const int c0 = (c - NVC) * KC;
+      const int nc = NFN - c0 < KC ? NFN - c0 : KC;
+      if constexpr (MODEL == 0) {
+        // P_p onto r_p; psi face by face onto lf, which joins the velocity
+        // components as n_f,c lf once face f is complete
+        int cc = 0;
+        while (cc < nc) {
+          const int f = (c0 + cc) / Nfp;
+          const int fe = (f + 1) * Nfp - c0;  // end of face f, chunk-relative
+          const int ce = fe < nc ? fe : nc;
 #pragma unroll 2
-      for (int cc = 0; cc < nc; ++cc) {
-        float l[TM];
-        ldA(A + cc * MT, l);
-        if constexpr (MODEL == 0) {
-          float pp[4][TE];
+          for (; cc < ce; ++cc) {
+            float l[TM], pp[TE], ps[TE];
+            ldA(A + cc * MT, l);
+            ldB(B + (0 * KC + cc) * NE, pp);
+            ldB(B + (1 * KC + cc) * NE, ps);
 #pragma unroll
-          for (int f = 0; f < 4; ++f) ldB(B + (f * KC + cc) * NE, pp[f]);
+            for (int t = 0; t < TE; ++t)
 #pragma unroll
-          for (int t = 0; t < TE; ++t)
+              for (int v = 0; v < TM; ++v) {
+                acc[3][t][v] = fmaf(l[v], pp[t], acc[3][t][v]);
+                lf[t][v] = fmaf(l[v], ps[t], lf[t][v]);
+              }
+          }
+          if (cc == fe) {
 #pragma unroll
-            for (int v = 0; v < TM; ++v) {
-              acc[3][t][v] = fmaf(l[v], pp[0][t], acc[3][t][v]);
-              acc[0][t][v] = fmaf(l[v], pp[1][t], acc[0][t][v]);
-              acc[1][t][v] = fmaf(l[v], pp[2][t], acc[1][t][v]);
-              acc[2][t][v] = fmaf(l[v], pp[3][t], acc[2][t][v]);
+            for (int x = 0; x < 3; ++x) {
+              float nv[TE];
+              ldB(B + (2 * KC + 3 * f + x) * NE, nv);
+#pragma unroll
+              for (int t = 0; t < TE; ++t)
+#pragma unroll
+                for (int v = 0; v < TM; ++v) acc[x][t][v] = fmaf(nv[t], lf[t][v], acc[x][t][v]);
             }
-        } else {
+#pragma unroll
+            for (int t = 0; t < TE; ++t)
+#pragma unroll
+              for (int v = 0; v < TM; ++v) lf[t][v] = 0.f;
+          }
+        }
+      } else {
+#pragma unroll 2
+        for (int cc = 0; cc < nc; ++cc) {
+          float l[TM];
+          ldA(A + cc * MT, l);
 #pragma unroll
           for (int f = 0; f < 9; ++f) {
             float pf[TE];

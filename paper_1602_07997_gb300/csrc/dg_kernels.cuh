@@ -54,6 +54,18 @@ struct Sz {
   static constexpr int KD = 3 * Np + NFN;
 };
 
+// Rows per element of the FP32 split step's GEMM input X: NV volume inputs
+// per node, NXS surface streams per face node (acoustic: the pressure penalty
+// and psi, the magnitude of the velocity penalty psi n_f; elastic: the 9
+// penalties), then, acoustic, the 4 x 3 face-normal components.
+template <int MODEL, int N>
+struct XRows {
+  static constexpr int NV = MODEL == 0 ? 4 : 12;
+  static constexpr int NXS = MODEL == 0 ? 2 : 9;
+  static constexpr int KXM = NV * Sz<N>::Np + NXS * Sz<N>::NFN;
+  static constexpr int KX = KXM + (MODEL == 0 ? 12 : 0);
+};
+
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -154,7 +166,7 @@ __device__ __forceinline__ constexpr float ref_normal(int f, int i) {
 // ---------------------------------------------------------------- smem plan
 constexpr int round4(int x) { return (x + 3) & ~3; }
 
-// FACT (acoustic, fused step): the surface inputs are two streams per face
+// FACT (acoustic, FP32 paths): the surface inputs are two streams per face
 // node, the pressure penalty and the magnitude psi of the velocity penalty
 // psi n_f (n_f is constant on a face of a straight-sided tetrahedron), plus
 // per-face penalty coefficients and neighbour sources.
@@ -418,7 +430,7 @@ struct SolveBatch {
 template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT, int XP, class Prov>
 __device__ __forceinline__ void step_body(const Prov& prov) {
   using S = Sz<N>;
-  constexpr bool FACT = MODEL == 0 && SPLIT == 0;
+  constexpr bool FACT = MODEL == 0 && XP == 0;  // every acoustic path but the tensor-core one
   using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM, FACT>;
   constexpr int Np = S::Np, Nfp = S::Nfp, NFN = S::NFN, Mpad = S::Mpad, RT = S::RT;
   constexpr int Nf = P::Nf, REC = P::REC, EBP = P::EBP;
@@ -724,17 +736,25 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       continue;
     } else if constexpr (SPLIT > 0) {
       // split step, front half: the GEMM inputs leave for the global buffer
-      // X[tile][row][NE] (row: volume inputs, then penalties; NE = SPLIT
-      // elements per tile), 4 elements per float4
-      constexpr int NV = MODEL == 0 ? 4 : 12;
-      constexpr int KX = NV * Np + Nf * NFN;
+      // X[tile][row][NE] (rows of XRows; NE = SPLIT elements per tile), 4
+      // elements per float4
+      using XR = XRows<MODEL, N>;
+      constexpr int NV = XR::NV, KXM = XR::KXM, KX = XR::KX;
       constexpr int NE = SPLIT;
       static_assert(NE % 4 == 0 && (NE % EB == 0 || EB % NE == 0), "element blocks inside column tiles");
+      static_assert(KXM == NV * Np + (FACT ? 2 : Nf) * NFN, "surface streams of the split layout");
       for (int i = tid; i < KX * (EB / 4); i += NT) {
         const int e4 = i % (EB / 4), row = i / (EB / 4);
-        const float* src = row < NV * Np ? sXv + row * EBP : sXs + (row - NV * Np) * EBP;
+        float4 v;
+        if (row < KXM) {
+          const float* src = row < NV * Np ? sXv + row * EBP : sXs + (row - NV * Np) * EBP;
+          v = make_float4(src[4 * e4], src[4 * e4 + 1], src[4 * e4 + 2], src[4 * e4 + 3]);
+        } else {  // normal component c of face f
+          const int f = (row - KXM) / 3, c = (row - KXM) % 3;
+          const float* nf = sFn + (16 * e4 + f) * 4 + c;
+          v = make_float4(nf[0], nf[16], nf[32], nf[48]);
+        }
         const int k = k0 + 4 * e4;
-        const float4 v = make_float4(src[4 * e4], src[4 * e4 + 1], src[4 * e4 + 2], src[4 * e4 + 3]);
         *reinterpret_cast<float4*>(a.xg + (size_t(k / NE) * KX + row) * NE + (k % NE)) = v;
       }
       continue;

@@ -35,12 +35,12 @@ KernelCfg make_front_cfg() {
   constexpr int EB = front_eb<MODEL, N>();
   constexpr int NT = threads_for<N, EB, 1>();
   using SS = SplitShape<MODEL, N>;
-  static_assert(Plan<MODEL, N, EB, false, false>::bytes <= 227 * 1024, "shared memory budget");
+  static_assert(Plan<MODEL, N, EB, false, false, MODEL == 0>::bytes <= 227 * 1024, "shared memory budget");
   KernelCfg c{};
   c.EB = EB;
   c.TN = 1;
   c.NT = NT;
-  c.smem = Plan<MODEL, N, EB, false, false>::bytes;
+  c.smem = Plan<MODEL, N, EB, false, false, MODEL == 0>::bytes;
   c.fn = dg_step_kernel<MODEL, N, EB, 1, NT, false, false, SS::NE, 0>;
   c.split = 0;
   c.gemm_ne = SS::NE;
@@ -61,7 +61,7 @@ const KernelCfg* front_cfg(int model, int N) {
   return model == 0 ? &ac[N - 1] : &el[N - 1];
 }
 
-int library_products(int model) { return model == 0 ? 7 : 18; }
+int library_products(int model) { return model == 0 ? 8 : 18; }
 
 // One strided-batched GEMM per (product, input block): for every column tile t
 //   Y_p[t NE + e][i] (+)= sum_r ops2[(arow + r) MP2 + i] X_t[brow + r][e],
@@ -79,7 +79,7 @@ int library_gemms(void* cublas, int model, int N, const StepArgs& a, float* Y, s
   cublasHandle_t h = static_cast<cublasHandle_t>(cublas);
   const KernelCfg* f = front_cfg(model, N);
   if (!f) return -1;
-  const int Np = (N + 1) * (N + 2) * (N + 3) / 6, NFN = 2 * (N + 1) * (N + 2);
+  const int Nfp = (N + 1) * (N + 2) / 2, Np = (N + 1) * (N + 2) * (N + 3) / 6, NFN = 4 * Nfp;
   const int NE = f->gemm_ne, KX = f->gemm_kx, MP2 = f->gemm_mp2;
   const int nt = (a.K + NE - 1) / NE;
   auto Yp = [&](int p) { return Y + size_t(p) * yprod; };
@@ -88,10 +88,11 @@ int library_gemms(void* cublas, int model, int N, const StepArgs& a, float* Y, s
     if (s == CUBLAS_STATUS_SUCCESS) s = gemm(h, Np, NE, KX, MP2, nt, a.ops2, a.xg, Yp(p), arow, brow, klen, beta);
   };
   if (model == 0) {
-    // X rows: p, w_0..2 (Np each), P_p, P_v0..2 (4 Nfp each)
+    // X rows: p, w_0..2 (Np each), P_p, psi (4 Nfp each), face normals
     for (int d = 0; d < 3; ++d) G(d, d * Np, 0, Np, 0.f);              // G_d = D_d p
     G(3, 0, Np, 3 * Np + NFN, 0.f);                                    // R = [D_r D_s D_t LIFT] [w; P_p]
-    for (int c = 0; c < 3; ++c) G(4 + c, 3 * Np, 4 * Np + (1 + c) * NFN, NFN, 0.f);  // L_c = LIFT P_vc
+    for (int f = 0; f < 4; ++f)                                        // L_f = LIFT_f psi_f
+      G(4 + f, 3 * Np + f * Nfp, 4 * Np + NFN + f * Nfp, Nfp, 0.f);
   } else {
     // X rows: v_0..2, s_cd (3 + 3c + d) (Np each), P_0..8 (4 Nfp each)
     for (int c = 0; c < 3; ++c)
@@ -121,11 +122,20 @@ __global__ void __launch_bounds__(256) library_epilogue_kernel(const StepArgs a,
     auto y = [&](int p) { return __ldg(Y + size_t(p) * yprod + t); };
     float r[Nf];
     if constexpr (MODEL == 0) {
+      // velocity lift sum_f n_f L_f, the normals from the X rows of element k
+      using XR = XRows<MODEL, N>;
+      constexpr int NE = SplitShape<MODEL, N>::NE;
+      const float* nk = a.xg + (size_t(k / NE) * XR::KX + XR::KXM) * NE + k % NE;
       const float rinv = __ldg(gk + 10);
       const float G0 = y(0), G1 = y(1), G2 = y(2);
       r[0] = y(3);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) r[1 + c] = y(4 + c) - rinv * (g[3 * c] * G0 + g[3 * c + 1] * G1 + g[3 * c + 2] * G2);
+      for (int c = 0; c < 3; ++c) {
+        float lv = 0.f;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) lv = fmaf(__ldg(nk + (3 * f + c) * NE), y(4 + f), lv);
+        r[1 + c] = lv - rinv * (g[3 * c] * G0 + g[3 * c + 1] * G1 + g[3 * c + 2] * G2);
+      }
     } else {
       const float lam = __ldg(gk + 9), mu = __ldg(gk + 10);
       float U[9];
