@@ -33,7 +33,8 @@ Readings where the paper is silent (see the design notes):
   r^{-1}, r^{-2} is supplied.
 * point sources: amp(t_m) M_k^{-1} l(x_s) is added to r_p (acoustic) or
   amp(t_m) (d_i / rho_k) M_k^{-1} l(x_s) to r_{v_i} (elastic), in the tet
-  whose smallest barycentric of x_s is largest.
+  whose smallest barycentric of x_s is largest; several sources add their
+  terms.
 """
 
 import numpy as np
@@ -146,7 +147,7 @@ class Solver:
             self.cmax = self.cp
         self.Nf = nfields(model)
         self.K = K
-        self.src = None
+        self.srcs = []  # (element, M_k^{-1} l(x_s), amplitudes, direction) per source
 
     # ------------------------------------------------------------------
     def node_coords(self):
@@ -195,8 +196,7 @@ class Solver:
         q = np.asarray(q, dtype=np.float64)
         E = slice(None) if elems is None else np.asarray(elems, dtype=np.int64)
         r = self._rhs_acoustic(q, E) if self.model == ACOUSTIC else self._rhs_elastic(q, E)
-        if self.src is not None and step is not None:
-            k, b, amp, d = self.src
+        for k, b, amp, d in (self.srcs if step is not None else []):
             a = amp[step] if step < len(amp) else 0.0
             rows = [k] if elems is None else list(np.nonzero(np.asarray(elems) == k)[0])
             for row in rows:
@@ -307,6 +307,12 @@ class Solver:
         return out
 
     def set_source(self, xs, amp, direction=(0.0, 0.0, 1.0)):
+        """One point source at xs (replacing any others); returns its tet."""
+        self.srcs = []
+        return self.add_source(xs, amp, direction)
+
+    def add_source(self, xs, amp, direction=(0.0, 0.0, 1.0)):
+        """One more point source at xs; returns its tet."""
         m, R = self.mesh, self.ref
         xs = np.asarray(xs, dtype=np.float64)
         x1 = m.verts[m.tets[:, 0]]
@@ -316,7 +322,7 @@ class Solver:
         k = int(np.argmax(lam.min(axis=1)))
         ell = R.lag.eval(rst[k][None, :])[0]
         b = R.Minv @ ell / m.J[k]
-        self.src = (k, b, np.asarray(amp, dtype=np.float64), np.asarray(direction, dtype=np.float64))
+        self.srcs.append((k, b, np.asarray(amp, dtype=np.float64), np.asarray(direction, dtype=np.float64)))
         return k
 
     # ------------------------------------------------------------------

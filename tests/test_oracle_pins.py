@@ -305,7 +305,7 @@ def test_source_is_point_evaluation():
     S = Solver("acoustic", 3, verts, tets, np.ones((tets.shape[0], 2)))
     xs = np.array([0.41, 0.57, 0.33])
     k = S.set_source(xs, amp=[1.0])
-    _, b, _, _ = S.src
+    _, b, _, _ = S.srcs[0]
     rng = np.random.default_rng(0)
     # u = a polynomial of degree 3 in physical coordinates
     cfs = rng.normal(size=4)
@@ -316,6 +316,37 @@ def test_source_is_point_evaluation():
     # and the tet really contains x_s
     lam = np.linalg.solve(np.vstack([verts[tets[k]].T, np.ones(4)]), np.append(xs, 1.0))
     assert lam.min() > 0
+
+
+@pytest.mark.parametrize("model,N", [("acoustic", 2), ("elastic", 1)])
+def test_sources_superpose(model, N):
+    """The scheme is linear in the forcing: from a zero state, sources A and B
+    together give the sum of the runs with A alone and with B alone; two
+    sources at one point act as one source with the summed amplitudes."""
+    verts, tets = _small_mesh(2)
+    K = tets.shape[0]
+    coeffs = (W.acoustic_coefficients(K, 1, 3, seed=5) if model == "acoustic"
+              else W.elastic_two_layer(verts, tets, seed=5))
+    xa, xb = np.array([0.31, 0.42, 0.27]), np.array([0.7, 0.25, 0.6])
+    t = np.arange(12)
+    amp_a, amp_b = np.sin(0.7 * t + 0.2), np.cos(0.3 * t) * (t < 9)
+    dirb = (0.6, 0.0, 0.8)
+
+    def run(srcs):
+        S = Solver(model, N, verts, tets, coeffs)
+        for xs, amp, d in srcs:
+            S.add_source(xs, amp, d)
+        st = AB3Stepper(S, np.zeros((K, S.Nf, S.ref.Np)), S.suggest_dt())
+        st.step(12)
+        return st.q
+
+    qa = run([(xa, amp_a, (0, 0, 1))])
+    qb = run([(xb, amp_b, dirb)])
+    qab = run([(xa, amp_a, (0, 0, 1)), (xb, amp_b, dirb)])
+    assert np.abs(qa).max() > 0 and np.abs(qb).max() > 0
+    assert np.abs(qab - (qa + qb)).max() <= 1e-12 * np.abs(qab).max()
+    q2 = run([(xa, amp_a, (0, 0, 1)), (xa, 2.5 * amp_a, (0, 0, 1))])
+    assert np.abs(q2 - 3.5 * qa).max() <= 1e-12 * np.abs(q2).max()
 
 
 # ---------------------------------------------------------------- time stepping
