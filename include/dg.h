@@ -235,8 +235,17 @@ int dg_node_coords(const dg_handle *h, double *xyz);
 /* Point source at xs: at step m the RHS gets amp[m] M_k^{-1} l(xs) on p
  * (acoustic) or amp[m] (dir_i / rho_k) M_k^{-1} l(xs) on v_i (elastic), in
  * the tet whose smallest barycentric coordinate of xs is largest; amp[m] = 0
- * for m >= namp.  amp == NULL removes the source.  Host pointers.           */
+ * for m >= namp.  dg_set_source replaces every source of the handle by this
+ * one (amp == NULL removes them all); dg_add_source adds one more (several
+ * sources add their terms; DG_EINVAL past DG_MAX_SOURCES, or with amp ==
+ * NULL).  Both copy their inputs (host pointers) and apply to dg_step,
+ * dg_rhs and dg_rhs_host_noalloc with every strategy and precision; the
+ * first source is added inside the step kernels, the others by one small
+ * kernel after them.                                                        */
+enum { DG_MAX_SOURCES = 64 };
 int dg_set_source(dg_handle *h, const double xs[3], const double dir[3],
+                  const double *amp, int64_t namp);
+int dg_add_source(dg_handle *h, const double xs[3], const double dir[3],
                   const double *amp, int64_t namp);
 
 /* dt = cfl * min_{k,f} 1 / (c_max,k Fscale_{k,f} ((N+1)(N+2)/2 + 2)), host
@@ -279,11 +288,14 @@ typedef struct {
                             the batched FP32 kernels, else DG_EINVAL);
                             block_elems and stream are ignored */
   const float *q0;       /* host [K][Nf][Np]; NULL = zero state              */
-  const double *src_xyz; /* NULL = no source                                  */
-  const double *src_dir; /* elastic only; NULL = (0,0,1)                      */
-  const double *src_amp; /* amplitudes per step                               */
+  const double *src_xyz; /* [nsrc][3]; NULL = no source                       */
+  const double *src_dir; /* elastic only: [nsrc][3]; NULL = (0,0,1) for all   */
+  const double *src_amp; /* [nsrc][src_namp] amplitudes per step              */
   int64_t src_namp;
   int nsteps;
+  int nsrc;              /* point sources in the arrays above (as
+                            dg_add_source); 0 = one when src_xyz is set,
+                            at most DG_MAX_SOURCES                          */
 } dg_request;
 
 /* hbm_budget_bytes = 0: no budget beyond the free device memory.           */

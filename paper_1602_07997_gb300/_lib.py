@@ -23,7 +23,7 @@ STRATEGY = {"fused": 0, "library": 1, "plain": 2}
 
 # every symbol that include/dg.h declares
 EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", "dg_rhs", "dg_step",
-           "dg_set_dt", "dg_sync", "dg_autotune", "dg_kernel_info", "dg_set_variant", "dg_node_coords", "dg_set_source", "dg_suggest_dt",
+           "dg_set_dt", "dg_sync", "dg_autotune", "dg_kernel_info", "dg_set_variant", "dg_node_coords", "dg_set_source", "dg_add_source", "dg_suggest_dt",
            "dg_reference_element", "dg_last_error", "dg_server_create", "dg_submit", "dg_poll",
            "dg_cancel", "dg_server_stats", "dg_server_destroy", "dg_rhs_host_noalloc", "dg_set_receivers",
            "dg_get_traces")
@@ -49,7 +49,8 @@ class Request(C.Structure):
     _fields_ = [("mesh", C.POINTER(Mesh)), ("coeffs", C.POINTER(C.c_double)), ("N", C.c_int),
                 ("model", C.c_int), ("opts", Opts), ("q0", C.POINTER(C.c_float)),
                 ("src_xyz", C.POINTER(C.c_double)), ("src_dir", C.POINTER(C.c_double)),
-                ("src_amp", C.POINTER(C.c_double)), ("src_namp", C.c_int64), ("nsteps", C.c_int)]
+                ("src_amp", C.POINTER(C.c_double)), ("src_namp", C.c_int64), ("nsteps", C.c_int),
+                ("nsrc", C.c_int)]
 
 
 _lib = None
@@ -81,6 +82,7 @@ def lib():
         "dg_set_variant": (i32, [vp, i32]),
         "dg_node_coords": (i32, [vp, P(dbl)]),
         "dg_set_source": (i32, [vp, P(dbl), P(dbl), P(dbl), i64]),
+        "dg_add_source": (i32, [vp, P(dbl), P(dbl), P(dbl), i64]),
         "dg_suggest_dt": (i32, [P(Mesh), P(dbl), i32, i32, dbl, P(dbl)]),
         "dg_reference_element": (i32, [i32, P(dbl), P(dbl), P(dbl), P(dbl), P(dbl), P(i32)]),
         "dg_last_error": (C.c_char_p, []),
@@ -285,6 +287,13 @@ class Solver:
         a = np.ascontiguousarray(amp, dtype=np.float64)
         check(lib().dg_set_source(self.h, _dptr(xs), _dptr(d), _dptr(a), a.size))
 
+    def add_source(self, xs, amp, direction=(0.0, 0.0, 1.0)):
+        """One more point source (several sources add their terms)."""
+        xs = np.ascontiguousarray(xs, dtype=np.float64)
+        d = np.ascontiguousarray(direction, dtype=np.float64)
+        a = np.ascontiguousarray(amp, dtype=np.float64)
+        check(lib().dg_add_source(self.h, _dptr(xs), _dptr(d), _dptr(a), a.size))
+
 
     def set_receivers(self, xyz):
         """Receivers at xyz [nrec][3]: the fields there are recorded after every step."""
@@ -337,10 +346,16 @@ class Server:
             r.q0 = q0a.ctypes.data_as(C.POINTER(C.c_float))
         xs = d = a = None
         if source is not None and amp is not None:
-            xs = np.ascontiguousarray(source, dtype=np.float64)
-            d = np.ascontiguousarray(direction, dtype=np.float64)
-            a = np.ascontiguousarray(amp, dtype=np.float64)
-            r.src_xyz, r.src_dir, r.src_amp, r.src_namp = _dptr(xs), _dptr(d), _dptr(a), a.size
+            # one source: source [3], amp [namp]; several: source [n][3],
+            # amp [n][namp], direction [3] (for all) or [n][3]
+            xs = np.ascontiguousarray(np.atleast_2d(source), dtype=np.float64)
+            ns = xs.shape[0]
+            a = np.ascontiguousarray(np.atleast_2d(amp), dtype=np.float64)
+            if a.shape[0] != ns:
+                raise ValueError("amp needs one row per source")
+            d = np.ascontiguousarray(np.broadcast_to(np.asarray(direction, dtype=np.float64), (ns, 3)))
+            r.src_xyz, r.src_dir, r.src_amp, r.src_namp = _dptr(xs), _dptr(d), _dptr(a), a.shape[1]
+            r.nsrc = ns
         t = C.c_uint64()
         check(lib().dg_submit(self.s, C.byref(r), C.byref(t)))
         self._meta[t.value] = (K, Nf, Np)

@@ -250,6 +250,7 @@ Handle::~Handle() {
   if (d_r0) cudaFree(d_r0);
   if (d_recel) cudaFree(d_recel);
   if (d_traces) cudaFree(d_traces);
+  if (d_xs) cudaFree(d_xs);
   if (cublas) cublasDestroy(static_cast<cublasHandle_t>(cublas));
 }
 
@@ -296,12 +297,14 @@ int Handle::ensure_strategy() {
 int Handle::launch(dgk::StepArgs a) {
   if (opts.strategy == DG_STRATEGY_FUSED) {
     DG_CUDA(dgk::launch_step(cfg, a, stream));
+    DG_CUDA(dgk::launch_xsrc(xs, step, Nf * Np, a, stream));
     return DG_OK;
   }
   int rc = ensure_strategy();
   if (rc) return rc;
   if (opts.strategy == DG_STRATEGY_PLAIN) {
     DG_CUDA(dgk::launch_plain_step(model, N, a, d_r0, stream));
+    DG_CUDA(dgk::launch_xsrc(xs, step, Nf * Np, a, stream));
     return DG_OK;
   }
   // library route: front half, GEMMs, epilogue
@@ -313,6 +316,7 @@ int Handle::launch(dgk::StepArgs a) {
   const int st = dgk::library_gemms(cublas, model, N, a, d_liby, libyprod);
   if (st != 0) return fail(DG_ECUDA, "cuBLAS SGEMM failed with status " + std::to_string(st));
   DG_CUDA(dgk::launch_library_epilogue(model, N, a, d_liby, libyprod, stream));
+  DG_CUDA(dgk::launch_xsrc(xs, step, Nf * Np, a, stream));
   return DG_OK;
 }
 
@@ -497,6 +501,71 @@ int64_t Handle::locate(const double x[3], double rst_out[3]) const {
   return (best < 0 || bestmin < -1e-9) ? -1 : best;
 }
 
+int Handle::source_vector(const double x[3], const double dir[3], int64_t* elem, std::vector<float>& vec) const {
+  if (!x) return fail(DG_EINVAL, "source position is NULL");
+  double brst[3] = {0, 0, 0};
+  const int64_t best = locate(x, brst);
+  if (best < 0) return fail(DG_EINVAL, "source position outside the mesh");
+  // M_k^{-1} l(x_s) = V psi(x_s) / J_k  (V orthonormal Vandermonde)
+  std::vector<double> psi(ref.Np), b(ref.Np, 0.0);
+  ref.basis(brst[0], brst[1], brst[2], psi.data());
+  for (int i = 0; i < ref.Np; ++i) {
+    double acc = 0;
+    for (int m = 0; m < ref.Np; ++m) acc += ref.V[size_t(i) * ref.Np + m] * psi[m];
+    b[i] = acc / hm.J[best];
+  }
+  vec.assign(size_t(Nf) * ref.Np, 0.0f);
+  if (model == DG_ACOUSTIC) {
+    for (int i = 0; i < ref.Np; ++i) vec[i] = float(b[i]);
+  } else {
+    double dd[3] = {0, 0, 1};
+    if (dir) std::memcpy(dd, dir, sizeof(dd));
+    const double rho = coeffs[3 * best + 2];
+    for (int c = 0; c < 3; ++c)
+      for (int i = 0; i < ref.Np; ++i) vec[size_t(c) * ref.Np + i] = float(dd[c] / rho * b[i]);
+  }
+  *elem = best;
+  return DG_OK;
+}
+
+// Device copy of the sources beyond the first: elements, vectors and the
+// amplitudes zero-padded to the longest history, in one allocation.
+int Handle::upload_xsrc() {
+  const int n = int(xs_elem.size());
+  int namp = 0;
+  for (const auto& v : xs_amp) namp = std::max(namp, int(v.size()));
+  if (d_xs) {
+    DG_CUDA(cudaStreamSynchronize(stream));
+    cudaFree(d_xs);
+    d_xs = nullptr;
+  }
+  xs = dgk::XSrc{};
+  if (n == 0) return DG_OK;
+  const size_t NfNp = size_t(Nf) * Np;
+  const size_t o_vec = (size_t(n) * 4 + 15) & ~size_t(15);
+  const size_t o_amp = o_vec + size_t(n) * NfNp * 4;
+  const size_t bytes = o_amp + size_t(n) * namp * 4;
+  if (cudaMalloc(&d_xs, bytes) != cudaSuccess) {
+    d_xs = nullptr;
+    return fail(DG_ENOMEM, "source tables");
+  }
+  std::vector<unsigned char> host(bytes, 0);
+  std::memcpy(host.data(), xs_elem.data(), size_t(n) * 4);
+  std::memcpy(host.data() + o_vec, xs_vec.data(), size_t(n) * NfNp * 4);
+  float* ha = reinterpret_cast<float*>(host.data() + o_amp);
+  for (int s = 0; s < n; ++s)
+    for (size_t m = 0; m < xs_amp[s].size(); ++m) ha[size_t(s) * namp + m] = float(xs_amp[s][m]);
+  DG_CUDA(cudaMemcpyAsync(d_xs, host.data(), bytes, cudaMemcpyHostToDevice, stream));
+  DG_CUDA(cudaStreamSynchronize(stream));
+  auto* base = static_cast<unsigned char*>(d_xs);
+  xs.n = n;
+  xs.namp = namp;
+  xs.elem = reinterpret_cast<const int*>(base);
+  xs.vec = reinterpret_cast<const float*>(base + o_vec);
+  xs.amp = reinterpret_cast<const float*>(base + o_amp);
+  return DG_OK;
+}
+
 }  // namespace dg
 
 using dg::fail;
@@ -633,36 +702,38 @@ int dg_set_source(dg_handle* h, const double xs[3], const double dir[3], const d
   if (!amp || namp <= 0) {
     h->src_elem = -1;
     h->src_amp.clear();
-    return DG_OK;
+    h->xs_elem.clear();
+    h->xs_vec.clear();
+    h->xs_amp.clear();
+    return h->upload_xsrc();
   }
-  if (!xs) return fail(DG_EINVAL, "source position is NULL");
-  double brst[3] = {0, 0, 0};
-  const int64_t best = h->locate(xs, brst);
-  if (best < 0) return fail(DG_EINVAL, "source position outside the mesh");
-  // M_k^{-1} l(x_s) = V psi(x_s) / J_k  (V orthonormal Vandermonde)
-  const auto& R = h->ref;
-  std::vector<double> psi(R.Np), b(R.Np, 0.0);
-  R.basis(brst[0], brst[1], brst[2], psi.data());
-  for (int i = 0; i < R.Np; ++i) {
-    double acc = 0;
-    for (int m = 0; m < R.Np; ++m) acc += R.V[size_t(i) * R.Np + m] * psi[m];
-    b[i] = acc / h->hm.J[best];
-  }
-  std::vector<float> vec(size_t(h->Nf) * R.Np, 0.0f);
-  if (h->model == DG_ACOUSTIC) {
-    for (int i = 0; i < R.Np; ++i) vec[i] = float(b[i]);
-  } else {
-    double dd[3] = {0, 0, 1};
-    if (dir) std::memcpy(dd, dir, sizeof(dd));
-    double rho = h->coeffs[3 * best + 2];
-    for (int c = 0; c < 3; ++c)
-      for (int i = 0; i < R.Np; ++i) vec[size_t(c) * R.Np + i] = float(dd[c] / rho * b[i]);
-  }
+  int64_t best = -1;
+  std::vector<float> vec;
+  const int rc = h->source_vector(xs, dir, &best, vec);
+  if (rc) return rc;
   DG_CUDA(cudaMemcpyAsync(h->d_src, vec.data(), vec.size() * 4, cudaMemcpyHostToDevice, h->stream));
   DG_CUDA(cudaStreamSynchronize(h->stream));
   h->src_elem = int(best);
   h->src_amp.assign(amp, amp + namp);
-  return DG_OK;
+  h->xs_elem.clear();
+  h->xs_vec.clear();
+  h->xs_amp.clear();
+  return h->upload_xsrc();
+}
+
+int dg_add_source(dg_handle* h, const double xs[3], const double dir[3], const double* amp, int64_t namp) {
+  if (!h) return fail(DG_EINVAL, "NULL handle");
+  if (!amp || namp <= 0) return fail(DG_EINVAL, "a source needs amplitudes");
+  if (h->src_elem < 0) return dg_set_source(h, xs, dir, amp, namp);
+  if (int(h->xs_elem.size()) + 1 >= DG_MAX_SOURCES) return fail(DG_EINVAL, "too many sources");
+  int64_t best = -1;
+  std::vector<float> vec;
+  const int rc = h->source_vector(xs, dir, &best, vec);
+  if (rc) return rc;
+  h->xs_elem.push_back(int(best));
+  h->xs_vec.insert(h->xs_vec.end(), vec.begin(), vec.end());
+  h->xs_amp.emplace_back(amp, amp + namp);
+  return h->upload_xsrc();
 }
 
 // Gauss-Jordan inverse with partial pivoting of an n x n row-major matrix.

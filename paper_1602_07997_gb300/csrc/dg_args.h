@@ -22,6 +22,16 @@ struct Rec {
 // face and rotation one of the 6 face-node permutations.
 constexpr int kNbrShift = 5;
 
+// Point sources of a solve beyond the first (which the step kernels add):
+// source s adds amp[s][m] vec[s] to r^m of element elem[s] at step m.
+struct XSrc {
+  int n;                 // number of sources (0: none)
+  int namp;              // amplitudes per source (zero past a source's own count)
+  const int* elem;       // [n]
+  const float* vec;      // [n][Nf Np]
+  const float* amp;      // [n][namp]
+};
+
 struct StepArgs {
   const float* q;        // q^m   [Kpad][Nf][Np]
   float* qn;             // q^m+1 [Kpad][Nf][Np]            (mode 0)
@@ -66,6 +76,7 @@ struct SolveDev {
   int r1slot;            // r[r1slot] holds r^{m-1}
   int steps_left;        // the advance kernel stops moving a solve at 0
   float* xg;             // split step: the solve's GEMM input buffer
+  XSrc xs;               // its point sources beyond the first
 };
 
 struct BatchArgs {
@@ -116,6 +127,12 @@ cudaError_t launch_step(const KernelCfg* cfg, const StepArgs& args, cudaStream_t
 cudaError_t launch_step_batched(const KernelCfg* cfg, const BatchArgs& args, cudaStream_t stream);
 // Advance the device-side step state of the solves (one thread per solve).
 cudaError_t launch_advance(SolveDev* solves, int nsolves, cudaStream_t stream);
+// Point sources beyond the first, after the step's kernels (same stream):
+// mode 0 adds a v to r^m (a.r2) and dt a1 a v to q^{m+1} (a.qn) -- the AB3
+// update is linear in r^m; mode 1 adds a v to a.rout (a = amp[s][m]).
+cudaError_t launch_xsrc(const XSrc& xs, long long step, int NfNp, const StepArgs& a, cudaStream_t stream);
+// The same for every solve of a batch with sources, before its advance.
+cudaError_t launch_xsrc_batched(const BatchArgs& b, int NfNp, cudaStream_t stream);
 // Receiver sample: out[r][f] = sum_i vec[r][i] q[elem[r]][f][i].
 cudaError_t launch_sample(const float* q, const int* elem, const float* vec, int nrec, int Nf, int Np, float* out,
                           cudaStream_t stream);

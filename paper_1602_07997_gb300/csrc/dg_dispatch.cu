@@ -104,6 +104,50 @@ cudaError_t launch_sample(const float* q, const int* elem, const float* vec, int
   return cudaGetLastError();
 }
 
+// Thread i owns field-node i of every source element, so sources that share
+// an element add up in order without races.
+__device__ __forceinline__ void add_xsrc(const XSrc& xs, long long m, int NfNp, int mode, float dta1, float* qn,
+                                         float* r, float* rout) {
+  for (int i = threadIdx.x; i < NfNp; i += blockDim.x)
+    for (int s = 0; s < xs.n; ++s) {
+      const float am = (m >= 0 && m < xs.namp) ? xs.amp[size_t(s) * xs.namp + m] : 0.f;
+      const float v = am * xs.vec[size_t(s) * NfNp + i];
+      const size_t idx = size_t(xs.elem[s]) * NfNp + i;
+      if (mode == 0) {
+        r[idx] += v;
+        qn[idx] = fmaf(dta1, v, qn[idx]);
+      } else {
+        rout[idx] += v;
+      }
+    }
+}
+
+__global__ void __launch_bounds__(256) xsrc_kernel(const XSrc xs, long long m, int NfNp, int mode, float dta1,
+                                                   float* qn, float* r, float* rout) {
+  add_xsrc(xs, m, NfNp, mode, dta1, qn, r, rout);
+}
+
+// one CTA per solve of the batch, with the buffers and step of its step kernel
+__global__ void __launch_bounds__(256) xsrc_batched_kernel(const BatchArgs b, int NfNp) {
+  const SolveDev& d = b.solves[blockIdx.x];
+  if (d.xs.n == 0 || d.steps_left <= 0) return;
+  StepArgs a;
+  solve_args(b, d, a);
+  add_xsrc(d.xs, d.step, NfNp, 0, a.dt * a.a1, a.qn, a.r2, nullptr);
+}
+
+cudaError_t launch_xsrc(const XSrc& xs, long long step, int NfNp, const StepArgs& a, cudaStream_t stream) {
+  if (xs.n <= 0) return cudaSuccess;
+  xsrc_kernel<<<1, 256, 0, stream>>>(xs, step, NfNp, a.mode, a.dt * a.a1, a.qn, a.r2, a.rout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xsrc_batched(const BatchArgs& b, int NfNp, cudaStream_t stream) {
+  if (b.nsolves <= 0) return cudaSuccess;
+  xsrc_batched_kernel<<<b.nsolves, 256, 0, stream>>>(b, NfNp);
+  return cudaGetLastError();
+}
+
 __global__ void advance_kernel(SolveDev* s, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || s[i].steps_left <= 0) return;

@@ -433,9 +433,16 @@ struct GemmB {
   static constexpr int TM = MODEL == 0 ? 8 : 4;           // rows per thread tile
   static constexpr int TE = (MODEL == 0 ? 4 : 2) / (NARROW ? 2 : 1);  // elements per thread tile
   // output rows per CTA (MT / TM even, so that the CTA is whole warps)
-  static constexpr int MT =
+  static constexpr int MT_WIDE =
       MODEL == 0 ? (N <= 2 ? 16 : N == 3 ? 32 : N == 4 ? 48 : N == 5 ? 64 : N == 6 ? 96 : N == 7 ? 128 : 96)
                  : (N <= 3 ? 24 : N == 4 ? 40 : N == 5 ? 56 : N == 6 ? 48 : N == 7 ? 64 : 56);
+  // narrow: a warp is one row group of 32 elements, so any multiple of TM
+  // rows makes whole warps; row tiles close to Np / ceil(Np / MT_WIDE) waste
+  // fewer padding rows (acoustic Np = 84, 120 at N = 6, 7; at N = 8 two tiles
+  // of 88 rows measured 2 % slower than two of 96)
+  static constexpr int MT_NARROW = MODEL == 0 ? (N == 6 ? 88 : N == 7 ? 120 : MT_WIDE)
+                                              : (N == 6 ? 44 : N == 7 ? 60 : MT_WIDE);
+  static constexpr int MT = NARROW ? MT_NARROW : MT_WIDE;
   static constexpr int MP2 = (Np + MT - 1) / MT * MT;     // padded rows of the split operator blob
   static constexpr int KC = 16;                           // K chunk (volume indices or face nodes)
   static constexpr int NS = 3;                            // cp.async stages
@@ -520,7 +527,8 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
   };
 
   // thread tile: rows il..il+TM-1 of the CTA's slice, elements e0..e0+TE-1;
-  // the lanes of a warp span the elements (two row groups per warp)
+  // the lanes of a warp span the elements (NE / TE of them: two row groups
+  // per warp at TE = 4, one otherwise)
   constexpr int CT = NE / TE;
   const int ct = tid % CT, rt = tid / CT;
   const int il = TM * rt, e0 = TE * ct;

@@ -66,6 +66,13 @@ struct Handle {
   int have = 0;    // stored RHS levels (0, 1, 2)
   int src_elem = -1;
   std::vector<double> src_amp;
+  // point sources beyond the first (added after the step kernels): host
+  // copies, one device allocation and its view
+  std::vector<int> xs_elem;
+  std::vector<float> xs_vec;                // [n][Nf Np]
+  std::vector<std::vector<double>> xs_amp;  // amplitudes of each source
+  void* d_xs = nullptr;
+  dgk::XSrc xs{};
   // receivers: element and interpolation vector per receiver (device), traces
   int nrec = 0;
   int* d_recel = nullptr;
@@ -78,6 +85,9 @@ struct Handle {
   // element whose smallest barycentric coordinate of x is largest, and the
   // reference coordinates of x in it; -1 if x is outside the mesh
   int64_t locate(const double x[3], double rst[3]) const;
+  // element and RHS vector [Nf][Np] of a point source at x (dg_set_source)
+  int source_vector(const double x[3], const double dir[3], int64_t* elem, std::vector<float>& vec) const;
+  int upload_xsrc();
   int ensure_split(const dgk::KernelCfg* c);
   int ensure_strategy();
   // one step (a.mode 0) or RHS (mode 1) with the handle's strategy

@@ -193,14 +193,15 @@ struct Plan {
   static constexpr int oT1 = round4(oT0 + nT);
   static constexpr int oOps = round4(oT1 + nT);
   static constexpr int oFn = round4(oOps + nOps);          // [EB][4] float4: n, Fscale
-  static constexpr int oCo = oFn + EB * 16;                // [EB][4] float4: penalty coefficients (FACT)
+  static constexpr int oNt = oFn + EB * 16;                // [4 x 3][EBP]: normals, element fastest (FACT)
+  static constexpr int oCo = round4(oNt + (FACT ? 12 * EBP : 0));  // [EB][4] float4: penalty coefficients (FACT)
   static constexpr int oFi = oCo + (FACT ? EB * 16 : 0);   // [EB][4] int2: neighbour source (FACT)
   static constexpr int oFtab = oFi + (FACT ? EB * 8 : 0);  // int [10][Nfp]
   static constexpr int oPtab = oFtab + 10 * S::Nfp;        // int [4][6][Nfp]: neighbour node (FACT)
   static constexpr int oBar = round4(oPtab + (FACT ? 24 * S::Nfp : 0));
   static constexpr int nFloats = oBar + 8;                 // 3 mbarriers
   static constexpr size_t bytes = size_t(nFloats) * 4;
-  static_assert(nXvol >= nQ, "the RHS of a block is staged in the volume-input buffer");
+  static_assert(nXvol >= Nf * S::Np * EBP, "the RHS of a block is staged in the volume-input buffer");
 };
 
 // Split step for the tensor cores: the front half leaves its GEMM inputs as
@@ -448,6 +449,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
   const int mode = prov.mode();
   float* sFn = smem + P::oFn;
   int* sFtab = reinterpret_cast<int*>(smem + P::oFtab);
+  float* sNt = smem + P::oNt;
   float4* sCo = reinterpret_cast<float4*>(smem + P::oCo);
   int2* sFi = reinterpret_cast<int2*>(smem + P::oFi);
   int* sPtab = reinterpret_cast<int*>(smem + P::oPtab);
@@ -566,6 +568,9 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       const float4 fn = face_normal(sRec + e * REC, f);
       *reinterpret_cast<float4*>(sFn + i * 4) = fn;
       if constexpr (FACT) {
+        sNt[(3 * f + 0) * EBP + e] = fn.x;
+        sNt[(3 * f + 1) * EBP + e] = fn.y;
+        sNt[(3 * f + 2) * EBP + e] = fn.z;
         // penalty coefficients of the face, pen_p = A jp + B jvn and
         // psi = C jp + D jvn with jp = [[p]]/2, jvn = [[v]].n/2 (Fscale folded
         // in), and where the neighbour trace comes from: -1 outer boundary,
@@ -837,14 +842,17 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
           const float rinv = gk[10];
           float lv[3][4];
           if constexpr (FACT) {
-            const float4* nf = reinterpret_cast<const float4*>(sFn) + (e0 + t) * 4;
-            const float4 n0 = nf[0], n1 = nf[1], n2 = nf[2], n3 = nf[3];
+            float nf[4][3];  // face normals of the element, element fastest in shared memory
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              lv[0][v] = n0.x * L[0][t][v] + n1.x * L[1][t][v] + n2.x * L[2][t][v] + n3.x * L[NL - 1][t][v];
-              lv[1][v] = n0.y * L[0][t][v] + n1.y * L[1][t][v] + n2.y * L[2][t][v] + n3.y * L[NL - 1][t][v];
-              lv[2][v] = n0.z * L[0][t][v] + n1.z * L[1][t][v] + n2.z * L[2][t][v] + n3.z * L[NL - 1][t][v];
-            }
+            for (int f = 0; f < 4; ++f)
+#pragma unroll
+              for (int c = 0; c < 3; ++c) nf[f][c] = sNt[(3 * f + c) * EBP + e0 + t];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+              for (int v = 0; v < 4; ++v)
+                lv[c][v] = nf[0][c] * L[0][t][v] + nf[1][c] * L[1][t][v] + nf[2][c] * L[2][t][v] +
+                           nf[3][c] * L[NL - 1][t][v];
           } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c)
@@ -960,7 +968,8 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     }
 
     // -------- AB3 update: the block's RHS goes to the (now free) volume-input
-    // buffer as [EB][Nf][Np]; one flat, vectorised pass then updates the block
+    // buffer as [Nf Np][EBP] (element fastest: the tile stores are free of
+    // bank conflicts); one flat pass over [EB][Nf][Np] then updates the block
     __syncthreads();  // every tile has finished reading the GEMM inputs
     float* sRhs = sXv;
     if (has_tile) {
@@ -970,8 +979,25 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
         for (int v = 0; v < 4; ++v)
           if (i0 + v < Np)
 #pragma unroll
-            for (int c = 0; c < Nf; ++c) sRhs[(e0 + t) * Nf * Np + c * Np + i0 + v] = r[t][c][v];
+            for (int c = 0; c < Nf; ++c) sRhs[(c * Np + i0 + v) * EBP + e0 + t] = r[t][c][v];
     }
+    // the 4 RHS values of float4 i of the block's [EB][Nf][Np] fields
+    auto rhs4 = [&](int i) {
+      constexpr int NQ = Nf * Np;
+      float o[4];
+      if constexpr (NQ % 4 == 0) {
+        const int e = (4 * i) / NQ, r0 = 4 * i - e * NQ;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o[u] = sRhs[(r0 + u) * EBP + e];
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int l = 4 * i + u, e = l / NQ;
+          o[u] = sRhs[(l - e * NQ) * EBP + e];
+        }
+      }
+      return make_float4(o[0], o[1], o[2], o[3]);
+    };
     bool okr = true;
     if constexpr (R_SMEM) okr = mbar_wait_bounded(&bars[2], uint32_t(it & 1), err);  // history landed
     if (!__syncthreads_and(okr)) {
@@ -983,7 +1009,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       // q^{m+1} replaces r^{m-1} and r^m replaces r^{m-2} in sR, then both are bulk-stored
       for (int i = tid; i < P::nQ / 4; i += NT) {
         const float4 q4 = reinterpret_cast<const float4*>(sQ)[i];
-        const float4 r4 = reinterpret_cast<const float4*>(sRhs)[i];
+        const float4 r4 = rhs4(i);
         float4* h1 = reinterpret_cast<float4*>(sR) + i;
         float4* h2 = reinterpret_cast<float4*>(sR + P::nQ) + i;
         const float4 p1 = *h1, p2 = *h2;
@@ -1023,7 +1049,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
           const int i = i0 + u * NT;
           if (i < P::nQ / 4) {
             const float4 q4 = reinterpret_cast<const float4*>(sQ)[i];
-            const float4 r4 = reinterpret_cast<const float4*>(sRhs)[i];
+            const float4 r4 = rhs4(i);
             gqn[i] = make_float4(fmaf(dt, a1 * r4.x + a2 * p1[u].x + a3 * p2[u].x, q4.x),
                                  fmaf(dt, a1 * r4.y + a2 * p1[u].y + a3 * p2[u].y, q4.y),
                                  fmaf(dt, a1 * r4.z + a2 * p1[u].z + a3 * p2[u].z, q4.z),

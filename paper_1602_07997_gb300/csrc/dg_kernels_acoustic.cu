@@ -21,21 +21,21 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_cfg<0, 3, 16, true, true>(), make_cfg<0, 3, 32, true, true>(),
                                  make_cfg<0, 3, 16, true, true, 1, 128>(), make_cfg<0, 3, 8, true, true>(),
                                  make_cfg<0, 3, 32, true, true, 1, 256>(), make_cfg<0, 3, 32, true, true, 1, 512>()};
-  static const KernelCfg v4[] = {make_cfg<0, 4, 8, true, true, 1, 256>(), make_cfg<0, 4, 4, true, true>(),
+  static const KernelCfg v4[] = {make_cfg<0, 4, 12, true, true, 1, 256>(), make_cfg<0, 4, 4, true, true>(),
                                  make_cfg<0, 4, 8, true, true, 2>(), make_cfg<0, 4, 8, true, true>(),
                                  make_cfg<0, 4, 8, true, true, 1, 128>(), make_cfg<0, 4, 16, true, true, 1, 256>(),
-                                 make_cfg<0, 4, 12, true, true>(), make_cfg<0, 4, 12, true, true, 1, 256>()};
+                                 make_cfg<0, 4, 12, true, true>(), make_cfg<0, 4, 8, true, true, 1, 256>()};
   static const KernelCfg v5[] = {make_split_cfg<0, 5, 8, 2, 256>(), make_cfg<0, 5, 8, false, true, 2>(),
                                  make_cfg<0, 5, 4, true, true>(), make_cfg<0, 5, 12, false, true, 2>(),
                                  make_split_cfg<0, 5, 8>(), make_cfg<0, 5, 8, false, true>(),
                                  make_split_cfg<0, 5, 4, 2>(), make_split_cfg<0, 5, 8, 2>(),
                                  make_split_cfg<0, 5, 8, 2, 384>(), make_split_cfg<0, 5, 8, 2, 512>()};
-  static const KernelCfg v6[] = {make_split_cfg<0, 6, 8, 1, 384>(), make_cfg<0, 6, 4, false, true>(),
+  static const KernelCfg v6[] = {make_split_cfg<0, 6, 8, 3, 384>(), make_cfg<0, 6, 4, false, true>(),
                                  make_cfg<0, 6, 8, false, true, 2>(), make_cfg<0, 6, 4, false, true, 2>(),
                                  make_cfg<0, 6, 8, false, true>(), make_split_cfg<0, 6, 4>(),
                                  make_split_cfg<0, 6, 8, 2>(), make_split_cfg<0, 6, 8, 3>(),
                                  make_split_cfg<0, 6, 4, 2>(), make_split_cfg<0, 6, 8>(),
-                                 make_split_cfg<0, 6, 8, 1, 512>(), make_split_cfg<0, 6, 8, 3, 384>()};
+                                 make_split_cfg<0, 6, 8, 1, 512>(), make_split_cfg<0, 6, 8, 1, 384>()};
   static const KernelCfg v7[] = {make_split_cfg<0, 7, 8, 3, 512>(), make_cfg<0, 7, 4, false, true, 2>(),
                                  make_cfg<0, 7, 8, false, true, 2>(), make_cfg<0, 7, 4, false, true, 4>(),
                                  make_split_cfg<0, 7, 8>(), make_split_cfg<0, 7, 4>(),

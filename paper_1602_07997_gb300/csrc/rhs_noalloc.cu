@@ -68,6 +68,8 @@ extern "C" int dg_rhs_host_noalloc(dg_handle* h, float* r_out) {
   a.rout = scratch;
   e = dgk::launch_step(cfg, a, h->stream);
   if (e != cudaSuccess) return dg::cuda_fail(e, "launch");
+  e = dgk::launch_xsrc(h->xs, h->step, h->Nf * h->Np, a, h->stream);  // sources beyond the first
+  if (e != cudaSuccess) return dg::cuda_fail(e, "launch");
   e = cudaMemcpyAsync(r_out, scratch, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return dg::cuda_fail(e, "copy to host");
   e = cudaStreamSynchronize(h->stream);

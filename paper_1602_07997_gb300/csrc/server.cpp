@@ -55,6 +55,9 @@ struct Request {
   dg_opts opts{};
   bool has_src = false;
   double xs[3] = {0, 0, 0}, dir[3] = {0, 0, 1};
+  // sources beyond the first: positions [n][3], directions [n][3], amplitudes [n][namp]
+  std::vector<double> ex_xyz, ex_dir, ex_amp;
+  int64_t ex_namp = 0;
   double t_submit = 0, t_done = 0;
   int status = kQueued;
   bool cancel = false;
@@ -81,6 +84,7 @@ struct Group {
   int* d_tile_solve = nullptr;
   int capacity = 0, block_capacity = 0, tile_capacity = 0;
   int total_blocks = 0, total_tiles = 0;
+  bool has_xs = false;  // a member has sources beyond the first
 };
 
 }  // namespace
@@ -201,6 +205,8 @@ bool Server::admit_one(std::shared_ptr<Request> r) {
   }
   if (rc == DG_OK && !r->q0.empty()) rc = dg_set_state(h, r->q0.data(), nullptr, nullptr, 0, 0);
   if (rc == DG_OK && r->has_src) rc = dg_set_source(h, r->xs, r->dir, r->amp.data(), int64_t(r->amp.size()));
+  for (size_t s = 0; rc == DG_OK && s < r->ex_xyz.size() / 3; ++s)
+    rc = dg_add_source(h, &r->ex_xyz[3 * s], &r->ex_dir[3 * s], &r->ex_amp[s * r->ex_namp], r->ex_namp);
   auto a = std::make_unique<Active>();
   if (rc == DG_OK && h->src_elem >= 0) {
     std::vector<float> af(r->amp.begin(), r->amp.end());
@@ -307,6 +313,7 @@ int Server::rebuild() {
         return fail(DG_ENOMEM, "server tables");
     }
     std::vector<dgk::SolveDev> sd(n);
+    g.has_xs = false;
     std::vector<int> bs(n + 1, 0), ts(n + 1, 0);
     std::vector<int> bsolve, tsolve;
     for (int i = 0; i < n; ++i) {
@@ -334,6 +341,8 @@ int Server::rebuild() {
       d.r1slot = h->r1slot;
       d.steps_left = a->steps_left;
       d.xg = h->d_x;
+      d.xs = h->xs;
+      g.has_xs = g.has_xs || h->xs.n > 0;
       bs[i + 1] = bs[i] + int((h->K + g.cfg->EB - 1) / g.cfg->EB);
       bsolve.insert(bsolve.end(), size_t(bs[i + 1] - bs[i]), i);
       ts[i + 1] = ts[i] + (g.cfg->split ? g.cfg->gemm_mtiles * int((h->K + g.cfg->gemm_ne - 1) / g.cfg->gemm_ne) : 0);
@@ -389,6 +398,8 @@ int Server::rebuild() {
     if (n == 0) continue;
     dgk::BatchArgs b = batch_args(g, d_err);
     if (e == cudaSuccess) e = dgk::launch_step_batched(g.cfg, b, stream);
+    if (e == cudaSuccess && g.has_xs)
+      e = dgk::launch_xsrc_batched(b, dg::num_fields(g.model) * dg::num_nodes(g.N), stream);
   }
   for (auto& kv : groups) {
     Group& g = kv.second;
@@ -565,6 +576,7 @@ int dg_submit(dg_server* s, const dg_request* req, uint64_t* ticket) {
   if (req->N < 1 || req->N > 8) return fail(DG_EINVAL, "polynomial degree N must be in 1..8");
   if (req->model != DG_ACOUSTIC && req->model != DG_ELASTIC) return fail(DG_EINVAL, "unknown model");
   if (req->nsteps < 0) return fail(DG_EINVAL, "negative step count");
+  if (req->nsrc < 0 || req->nsrc > DG_MAX_SOURCES) return fail(DG_EINVAL, "source count outside 0..DG_MAX_SOURCES");
   if (!(req->opts.dt > 0)) return fail(DG_EINVAL, "dt must be positive");
   if (req->opts.precision != DG_FP32 || req->opts.strategy != DG_STRATEGY_FUSED)
     return fail(DG_EINVAL, "served solves run the batched FP32 fused kernels: precision must be DG_FP32 and "
@@ -582,10 +594,19 @@ int dg_submit(dg_server* s, const dg_request* req, uint64_t* ticket) {
   r->opts = req->opts;
   if (req->q0) r->q0.assign(req->q0, req->q0 + size_t(m->ntets) * dg::num_fields(req->model) * dg::num_nodes(req->N));
   if (req->src_xyz && req->src_amp && req->src_namp > 0) {
+    const int ns = req->nsrc > 0 ? req->nsrc : 1;
     r->has_src = true;
     std::memcpy(r->xs, req->src_xyz, sizeof(r->xs));
     if (req->src_dir) std::memcpy(r->dir, req->src_dir, sizeof(r->dir));
     r->amp.assign(req->src_amp, req->src_amp + req->src_namp);
+    if (ns > 1) {
+      r->ex_xyz.assign(req->src_xyz + 3, req->src_xyz + 3 * size_t(ns));
+      if (req->src_dir) r->ex_dir.assign(req->src_dir + 3, req->src_dir + 3 * size_t(ns));
+      else
+        for (int s = 1; s < ns; ++s) r->ex_dir.insert(r->ex_dir.end(), {0.0, 0.0, 1.0});
+      r->ex_amp.assign(req->src_amp + req->src_namp, req->src_amp + size_t(ns) * req->src_namp);
+      r->ex_namp = req->src_namp;
+    }
   }
   r->t_submit = dg::now_s();
   {
