@@ -540,7 +540,7 @@ def run(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
-        cpu = cpu_baseline(model, Ns=(2, 4), steps=1)
+        cpu = cpu_baseline(model, Ns=(2, 4), steps=6)  # about 10 s of oracle work
 
     served = None
     if rank == 0 and not args.no_serve:
