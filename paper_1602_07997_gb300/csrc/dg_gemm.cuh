@@ -115,6 +115,7 @@ struct GemmA {
   static constexpr int NT = (MT / (4 * RQ)) * (NE / TN);  // threads per CTA
   static constexpr int NVC = (S::Np + JC - 1) / JC;       // volume chunks
   static constexpr int NLC = (S::NFN + CC - 1) / CC;      // lift chunks
+  static constexpr int MINB = 1;                          // resident CTAs the registers are sized for
   // per buffer: A rows (3 JC volume, CC lift) x MT, X rows (NV JC volume;
   // lift: 2 CC streams + 12 normal rows acoustic, Nf CC elastic) x NE
   static constexpr int nA = (3 * JC > CC ? 3 * JC : CC) * MT;
@@ -422,7 +423,9 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
 }
 
 // NARROW: elements per thread halved (fewer registers, two CTAs per SM).
-template <int MODEL, int N, bool NARROW = false>
+// SMALL (narrow only): short row tiles that divide Np (almost) exactly and
+// registers sized for two resident CTAs per SM.
+template <int MODEL, int N, bool NARROW = false, bool SMALL = false>
 struct GemmB {
   using S = Sz<N>;
   static constexpr int Np = S::Np, NFN = S::NFN;
@@ -442,7 +445,11 @@ struct GemmB {
   // of 88 rows measured 2 % slower than two of 96)
   static constexpr int MT_NARROW = MODEL == 0 ? (N == 6 ? 88 : N == 7 ? 120 : MT_WIDE)
                                               : (N == 6 ? 44 : N == 7 ? 60 : MT_WIDE);
-  static constexpr int MT = NARROW ? MT_NARROW : MT_WIDE;
+  // (acoustic N = 5: one tile of exactly Np = 56 rows, 13 % faster than
+  // 64-row tiles; three short tiles at N = 7, 8 re-read X and spill)
+  static constexpr int MT_SMALL = MODEL == 0 && N == 5 ? 56 : MT_NARROW;
+  static constexpr int MT = SMALL ? MT_SMALL : NARROW ? MT_NARROW : MT_WIDE;
+  static constexpr int MINB = SMALL ? 2 : 1;  // resident CTAs the registers are sized for
   static constexpr int MP2 = (Np + MT - 1) / MT * MT;     // padded rows of the split operator blob
   static constexpr int KC = 16;                           // K chunk (volume indices or face nodes)
   static constexpr int NS = 3;                            // cp.async stages
@@ -463,9 +470,9 @@ struct GemmB {
   static_assert(MT % 4 == 0 && NE % 4 == 0 && TM % 4 == 0, "16-byte copies and loads");
 };
 
-template <int MODEL, int N, bool NARROW = false>
+template <int MODEL, int N, bool NARROW = false, bool SMALL = false>
 __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, const int ntile) {
-  using SS = GemmB<MODEL, N, NARROW>;
+  using SS = GemmB<MODEL, N, NARROW, SMALL>;
   constexpr int Np = SS::Np, NFN = SS::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NE, TM = SS::TM, TE = SS::TE;
   constexpr int Nfp = Sz<N>::Nfp, NXS = XRows<MODEL, N>::NXS, KXM = XRows<MODEL, N>::KXM;
   constexpr int MT = SS::MT, MP2 = SplitShape<MODEL, N>::OPP, KC = SS::KC, NT = SS::NT, NS = SS::NS;
@@ -766,7 +773,8 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
 }
 
 // Design V of the FP32 GEMM (V = 2: design B, V = 3: design B with half the
-// elements per thread, otherwise design A).
+// elements per thread, V = 4: V = 3 with short row tiles and two CTAs per SM,
+// otherwise design A).
 template <int MODEL, int N, int V>
 struct GemmOf {
   using T = GemmA<MODEL, N>;
@@ -782,11 +790,19 @@ struct GemmOf<MODEL, N, 3> {
   using T = GemmB<MODEL, N, true>;
   __device__ static void body(const StepArgs& a, int mtile, int ntile) { gemm_b_body<MODEL, N, true>(a, mtile, ntile); }
 };
+template <int MODEL, int N>
+struct GemmOf<MODEL, N, 4> {
+  using T = GemmB<MODEL, N, true, true>;
+  __device__ static void body(const StepArgs& a, int mtile, int ntile) {
+    gemm_b_body<MODEL, N, true, true>(a, mtile, ntile);
+  }
+};
 
 // One solve: row tiles fastest, so that the CTAs that share a column tile of
 // X run together and read it from L2.  V selects the design (1 = A, 2 = B).
 template <int MODEL, int N, int V>
-__global__ void __launch_bounds__(GemmOf<MODEL, N, V>::T::NT) dg_split_gemm_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(GemmOf<MODEL, N, V>::T::NT, GemmOf<MODEL, N, V>::T::MINB)
+    dg_split_gemm_kernel(const StepArgs a) {
   using G = typename GemmOf<MODEL, N, V>::T;
   constexpr int MTILES = (Sz<N>::Np + G::MT - 1) / G::MT;
   GemmOf<MODEL, N, V>::body(a, int(blockIdx.x) % MTILES, int(blockIdx.x) / MTILES);
@@ -795,7 +811,8 @@ __global__ void __launch_bounds__(GemmOf<MODEL, N, V>::T::NT) dg_split_gemm_kern
 // Every solve of a batch: global tile -> (solve, local tile) through the
 // batch's tile tables, the solve's arguments from its device-side state.
 template <int MODEL, int N, int V>
-__global__ void __launch_bounds__(GemmOf<MODEL, N, V>::T::NT) dg_split_gemm_batched_kernel(const BatchArgs b) {
+__global__ void __launch_bounds__(GemmOf<MODEL, N, V>::T::NT, GemmOf<MODEL, N, V>::T::MINB)
+    dg_split_gemm_batched_kernel(const BatchArgs b) {
   using G = typename GemmOf<MODEL, N, V>::T;
   constexpr int MTILES = (Sz<N>::Np + G::MT - 1) / G::MT;
   const int so = __ldg(b.tile_solve + blockIdx.x);

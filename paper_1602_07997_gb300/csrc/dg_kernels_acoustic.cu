@@ -25,8 +25,9 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_cfg<0, 4, 8, true, true, 2>(), make_cfg<0, 4, 8, true, true>(),
                                  make_cfg<0, 4, 8, true, true, 1, 128>(), make_cfg<0, 4, 16, true, true, 1, 256>(),
                                  make_cfg<0, 4, 12, true, true>(), make_cfg<0, 4, 8, true, true, 1, 256>()};
-  static const KernelCfg v5[] = {make_split_cfg<0, 5, 8, 2, 256>(), make_cfg<0, 5, 8, false, true, 2>(),
-                                 make_cfg<0, 5, 4, true, true>(), make_cfg<0, 5, 12, false, true, 2>(),
+  static const KernelCfg v5[] = {make_split_cfg<0, 5, 8, 4, 384>(), make_split_cfg<0, 5, 8, 2, 256>(),
+                                 make_cfg<0, 5, 8, false, true, 2>(), make_cfg<0, 5, 4, true, true>(),
+                                 make_cfg<0, 5, 12, false, true, 2>(),
                                  make_split_cfg<0, 5, 8>(), make_cfg<0, 5, 8, false, true>(),
                                  make_split_cfg<0, 5, 4, 2>(), make_split_cfg<0, 5, 8, 2>(),
                                  make_split_cfg<0, 5, 8, 2, 384>(), make_split_cfg<0, 5, 8, 2, 512>()};
@@ -49,7 +50,7 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_split_cfg<0, 8, 4, 3>(), make_split_cfg<0, 8, 8, 3, 512>(),
                                  make_split_cfg<0, 8, 8, 3>(), make_split_cfg<0, 8, 8, 2, 512>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
-  static const int cnt[8] = {8, 8, 8, 8, 10, 12, 12, 12};
+  static const int cnt[8] = {8, 8, 8, 8, 11, 12, 12, 12};
   if (N < 1 || N > 8) return nullptr;
   *count = cnt[N - 1];
   return tab[N - 1];
