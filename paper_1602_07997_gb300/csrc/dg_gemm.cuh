@@ -581,6 +581,9 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
 
 #pragma unroll
   for (int s = 0; s < NS - 1; ++s) issue(s);
+  // row groups wholly past Np (padding of the last row tile) skip the
+  // products; they still copy and meet every barrier
+  const bool rows_live = row0 + il < Np;
   for (int c = 0; c < NCH; ++c) {
     issue(c + NS - 1);
     cp_async_wait_n<NS - 1>();  // chunk c has landed
@@ -588,7 +591,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
     const float* A = sA(c % NS) + il;
     const float* B = sB(c % NS) + e0;
     if (c < NVC) {
-      const int nj = Np - c * KC < KC ? Np - c * KC : KC;
+      const int nj = !rows_live ? 0 : Np - c * KC < KC ? Np - c * KC : KC;
 #pragma unroll 2
       for (int jj = 0; jj < nj; ++jj) {
         float ad[3][TM];
@@ -674,7 +677,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
       }
     } else {
       const int c0 = (c - NVC) * KC;
-      const int nc = NFN - c0 < KC ? NFN - c0 : KC;
+      const int nc = !rows_live ? 0 : NFN - c0 < KC ? NFN - c0 : KC;
       if constexpr (MODEL == 0) {
         // P_p onto r_p; psi face by face onto lf, which joins the velocity
         // components as n_f,c lf once face f is complete
