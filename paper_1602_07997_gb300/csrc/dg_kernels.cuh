@@ -170,18 +170,26 @@ constexpr int round4(int x) { return (x + 3) & ~3; }
 // node, the pressure penalty and the magnitude psi of the velocity penalty
 // psi n_f (n_f is constant on a face of a straight-sided tetrahedron), plus
 // per-face penalty coefficients and neighbour sources.
-template <int MODEL, int N, int EB, bool OPS_SMEM, bool R_SMEM, bool FACT = false>
+// DIRECT (FP32 split front half): the GEMM inputs go straight from the
+// compute loops to X in global memory, no staging buffers.
+template <int MODEL, int N, int EB, bool OPS_SMEM, bool R_SMEM, bool FACT = false, bool DIRECT = false>
 struct Plan {
   using S = Sz<N>;
   static constexpr int Nf = MODEL == 0 ? 4 : 9;
   static constexpr int REC = Rec<MODEL>::size;
   static constexpr int EBP = EB + 1;                      // odd row stride of element-fastest arrays
   static constexpr int nQ = EB * Nf * S::Np;
-  static constexpr int nStage = round4(nQ + EB * REC) + EB * 4;  // q, records, neighbour words
-  static constexpr int sQ = 0, sRec = nQ, sNbr = round4(nQ + EB * REC);
+  // element stride of q in the stage: DIRECT reads it element-fastest across
+  // lanes, so a stride that is a multiple of 8 words gets 4 words of padding
+  // (8 consecutive elements then start in 8 different 4-bank groups) and the
+  // elements are copied one by one
+  static constexpr int QPAD = (DIRECT && (Nf * S::Np) % 8 == 0) ? 4 : 0;
+  static constexpr int QS = Nf * S::Np + QPAD;
+  static constexpr int nStage = round4(EB * QS + EB * REC) + EB * 4;  // q, records, neighbour words
+  static constexpr int sQ = 0, sRec = EB * QS, sNbr = round4(EB * QS + EB * REC);
   static constexpr int nR = R_SMEM ? 2 * nQ : 0;
-  static constexpr int nXvol = (MODEL == 0 ? 4 : 12) * S::Np * EBP;
-  static constexpr int nXsur = (FACT ? 2 : Nf) * S::NFN * EBP;
+  static constexpr int nXvol = DIRECT ? 0 : (MODEL == 0 ? 4 : 12) * S::Np * EBP;
+  static constexpr int nXsur = DIRECT ? 0 : (FACT ? 2 : Nf) * S::NFN * EBP;
   static constexpr int nT = Nf * S::NFN * EBP;             // neighbour traces [Nf][4Nfp][EBP]
   static constexpr int nOps = OPS_SMEM ? S::KD * S::Mpad : 0;
   static constexpr int oStage0 = 0;
@@ -201,7 +209,7 @@ struct Plan {
   static constexpr int oBar = round4(oPtab + (FACT ? 24 * S::Nfp : 0));
   static constexpr int nFloats = oBar + 8;                 // 3 mbarriers
   static constexpr size_t bytes = size_t(nFloats) * 4;
-  static_assert(nXvol >= Nf * S::Np * EBP, "the RHS of a block is staged in the volume-input buffer");
+  static_assert(DIRECT || nXvol >= Nf * S::Np * EBP, "the RHS of a block is staged in the volume-input buffer");
 };
 
 // Split step for the tensor cores: the front half leaves its GEMM inputs as
@@ -432,7 +440,8 @@ template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, 
 __device__ __forceinline__ void step_body(const Prov& prov) {
   using S = Sz<N>;
   constexpr bool FACT = MODEL == 0 && XP == 0;  // every acoustic path but the tensor-core one
-  using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM, FACT>;
+  constexpr bool DIRECT = SPLIT > 0 && XP == 0;  // FP32 split front half: X written from the loops
+  using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM, FACT, DIRECT>;
   constexpr int Np = S::Np, Nfp = S::Nfp, NFN = S::NFN, Mpad = S::Mpad, RT = S::RT;
   constexpr int Nf = P::Nf, REC = P::REC, EBP = P::EBP;
   constexpr int NTILE = RT * (EB / TN);  // tiles of 4 output nodes x TN elements
@@ -453,6 +462,11 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
   float4* sCo = reinterpret_cast<float4*>(smem + P::oCo);
   int2* sFi = reinterpret_cast<int2*>(smem + P::oFi);
   int* sPtab = reinterpret_cast<int*>(smem + P::oPtab);
+  // DIRECT: address of GEMM input row `row` of element k in X[tile][row][NE]
+  constexpr int XNE = SPLIT > 0 ? SPLIT : 1;
+  auto xrow = [](const StepArgs& A, int row, int k) {
+    return A.xg + (size_t(k / XNE) * XRows<MODEL, N>::KX + row) * XNE + (k % XNE);
+  };
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P::oBar);
 
   const int tid = threadIdx.x;
@@ -468,7 +482,12 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     const int k0 = lb * EB;
     const uint32_t bo = (OPS_SMEM && with_ops) ? uint32_t(S::KD * Mpad * 4) : 0u;
     mbar_arrive_expect_tx(&bars[s], kStageBytes + bo);
-    tma_bulk_g2s(st + P::sQ, a.q + size_t(k0) * Nf * Np, kQBytes, &bars[s]);
+    if constexpr (P::QPAD == 0) {
+      tma_bulk_g2s(st + P::sQ, a.q + size_t(k0) * Nf * Np, kQBytes, &bars[s]);
+    } else {
+      for (int e = 0; e < EB; ++e)
+        tma_bulk_g2s(st + P::sQ + e * P::QS, a.q + size_t(k0 + e) * Nf * Np, uint32_t(Nf * Np * 4), &bars[s]);
+    }
     tma_bulk_g2s(st + P::sRec, a.rec + size_t(k0) * REC, kRecBytes, &bars[s]);
     tma_bulk_g2s(st + P::sNbr, a.nbr + k0, uint32_t(EB * 16), &bars[s]);
     if (OPS_SMEM && with_ops) tma_bulk_g2s(smem + P::oOps, a.ops, bo, &bars[s]);
@@ -571,6 +590,12 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
         sNt[(3 * f + 0) * EBP + e] = fn.x;
         sNt[(3 * f + 1) * EBP + e] = fn.y;
         sNt[(3 * f + 2) * EBP + e] = fn.z;
+        if constexpr (DIRECT) {
+          constexpr int KXM = XRows<MODEL, N>::KXM;
+          *xrow(a, KXM + 3 * f + 0, k0 + e) = fn.x;
+          *xrow(a, KXM + 3 * f + 1, k0 + e) = fn.y;
+          *xrow(a, KXM + 3 * f + 2, k0 + e) = fn.z;
+        }
         // penalty coefficients of the face, pen_p = A jp + B jvn and
         // psi = C jp + D jvn with jp = [[p]]/2, jvn = [[v]].n/2 (Fscale folded
         // in), and where the neighbour trace comes from: -1 outer boundary,
@@ -593,24 +618,29 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
         int2 fi = make_int2(-1, 0);
         if (w >= 0) {
           const int le = (w >> kNbrShift) - k0;
-          fi.x = (le >= 0 && le < EB) ? le * Nf * Np : -2;
+          fi.x = (le >= 0 && le < EB) ? le * P::QS : -2;
           fi.y = ((w & 3) * 6 + ((w >> 2) & 7)) * Nfp;
         }
         sFi[i] = fi;
       }
     }
-    // -------- volume inputs (node index fastest: conflict-free reads of q)
+    // -------- volume inputs (node index fastest: conflict-free reads of q;
+    // DIRECT: element index fastest, each row of X gets EB consecutive words)
     for (int i = tid; i < EB * Np; i += NT) {
-      const int j = i % Np, e = i / Np;
+      const int j = DIRECT ? i / EB : i % Np, e = DIRECT ? i % EB : i / Np;
       const float* gk = sRec + e * REC;
-      const float* qe = sQ + e * Nf * Np;
+      const float* qe = sQ + e * P::QS;
+      // volume input v at node j of element e
+      auto put = [&](int v, float x) {
+        if constexpr (DIRECT) *xrow(a, v * Np + j, k0 + e) = x;
+        else sXv[(v * Np + j) * EBP + e] = x;
+      };
       if constexpr (MODEL == 0) {
         const float kap = gk[9];
         const float v0 = qe[Np + j], v1 = qe[2 * Np + j], v2 = qe[3 * Np + j];
-        sXv[(0 * Np + j) * EBP + e] = qe[j];
+        put(0, qe[j]);
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-          sXv[((1 + d) * Np + j) * EBP + e] = -kap * (gk[d] * v0 + gk[3 + d] * v1 + gk[6 + d] * v2);
+        for (int d = 0; d < 3; ++d) put(1 + d, -kap * (gk[d] * v0 + gk[3 + d] * v1 + gk[6 + d] * v2));
       } else {
         const float rinv = gk[11];
         float sg[3][3];
@@ -619,29 +649,29 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
         sg[0][2] = sg[2][0] = qe[7 * Np + j];
         sg[1][2] = sg[2][1] = qe[8 * Np + j];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) sXv[(c * Np + j) * EBP + e] = qe[c * Np + j];
+        for (int c = 0; c < 3; ++c) put(c, qe[c * Np + j]);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int d = 0; d < 3; ++d)
-            sXv[((3 + 3 * c + d) * Np + j) * EBP + e] =
-                rinv * (gk[d] * sg[c][0] + gk[3 + d] * sg[c][1] + gk[6 + d] * sg[c][2]);
+            put(3 + 3 * c + d, rinv * (gk[d] * sg[c][0] + gk[3 + d] * sg[c][1] + gk[6 + d] * sg[c][2]));
       }
     }
     __syncthreads();  // sFn ready
 
     // -------- traces and penalty terms at the 4 Nfp face nodes (face node fastest)
+    constexpr int NVX = XRows<MODEL, N>::NV;  // DIRECT: the surface rows of X follow NVX Np volume rows
     if constexpr (FACT) {
       constexpr int XS = NFN * EBP;
       for (int i = tid; i < EB * NFN; i += NT) {
-        const int fm = i % NFN, e = i / NFN;
+        const int fm = DIRECT ? i / EB : i % NFN, e = DIRECT ? i % EB : i / NFN;
         const int f = fm / Nfp, m = fm - f * Nfp;
         const int fi = e * 4 + f;
         const int2 src = sFi[fi];
         const float4 fn = *reinterpret_cast<const float4*>(sFn + fi * 4);
         const float4 co = sCo[fi];
         const int nM = sFtab[f * Nfp + m];
-        const float* qe = sQ + e * Nf * Np + nM;
+        const float* qe = sQ + e * P::QS + nM;
         const float pM = qe[0], vM0 = qe[Np], vM1 = qe[2 * Np], vM2 = qe[3 * Np];
         float jp, jvn;
         if (src.x == -1) {  // rigid wall: p+ = p-, v+ = v- - 2 (v-.n) n
@@ -659,13 +689,19 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
           jp = 0.5f * (pP - pM);
           jvn = 0.5f * ((vP0 - vM0) * fn.x + (vP1 - vM1) * fn.y + (vP2 - vM2) * fn.z);
         }
-        float* X = sXs + fm * EBP + e;
-        X[0] = co.x * jp + co.y * jvn;
-        X[XS] = co.z * jp + co.w * jvn;
+        const float pp = co.x * jp + co.y * jvn, ps = co.z * jp + co.w * jvn;
+        if constexpr (DIRECT) {
+          *xrow(a, NVX * Np + fm, k0 + e) = pp;
+          *xrow(a, NVX * Np + NFN + fm, k0 + e) = ps;
+        } else {
+          float* X = sXs + fm * EBP + e;
+          X[0] = pp;
+          X[XS] = ps;
+        }
       }
     } else
     for (int i = tid; i < EB * NFN; i += NT) {
-      const int fm = i % NFN, e = i / NFN;
+      const int fm = DIRECT ? i / EB : i % NFN, e = DIRECT ? i % EB : i / NFN;
       const int f = fm / Nfp, m = fm - f * Nfp;
       const int nM = sFtab[f * Nfp + m];
       const int4 nb = sNbr[e];
@@ -678,7 +714,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
         if (le >= 0 && le < EB) {
           const int rot = (w >> 2) & 7, f2 = w & 3;
           const int nP = sFtab[f2 * Nfp + sFtab[4 * Nfp + rot * Nfp + m]];
-          const float* qn = sQ + le * Nf * Np;
+          const float* qn = sQ + le * P::QS;
 #pragma unroll
           for (int c = 0; c < Nf; ++c) qPv[c] = qn[c * Np + nP];
         } else {
@@ -686,18 +722,33 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
           for (int c = 0; c < Nf; ++c) qPv[c] = sT[(c * NFN + fm) * EBP + e];
         }
       }
-      const float* qe = sQ + e * Nf * Np;
+      const float* qe = sQ + e * P::QS;
       const float4 fn = *reinterpret_cast<const float4*>(sFn + (e * 4 + f) * 4);
       const float* gM = sRec + e * REC;
       float qM[Nf];
 #pragma unroll
       for (int c = 0; c < Nf; ++c) qM[c] = qe[c * Np + nM];
-      float* X = sXs + fm * EBP + e;
-      constexpr int XS = NFN * EBP;
       float pen[Nf];
       face_penalty<MODEL>(gM, f, bnd, qM, qPv, fn, a.flux, a.bc, pen);
+      if constexpr (DIRECT) {
 #pragma unroll
-      for (int c = 0; c < Nf; ++c) X[c * XS] = pen[c];
+        for (int c = 0; c < Nf; ++c) *xrow(a, NVX * Np + c * NFN + fm, k0 + e) = pen[c];
+      } else {
+        float* X = sXs + fm * EBP + e;
+        constexpr int XS = NFN * EBP;
+#pragma unroll
+        for (int c = 0; c < Nf; ++c) X[c * XS] = pen[c];
+      }
+    }
+    if constexpr (DIRECT) {
+      // every GEMM input of the block is in X: start the next block's
+      // neighbour gathers (its trace buffer was last read before the
+      // barrier at the top of this block) and move on
+      static_assert(SPLIT % 4 == 0 && (SPLIT % EB == 0 || EB % SPLIT == 0), "element blocks inside column tiles");
+      if (b + G < nblk) {
+        if (mbar_wait_bounded(&bars[s ^ 1], uint32_t(((it + 1) >> 1) & 1), err)) issue_gathers(nxt_a, nxt_lb, s ^ 1);
+      }
+      continue;
     }
     __syncthreads();
     // the next block's stage was issued at the top of this block: once it has
@@ -737,30 +788,6 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
 #pragma unroll
         for (int h = 0; h < XP; ++h)
           *reinterpret_cast<uint4*>(dst + size_t(h) * nvs * TX::BV) = pc[h];
-      }
-      continue;
-    } else if constexpr (SPLIT > 0) {
-      // split step, front half: the GEMM inputs leave for the global buffer
-      // X[tile][row][NE] (rows of XRows; NE = SPLIT elements per tile), 4
-      // elements per float4
-      using XR = XRows<MODEL, N>;
-      constexpr int NV = XR::NV, KXM = XR::KXM, KX = XR::KX;
-      constexpr int NE = SPLIT;
-      static_assert(NE % 4 == 0 && (NE % EB == 0 || EB % NE == 0), "element blocks inside column tiles");
-      static_assert(KXM == NV * Np + (FACT ? 2 : Nf) * NFN, "surface streams of the split layout");
-      for (int i = tid; i < KX * (EB / 4); i += NT) {
-        const int e4 = i % (EB / 4), row = i / (EB / 4);
-        float4 v;
-        if (row < KXM) {
-          const float* src = row < NV * Np ? sXv + row * EBP : sXs + (row - NV * Np) * EBP;
-          v = make_float4(src[4 * e4], src[4 * e4 + 1], src[4 * e4 + 2], src[4 * e4 + 3]);
-        } else {  // normal component c of face f
-          const int f = (row - KXM) / 3, c = (row - KXM) % 3;
-          const float* nf = sFn + (16 * e4 + f) * 4 + c;
-          v = make_float4(nf[0], nf[16], nf[32], nf[48]);
-        }
-        const int k = k0 + 4 * e4;
-        *reinterpret_cast<float4*>(a.xg + (size_t(k / NE) * KX + row) * NE + (k % NE)) = v;
       }
       continue;
     }

@@ -43,7 +43,7 @@ template <int MODEL, int N, int EB, int V = 1, int NT = threads_for<N, EB, 1>()>
 KernelCfg make_split_cfg() {
   using SS = SplitShape<MODEL, N>;
   using G = typename GemmOf<MODEL, N, V>::T;
-  static_assert(Plan<MODEL, N, EB, false, false, MODEL == 0>::bytes <= 227 * 1024, "shared memory budget");
+  static_assert(Plan<MODEL, N, EB, false, false, MODEL == 0, true>::bytes <= 227 * 1024, "shared memory budget");
   static_assert(G::smem <= 227 * 1024, "shared memory budget (GEMM)");
   static_assert((Sz<N>::Np + G::MT - 1) / G::MT * G::MT <= SS::OPP, "row tiles inside the operator pitch");
 
@@ -53,7 +53,7 @@ KernelCfg make_split_cfg() {
   c.NT = NT;
   c.ops_smem = false;
   c.r_smem = false;
-  c.smem = Plan<MODEL, N, EB, false, false, MODEL == 0>::bytes;
+  c.smem = Plan<MODEL, N, EB, false, false, MODEL == 0, true>::bytes;
   c.fn = dg_step_kernel<MODEL, N, EB, 1, NT, false, false, SS::NE>;
   c.fn_batched = dg_step_batched_kernel<MODEL, N, EB, 1, NT, false, false, SS::NE>;
   c.split = 1;

@@ -35,12 +35,12 @@ KernelCfg make_front_cfg() {
   constexpr int EB = front_eb<MODEL, N>();
   constexpr int NT = threads_for<N, EB, 1>();
   using SS = SplitShape<MODEL, N>;
-  static_assert(Plan<MODEL, N, EB, false, false, MODEL == 0>::bytes <= 227 * 1024, "shared memory budget");
+  static_assert(Plan<MODEL, N, EB, false, false, MODEL == 0, true>::bytes <= 227 * 1024, "shared memory budget");
   KernelCfg c{};
   c.EB = EB;
   c.TN = 1;
   c.NT = NT;
-  c.smem = Plan<MODEL, N, EB, false, false, MODEL == 0>::bytes;
+  c.smem = Plan<MODEL, N, EB, false, false, MODEL == 0, true>::bytes;
   c.fn = dg_step_kernel<MODEL, N, EB, 1, NT, false, false, SS::NE, 0>;
   c.split = 0;
   c.gemm_ne = SS::NE;
