@@ -72,11 +72,12 @@ __device__ __forceinline__ void ab3_batch(const StepArgs& a, const size_t* idx, 
   }
 }
 
-// The AB3 inputs of a column tile into L2 while its products run (q, r^{m-1},
-// r^{m-2} are padded past K: a whole tile stays inside the allocation).
+// The AB3 inputs of NE elements from element k0 into L2 while their products
+// run (q, r^{m-1}, r^{m-2} are padded past K: a whole tile stays inside the
+// allocation).
 template <int Nf, int Np, int NE>
-__device__ __forceinline__ void prefetch_tile_l2(const StepArgs& a, int ntile) {
-  const size_t e0 = size_t(ntile) * NE * Nf * Np;
+__device__ __forceinline__ void prefetch_tile_l2(const StepArgs& a, int k0) {
+  const size_t e0 = size_t(k0) * Nf * Np;
   constexpr uint32_t bytes = uint32_t(NE * Nf * Np * 4);
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.q + e0), "r"(bytes) : "memory");
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.r1 + e0), "r"(bytes) : "memory");
@@ -116,6 +117,7 @@ struct GemmA {
   static constexpr int NVC = (S::Np + JC - 1) / JC;       // volume chunks
   static constexpr int NLC = (S::NFN + CC - 1) / CC;      // lift chunks
   static constexpr int MINB = 1;                          // resident CTAs the registers are sized for
+  static constexpr int MTILES_L = (S::Np + MT - 1) / MT;  // row tiles (launch grid: x column tiles)
   // per buffer: A rows (3 JC volume, CC lift) x MT, X rows (NV JC volume;
   // lift: 2 CC streams + 12 normal rows acoustic, Nf CC elastic) x NE
   static constexpr int nA = (3 * JC > CC ? 3 * JC : CC) * MT;
@@ -147,7 +149,7 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
   const int row0 = mtile * MT;
   const float* X = a.xg + size_t(ntile) * SplitShape<MODEL, N>::x_floats_per_tile;
   const float* OP = a.ops2;  // [3 Np + NFN][MP2]
-  if (tid == 0 && mtile == 0 && a.mode == 0) prefetch_tile_l2<Nf, Np, NE>(a, ntile);
+  if (tid == 0 && mtile == 0 && a.mode == 0) prefetch_tile_l2<Nf, Np, NE>(a, ntile * NE);
 
   // chunk c -> shared buffer (c & 1)
   auto issue = [&](int c) {
@@ -424,15 +426,19 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
 
 // NARROW: elements per thread halved (fewer registers, two CTAs per SM).
 // SMALL (narrow only): short row tiles that divide Np (almost) exactly and
-// registers sized for two resident CTAs per SM.
-template <int MODEL, int N, bool NARROW = false, bool SMALL = false>
+// registers sized for two resident CTAs per SM.  HALF (narrow only): a CTA
+// takes half of a column tile of X (32 acoustic elements), so that two CTAs
+// fit per SM with the registers of the narrow design.
+template <int MODEL, int N, bool NARROW = false, bool SMALL = false, bool HALF = false>
 struct GemmB {
   using S = Sz<N>;
   static constexpr int Np = S::Np, NFN = S::NFN;
   static constexpr int Nf = MODEL == 0 ? 4 : 9;
   static constexpr int NV = XRows<MODEL, N>::NV;          // X rows per volume index j
   static constexpr int KX = XRows<MODEL, N>::KX;          // X rows per element
-  static constexpr int NE = MODEL == 0 ? 64 : 32;         // elements per column tile
+  static constexpr int NE = MODEL == 0 ? 64 : 32;         // elements per column tile of X
+  static constexpr int NSUB = HALF ? 2 : 1;               // CTAs per column tile
+  static constexpr int NEG = NE / NSUB;                   // elements per CTA
   static constexpr int TM = MODEL == 0 ? 8 : 4;           // rows per thread tile
   static constexpr int TE = (MODEL == 0 ? 4 : 2) / (NARROW ? 2 : 1);  // elements per thread tile
   // output rows per CTA (MT / TM even, so that the CTA is whole warps)
@@ -448,32 +454,40 @@ struct GemmB {
   // (acoustic N = 5: one tile of exactly Np = 56 rows, 13 % faster than
   // 64-row tiles; three short tiles at N = 7, 8 re-read X and spill)
   static constexpr int MT_SMALL = MODEL == 0 && N == 5 ? 56 : MT_NARROW;
-  static constexpr int MT = SMALL ? MT_SMALL : NARROW ? MT_NARROW : MT_WIDE;
-  static constexpr int MINB = SMALL ? 2 : 1;  // resident CTAs the registers are sized for
+  // (HALF: 16 lanes per row group, so an even number of row groups: MT_WIDE)
+  static constexpr int MT = SMALL ? MT_SMALL : (NARROW && !HALF) ? MT_NARROW : MT_WIDE;
+  static constexpr int MINB = SMALL || HALF ? 2 : 1;  // resident CTAs the registers are sized for
   static constexpr int MP2 = (Np + MT - 1) / MT * MT;     // padded rows of the split operator blob
   static constexpr int KC = 16;                           // K chunk (volume indices or face nodes)
   static constexpr int NS = 3;                            // cp.async stages
-  static constexpr int NT = (MT / TM) * (NE / TE);        // threads per CTA
+  static constexpr int NT = (MT / TM) * (NEG / TE);       // threads per CTA
+  static constexpr int MTILES_R = (Np + MT - 1) / MT;     // row tiles
+  static constexpr int MTILES_L = MTILES_R * NSUB;        // CTAs per column tile (launch grid: x column tiles)
   static constexpr int NVC = (Np + KC - 1) / KC;          // volume chunks
   static constexpr int NLC = (NFN + KC - 1) / KC;         // lift chunks
   // X rows of one chunk: NV KC (volume); lift: 2 KC streams + 12 normal
   // rows (acoustic), Nf KC (elastic)
   static constexpr int LB = MODEL == 0 ? 2 * KC + 12 : Nf * KC;
   static constexpr int nA = 3 * KC * MT;                  // operator rows of one stage
-  static constexpr int nB = (NV * KC > LB ? NV * KC : LB) * NE;  // X rows of one stage
-  static constexpr int NEP = NE + 1;                      // row stride of the staged RHS field
+  static constexpr int nB = (NV * KC > LB ? NV * KC : LB) * NEG;  // X rows of one stage
+  static constexpr int NEP = NEG + 1;                     // row stride of the staged RHS field
   static constexpr int nOut = MT * NEP;
   static constexpr int nStage = nA + nB;
   static constexpr size_t smem = size_t(NS * nStage > nOut ? NS * nStage : nOut) * 4;
   static constexpr size_t x_floats_per_tile = size_t(KX) * NE;
   static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
-  static_assert(MT % 4 == 0 && NE % 4 == 0 && TM % 4 == 0, "16-byte copies and loads");
+  static_assert(MT % 4 == 0 && NEG % 4 == 0 && TM % 4 == 0, "16-byte copies and loads");
+  static_assert(!HALF || NARROW, "half column tiles with the narrow thread tile");
 };
 
-template <int MODEL, int N, bool NARROW = false, bool SMALL = false>
-__device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, const int ntile) {
-  using SS = GemmB<MODEL, N, NARROW, SMALL>;
-  constexpr int Np = SS::Np, NFN = SS::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NE, TM = SS::TM, TE = SS::TE;
+template <int MODEL, int N, bool NARROW = false, bool SMALL = false, bool HALF = false>
+__device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l, const int ntile) {
+  using SS = GemmB<MODEL, N, NARROW, SMALL, HALF>;
+  // NE: elements of this CTA; XNE: row stride of X (elements per column tile)
+  constexpr int Np = SS::Np, NFN = SS::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NEG, TM = SS::TM, TE = SS::TE;
+  constexpr int XNE = SS::NE;
+  const int mtile = mtile_l % SS::MTILES_R, half = mtile_l / SS::MTILES_R;
+  const int kbase = ntile * XNE + half * NE;  // first element of the CTA
   constexpr int Nfp = Sz<N>::Nfp, NXS = XRows<MODEL, N>::NXS, KXM = XRows<MODEL, N>::KXM;
   constexpr int MT = SS::MT, MP2 = SplitShape<MODEL, N>::OPP, KC = SS::KC, NT = SS::NT, NS = SS::NS;
   constexpr int NVC = SS::NVC, NLC = SS::NLC, NCH = NVC + NLC;
@@ -486,9 +500,9 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
 
   const int tid = threadIdx.x;
   const int row0 = mtile * MT;
-  const float* X = a.xg + size_t(ntile) * SplitShape<MODEL, N>::x_floats_per_tile;
+  const float* X = a.xg + size_t(ntile) * SplitShape<MODEL, N>::x_floats_per_tile + half * NE;
   const float* OP = a.ops2;  // [3 Np + NFN][MP2]
-  if (tid == 0 && mtile == 0 && a.mode == 0) prefetch_tile_l2<Nf, Np, NE>(a, ntile);
+  if (tid == 0 && mtile == 0 && a.mode == 0) prefetch_tile_l2<Nf, Np, NE>(a, kbase);
 
   // chunk c -> stage c % NS: operator rows [KC][MT] (3 of them for a volume
   // chunk), X rows [vector][KC][NE]; rows past Np / 4 Nfp are neither copied
@@ -508,7 +522,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
         for (int i = tid; i < NV * nj * (NE / 4); i += NT) {
           const int q4 = i % (NE / 4), rr = i / (NE / 4);
           const int f = rr / nj, jj = rr - f * nj;
-          cp_async16(B + (f * KC + jj) * NE + 4 * q4, X + size_t(f * Np + j0 + jj) * NE + 4 * q4);
+          cp_async16(B + (f * KC + jj) * NE + 4 * q4, X + size_t(f * Np + j0 + jj) * XNE + 4 * q4);
         }
       } else {
         const int c0 = (c - NVC) * KC;
@@ -520,12 +534,12 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
         for (int i = tid; i < NXS * nc * (NE / 4); i += NT) {
           const int q4 = i % (NE / 4), rr = i / (NE / 4);
           const int f = rr / nc, cc = rr - f * nc;
-          cp_async16(B + (f * KC + cc) * NE + 4 * q4, X + size_t(NV * Np + f * NFN + c0 + cc) * NE + 4 * q4);
+          cp_async16(B + (f * KC + cc) * NE + 4 * q4, X + size_t(NV * Np + f * NFN + c0 + cc) * XNE + 4 * q4);
         }
         if constexpr (MODEL == 0) {  // the face normals, after the two streams
           for (int i = tid; i < 12 * (NE / 4); i += NT) {
             const int q4 = i % (NE / 4), r = i / (NE / 4);
-            cp_async16(B + (2 * KC + r) * NE + 4 * q4, X + size_t(KXM + r) * NE + 4 * q4);
+            cp_async16(B + (2 * KC + r) * NE + 4 * q4, X + size_t(KXM + r) * XNE + 4 * q4);
           }
         }
       }
@@ -638,7 +652,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
         // boundary: derivative products -> RHS components (per element column)
 #pragma unroll
         for (int t = 0; t < TE; ++t) {
-          const int k = ntile * NE + e0 + t;
+          const int k = kbase + e0 + t;
           const int kk = k < a.K ? k : a.K - 1;  // padding columns: any valid record
           const float* gk = a.rec + size_t(kk) * REC;
           float g[9];
@@ -761,7 +775,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
       for (int u = 0; u < U; ++u) {
         const int p = p0 + u * NT;
         const int e = p / MT, rr = p - e * MT;
-        const int k = ntile * NE + e;
+        const int k = kbase + e;
         on[u] = p < NE * MT && k < a.K && rr < rows;
         const int i = row0 + rr;
         float r = on[u] ? sOut[rr * NEP + e] : 0.f;
@@ -777,6 +791,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile, 
 
 // Design V of the FP32 GEMM (V = 2: design B, V = 3: design B with half the
 // elements per thread, V = 4: V = 3 with short row tiles and two CTAs per SM,
+// V = 5: V = 3 with half a column tile per CTA and two CTAs per SM,
 // otherwise design A).
 template <int MODEL, int N, int V>
 struct GemmOf {
@@ -800,6 +815,13 @@ struct GemmOf<MODEL, N, 4> {
     gemm_b_body<MODEL, N, true, true>(a, mtile, ntile);
   }
 };
+template <int MODEL, int N>
+struct GemmOf<MODEL, N, 5> {
+  using T = GemmB<MODEL, N, true, false, true>;
+  __device__ static void body(const StepArgs& a, int mtile, int ntile) {
+    gemm_b_body<MODEL, N, true, false, true>(a, mtile, ntile);
+  }
+};
 
 // One solve: row tiles fastest, so that the CTAs that share a column tile of
 // X run together and read it from L2.  V selects the design (1 = A, 2 = B).
@@ -807,7 +829,7 @@ template <int MODEL, int N, int V>
 __global__ void __launch_bounds__(GemmOf<MODEL, N, V>::T::NT, GemmOf<MODEL, N, V>::T::MINB)
     dg_split_gemm_kernel(const StepArgs a) {
   using G = typename GemmOf<MODEL, N, V>::T;
-  constexpr int MTILES = (Sz<N>::Np + G::MT - 1) / G::MT;
+  constexpr int MTILES = G::MTILES_L;
   GemmOf<MODEL, N, V>::body(a, int(blockIdx.x) % MTILES, int(blockIdx.x) / MTILES);
 }
 
@@ -817,7 +839,7 @@ template <int MODEL, int N, int V>
 __global__ void __launch_bounds__(GemmOf<MODEL, N, V>::T::NT, GemmOf<MODEL, N, V>::T::MINB)
     dg_split_gemm_batched_kernel(const BatchArgs b) {
   using G = typename GemmOf<MODEL, N, V>::T;
-  constexpr int MTILES = (Sz<N>::Np + G::MT - 1) / G::MT;
+  constexpr int MTILES = G::MTILES_L;
   const int so = __ldg(b.tile_solve + blockIdx.x);
   const int lt = int(blockIdx.x) - __ldg(b.tile_start + so);
   StepArgs a;

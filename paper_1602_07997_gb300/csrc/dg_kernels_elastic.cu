@@ -22,24 +22,30 @@ const KernelCfg* kernel_variants_elastic(int N, int* count) {
                                  make_split_cfg<1, 4, 8, 2>(), make_cfg<1, 4, 4, true, true, 1, 128>(),
                                  make_cfg<1, 4, 4, true, true, 1, 256>(), make_split_cfg<1, 4, 4, 3, 256>(),
                                  make_cfg<1, 4, 4, true, true>()};
-  static const KernelCfg v5[] = {make_split_cfg<1, 5, 4, 3, 512>(), make_cfg<1, 5, 4, false, false>(),
+  static const KernelCfg v5[] = {make_split_cfg<1, 5, 8, 5, 512>(), make_cfg<1, 5, 4, false, false>(),
                                  make_split_cfg<1, 5, 4>(), make_split_cfg<1, 5, 4, 2>(),
                                  make_cfg<1, 5, 4, false, true>(), make_split_cfg<1, 5, 4, 3, 256>(),
-                                 make_split_cfg<1, 5, 4, 3, 384>(), make_split_cfg<1, 5, 4, 3>()};
-  static const KernelCfg v6[] = {make_split_cfg<1, 6, 4, 3, 512>(), make_cfg<1, 6, 4, false, false, 2>(),
+                                 make_split_cfg<1, 5, 4, 3, 384>(), make_split_cfg<1, 5, 4, 3>(),
+                                 make_split_cfg<1, 5, 4, 3, 512>(), make_split_cfg<1, 5, 8, 3, 512>()};
+  static const KernelCfg v6[] = {make_split_cfg<1, 6, 8, 5, 512>(), make_cfg<1, 6, 4, false, false, 2>(),
                                  make_split_cfg<1, 6, 4>(), make_split_cfg<1, 6, 4, 2>(),
                                  make_cfg<1, 6, 4, false, false>(), make_split_cfg<1, 6, 4, 3, 256>(),
-                                 make_split_cfg<1, 6, 4, 3, 384>(), make_split_cfg<1, 6, 4, 3>()};
-  static const KernelCfg v7[] = {make_split_cfg<1, 7, 4, 3, 512>(), make_cfg<1, 7, 4, false, false, 2>(),
+                                 make_split_cfg<1, 6, 4, 3, 384>(), make_split_cfg<1, 6, 4, 3>(),
+                                 make_split_cfg<1, 6, 4, 5, 512>(), make_split_cfg<1, 6, 4, 3, 512>(),
+                                 make_split_cfg<1, 6, 8, 3, 512>()};
+  static const KernelCfg v7[] = {make_split_cfg<1, 7, 8, 5, 512>(), make_cfg<1, 7, 4, false, false, 2>(),
                                  make_split_cfg<1, 7, 4>(), make_split_cfg<1, 7, 4, 2>(),
                                  make_cfg<1, 7, 4, false, false>(), make_split_cfg<1, 7, 4, 3, 256>(),
-                                 make_split_cfg<1, 7, 4, 3, 384>(), make_split_cfg<1, 7, 4, 3>()};
-  static const KernelCfg v8[] = {make_split_cfg<1, 8, 4, 2, 384>(), make_cfg<1, 8, 4, false, false, 2>(),
+                                 make_split_cfg<1, 7, 4, 3, 384>(), make_split_cfg<1, 7, 4, 3>(),
+                                 make_split_cfg<1, 7, 4, 3, 512>(), make_split_cfg<1, 7, 8, 3, 512>(),
+                                 make_split_cfg<1, 7, 4, 5, 512>()};
+  static const KernelCfg v8[] = {make_split_cfg<1, 8, 4, 5, 384>(), make_cfg<1, 8, 4, false, false, 2>(),
                                  make_split_cfg<1, 8, 4>(), make_cfg<1, 8, 4, false, false>(),
                                  make_split_cfg<1, 8, 4, 3>(), make_split_cfg<1, 8, 4, 3, 256>(),
-                                 make_split_cfg<1, 8, 4, 3, 384>(), make_split_cfg<1, 8, 4, 2>()};
+                                 make_split_cfg<1, 8, 4, 3, 384>(), make_split_cfg<1, 8, 4, 2>(),
+                                 make_split_cfg<1, 8, 4, 2, 384>(), make_split_cfg<1, 8, 4, 5, 512>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
-  static const int cnt[8] = {5, 5, 7, 9, 8, 8, 8, 8};
+  static const int cnt[8] = {5, 5, 7, 9, 10, 11, 11, 10};
   if (N < 1 || N > 8) return nullptr;
   *count = cnt[N - 1];
   return tab[N - 1];

@@ -63,7 +63,7 @@ KernelCfg make_split_cfg() {
   c.gemm_threads = G::NT;
   c.gemm_ne = SS::NE;
   c.gemm_mt = G::MT;
-  c.gemm_mtiles = (Sz<N>::Np + G::MT - 1) / G::MT;
+  c.gemm_mtiles = G::MTILES_L;
   c.gemm_kx = SS::KX;
   c.gemm_mp2 = SS::OPP;
   c.gemm_nsplit = 0;
