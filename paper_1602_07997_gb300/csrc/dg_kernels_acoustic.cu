@@ -45,15 +45,14 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_split_cfg<0, 7, 4, 3>(), make_split_cfg<0, 7, 8, 3>(),
                                  make_split_cfg<0, 7, 8, 3, 768>(), make_split_cfg<0, 7, 8, 1, 512>(),
                                  make_split_cfg<0, 7, 8, 3, 512>()};
-  static const KernelCfg v8[] = {make_split_cfg<0, 8, 8, 3, 768>(), make_cfg<0, 8, 4, false, true, 2>(),
+  static const KernelCfg v8[] = {make_split_cfg<0, 8, 8, 3, 512>(), make_cfg<0, 8, 4, false, true, 2>(),
                                  make_cfg<0, 8, 4, false, true, 4>(), make_cfg<0, 8, 8, false, true, 2>(),
                                  make_split_cfg<0, 8, 4>(), make_split_cfg<0, 8, 8>(),
                                  make_split_cfg<0, 8, 8, 2>(), make_cfg<0, 8, 4, false, true>(),
-                                 make_split_cfg<0, 8, 4, 3>(), make_split_cfg<0, 8, 8, 3, 512>(),
-                                 make_split_cfg<0, 8, 8, 3>(), make_split_cfg<0, 8, 8, 2, 512>(),
+                                 make_split_cfg<0, 8, 4, 3>(), make_split_cfg<0, 8, 8, 2, 512>(),
                                  make_split_cfg<0, 8, 8, 5, 768>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
-  static const int cnt[8] = {8, 8, 8, 8, 11, 13, 13, 13};
+  static const int cnt[8] = {8, 8, 8, 8, 11, 13, 13, 11};
   if (N < 1 || N > 8) return nullptr;
   *count = cnt[N - 1];
   return tab[N - 1];
