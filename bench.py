@@ -162,10 +162,13 @@ def aggregate(t_local, updates, world):
     return float(t.item()), float(u.item())
 
 
-def served_benchmark(P, count=64, steps=500, seed=1004, max_n=32):
+def served_benchmark(P, count=64, steps=500, seed=1004, max_n=32, rates=(0.5, 0.9)):
     """Served stream: acoustic shots with Poisson arrivals at 0.7 x the batched
     capacity (measured first with every request submitted at once), p50/p99 of
-    submit -> result latency, against the same requests run one at a time."""
+    submit -> result latency, against the same requests run one at a time; and
+    a sweep of the arrival rate (`rates` x capacity, batched server runs; the
+    one-at-a-time latencies there follow from a FIFO queue over the service
+    times measured at 0.7, since that executor runs one request at a time)."""
     import workloads as W
     from workloads.configs import request_mesh
     reqs = W.config4_requests(count, seed=seed)
@@ -211,15 +214,17 @@ def served_benchmark(P, count=64, steps=500, seed=1004, max_n=32):
     mk, lat, launches = run_server(list(arr))
     # plain: the same requests one at a time through dg_step, in arrival order
     t0 = time.perf_counter()
-    plain_lat = []
+    plain_lat, service = [], []
     for (r, v, t, c, d, a), ta in zip(prepared, arr):
         while time.perf_counter() - t0 < ta:
             time.sleep(0.0005)
+        ts = time.perf_counter()
         g = P.Solver(v, t, c, r["N"], "acoustic", dt=d)
         g.set_source(r["source"], a)
         g.step(steps)
         g.get_state()
         g.close()
+        service.append(time.perf_counter() - ts)
         plain_lat.append(time.perf_counter() - t0 - ta)
     mk_plain = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -231,6 +236,24 @@ def served_benchmark(P, count=64, steps=500, seed=1004, max_n=32):
         g.close()
     mk_plain0 = time.perf_counter() - t0
     q = lambda x, p: float(np.percentile(np.asarray(x), p))
+
+    def fifo(arrivals):
+        free, out = 0.0, []
+        for ta, sv in zip(arrivals, service):
+            free = max(ta, free) + sv
+            out.append(free - ta)
+        return out
+
+    sweep = [{"rate_frac": 0.7, "p50_s": q(lat, 50), "p99_s": q(lat, 99), "makespan_s": mk,
+              "plain_p50_s": q(plain_lat, 50), "plain_p99_s": q(plain_lat, 99)}]
+    for frac in rates:
+        af = np.cumsum(np.random.default_rng(seed + int(1000 * frac)).exponential(1.0 / (frac * capacity),
+                                                                                  size=len(prepared)))
+        mkf, latf, _ = run_server(list(af))
+        pl = fifo(af)
+        sweep.append({"rate_frac": frac, "p50_s": q(latf, 50), "p99_s": q(latf, 99), "makespan_s": mkf,
+                      "plain_p50_s": q(pl, 50), "plain_p99_s": q(pl, 99)})
+    sweep.sort(key=lambda x: x["rate_frac"])
     return {"requests": len(prepared), "steps": steps, "degrees": [3, 5, 7],
             "mesh_tets": [int(p[2].shape[0]) for p in prepared],
             "capacity_req_per_s": capacity, "arrival_rate_req_per_s": rate,
@@ -239,7 +262,9 @@ def served_benchmark(P, count=64, steps=500, seed=1004, max_n=32):
             "batched_updates_per_s": work / mk0, "launches": launches,
             "plain_p50_s": q(plain_lat, 50), "plain_p99_s": q(plain_lat, 99), "plain_makespan_s": mk_plain,
             "plain_all_at_once_makespan_s": mk_plain0, "plain_updates_per_s": work / mk_plain0,
-            "note": "latency = submit to result in host memory (includes host set-up of the request)"}
+            "rate_sweep": sweep,
+            "note": "latency = submit to result in host memory (includes host set-up of the request); "
+                    "rate_sweep plain latencies: FIFO over the measured one-at-a-time service times"}
 
 
 def build_meshes(model, Ns):
