@@ -81,6 +81,14 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// raise the transaction count of the current phase without arriving
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
 __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -171,8 +179,11 @@ constexpr int round4(int x) { return (x + 3) & ~3; }
 // psi n_f (n_f is constant on a face of a straight-sided tetrahedron), plus
 // per-face penalty coefficients and neighbour sources.
 // DIRECT (FP32 split front half): the GEMM inputs go straight from the
-// compute loops to X in global memory, no staging buffers.
-template <int MODEL, int N, int EB, bool OPS_SMEM, bool R_SMEM, bool FACT = false, bool DIRECT = false>
+// compute loops to X in global memory, no staging buffers.  HALO (acoustic
+// fused step): the neighbours outside the block arrive whole, one bulk copy
+// of Nf Np floats per (element, face) slot, instead of their face-node traces.
+template <int MODEL, int N, int EB, bool OPS_SMEM, bool R_SMEM, bool FACT = false, bool DIRECT = false,
+          bool HALO = false>
 struct Plan {
   using S = Sz<N>;
   static constexpr int Nf = MODEL == 0 ? 4 : 9;
@@ -190,7 +201,8 @@ struct Plan {
   static constexpr int nR = R_SMEM ? 2 * nQ : 0;
   static constexpr int nXvol = DIRECT ? 0 : (MODEL == 0 ? 4 : 12) * S::Np * EBP;
   static constexpr int nXsur = DIRECT ? 0 : (FACT ? 2 : Nf) * S::NFN * EBP;
-  static constexpr int nT = Nf * S::NFN * EBP;             // neighbour traces [Nf][4Nfp][EBP]
+  static constexpr int nT = HALO ? 4 * EB * Nf * S::Np     // halo slots [EB][4][Nf][Np]
+                                : Nf * S::NFN * EBP;      // neighbour traces [Nf][4Nfp][EBP]
   static constexpr int nOps = OPS_SMEM ? S::KD * S::Mpad : 0;
   static constexpr int oStage0 = 0;
   static constexpr int oStage1 = oStage0 + nStage;
@@ -207,7 +219,7 @@ struct Plan {
   static constexpr int oFtab = oFi + (FACT ? EB * 8 : 0);  // int [10][Nfp]
   static constexpr int oPtab = oFtab + 10 * S::Nfp;        // int [4][6][Nfp]: neighbour node (FACT)
   static constexpr int oBar = round4(oPtab + (FACT ? 24 * S::Nfp : 0));
-  static constexpr int nFloats = oBar + 8;                 // 3 mbarriers
+  static constexpr int nFloats = oBar + 10;                // 5 mbarriers
   static constexpr size_t bytes = size_t(nFloats) * 4;
   static_assert(DIRECT || nXvol >= Nf * S::Np * EBP, "the RHS of a block is staged in the volume-input buffer");
 };
@@ -436,12 +448,14 @@ struct SolveBatch {
 };
 
 // ---------------------------------------------------------------- kernel body
-template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT, int XP, class Prov>
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT, int XP, bool HALO,
+          class Prov>
 __device__ __forceinline__ void step_body(const Prov& prov) {
   using S = Sz<N>;
   constexpr bool FACT = MODEL == 0 && XP == 0;  // every acoustic path but the tensor-core one
   constexpr bool DIRECT = SPLIT > 0 && XP == 0;  // FP32 split front half: X written from the loops
-  using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM, FACT, DIRECT>;
+  static_assert(!HALO || (FACT && SPLIT == 0), "whole-neighbour halos in the acoustic fused step");
+  using P = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM, FACT, DIRECT, HALO>;
   constexpr int Np = S::Np, Nfp = S::Nfp, NFN = S::NFN, Mpad = S::Mpad, RT = S::RT;
   constexpr int Nf = P::Nf, REC = P::REC, EBP = P::EBP;
   constexpr int NTILE = RT * (EB / TN);  // tiles of 4 output nodes x TN elements
@@ -500,11 +514,30 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     }
   };
   // neighbour traces of block b that live outside it: 4-byte async copies
-  // (cp.async) into trace buffer s, layout [Nf][4 Nfp][EBP], face node fastest
+  // (cp.async) into trace buffer s, layout [Nf][4 Nfp][EBP], face node fastest;
+  // HALO: the whole neighbour, one bulk copy per (element, face) slot of
+  // buffer s, every thread arriving once on its barrier after registering
+  // the bytes of its own copies
   auto issue_gathers = [&](const StepArgs& a, int lb, int s) {
     const int k0 = lb * EB;
     const int4* nb_s = reinterpret_cast<const int4*>(stage(s) + P::sNbr);
     float* T = smem + (s ? P::oT1 : P::oT0);
+    if constexpr (HALO) {
+      constexpr uint32_t kElem = uint32_t(Nf * Np * 4);
+      for (int i = tid; i < EB * 4; i += NT) {
+        const int e = i >> 2, f = i & 3;
+        const int4 nb = nb_s[e];
+        const int w = (f == 0) ? nb.x : (f == 1) ? nb.y : (f == 2) ? nb.z : nb.w;
+        if (w < 0) continue;
+        const int kn = w >> kNbrShift;
+        const int le = kn - k0;
+        if (le >= 0 && le < EB) continue;
+        mbar_expect_tx(&bars[3 + s], kElem);
+        tma_bulk_g2s(T + i * Nf * Np, a.q + size_t(kn) * Nf * Np, kElem, &bars[3 + s]);
+      }
+      mbar_arrive(&bars[3 + s]);
+      return;
+    }
     for (int i = tid; i < EB * NFN; i += NT) {
       const int fm = i % NFN, e = i / NFN;
       const int f = fm / Nfp, m = fm - f * Nfp;
@@ -527,6 +560,8 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     mbar_init(&bars[2], 1);
+    mbar_init(&bars[3], NT);  // halo buffers: one arrival per thread
+    mbar_init(&bars[4], NT);
     fence_barrier_init();
   }
   __syncthreads();
@@ -561,9 +596,11 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     const int k0 = lb * EB;
     if (b + G < nblk) prov.get(b + G, nxt_a, nxt_lb);
     bool ok = mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), err);
-    cp_async_wait_all();  // this block's neighbour traces
+    if constexpr (HALO) ok = mbar_wait_bounded(&bars[3 + s], uint32_t((it >> 1) & 1), err) && ok;
+    else cp_async_wait_all();  // this block's neighbour traces
     if (!__syncthreads_and(ok)) {
       mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), nullptr);
+      if constexpr (HALO) mbar_wait_bounded(&bars[3 + s], uint32_t((it >> 1) & 1), nullptr);
       return;
     }
     // everyone is past the previous block: stage s^1, sR, the inputs and trace buffer s^1 are free
@@ -681,6 +718,9 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
           float pP, vP0, vP1, vP2;
           if (src.x >= 0) {
             const float* qn = sQ + src.x + sPtab[src.y + m];
+            pP = qn[0]; vP0 = qn[Np]; vP1 = qn[2 * Np]; vP2 = qn[3 * Np];
+          } else if constexpr (HALO) {
+            const float* qn = sT + fi * Nf * Np + sPtab[src.y + m];
             pP = qn[0]; vP0 = qn[Np]; vP1 = qn[2 * Np]; vP2 = qn[3 * Np];
           } else {
             const float* T = sT + fm * EBP + e;
@@ -1093,19 +1133,20 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
 // One solve per launch (dg_rhs / dg_step); SPLIT > 0: front half of the split
 // step writing X in column tiles of SPLIT elements (FP32 rows, or XP BF16
 // pieces in the tensor-core chunk layout when XP > 0).
-template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT = 0, int XP = 0>
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT = 0, int XP = 0,
+          bool HALO = false>
 __global__ void __launch_bounds__(NT) dg_step_kernel(const StepArgs a) {
   SingleSolve p{a, EB};
-  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, SPLIT, XP>(p);
+  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, SPLIT, XP, HALO>(p);
 }
 
 // Every solve of a batch (same model and N) in one persistent launch; the
 // per-solve step index, AB3 phase and buffer parity are read from device
 // memory.  SPLIT > 0: front half of the batch's split step.
-template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT = 0>
+template <int MODEL, int N, int EB, int TN, int NT, bool OPS_SMEM, bool R_SMEM, int SPLIT = 0, bool HALO = false>
 __global__ void __launch_bounds__(NT) dg_step_batched_kernel(const BatchArgs b) {
   SolveBatch p{b};
-  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, SPLIT, 0>(p);
+  step_body<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, SPLIT, 0, HALO>(p);
 }
 
 }  // namespace dgk

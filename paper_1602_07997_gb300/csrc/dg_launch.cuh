@@ -13,18 +13,21 @@ constexpr int threads_for() {
   return (u + 31) / 32 * 32;
 }
 
-template <int MODEL, int N, int EB, bool OPS_SMEM, bool R_SMEM, int TN = 1, int NT = threads_for<N, EB, TN>()>
+// HALO: neighbours outside the block fetched whole by bulk copies (acoustic).
+template <int MODEL, int N, int EB, bool OPS_SMEM, bool R_SMEM, int TN = 1, int NT = threads_for<N, EB, TN>(),
+          bool HALO = false>
 KernelCfg make_cfg() {
-  static_assert(Plan<MODEL, N, EB, OPS_SMEM, R_SMEM, MODEL == 0>::bytes <= 227 * 1024, "shared memory budget");
+  static_assert(Plan<MODEL, N, EB, OPS_SMEM, R_SMEM, MODEL == 0, false, HALO>::bytes <= 227 * 1024,
+                "shared memory budget");
   KernelCfg c;
   c.EB = EB;
   c.TN = TN;
   c.NT = NT;
   c.ops_smem = OPS_SMEM;
   c.r_smem = R_SMEM;
-  c.smem = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM, MODEL == 0>::bytes;
-  c.fn = dg_step_kernel<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>;
-  c.fn_batched = dg_step_batched_kernel<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM>;
+  c.smem = Plan<MODEL, N, EB, OPS_SMEM, R_SMEM, MODEL == 0, false, HALO>::bytes;
+  c.fn = dg_step_kernel<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, 0, 0, HALO>;
+  c.fn_batched = dg_step_batched_kernel<MODEL, N, EB, TN, NT, OPS_SMEM, R_SMEM, 0, HALO>;
   c.split = 0;
   c.fn_gemm = nullptr;
   c.fn_gemm_batched = nullptr;

@@ -156,10 +156,6 @@ __device__ __forceinline__ void tc_prod(uint32_t tcol, uint64_t a0, uint64_t b0,
              (ha == 0 && hb == 0) ? (first ^ 1u) : 1u);
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
