@@ -212,10 +212,10 @@ struct Plan {
   static constexpr int oT0 = round4(oXsur + nXsur);
   static constexpr int oT1 = round4(oT0 + nT);
   static constexpr int oOps = round4(oT1 + nT);
-  static constexpr int oFn = round4(oOps + nOps);          // [EB][4] float4: n, Fscale
+  static constexpr int oFn = round4(oOps + nOps);          // [4][EB] float4: n, Fscale
   static constexpr int oNt = oFn + EB * 16;                // [4 x 3][EBP]: normals, element fastest (FACT)
-  static constexpr int oCo = round4(oNt + (FACT ? 12 * EBP : 0));  // [EB][4] float4: penalty coefficients (FACT)
-  static constexpr int oFi = oCo + (FACT ? EB * 16 : 0);   // [EB][4] int2: neighbour source (FACT)
+  static constexpr int oCo = round4(oNt + (FACT ? 12 * EBP : 0));  // [4][EB] float4: penalty coefficients (FACT)
+  static constexpr int oFi = oCo + (FACT ? EB * 16 : 0);   // [4][EB] int2: neighbour source (FACT)
   static constexpr int oFtab = oFi + (FACT ? EB * 8 : 0);  // int [10][Nfp]
   static constexpr int oPtab = oFtab + 10 * S::Nfp;        // int [4][6][Nfp]: neighbour node (FACT)
   static constexpr int oBar = round4(oPtab + (FACT ? 24 * S::Nfp : 0));
@@ -618,9 +618,11 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       }
     }
 
-    // -------- face normals and Fscale (n = g N_f / |g N_f|)
+    // -------- face normals and Fscale (n = g N_f / |g N_f|); the per-face
+    // arrays are face-major, entry i = f EB + e (element-fastest lanes read
+    // consecutive entries)
     for (int i = tid; i < EB * 4; i += NT) {
-      const int e = i >> 2, f = i & 3;
+      const int e = i % EB, f = i / EB;
       const float4 fn = face_normal(sRec + e * REC, f);
       *reinterpret_cast<float4*>(sFn + i * 4) = fn;
       if constexpr (FACT) {
@@ -703,10 +705,11 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       for (int i = tid; i < EB * NFN; i += NT) {
         const int fm = DIRECT ? i / EB : i % NFN, e = DIRECT ? i % EB : i / NFN;
         const int f = fm / Nfp, m = fm - f * Nfp;
-        const int fi = e * 4 + f;
-        const int2 src = sFi[fi];
-        const float4 fn = *reinterpret_cast<const float4*>(sFn + fi * 4);
-        const float4 co = sCo[fi];
+        const int fe = f * EB + e;  // per-face arrays
+        const int fi = e * 4 + f;   // halo slot
+        const int2 src = sFi[fe];
+        const float4 fn = *reinterpret_cast<const float4*>(sFn + fe * 4);
+        const float4 co = sCo[fe];
         const int nM = sFtab[f * Nfp + m];
         const float* qe = sQ + e * P::QS + nM;
         const float pM = qe[0], vM0 = qe[Np], vM1 = qe[2 * Np], vM2 = qe[3 * Np];
@@ -763,7 +766,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
         }
       }
       const float* qe = sQ + e * P::QS;
-      const float4 fn = *reinterpret_cast<const float4*>(sFn + (e * 4 + f) * 4);
+      const float4 fn = *reinterpret_cast<const float4*>(sFn + (f * EB + e) * 4);
       const float* gM = sRec + e * REC;
       float qM[Nf];
 #pragma unroll
