@@ -201,8 +201,14 @@ struct Plan {
   static constexpr int nR = R_SMEM ? 2 * nQ : 0;
   static constexpr int nXvol = DIRECT ? 0 : (MODEL == 0 ? 4 : 12) * S::Np * EBP;
   static constexpr int nXsur = DIRECT ? 0 : (FACT ? 2 : Nf) * S::NFN * EBP;
-  static constexpr int nT = HALO ? 4 * EB * Nf * S::Np     // halo slots [EB][4][Nf][Np]
+  // halo slot stride: Nf Np floats, + 4 when that is a multiple of 8 words
+  // (the 4 slots of an element then start in different bank groups)
+  static constexpr int HS = Nf * S::Np + ((Nf * S::Np) % 8 == 0 ? 4 : 0);
+  static constexpr int nT = HALO ? 4 * EB * HS              // halo slots [EB][4][HS]
                                 : Nf * S::NFN * EBP;      // neighbour traces [Nf][4Nfp][EBP]
+  // per-face arrays [4][EBF]: the odd row stride keeps the 4 faces of an
+  // element in different banks when lanes run over face nodes
+  static constexpr int EBF = EB + 1;
   static constexpr int nOps = OPS_SMEM ? S::KD * S::Mpad : 0;
   static constexpr int oStage0 = 0;
   static constexpr int oStage1 = oStage0 + nStage;
@@ -212,11 +218,11 @@ struct Plan {
   static constexpr int oT0 = round4(oXsur + nXsur);
   static constexpr int oT1 = round4(oT0 + nT);
   static constexpr int oOps = round4(oT1 + nT);
-  static constexpr int oFn = round4(oOps + nOps);          // [4][EB] float4: n, Fscale
-  static constexpr int oNt = oFn + EB * 16;                // [4 x 3][EBP]: normals, element fastest (FACT)
-  static constexpr int oCo = round4(oNt + (FACT ? 12 * EBP : 0));  // [4][EB] float4: penalty coefficients (FACT)
-  static constexpr int oFi = oCo + (FACT ? EB * 16 : 0);   // [4][EB] int2: neighbour source (FACT)
-  static constexpr int oFtab = oFi + (FACT ? EB * 8 : 0);  // int [10][Nfp]
+  static constexpr int oFn = round4(oOps + nOps);          // [4][EBF] float4: n, Fscale
+  static constexpr int oNt = oFn + EBF * 16;               // [4 x 3][EBP]: normals, element fastest (FACT)
+  static constexpr int oCo = round4(oNt + (FACT ? 12 * EBP : 0));  // [4][EBF] float4: penalty coefficients (FACT)
+  static constexpr int oFi = oCo + (FACT ? EBF * 16 : 0);  // [4][EBF] int2: neighbour source (FACT)
+  static constexpr int oFtab = oFi + (FACT ? EBF * 8 : 0); // int [10][Nfp]
   static constexpr int oPtab = oFtab + 10 * S::Nfp;        // int [4][6][Nfp]: neighbour node (FACT)
   static constexpr int oBar = round4(oPtab + (FACT ? 24 * S::Nfp : 0));
   static constexpr int nFloats = oBar + 10;                // 5 mbarriers
@@ -533,7 +539,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
         const int le = kn - k0;
         if (le >= 0 && le < EB) continue;
         mbar_expect_tx(&bars[3 + s], kElem);
-        tma_bulk_g2s(T + i * Nf * Np, a.q + size_t(kn) * Nf * Np, kElem, &bars[3 + s]);
+        tma_bulk_g2s(T + i * P::HS, a.q + size_t(kn) * Nf * Np, kElem, &bars[3 + s]);
       }
       mbar_arrive(&bars[3 + s]);
       return;
@@ -619,12 +625,13 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     }
 
     // -------- face normals and Fscale (n = g N_f / |g N_f|); the per-face
-    // arrays are face-major, entry i = f EB + e (element-fastest lanes read
+    // arrays are face-major, entry f EBF + e (element-fastest lanes read
     // consecutive entries)
     for (int i = tid; i < EB * 4; i += NT) {
       const int e = i % EB, f = i / EB;
       const float4 fn = face_normal(sRec + e * REC, f);
-      *reinterpret_cast<float4*>(sFn + i * 4) = fn;
+      const int fe = f * P::EBF + e;
+      *reinterpret_cast<float4*>(sFn + fe * 4) = fn;
       if constexpr (FACT) {
         sNt[(3 * f + 0) * EBP + e] = fn.x;
         sNt[(3 * f + 1) * EBP + e] = fn.y;
@@ -651,7 +658,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
         } else {
           co = make_float4(0.f, -fs * kap, -fs * rinv, 0.f);
         }
-        sCo[i] = co;
+        sCo[fe] = co;
         const int4 nb = sNbr[e];
         const int w = (f == 0) ? nb.x : (f == 1) ? nb.y : (f == 2) ? nb.z : nb.w;
         int2 fi = make_int2(-1, 0);
@@ -660,7 +667,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
           fi.x = (le >= 0 && le < EB) ? le * P::QS : -2;
           fi.y = ((w & 3) * 6 + ((w >> 2) & 7)) * Nfp;
         }
-        sFi[i] = fi;
+        sFi[fe] = fi;
       }
     }
     // -------- volume inputs (node index fastest: conflict-free reads of q;
@@ -705,7 +712,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       for (int i = tid; i < EB * NFN; i += NT) {
         const int fm = DIRECT ? i / EB : i % NFN, e = DIRECT ? i % EB : i / NFN;
         const int f = fm / Nfp, m = fm - f * Nfp;
-        const int fe = f * EB + e;  // per-face arrays
+        const int fe = f * P::EBF + e;  // per-face arrays
         const int fi = e * 4 + f;   // halo slot
         const int2 src = sFi[fe];
         const float4 fn = *reinterpret_cast<const float4*>(sFn + fe * 4);
@@ -723,7 +730,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
             const float* qn = sQ + src.x + sPtab[src.y + m];
             pP = qn[0]; vP0 = qn[Np]; vP1 = qn[2 * Np]; vP2 = qn[3 * Np];
           } else if constexpr (HALO) {
-            const float* qn = sT + fi * Nf * Np + sPtab[src.y + m];
+            const float* qn = sT + fi * P::HS + sPtab[src.y + m];
             pP = qn[0]; vP0 = qn[Np]; vP1 = qn[2 * Np]; vP2 = qn[3 * Np];
           } else {
             const float* T = sT + fm * EBP + e;
@@ -766,7 +773,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
         }
       }
       const float* qe = sQ + e * P::QS;
-      const float4 fn = *reinterpret_cast<const float4*>(sFn + (f * EB + e) * 4);
+      const float4 fn = *reinterpret_cast<const float4*>(sFn + (f * P::EBF + e) * 4);
       const float* gM = sRec + e * REC;
       float qM[Nf];
 #pragma unroll
