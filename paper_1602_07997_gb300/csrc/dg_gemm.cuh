@@ -478,6 +478,7 @@ struct GemmB {
   static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
   static_assert(MT % 4 == 0 && NEG % 4 == 0 && TM % 4 == 0, "16-byte copies and loads");
   static_assert(!HALF || NARROW, "half column tiles with the narrow thread tile");
+  static_assert(NS >= 2, "the copy of a chunk is issued after the barrier that retires its stage");
 };
 
 template <int MODEL, int N, bool NARROW = false, bool SMALL = false, bool HALF = false>
@@ -599,9 +600,11 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
   // products; they still copy and meet every barrier
   const bool rows_live = row0 + il < Np;
   for (int c = 0; c < NCH; ++c) {
-    issue(c + NS - 1);
-    cp_async_wait_n<NS - 1>();  // chunk c has landed
+    cp_async_wait_n<NS - 2>();  // chunk c has landed (chunks up to c + NS - 2 may be in flight)
+    // ... for every thread; and every thread is done with chunk c - 1, whose
+    // stage the next copy refills: one barrier per chunk
     __syncthreads();
+    issue(c + NS - 1);
     const float* A = sA(c % NS) + il;
     const float* B = sB(c % NS) + e0;
     if (c < NVC) {
@@ -749,7 +752,6 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
         }
       }
     }
-    __syncthreads();  // stage c % NS is refilled by chunk c + NS
   }
   cp_async_wait_n<0>();
   __syncthreads();
