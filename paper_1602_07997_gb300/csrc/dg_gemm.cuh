@@ -459,7 +459,10 @@ struct GemmB {
   static constexpr int MINB = SMALL || HALF ? 2 : 1;  // resident CTAs the registers are sized for
   static constexpr int MP2 = (Np + MT - 1) / MT * MT;     // padded rows of the split operator blob
   static constexpr int KC = 16;                           // K chunk (volume indices or face nodes)
-  static constexpr int NS = 3;                            // cp.async stages
+  // cp.async stages: 4 for the acoustic tiles that have the SM to themselves,
+  // 3 where two CTAs share it (SMALL, HALF) and for the elastic tiles (a
+  // fourth stage cost elastic N = 3 a third of its resident CTAs)
+  static constexpr int NS = (MODEL == 0 && !SMALL && !HALF) ? 4 : 3;
   static constexpr int NT = (MT / TM) * (NEG / TE);       // threads per CTA
   static constexpr int MTILES_R = (Np + MT - 1) / MT;     // row tiles
   static constexpr int MTILES_L = MTILES_R * NSUB;        // CTAs per column tile (launch grid: x column tiles)
