@@ -121,7 +121,7 @@ struct GemmA {
   // per buffer: A rows (3 JC volume, CC lift) x MT, X rows (NV JC volume;
   // lift: 2 CC streams + 12 normal rows acoustic, Nf CC elastic) x NE
   static constexpr int nA = (3 * JC > CC ? 3 * JC : CC) * MT;
-  static constexpr int LB = MODEL == 0 ? 2 * CC + 12 : Nf * CC;
+  static constexpr int LB = XRows<MODEL, N>::NXS * CC + 12;
   static constexpr int nB = (NV * JC > LB ? NV * JC : LB) * NE;
   static constexpr int NEP = NE + (TN == 2 ? 2 : 1);       // row stride of the staged RHS tile
   static constexpr int nOut = Nf * MT * NEP;              // RHS tile [Nf][MT][NEP], reuses the B buffers
@@ -182,11 +182,10 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
         const int f = rr / nc, cc = rr - f * nc;
         cp_async16(B + (f * CC + cc) * NE + 4 * q4, X + size_t(NV * Np + f * NFN + c0 + cc) * NE + 4 * q4);
       }
-      if constexpr (MODEL == 0) {  // the face normals, after the two streams
-        for (int i = tid; i < 12 * (NE / 4); i += NT) {
-          const int q4 = i % (NE / 4), r = i / (NE / 4);
-          cp_async16(B + (2 * CC + r) * NE + 4 * q4, X + size_t(KXM + r) * NE + 4 * q4);
-        }
+      // the face normals, after the streams
+      for (int i = tid; i < 12 * (NE / 4); i += NT) {
+        const int q4 = i % (NE / 4), r = i / (NE / 4);
+        cp_async16(B + (NXS * CC + r) * NE + 4 * q4, X + size_t(KXM + r) * NE + 4 * q4);
       }
     }
     cp_async_commit();
@@ -212,12 +211,19 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
 #pragma unroll
       for (int v = 0; v < RV; ++v) acc[x][t][v] = 0.f;
   float accS[MODEL == 0 ? 1 : 6][TN][RV];  // elastic LIFT P_sigma
+  float W[MODEL == 0 ? 1 : 3][TN][RV];     // elastic LIFT_f (Fscale dv) of the current face f
 #pragma unroll
   for (int x = 0; x < (MODEL == 0 ? 1 : 6); ++x)
 #pragma unroll
     for (int t = 0; t < TN; ++t)
 #pragma unroll
       for (int v = 0; v < RV; ++v) accS[x][t][v] = 0.f;
+#pragma unroll
+  for (int x = 0; x < (MODEL == 0 ? 1 : 3); ++x)
+#pragma unroll
+    for (int t = 0; t < TN; ++t)
+#pragma unroll
+      for (int v = 0; v < RV; ++v) W[x][t][v] = 0.f;
 
   issue(0);
   for (int c = 0; c < NCH; ++c) {
@@ -323,24 +329,54 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
           }
         }
       } else {
+        // Fscale p_v onto Rv; Fscale dv face by face onto W, which joins the
+        // stress LIFT as lambda (n.W) I + mu (n W^T + W n^T) at the face end
+        int cc = 0;
+        while (cc < nc) {
+          const int f = (c0 + cc) / Nfp;
+          const int fe = (f + 1) * Nfp - c0;  // end of face f, chunk-relative
+          const int ce = fe < nc ? fe : nc;
 #pragma unroll 2
-        for (int cc = 0; cc < nc; ++cc) {
-          float4 l[RQ];
+          for (; cc < ce; ++cc) {
+            float4 l[RQ];
 #pragma unroll
-          for (int q = 0; q < RQ; ++q) l[q] = *reinterpret_cast<const float4*>(A + cc * MT + 4 * q);
+            for (int q = 0; q < RQ; ++q) l[q] = *reinterpret_cast<const float4*>(A + cc * MT + 4 * q);
 #pragma unroll
-          for (int t = 0; t < TN; ++t) {
+            for (int t = 0; t < TN; ++t) {
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-              const float p = B[(f * CC + cc) * NE + t];
+              for (int x = 0; x < 3; ++x) {
+                const float p = B[(x * CC + cc) * NE + t];
 #pragma unroll
-              for (int q = 0; q < RQ; ++q) fma4(&acc[9 + f][t][4 * q], l[q], p);
+                for (int q = 0; q < RQ; ++q) fma4(&acc[9 + x][t][4 * q], l[q], p);
+              }
+#pragma unroll
+              for (int x = 0; x < 3; ++x) {
+                const float p = B[((3 + x) * CC + cc) * NE + t];
+#pragma unroll
+                for (int q = 0; q < RQ; ++q) fma4(&W[x][t][4 * q], l[q], p);
+              }
             }
+          }
+          if (cc == fe) {
 #pragma unroll
-            for (int f = 0; f < 6; ++f) {
-              const float p = B[((3 + f) * CC + cc) * NE + t];
+            for (int t = 0; t < TN; ++t) {
+              const int k = ntile * NE + e0 + t;
+              const float* gk = a.rec + size_t(k < a.K ? k : a.K - 1) * REC;
+              const float lam = __ldg(gk + 9), mu = __ldg(gk + 10);
+              const float nx = B[(NXS * CC + 3 * f + 0) * NE + t], ny = B[(NXS * CC + 3 * f + 1) * NE + t],
+                          nz = B[(NXS * CC + 3 * f + 2) * NE + t];
 #pragma unroll
-              for (int q = 0; q < RQ; ++q) fma4(&accS[f][t][4 * q], l[q], p);
+              for (int v = 0; v < RV; ++v) {
+                const float w0 = W[0][t][v], w1 = W[1][t][v], w2 = W[2][t][v];
+                const float lnw = lam * (nx * w0 + ny * w1 + nz * w2);
+                accS[0][t][v] += lnw + 2.f * mu * nx * w0;
+                accS[1][t][v] += lnw + 2.f * mu * ny * w1;
+                accS[2][t][v] += lnw + 2.f * mu * nz * w2;
+                accS[3][t][v] += mu * (nx * w1 + ny * w0);
+                accS[4][t][v] += mu * (nx * w2 + nz * w0);
+                accS[5][t][v] += mu * (ny * w2 + nz * w1);
+                W[0][t][v] = W[1][t][v] = W[2][t][v] = 0.f;
+              }
             }
           }
         }
@@ -470,7 +506,7 @@ struct GemmB {
   static constexpr int NLC = (NFN + KC - 1) / KC;         // lift chunks
   // X rows of one chunk: NV KC (volume); lift: 2 KC streams + 12 normal
   // rows (acoustic), Nf KC (elastic)
-  static constexpr int LB = MODEL == 0 ? 2 * KC + 12 : Nf * KC;
+  static constexpr int LB = XRows<MODEL, N>::NXS * KC + 12;
   static constexpr int nA = 3 * KC * MT;                  // operator rows of one stage
   static constexpr int nB = (NV * KC > LB ? NV * KC : LB) * NEG;  // X rows of one stage
   static constexpr int NEP = NEG + 1;                     // row stride of the staged RHS field
@@ -540,11 +576,10 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
           const int f = rr / nc, cc = rr - f * nc;
           cp_async16(B + (f * KC + cc) * NE + 4 * q4, X + size_t(NV * Np + f * NFN + c0 + cc) * XNE + 4 * q4);
         }
-        if constexpr (MODEL == 0) {  // the face normals, after the two streams
-          for (int i = tid; i < 12 * (NE / 4); i += NT) {
-            const int q4 = i % (NE / 4), r = i / (NE / 4);
-            cp_async16(B + (2 * KC + r) * NE + 4 * q4, X + size_t(KXM + r) * XNE + 4 * q4);
-          }
+        // the face normals, after the streams
+        for (int i = tid; i < 12 * (NE / 4); i += NT) {
+          const int q4 = i % (NE / 4), r = i / (NE / 4);
+          cp_async16(B + (NXS * KC + r) * NE + 4 * q4, X + size_t(KXM + r) * XNE + 4 * q4);
         }
       }
     }
@@ -570,6 +605,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
   for (int t = 0; t < (MODEL == 0 ? TE : 1); ++t)
 #pragma unroll
     for (int v = 0; v < TM; ++v) lf[t][v] = 0.f;
+  float lamv[TE], muv[TE];  // elastic: Lame coefficients of the element columns (set at the boundary)
 
   auto ldA = [&](const float* p, float* o) {  // TM consecutive rows, as float4s
 #pragma unroll
@@ -675,6 +711,8 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
             }
           } else {
             const float lam = __ldg(gk + 9), mu = __ldg(gk + 10);
+            lamv[t] = lam;
+            muv[t] = mu;
 #pragma unroll
             for (int v = 0; v < TM; ++v) {
               float gv[3][3];
@@ -691,6 +729,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
               acc[3][t][v] = mu * (gv[0][1] + gv[1][0]);
               acc[4][t][v] = mu * (gv[0][2] + gv[2][0]);
               acc[5][t][v] = mu * (gv[1][2] + gv[2][1]);
+              acc[6][t][v] = acc[7][t][v] = acc[8][t][v] = 0.f;  // W: LIFT_f dv of the current face
             }
           }
         }
@@ -737,20 +776,48 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
           }
         }
       } else {
+        // Fscale p_v onto Rv (accumulators 9..11); Fscale dv face by face
+        // onto W (6..8), which joins the stress components as
+        // lambda (n.W) I + mu (n W^T + W n^T) once face f is complete
+        int cc = 0;
+        while (cc < nc) {
+          const int f = (c0 + cc) / Nfp;
+          const int fe = (f + 1) * Nfp - c0;  // end of face f, chunk-relative
+          const int ce = fe < nc ? fe : nc;
 #pragma unroll 2
-        for (int cc = 0; cc < nc; ++cc) {
-          float l[TM];
-          ldA(A + cc * MT, l);
+          for (; cc < ce; ++cc) {
+            float l[TM];
+            ldA(A + cc * MT, l);
 #pragma unroll
-          for (int f = 0; f < 9; ++f) {
-            float pf[TE];
-            ldB(B + (f * KC + cc) * NE, pf);
-            // P_v,c onto Rv_c (accumulators 9..11), P_sig,x onto S_x (0..5)
-            const int slot = f < 3 ? 9 + f : f - 3;
+            for (int x = 0; x < 6; ++x) {
+              float pf[TE];
+              ldB(B + (x * KC + cc) * NE, pf);
+              const int slot = x < 3 ? 9 + x : 3 + x;
+#pragma unroll
+              for (int t = 0; t < TE; ++t)
+#pragma unroll
+                for (int v = 0; v < TM; ++v) acc[slot][t][v] = fmaf(l[v], pf[t], acc[slot][t][v]);
+            }
+          }
+          if (cc == fe) {
+            float nv[3][TE];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) ldB(B + (NXS * KC + 3 * f + x) * NE, nv[x]);
 #pragma unroll
             for (int t = 0; t < TE; ++t)
 #pragma unroll
-              for (int v = 0; v < TM; ++v) acc[slot][t][v] = fmaf(l[v], pf[t], acc[slot][t][v]);
+              for (int v = 0; v < TM; ++v) {
+                const float w0 = acc[6][t][v], w1 = acc[7][t][v], w2 = acc[8][t][v];
+                const float nx = nv[0][t], ny = nv[1][t], nz = nv[2][t];
+                const float lnw = lamv[t] * (nx * w0 + ny * w1 + nz * w2), m2 = 2.f * muv[t];
+                acc[0][t][v] += lnw + m2 * nx * w0;
+                acc[1][t][v] += lnw + m2 * ny * w1;
+                acc[2][t][v] += lnw + m2 * nz * w2;
+                acc[3][t][v] += muv[t] * (nx * w1 + ny * w0);
+                acc[4][t][v] += muv[t] * (nx * w2 + nz * w0);
+                acc[5][t][v] += muv[t] * (ny * w2 + nz * w1);
+                acc[6][t][v] = acc[7][t][v] = acc[8][t][v] = 0.f;
+              }
           }
         }
       }

@@ -56,14 +56,15 @@ struct Sz {
 
 // Rows per element of the FP32 split step's GEMM input X: NV volume inputs
 // per node, NXS surface streams per face node (acoustic: the pressure penalty
-// and psi, the magnitude of the velocity penalty psi n_f; elastic: the 9
-// penalties), then, acoustic, the 4 x 3 face-normal components.
+// and psi, the magnitude of the velocity penalty psi n_f; elastic: Fscale p_v
+// and Fscale dv, of which the 9 penalties are made with the face normal and
+// the Lame coefficients), then the 4 x 3 face-normal components.
 template <int MODEL, int N>
 struct XRows {
   static constexpr int NV = MODEL == 0 ? 4 : 12;
-  static constexpr int NXS = MODEL == 0 ? 2 : 9;
+  static constexpr int NXS = MODEL == 0 ? 2 : 6;
   static constexpr int KXM = NV * Sz<N>::Np + NXS * Sz<N>::NFN;
-  static constexpr int KX = KXM + (MODEL == 0 ? 12 : 0);
+  static constexpr int KX = KXM + 12;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -299,9 +300,12 @@ __device__ __forceinline__ float4 face_normal(const float* g, int f) {
 //   gM: the element's record; f: its face; qM, qP: own and neighbour traces
 //   (qP unused on the boundary); fn = (n_x, n_y, n_z, Fscale) of the face.
 //   pen[Nf]: acoustic (dp, dv_x, dv_y, dv_z), elastic (p_v[3], P_sigma[6]).
+//   pvdv (elastic, optional): instead of pen, (Fscale p_v, Fscale dv) -- the
+//   stress penalty is lambda (n.dv) I + mu (n dv^T + dv n^T), times Fscale
 template <int MODEL>
 __device__ __forceinline__ void face_penalty(const float* gM, int f, bool bnd, const float* qM, const float* qPv,
-                                             const float4 fn, int flux, int bc, float* pen) {
+                                             const float4 fn, int flux, int bc, float* pen,
+                                             float* pvdv = nullptr) {
   const float nx = fn.x, ny = fn.y, nz = fn.z, fs = fn.w;
   if constexpr (MODEL == 0) {
     const float kap = gM[9], rinv = gM[10], ZM = gM[11], zP = gM[12 + f];
@@ -376,6 +380,14 @@ __device__ __forceinline__ void face_penalty(const float* gM, int f, bool bnd, c
         dv[c] = jv[c];
         pv[c] = rinv * jt[c];
       }
+    }
+    if (pvdv) {  // the two vectors the 9 penalties are made of, Fscale included
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pvdv[c] = fs * pv[c];
+        pvdv[3 + c] = fs * dv[c];
+      }
+      return;
     }
     const float ndv = nx * dv[0] + ny * dv[1] + nz * dv[2];
     pen[0] = fs * pv[0];
@@ -632,16 +644,17 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       const float4 fn = face_normal(sRec + e * REC, f);
       const int fe = f * P::EBF + e;
       *reinterpret_cast<float4*>(sFn + fe * 4) = fn;
+      if constexpr (DIRECT) {  // the face normals are GEMM inputs too
+        constexpr int KXM = XRows<MODEL, N>::KXM;
+        *xrow(a, KXM + 3 * f + 0, k0 + e) = fn.x;
+        *xrow(a, KXM + 3 * f + 1, k0 + e) = fn.y;
+        *xrow(a, KXM + 3 * f + 2, k0 + e) = fn.z;
+      }
       if constexpr (FACT) {
         sNt[(3 * f + 0) * EBP + e] = fn.x;
         sNt[(3 * f + 1) * EBP + e] = fn.y;
         sNt[(3 * f + 2) * EBP + e] = fn.z;
-        if constexpr (DIRECT) {
-          constexpr int KXM = XRows<MODEL, N>::KXM;
-          *xrow(a, KXM + 3 * f + 0, k0 + e) = fn.x;
-          *xrow(a, KXM + 3 * f + 1, k0 + e) = fn.y;
-          *xrow(a, KXM + 3 * f + 2, k0 + e) = fn.z;
-        }
+
         // penalty coefficients of the face, pen_p = A jp + B jvn and
         // psi = C jp + D jvn with jp = [[p]]/2, jvn = [[v]].n/2 (Fscale folded
         // in), and where the neighbour trace comes from: -1 outer boundary,
@@ -779,11 +792,14 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
 #pragma unroll
       for (int c = 0; c < Nf; ++c) qM[c] = qe[c * Np + nM];
       float pen[Nf];
-      face_penalty<MODEL>(gM, f, bnd, qM, qPv, fn, a.flux, a.bc, pen);
-      if constexpr (DIRECT) {
+      if constexpr (DIRECT) {  // elastic: the 6 streams Fscale p_v, Fscale dv
+        static_assert(MODEL == 1 && XRows<MODEL, N>::NXS == 6, "elastic surface streams of X");
+        float pd[6];
+        face_penalty<MODEL>(gM, f, bnd, qM, qPv, fn, a.flux, a.bc, pen, pd);
 #pragma unroll
-        for (int c = 0; c < Nf; ++c) *xrow(a, NVX * Np + c * NFN + fm, k0 + e) = pen[c];
+        for (int c = 0; c < 6; ++c) *xrow(a, NVX * Np + c * NFN + fm, k0 + e) = pd[c];
       } else {
+        face_penalty<MODEL>(gM, f, bnd, qM, qPv, fn, a.flux, a.bc, pen);
         float* X = sXs + fm * EBP + e;
         constexpr int XS = NFN * EBP;
 #pragma unroll

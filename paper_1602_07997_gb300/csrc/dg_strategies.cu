@@ -61,7 +61,7 @@ const KernelCfg* front_cfg(int model, int N) {
   return model == 0 ? &ac[N - 1] : &el[N - 1];
 }
 
-int library_products(int model) { return model == 0 ? 8 : 18; }
+int library_products(int model) { return model == 0 ? 8 : 24; }
 
 // One strided-batched GEMM per (product, input block): for every column tile t
 //   Y_p[t NE + e][i] (+)= sum_r ops2[(arow + r) MP2 + i] X_t[brow + r][e],
@@ -94,14 +94,17 @@ int library_gemms(void* cublas, int model, int N, const StepArgs& a, float* Y, s
     for (int f = 0; f < 4; ++f)                                        // L_f = LIFT_f psi_f
       G(4 + f, 3 * Np + f * Nfp, 4 * Np + NFN + f * Nfp, Nfp, 0.f);
   } else {
-    // X rows: v_0..2, s_cd (3 + 3c + d) (Np each), P_0..8 (4 Nfp each)
+    // X rows: v_0..2, s_cd (3 + 3c + d) (Np each), Fscale p_v,0..2 and
+    // Fscale dv_0..2 (4 Nfp each), face normals
     for (int c = 0; c < 3; ++c)
       for (int d = 0; d < 3; ++d) G(3 * c + d, d * Np, c * Np, Np, 0.f);  // U_cd = D_d v_c
     for (int c = 0; c < 3; ++c) {
       G(9 + c, 0, (3 + 3 * c) * Np, 3 * Np, 0.f);                          // sum_d D_d s_cd
-      G(9 + c, 3 * Np, 12 * Np + c * NFN, NFN, 1.f);                       // + LIFT P_vc
+      G(9 + c, 3 * Np, 12 * Np + c * NFN, NFN, 1.f);                       // + LIFT (Fscale p_v,c)
     }
-    for (int x = 0; x < 6; ++x) G(12 + x, 3 * Np, 12 * Np + (3 + x) * NFN, NFN, 0.f);  // S_x = LIFT P_sig,x
+    for (int f = 0; f < 4; ++f)                                            // W_f,c = LIFT_f (Fscale dv_c)
+      for (int c = 0; c < 3; ++c)
+        G(12 + 3 * f + c, 3 * Np + f * Nfp, 12 * Np + (3 + c) * NFN + f * Nfp, Nfp, 0.f);
   }
   return int(s);
 }
@@ -149,12 +152,29 @@ __global__ void __launch_bounds__(256) library_epilogue_kernel(const StepArgs a,
       const float div = gv[0][0] + gv[1][1] + gv[2][2];
 #pragma unroll
       for (int c = 0; c < 3; ++c) r[c] = y(9 + c);
-      r[3] = lam * div + 2.f * mu * gv[0][0] + y(12);
-      r[4] = lam * div + 2.f * mu * gv[1][1] + y(13);
-      r[5] = lam * div + 2.f * mu * gv[2][2] + y(14);
-      r[6] = mu * (gv[0][1] + gv[1][0]) + y(15);
-      r[7] = mu * (gv[0][2] + gv[2][0]) + y(16);
-      r[8] = mu * (gv[1][2] + gv[2][1]) + y(17);
+      r[3] = lam * div + 2.f * mu * gv[0][0];
+      r[4] = lam * div + 2.f * mu * gv[1][1];
+      r[5] = lam * div + 2.f * mu * gv[2][2];
+      r[6] = mu * (gv[0][1] + gv[1][0]);
+      r[7] = mu * (gv[0][2] + gv[2][0]);
+      r[8] = mu * (gv[1][2] + gv[2][1]);
+      // stress LIFT: lambda (n_f.W_f) I + mu (n_f W_f^T + W_f n_f^T) per face
+      using XR = XRows<MODEL, N>;
+      constexpr int NE = SplitShape<MODEL, N>::NE;
+      const float* nk = a.xg + (size_t(k / NE) * XR::KX + XR::KXM) * NE + k % NE;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const float nx = __ldg(nk + (3 * f) * NE), ny = __ldg(nk + (3 * f + 1) * NE);
+        const float nz = __ldg(nk + (3 * f + 2) * NE);
+        const float w0 = y(12 + 3 * f), w1 = y(13 + 3 * f), w2 = y(14 + 3 * f);
+        const float lnw = lam * (nx * w0 + ny * w1 + nz * w2);
+        r[3] += lnw + 2.f * mu * nx * w0;
+        r[4] += lnw + 2.f * mu * ny * w1;
+        r[5] += lnw + 2.f * mu * nz * w2;
+        r[6] += mu * (nx * w1 + ny * w0);
+        r[7] += mu * (nx * w2 + nz * w0);
+        r[8] += mu * (ny * w2 + nz * w1);
+      }
     }
     if (k == a.src_elem && a.srcvec) {
 #pragma unroll

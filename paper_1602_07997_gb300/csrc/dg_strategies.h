@@ -13,7 +13,7 @@ namespace dgk {
 // 1-3 writing X[tile][row][NE] (FP32); gemm_ne / gemm_kx / gemm_mp2 /
 // gemm_xtile describe X and the row-padded operator blob.
 const KernelCfg* front_cfg(int model, int N);
-// Number of operator products of the model (acoustic 7, elastic 18).
+// Number of library-route GEMM products of the model (acoustic 8, elastic 24).
 int library_products(int model);
 // The operator products of every column tile: cuBLAS strided-batched SGEMMs
 // on the handle's stream (cublas: a cublasHandle_t) into
