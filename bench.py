@@ -276,48 +276,73 @@ def build_meshes(model, Ns):
     return out
 
 
-def cpu_baseline(model="acoustic", Ns=(2, 4), steps=1):
-    """FP64 oracle, single thread, one AB3 step on the full ~2 M-node meshes of
-    the listed degrees (a bounded sample of the sweep)."""
+def cpu_baseline(model="acoustic", Ns=(2, 4), steps=1, steps_mt=0):
+    """FP64 oracle on the full ~2 M-node meshes of the listed degrees (a
+    bounded sample of the sweep): `steps` AB3 steps on one thread and, if
+    steps_mt > 0, `steps_mt` steps on every host core (the oracle's RHS of
+    element chunks in a thread pool -- its einsum loops release the GIL --
+    joined for the same AB3 stepper; the oracle itself is unchanged)."""
     code = r"""
 import json, sys, time, os
 sys.path.insert(0, %r)
 import numpy as np
+from concurrent.futures import ThreadPoolExecutor
 import workloads as W
 from oracle.dg import Solver, AB3Stepper
-res = []
+
+class Chunked:
+    def __init__(self, S, T):
+        self.S, self.pool = S, ThreadPoolExecutor(T)
+        self.chunks = np.array_split(np.arange(S.K), T)
+    def rhs(self, q, step=None):
+        return np.concatenate(list(self.pool.map(lambda E: self.S.rhs(q, step=step, elems=E), self.chunks)))
+
+T = os.cpu_count() or 1
+res, res_mt = [], []
 for N in %r:
     cfg = W.sweep_mesh(%r, N)
     S = Solver(%r, N, cfg["verts"], cfg["tets"], cfg["coeffs"])
     q = W.random_state(S.K, S.Nf, S.ref.Np, seed=0)
-    st = AB3Stepper(S, q, 1e-6)
-    t0 = time.perf_counter()
-    st.step(%d)
-    dt = time.perf_counter() - t0
-    res.append((S.K * S.ref.Np * S.Nf * %d, dt))
-print(json.dumps(res))
-""" % (ROOT, tuple(Ns), model, model, steps, steps)
+    if %d > 0:
+        st = AB3Stepper(S, q, 1e-6)
+        t0 = time.perf_counter()
+        st.step(%d)
+        res.append((S.K * S.ref.Np * S.Nf * %d, time.perf_counter() - t0))
+    if %d > 0:
+        st = AB3Stepper(Chunked(S, T), q, 1e-6)
+        t0 = time.perf_counter()
+        st.step(%d)
+        res_mt.append((S.K * S.ref.Np * S.Nf * %d, time.perf_counter() - t0))
+print(json.dumps({"one": res, "all": res_mt, "threads": T}))
+""" % (ROOT, tuple(Ns), model, model, steps, steps, steps, steps_mt, steps_mt, steps_mt)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if p.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": p.stderr[-500:]}
-    res = json.loads(p.stdout.strip().splitlines()[-1])
-    upd = sum(r[0] for r in res)
-    t = sum(r[1] for r in res)
-    return {"value": upd / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "FP64 oracle, %d AB3 step(s) on the full %s meshes for N=%s, single thread"
-                      % (steps, model, ",".join(str(n) for n in Ns)),
-            "seconds": round(t, 2)}
+    out = json.loads(p.stdout.strip().splitlines()[-1])
+    one = None if not out["one"] else {
+           "value": sum(r[0] for r in out["one"]) / sum(r[1] for r in out["one"]), "unit": UNIT, "cores": 1,
+           "kind": "oracle",
+           "sample": "FP64 oracle, %d AB3 step(s) on the full %s meshes for N=%s, single thread"
+                     % (steps, model, ",".join(str(n) for n in Ns)),
+           "seconds": round(sum(r[1] for r in out["one"]), 2)}
+    if not out["all"]:
+        return one
+    t = sum(r[1] for r in out["all"])
+    return {"value": sum(r[0] for r in out["all"]) / t, "unit": UNIT, "cores": out["threads"], "kind": "oracle",
+            "sample": "FP64 oracle, %d AB3 step(s) on the full %s meshes for N=%s, RHS of element chunks on "
+                      "%d threads" % (steps_mt, model, ",".join(str(n) for n in Ns), out["threads"]),
+            "seconds": round(t, 2), "single_core": one}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     t0 = time.time()
-    base = cpu_baseline("acoustic", Ns=(2, 4), steps=1)
+    base = cpu_baseline("acoustic", Ns=(2, 4), steps=0, steps_mt=4)
     per_step = []
     for _ in range(args.steps):
-        b = cpu_baseline("acoustic", Ns=(2,), steps=1)
+        b = cpu_baseline("acoustic", Ns=(2,), steps=0, steps_mt=4)
         per_step.append(b)
     vals = [b["value"] for b in per_step if b["value"]]
     v = statistics.median(vals) if vals else base["value"]
@@ -565,7 +590,7 @@ def run(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
-        cpu = cpu_baseline(model, Ns=(2, 4), steps=6)  # about 10 s of oracle work
+        cpu = cpu_baseline(model, Ns=(2, 4), steps=6, steps_mt=48)  # about 10 s of oracle work each
 
     served = None
     if rank == 0 and not args.no_serve:
