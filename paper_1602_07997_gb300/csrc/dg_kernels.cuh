@@ -566,7 +566,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       const int le = kn - k0;
       if (le >= 0 && le < EB) continue;
       const int rot = (w >> 2) & 7, f2 = w & 3;
-      const int nP = sFtab[f2 * Nfp + sFtab[4 * Nfp + rot * Nfp + m]];
+      const int nP = FACT ? sPtab[(f2 * 6 + rot) * Nfp + m] : sFtab[f2 * Nfp + sFtab[4 * Nfp + rot * Nfp + m]];
       const float* src = a.q + size_t(kn) * Nf * Np + nP;
 #pragma unroll
       for (int c = 0; c < Nf; ++c) cp_async4(T + (c * NFN + fm) * EBP + e, src + c * Np);
