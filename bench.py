@@ -612,14 +612,17 @@ def run(args, rank, world, local_rank):
 
 
 def kernel_rev():
-    """Hash of the kernel sources (a traffic figure is only valid for them)."""
+    """Hash of the kernel sources without their comments (a traffic figure is
+    only valid for the code it was measured on)."""
     import hashlib
+    import re
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_1602_07997_gb300", "csrc")
     for f in sorted(os.listdir(d)):
         if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+            with open(os.path.join(d, f), encoding="utf-8") as fh:
+                src = re.sub(r"/\*.*?\*/", "", re.sub(r"//[^\n]*", "", fh.read()), flags=re.S)
+            h.update("\n".join(l.rstrip() for l in src.splitlines() if l.strip()).encode())
     return h.hexdigest()[:12]
 
 

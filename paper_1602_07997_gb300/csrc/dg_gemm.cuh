@@ -5,31 +5,33 @@
 // memory next to a block of elements, so the fused kernel must stream it
 // from L2 once per block of a few elements.  The split step instead
 //   kernel A (the fused kernel's front half, SPLIT = NE): stages q, records
-//     and neighbour traces as usual, computes the volume inputs and the
-//     Fscale-weighted penalties, and writes them to a global buffer X laid
-//     out in column tiles of NE elements: X[tile][row][NE] (row = the input
-//     index of the operator products);
-//   kernel B (this file, two designs; the autotuner times both):
+//     and neighbour traces as usual, computes the volume inputs, the surface
+//     streams and the face normals, and writes them from its compute loops to
+//     a global buffer X laid out in column tiles of NE elements:
+//     X[tile][row][NE] (rows of XRows: the input indices of the products);
+//   kernel B (this file; the autotuner times the designs):
 //   design A: a CTA owns 32 output rows x NE elements, one thread 4 (or 8)
-//     rows x TN elements of every one of the 7 (acoustic) / 18 (elastic)
-//     products, double-buffered 16-deep K chunks, and the combination and
-//     AB3 update in the epilogue;
-//   design B: a CTA owns MT output rows x NE elements; operator
-//     rows and X rows stream through shared memory in 16-deep K chunks
-//     (16-byte cp.async, NS-stage ring), every operator row is reused by NE
-//     elements and every X row by MT rows.  One thread accumulates TM rows x
-//     TE elements.  The K loop runs the volume chunks (D_r, D_s, D_t) and then
-//     the LIFT chunks; at the boundary the accumulators of the pure derivative
-//     products are combined with the element's geometric factors into the
-//     RHS components, and the LIFT products accumulate straight onto them:
+//     rows x TN elements of every product, double-buffered 16-deep K chunks,
+//     and the combination and AB3 update in the epilogue;
+//   design B: a CTA owns MT output rows x NE elements (or half of NE: HALF);
+//     operator rows and X rows stream through shared memory in 16-deep K
+//     chunks (16-byte cp.async, NS-stage ring, one barrier per chunk), every
+//     operator row is reused by the CTA's elements and every X row by MT
+//     rows.  One thread accumulates TM rows x TE elements.  The K loop runs
+//     the volume chunks (D_r, D_s, D_t) and then the LIFT chunks; at the
+//     boundary the accumulators of the pure derivative products are combined
+//     with the element's geometric factors into the RHS components, and the
+//     LIFT products accumulate onto them:
 //       acoustic: G_d = D_d p and R = sum_d D_d w_d over the volume chunks;
-//                 then T_c = -(1/rho) sum_d g_cd G_d, and over the LIFT
-//                 chunks r_v,c = T_c + LIFT P_v,c, r_p = R + LIFT P_p
-//                 (4 accumulators per output instead of 7);
+//                 then T_c = -(1/rho) sum_d g_cd G_d; over the LIFT chunks
+//                 r_p = R + LIFT P_p and, face by face, L_f = LIFT_f psi,
+//                 which joins r_v,c = T_c + sum_f n_f,c L_f at each face end;
 //       elastic:  U_cd = D_d v_c and Rv_c = sum_d D_d s_cd over the volume
 //                 chunks; then the stress parts S (lambda div v + 2 mu dv_i/dx_i,
-//                 mu (dv_i/dx_j + dv_j/dx_i)) from U, and over the LIFT chunks
-//                 r_sig = S + LIFT P_sig, r_v,c = Rv_c + LIFT P_v,c.
+//                 mu (dv_i/dx_j + dv_j/dx_i)) from U; over the LIFT chunks
+//                 r_v,c = Rv_c + LIFT (Fscale p_v,c) and, face by face,
+//                 W_f = LIFT_f (Fscale dv), which joins the stress as
+//                 lambda (n_f.W_f) I + mu (n_f W_f^T + W_f n_f^T).
 //   The epilogue stages one field at a time in shared memory and runs the
 //   point source and the AB3 update (Eq. updateScheme) with coalesced accesses.
 #pragma once

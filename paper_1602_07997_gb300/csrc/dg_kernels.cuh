@@ -7,33 +7,35 @@
 //      (1-D TMA: cp.async.bulk + mbarrier, bounded wait); the copy of the
 //      next block into stage s^1, and of this block's AB3 history r^{m-1},
 //      r^{m-2} into shared memory, are issued now and land while it computes;
-//   2. face normals and Fscale = |g N_f| from the inverse metric;
+//      the traces of the neighbours outside the block arrived during the
+//      previous block (4-byte cp.async per face node and field, or, HALO,
+//      the whole neighbour by one bulk copy per element face);
+//   2. per element face: normal and Fscale = |g N_f| from the inverse metric
+//      and, acoustic, the penalty coefficients and the neighbour's source;
 //   3. element-wise GEMM inputs in shared memory, element index fastest:
 //      volume inputs (acoustic p and w_d = -kappa sum_c g_cd v_c; elastic v_c
 //      and s_cd = (1/rho) sum_m g_md sigma_cm) and the Fscale-weighted
 //      penalty terms at the 4 Nfp face nodes (own trace via the face mask,
 //      neighbour trace via the neighbour's face mask and one of the 6 face
 //      rotations; neighbours in the block come from shared memory, the
-//      others from global memory, several face nodes per thread in flight);
+//      others from the gathered traces); acoustic: two surface streams, the
+//      pressure penalty and psi (the velocity penalty is psi n_f);
 //   4. each thread owns a tile of 4 output nodes x TN elements (element
 //      index fastest across lanes) and accumulates every operator product of
 //      its tile in registers
 //      (Section 3.2: 6 Np x Np products + the merged LIFT product for the
 //      acoustic model, 18 + LIFT for the elastic model), operator rows as
 //      float4 from shared memory (or L1 when the blob exceeds the budget);
-//   5. epilogue from registers: geometric combination, point source, and the
-//      AB3 update (Eq. updateScheme) q^{m+1} = q^m + dt (a1 r^m + a2 r^{m-1}
-//      + a3 r^{m-2}); r^m overwrites r^{m-2} in global memory (read before
-//      written, same thread), q^{m+1} goes to the other ping-pong buffer
-//      because neighbours still read q^m.
+//   5. epilogue from registers: geometric combination (acoustic: the velocity
+//      lift sum_f n_f LIFT_f psi), point source, and the AB3 update (Eq.
+//      updateScheme) q^{m+1} = q^m + dt (a1 r^m + a2 r^{m-1} + a3 r^{m-2})
+//      over the block staged in shared memory; r^m overwrites r^{m-2},
+//      q^{m+1} goes to the other ping-pong buffer because neighbours still
+//      read q^m.
+// The split step's front half (SPLIT > 0) runs 1-3 and writes the GEMM
+// inputs to global memory (FP32: straight from the loops of 2-3, DIRECT;
+// tensor cores: BF16 pieces in the tcgen05 operand layout).
 //
-// RHS (Eq. dgLocalRhs) in the form computed here (g_cd = dr_d/dx_c):
-//   acoustic: r_p   = sum_d D_d w_d + LIFT (Fscale dp)
-//             r_v_c = -(1/rho) sum_d g_cd (D_d p) + LIFT (Fscale dv_c)
-//   elastic:  r_v_c = sum_d D_d s_cd + LIFT (Fscale p_v,c)
-//             r_sig_ij = lambda delta_ij div v + mu (dv_i/dx_j + dv_j/dx_i)
-//                        + LIFT (Fscale P_sig,ij),  dv_i/dx_j = sum_d g_jd (D_d v_i)
-// with the penalty terms of Section 2.1.
 #pragma once
 
 #include <cuda_bf16.h>
