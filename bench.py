@@ -24,6 +24,8 @@ Multi-GPU: replicas only (the single-GPU path does not shard); each rank runs
 the whole sweep and value = sum of the ranks' updates / max rank time.
 
 ``--impl reference`` times the FP64 oracle (the reference arm) instead.
+``--model elastic`` times the elastic sweep meshes in the main loop instead of
+the acoustic ones (used to profile the elastic kernels on their own).
 """
 
 import argparse
@@ -44,6 +46,9 @@ METRIC = "DG node-field updates/s and % HBM/FP32 roofline per N; served p50/p99 
 UNIT = "node-field updates/s"
 WORKLOAD = ("acoustic DG sweep N=1..8, jittered Kuhn cube meshes of ~2M nodes per degree, "
             "rho,c~U[1,3], rigid walls, upwind flux, FP32, AB3")
+WORKLOAD_ELASTIC = ("elastic DG sweep N=1..8, jittered Kuhn cube meshes of ~2M nodes per degree, "
+                    "two isotropic layers (lambda,mu,rho~U[1,2] below z=1/2, U[2,3] above), "
+                    "traction-free walls, upwind flux, FP32, AB3")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -81,16 +86,35 @@ def algorithmic(model, N, K):
 
 
 def executed_flops(model, N, K, factored):
-    """FLOPs the kernels execute (same terms as `algorithmic`): the acoustic
-    FP32 paths lift two surface streams per face node and rebuild the
-    velocity lift from the face normals (12 multiply-adds per node) instead of
-    lifting four penalty fields."""
+    """FLOPs the kernels execute (same terms as `algorithmic`).  Factored
+    paths lift surface streams instead of every penalty field: acoustic, two
+    streams per face node, the velocity lift rebuilt from the face normals
+    (12 multiply-adds per node); elastic, six streams (Fscale p_v and
+    Fscale dv), the stress lift folded face by face from lambda, mu and the
+    normal (16 multiply-adds per face and node: n.W, three diagonal and three
+    off-diagonal terms)."""
     byt, flop = algorithmic(model, N, K)
     if not factored:
         return flop
     Np = (N + 1) * (N + 2) * (N + 3) // 6
     Nfp = (N + 1) * (N + 2) // 2
-    return K * (2 * (6 * Np * Np + 8 * Np * Nfp + 12 * Np) + 8 * 4 * Np)
+    if model == "acoustic":
+        return K * (2 * (6 * Np * Np + 8 * Np * Nfp + 12 * Np) + 8 * 4 * Np)
+    return K * (2 * (18 * Np * Np + 24 * Np * Nfp + 64 * Np) + 8 * 9 * Np)
+
+
+def is_factored(model, g, precision, strategy):
+    """Whether g's step lifts surface streams (see `executed_flops`): the
+    library route always; the fused FP32 step for every acoustic kernel and
+    for the elastic split step; neither the plain route nor the tensor-core
+    modes (their front halves lift every penalty field)."""
+    if strategy == "plain":
+        return False
+    if strategy == "library":
+        return True
+    if precision != "fp32":
+        return False
+    return model == "acoustic" or g.kernel_info()["split"] == 1
 
 
 class ClockSampler:
@@ -445,7 +469,7 @@ def extra_sweeps(P, args, acoustic_cfgs, stream, pk):
             rows = {}
             for g, t in zip(solvers, ms):
                 rows[str(g.N)] = per_degree(model, g, t, pk, tensor=prec != "fp32",
-                                            factored=model == "acoustic" and prec == "fp32" and strat != "plain")
+                                            factored=is_factored(model, g, prec, strat))
                 rows[str(g.N)]["strategy"] = strat
                 if strat != "fused":
                     del rows[str(g.N)]["kernel"]
@@ -474,7 +498,7 @@ def run(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    model = "acoustic"
+    model = args.model
     Ns = [int(x) for x in args.degrees.split(",")]
     stream = torch.cuda.Stream(device=dev)
     cfgs = build_meshes(model, Ns)
@@ -521,10 +545,9 @@ def run(args, rank, world, local_rank):
     pk = peaks()
     per_N = {}
     dom = None
-    factored = model == "acoustic" and (args.strategy == "library" or
-                                        (args.strategy == "fused" and args.precision == "fp32"))
     for g, ms in zip(solvers, per_ms):
-        row = per_degree(model, g, ms, pk, tensor=args.precision != "fp32", factored=factored)
+        row = per_degree(model, g, ms, pk, tensor=args.precision != "fp32",
+                         factored=is_factored(model, g, args.precision, args.strategy))
         per_N[str(g.N)] = row
         if dom is None or ms > dom[1]:
             byt, flop = algorithmic(model, g.N, g.K)
@@ -547,15 +570,16 @@ def run(args, rank, world, local_rank):
                 "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     if bound != "hbm":
-        # the same step against the FLOPs the kernels execute (two surface streams)
-        roof["exec_achieved"] = executed_flops(model, g.N, g.K, factored) / (ms * 1e-3) / 1e12
+        # the same step against the FLOPs the kernels execute (surface streams lifted)
+        roof["exec_achieved"] = (executed_flops(model, g.N, g.K, is_factored(model, g, args.precision, args.strategy))
+                                 / (ms * 1e-3) / 1e12)
         roof["exec_frac"] = roof["exec_achieved"] / roof["peak"]
     roof["traffic"] = traffic
     ki = g.kernel_info()
-    roof["kernel"] = ("dg_step_kernel<acoustic, N=%d, EB=%d, TN=%d> (variant %d)"
-                      % (g.N, ki["block_elems"], ki["tile_elems"], ki["variant"]) if not ki["split"] else
-                      "split step, acoustic N=%d (front half + %s GEMM, variant %d)"
-                      % (g.N, "tcgen05" if ki["split"] == 2 else "FP32", ki["variant"]))
+    roof["kernel"] = ("dg_step_kernel<%s, N=%d, EB=%d, TN=%d> (variant %d)"
+                      % (model, g.N, ki["block_elems"], ki["tile_elems"], ki["variant"]) if not ki["split"] else
+                      "split step, %s N=%d (front half + %s GEMM, variant %d)"
+                      % (model, g.N, "tcgen05" if ki["split"] == 2 else "FP32", ki["variant"]))
     roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs (burst copy)" if bound == "hbm"
                            else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz")
 
@@ -602,7 +626,7 @@ def run(args, rank, world, local_rank):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else args.precision + " (f32 accumulate)",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "degrees": Ns,
+                "config": {"workload": WORKLOAD if model == "acoustic" else WORKLOAD_ELASTIC, "degrees": Ns,
                            "meshes": {str(g.N): g.K for g in solvers},
                            "l2": "inputs larger than L2: the 8 meshes hold ~1.3 GB, each ~130 MB",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -633,6 +657,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--degrees", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--model", default="acoustic", choices=["acoustic", "elastic"],
+                    help="model of the timed sweep (the headline is the acoustic one)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
