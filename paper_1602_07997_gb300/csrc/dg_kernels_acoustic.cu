@@ -15,14 +15,16 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_cfg<0, 1, 32, true, true>(), make_cfg<0, 1, 128, true, true>(),
                                  make_cfg<0, 1, 16, true, true>(), make_cfg<0, 1, 64, true, true, 1, 256>(),
                                  make_cfg<0, 1, 32, true, true, 1, 256>(), make_cfg<0, 1, 64, true, true, 1, 512>()};
-  static const KernelCfg v2[] = {make_cfg<0, 2, 32, true, true, 1, 256>(), make_cfg<0, 2, 32, true, true>(),
+  static const KernelCfg v2[] = {make_cfg<0, 2, 24, true, true, 1, 256>(), make_cfg<0, 2, 32, true, true>(),
                                  make_cfg<0, 2, 16, true, true>(), make_cfg<0, 2, 64, true, true>(),
                                  make_cfg<0, 2, 16, true, true, 1, 128>(), make_cfg<0, 2, 8, true, true>(),
-                                 make_cfg<0, 2, 16, true, true, 1, 256>(), make_cfg<0, 2, 32, true, true, 1, 512>()};
-  static const KernelCfg v3[] = {make_cfg<0, 3, 16, true, true, 1, 256>(), make_cfg<0, 3, 4, true, true>(),
+                                 make_cfg<0, 2, 16, true, true, 1, 256>(), make_cfg<0, 2, 32, true, true, 1, 512>(),
+                                 make_cfg<0, 2, 32, true, true, 1, 256>()};
+  static const KernelCfg v3[] = {make_cfg<0, 3, 12, true, true, 1, 256>(), make_cfg<0, 3, 4, true, true>(),
                                  make_cfg<0, 3, 16, true, true>(), make_cfg<0, 3, 32, true, true>(),
                                  make_cfg<0, 3, 16, true, true, 1, 128>(), make_cfg<0, 3, 8, true, true>(),
-                                 make_cfg<0, 3, 32, true, true, 1, 256>(), make_cfg<0, 3, 32, true, true, 1, 512>()};
+                                 make_cfg<0, 3, 32, true, true, 1, 256>(), make_cfg<0, 3, 32, true, true, 1, 512>(),
+                                 make_cfg<0, 3, 16, true, true, 1, 256>(), make_cfg<0, 3, 12, true, true, 1, 192>()};
   static const KernelCfg v4[] = {make_cfg<0, 4, 12, true, true, 1, 256>(), make_cfg<0, 4, 4, true, true>(),
                                  make_cfg<0, 4, 8, true, true, 2>(), make_cfg<0, 4, 8, true, true>(),
                                  make_cfg<0, 4, 8, true, true, 1, 128>(), make_cfg<0, 4, 16, true, true, 1, 256>(),
@@ -54,7 +56,8 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_split_cfg<0, 8, 4, 3>(), make_split_cfg<0, 8, 8, 2, 512>(),
                                  make_split_cfg<0, 8, 8, 5, 768>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
-  static const int cnt[8] = {9, 8, 8, 8, 11, 13, 13, 11};
+  static const int cnt[8] = {count_of(v1), count_of(v2), count_of(v3), count_of(v4),
+                             count_of(v5), count_of(v6), count_of(v7), count_of(v8)};
   if (N < 1 || N > 8) return nullptr;
   *count = cnt[N - 1];
   return tab[N - 1];

@@ -45,7 +45,8 @@ const KernelCfg* kernel_variants_elastic(int N, int* count) {
                                  make_split_cfg<1, 8, 4, 3, 384>(), make_split_cfg<1, 8, 4, 2>(),
                                  make_split_cfg<1, 8, 4, 2, 384>(), make_split_cfg<1, 8, 4, 5, 512>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
-  static const int cnt[8] = {5, 5, 7, 9, 10, 11, 11, 10};
+  static const int cnt[8] = {count_of(v1), count_of(v2), count_of(v3), count_of(v4),
+                             count_of(v5), count_of(v6), count_of(v7), count_of(v8)};
   if (N < 1 || N > 8) return nullptr;
   *count = cnt[N - 1];
   return tab[N - 1];

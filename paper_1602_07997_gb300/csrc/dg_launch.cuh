@@ -5,6 +5,12 @@
 
 namespace dgk {
 
+// number of variants in a table
+template <size_t M>
+constexpr int count_of(const KernelCfg (&)[M]) {
+  return int(M);
+}
+
 // threads per CTA: one output tile per thread, at least two warps, warp multiple
 template <int N, int EB, int TN>
 constexpr int threads_for() {
