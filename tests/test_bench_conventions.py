@@ -1,0 +1,96 @@
+"""Counting conventions behind bench.py's roofline figures (host logic, no GPU).
+
+The algorithmic bytes and FLOPs per element follow the operator products of
+Section 3.2 (Eq. dgLocalRhs): every volume product is one Np x Np matrix
+applied to one nodal field, every lift one Np x 4Nfp matrix applied to one
+face-node field.  The tests enumerate those products instead of restating
+the closed forms in bench.py.
+"""
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def sizes(N):
+    Np = (N + 1) * (N + 2) * (N + 3) // 6
+    Nfp = (N + 1) * (N + 2) // 2
+    return Np, Nfp
+
+
+def products(model):
+    """(volume products, lifted face fields) of the unfactored RHS."""
+    if model == "acoustic":
+        # grad p (3 derivatives of p) and div v (one derivative per velocity component)
+        vol = [("p", d) for d in range(3)] + [("v%d" % c, c) for c in range(3)]
+        return vol, 4
+    # velocity gradient (3 x 3) and stress divergence (3 components x 3 derivatives)
+    vol = [("v%d" % c, d) for c in range(3) for d in range(3)] + \
+          [("s%d%d" % (c, d), d) for c in range(3) for d in range(3)]
+    return vol, 9
+
+
+@pytest.mark.parametrize("model", ["acoustic", "elastic"])
+@pytest.mark.parametrize("N", range(1, 9))
+def test_algorithmic_counts_enumerate_the_products(model, N):
+    Np, Nfp = sizes(N)
+    Nf = 4 if model == "acoustic" else 9
+    vol, lifted = products(model)
+    mac = len(vol) * Np * Np + lifted * Np * 4 * Nfp
+    K = 37
+    byt, flop = bench.algorithmic(model, N, K)
+    # five FP32 arrays of Nf Np values (q^m, r^m-1, r^m-2 read; q^m+1, r^m written) + the record
+    assert byt == K * (5 * 4 * Nf * Np + 84)
+    # one multiply-add = 2 flops; AB3 = 8 flops per field-node
+    assert flop == K * (2 * mac + 8 * Nf * Np)
+    assert bench.executed_flops(model, N, K, False) == flop
+
+
+@pytest.mark.parametrize("model", ["acoustic", "elastic"])
+@pytest.mark.parametrize("N", range(1, 9))
+def test_factored_counts(model, N):
+    """Surface streams: acoustic lifts 2 streams and rebuilds 3 velocity
+    components from 4 face normals; elastic lifts 3 + 3 streams and folds 6
+    stress components per face (n.W 3, lambda scaling 1, diagonal 3 x 2,
+    off-diagonal 3 x 2 multiply-adds)."""
+    Np, Nfp = sizes(N)
+    vol, _ = products(model)
+    K = 5
+    if model == "acoustic":
+        streams, fold = 2, 3 * 4
+        Nf = 4
+    else:
+        streams, fold = 6, 4 * (3 + 1 + 6 + 6)
+        Nf = 9
+    mac = len(vol) * Np * Np + streams * Np * 4 * Nfp + fold * Np
+    ex = bench.executed_flops(model, N, K, True)
+    assert ex == K * (2 * mac + 8 * Nf * Np)
+    # the elastic fold (64 Np) outweighs the saved lifts (12 Np Nfp) at N = 1,
+    # where the fused elastic kernel keeps the nine penalty fields
+    if model == "acoustic" or N >= 2:
+        assert ex < bench.algorithmic(model, N, K)[1]
+
+
+class _G:
+    def __init__(self, split):
+        self.split = split
+
+    def kernel_info(self):
+        return {"split": self.split}
+
+
+@pytest.mark.parametrize("split", [0, 1, 2])
+def test_which_paths_lift_surface_streams(split):
+    g = _G(split)
+    # the library route factors in every mode; the plain route never
+    for model in ("acoustic", "elastic"):
+        assert bench.is_factored(model, g, "fp32", "library")
+        assert not bench.is_factored(model, g, "fp32", "plain")
+        # the tensor-core front halves lift every penalty field
+        assert not bench.is_factored(model, g, "bf16x6", "fused")
+    # fused FP32: every acoustic kernel, only the elastic split step
+    assert bench.is_factored("acoustic", g, "fp32", "fused")
+    assert bench.is_factored("elastic", g, "fp32", "fused") == (split == 1)
