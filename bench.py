@@ -122,16 +122,18 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    INTERVAL_MS = 50
+
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host time of arrival, csv line)
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -141,7 +143,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *a):
         if self.proc:
@@ -151,10 +153,16 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Median SM clock, maximum clock and throttle reasons of the samples
+        that arrived in [t0, t1 + one interval] (all samples if none did)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if t0 is not None:
+            inside = [x for x in lines if t0 <= x[0] <= t1 + self.INTERVAL_MS / 1e3]
+            lines = inside or lines
+        for _, ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -523,7 +531,15 @@ def run(args, rank, world, local_rank):
            for _ in range(nN)] for _ in range(args.steps)]
     e_all0, e_all1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
+        # untimed steps until the sampler is live (at most 3 s), so that its
+        # samples cover the timed region
+        t_wait = time.perf_counter()
+        while clk.proc and not clk.lines and time.perf_counter() - t_wait < 3.0:
+            for g in solvers:
+                g.step(1)
+            torch.cuda.synchronize()
         barrier()
+        t0 = time.perf_counter()
         e_all0.record(stream)
         for s in range(args.steps):
             for i, g in enumerate(solvers):
@@ -532,6 +548,8 @@ def run(args, rank, world, local_rank):
                 ev[s][i][1].record(stream)
         e_all1.record(stream)
         barrier()
+        t1 = time.perf_counter()
+    clocks = clk.summary(t0, t1)
     total_ms = e_all0.elapsed_time(e_all1)
     per_ms = [statistics.mean(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
               for i in range(nN)]
@@ -631,7 +649,7 @@ def run(args, rank, world, local_rank):
                            "l2": "inputs larger than L2: the 8 meshes hold ~1.3 GB, each ~130 MB",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "gpu_launches": launches, "roofline": roof, "per_N": per_N, "sweeps": sweeps,
-                "cpu_baseline": cpu, "e2e": e2e, "served": served, "clocks": clk.summary()}
+                "cpu_baseline": cpu, "e2e": e2e, "served": served, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 
@@ -653,7 +671,7 @@ def kernel_rev():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--degrees", default="1,2,3,4,5,6,7,8")

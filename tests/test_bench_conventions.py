@@ -94,3 +94,19 @@ def test_which_paths_lift_surface_streams(split):
     # fused FP32: every acoustic kernel, only the elastic split step
     assert bench.is_factored("acoustic", g, "fp32", "fused")
     assert bench.is_factored("elastic", g, "fp32", "fused") == (split == 1)
+
+
+def test_clock_summary_keeps_the_timed_window():
+    """Only samples that arrived inside the timed region (plus one interval)
+    count; throttle reasons are the ones active there."""
+    c = bench.ClockSampler(0)
+    idle = "1200, 2070, 150.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    load = "2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    capped = "1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active"
+    c.lines = [(0.00, idle), (0.05, idle), (1.00, load), (1.05, capped), (1.10, load), (3.00, idle)]
+    s = c.summary(1.0, 1.08)
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["reasons"] == ["sw_power_cap"]
+    # no sample inside the window: every sample counts
+    s = c.summary(2.0, 2.5)
+    assert s["samples"] == 6
+    assert bench.ClockSampler(0).summary()["samples"] == 0
