@@ -174,10 +174,13 @@ int dg_autotune(dg_handle *h, int reps, int *block_elems, double *ms_per_step, d
  * precision mode), elements per thread tile, and the step's form in *split:
  * 0 fused, 1 split with the FP32 CUDA-core GEMM, 2 split with the tensor-core
  * GEMM (the operator products run as a separate GEMM over 16-64-element
- * column tiles; needs an extra device buffer of (4 Np + 4 (4 Nfp)) floats per
- * element for the acoustic model, (12 Np + 9 (4 Nfp)) for the elastic one,
- * allocated on first use), and the index of the variant in use (as taken by
- * dg_set_variant).  Pointers may be NULL.                                   */
+ * column tiles; needs an extra device buffer, allocated on first use: per
+ * element (4 Np + 8 Nfp + 12) floats for the acoustic FP32 split step and
+ * (12 Np + 24 Nfp + 12) for the elastic one -- volume inputs, surface
+ * streams, face normals -- while the tensor-core form keeps every penalty
+ * field: 2 or 3 BF16 pieces of (4 Np + 16 Nfp) or (12 Np + 36 Nfp) values,
+ * each part rounded up to 16), and the index of the variant in use (as taken
+ * by dg_set_variant).  Pointers may be NULL.                                */
 int dg_kernel_info(const dg_handle *h, int *block_elems, int *threads, int64_t *smem_bytes,
                    int *variants, int *tile_elems, int *split, int *variant);
 /* Select compiled variant `index` (0 <= index < variants of the handle's
