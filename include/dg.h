@@ -95,7 +95,8 @@ enum { DG_FP32 = 0, DG_BF16X3 = 1, DG_BF16X6 = 2, DG_TF32 = 3 };
  *   DG_STRATEGY_LIBRARY the library route of Section 3.3: the fused kernel's
  *                       front half writes the operator-product inputs, cuBLAS
  *                       strided-batched SGEMMs compute the D_r/D_s/D_t and LIFT
- *                       products (7 GEMMs per step acoustic, 21 elastic), a
+ *                       products (8 GEMMs per step acoustic, 27 elastic: the
+ *                       surface streams are lifted face by face), a
  *                       streaming kernel does the geometric combination and
  *                       AB3.  Precision DG_FP32 (SGEMM) or DG_TF32 (cuBLAS TF32
  *                       tensor-core math; its error is far above 1e-5).
@@ -157,7 +158,10 @@ int dg_get_state(dg_handle *h, float *q, float *r1, float *r2, int64_t *step,
 int dg_rhs(dg_handle *h, float *r_out, int on_device);
 
 /* Advance nsteps AB3 steps (Eq. updateScheme) with the handle's dt; each step
- * is one fused launch (RHS + update).  Asynchronous on the handle's stream.  */
+ * is one fused launch (RHS + update), or two for the split step (front half,
+ * then the operator GEMM with the update), plus one small launch when the
+ * handle has more than one point source and one when it has receivers.
+ * Asynchronous on the handle's stream.                                      */
 int dg_step(dg_handle *h, int nsteps);
 int dg_set_dt(dg_handle *h, double dt);
 /* Autotuner: time every compiled variant of the step kernel (elements per
