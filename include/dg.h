@@ -278,8 +278,10 @@ const char *dg_last_error(void);
  * initial state, source, nsteps).  Requests are admitted while free device
  * memory (cudaMemGetInfo) minus a safety margin, and the optional budget,
  * cover their state; admitted solves of the same degree and model are
- * advanced together, one batched launch per (model, N) class per time step,
- * and new requests join between steps (continuous batching).  A finished
+ * advanced together, one batched step per (model, N) class per time step
+ * (one launch, or two for the split step, then a small launch that advances
+ * every solve's step counter and AB3 phase), and new requests join between
+ * steps (continuous batching).  A finished
  * solve's q is copied to host memory owned by the server until dg_poll
  * copies it out.
  * ------------------------------------------------------------------------ */
