@@ -2,7 +2,7 @@
 //
 //   library route (Section 3.3, "SGEMM" strategy): the fused kernel's front
 //     half writes the operator-product inputs X[tile][row][NE] (volume inputs,
-//     Fscale-weighted penalties); cuBLAS strided-batched SGEMMs over the column
+//     surface streams, face normals); cuBLAS strided-batched SGEMMs over the column
 //     tiles compute every operator product (D_r/D_s/D_t products and the LIFT
 //     products, one GEMM per product and input block) into Y[product][K][Np];
 //     a streaming kernel does the geometric combination, the source and the

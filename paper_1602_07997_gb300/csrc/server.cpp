@@ -7,8 +7,10 @@
 //      GPU keeps stepping the active solves meanwhile;
 //   2. batching: active solves are grouped by (model, N); one tick advances
 //      every active solve by one AB3 step with one persistent batched launch
-//      per group plus one tiny launch that advances the per-solve step state
-//      on the device; the tick is captured once in a CUDA graph and replayed
+//      per group (two for the split step: front half, then the GEMM over all
+//      the group's column tiles) plus one tiny launch that advances the
+//      per-solve step state on the device; the tick is captured once in a
+//      CUDA graph and replayed
 //      until the set of active solves changes;
 //   3. ticks run in chunks that end when the first active solve finishes (at
 //      most kMaxChunk ticks), so that requests that arrived meanwhile join at
