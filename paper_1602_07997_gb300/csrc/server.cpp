@@ -10,8 +10,7 @@
 //      per group (two for the split step: front half, then the GEMM over all
 //      the group's column tiles) plus one tiny launch that advances the
 //      per-solve step state on the device; the tick is captured once in a
-//      CUDA graph and replayed
-//      until the set of active solves changes;
+//      CUDA graph and replayed until the set of active solves changes;
 //   3. ticks run in chunks that end when the first active solve finishes (at
 //      most kMaxChunk ticks), so that requests that arrived meanwhile join at
 //      the next chunk boundary (continuous batching);
