@@ -110,3 +110,22 @@ def test_clock_summary_keeps_the_timed_window():
     s = c.summary(2.0, 2.5)
     assert s["samples"] == 6
     assert bench.ClockSampler(0).summary()["samples"] == 0
+
+
+def test_reference_arm_line(capsys):
+    """--impl reference: rank 0 prints one JSON line (oracle timed on the host
+    cores, the same metric and unit, e2e with no copies); other ranks print
+    nothing."""
+    import json
+    import types
+    args = types.SimpleNamespace(steps=2, warmup=1)
+    bench.run_reference(args, 1, 2)
+    assert capsys.readouterr().out == ""
+    bench.run_reference(args, 0, 1)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["steps"] == 2 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
