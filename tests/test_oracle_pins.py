@@ -14,8 +14,8 @@ import pytest
 
 import workloads as W
 from oracle.refelem import (RefElement, warp_blend_nodes, tri_quadrature, num_nodes,
-                            num_face_nodes, FACE_VERTS, Lagrange)
-from oracle.dg import Solver, AB3Stepper, acoustic_penalty, elastic_penalty, AB3, SIG
+                            num_face_nodes, FACE_VERTS)
+from oracle.dg import Solver, AB3Stepper, acoustic_penalty, elastic_penalty, AB3
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
