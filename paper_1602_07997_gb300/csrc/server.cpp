@@ -604,7 +604,7 @@ int dg_submit(dg_server* s, const dg_request* req, uint64_t* ticket) {
       r->ex_xyz.assign(req->src_xyz + 3, req->src_xyz + 3 * size_t(ns));
       if (req->src_dir) r->ex_dir.assign(req->src_dir + 3, req->src_dir + 3 * size_t(ns));
       else
-        for (int s = 1; s < ns; ++s) r->ex_dir.insert(r->ex_dir.end(), {0.0, 0.0, 1.0});
+        for (int j = 1; j < ns; ++j) r->ex_dir.insert(r->ex_dir.end(), {0.0, 0.0, 1.0});
       r->ex_amp.assign(req->src_amp + req->src_namp, req->src_amp + size_t(ns) * req->src_namp);
       r->ex_namp = req->src_namp;
     }
