@@ -172,7 +172,17 @@ def reference_element(N):
 
 
 class Solver:
-    """One DG discretisation on the GPU (a dg_handle)."""
+    """One DG discretisation on the GPU (a dg_handle, see dg_setup).
+
+    verts [nverts][3] and tets [K][4] (0-based, positively oriented) define a
+    conforming tetrahedral mesh; coeffs is [K][2] (rho, c) for the acoustic
+    model or [K][3] (lambda, mu, rho) for the elastic one; N in 1..8.  flux:
+    "upwind" or "centred"; bc: None (rigid wall acoustic, traction-free
+    elastic), "rigid" or "free"; dt: the step of `step` (see suggest_dt);
+    stream: a cudaStream_t as an integer (e.g. torch.cuda.Stream().cuda_stream);
+    precision: "fp32", "bf16x3", "bf16x6" or "tf32" (library strategy);
+    strategy: "fused", "library" or "plain".  States are [K][Nf][Np] float32,
+    as numpy arrays (host) or CUDA tensors (device)."""
 
     def __init__(self, verts, tets, coeffs, N, model="acoustic", flux="upwind", bc=None, dt=0.0,
                  stream=None, block_elems=0, precision="fp32", strategy="fused"):
@@ -201,6 +211,11 @@ class Solver:
     __del__ = close
 
     def set_state(self, q, r1=None, r2=None, step=0):
+        """Replace the state by q; r1 = r^{m-1} and r2 = r^{m-2} give the AB3
+        history (both or neither: without them the next steps start with Euler
+        and AB2).  step = the time-step index of q (it indexes source amplitudes)."""
+        if (r1 is None) != (r2 is None):
+            raise ValueError("r1 and r2 are given together or not at all")
         pq, dq, kq = _buf(q, np.float32, self.size)
         p1 = p2 = None
         keep = []
@@ -213,6 +228,8 @@ class Solver:
         check(lib().dg_set_state(self.h, pq, p1, p2, int(step), dq))
 
     def get_state(self, q=None, r1=None, r2=None):
+        """The state q (a new host array, or into q / r1 / r2 if given); sets
+        self.step_index and self.history (stored RHS levels, 0..2)."""
         ret = q is None
         if q is None:
             q = np.empty(self.shape, dtype=np.float32)
@@ -225,6 +242,7 @@ class Solver:
         return q if ret else None
 
     def rhs(self, out=None):
+        """r(q^m) at the current state, source included; the state is unchanged."""
         ret = out is None
         if out is None:
             out = np.empty(self.shape, dtype=np.float32)
@@ -247,9 +265,11 @@ class Solver:
         check(lib().dg_set_dt(self.h, float(dt)))
 
     def step(self, n=1):
+        """Advance n AB3 steps, asynchronously on the solver's stream."""
         check(lib().dg_step(self.h, int(n)))
 
     def sync(self):
+        """Wait for the stream; raises DGError (DG_ETIMEOUT) if a bounded device wait expired."""
         check(lib().dg_sync(self.h))
 
     def autotune(self, reps=5):
