@@ -118,12 +118,27 @@ def _dptr(a):
 def make_mesh(verts, tets):
     verts = np.ascontiguousarray(verts, dtype=np.float64)
     tets = np.ascontiguousarray(tets, dtype=np.int64)
+    if verts.ndim != 2 or verts.shape[1] != 3 or tets.ndim != 2 or tets.shape[1] != 4:
+        raise ValueError("verts must be [nverts][3] and tets [ntets][4], got %s and %s"
+                         % (verts.shape, tets.shape))
     m = Mesh(verts.shape[0], tets.shape[0], _dptr(verts), tets.ctypes.data_as(C.POINTER(C.c_int64)))
     return m, (verts, tets)  # keep the arrays alive with the struct
 
 
+def _coeffs(coeffs, K, model):
+    """Per-element coefficients as contiguous float64: [K][2] (rho, c) for the
+    acoustic model, [K][3] (lambda, mu, rho) for the elastic one."""
+    cf = np.ascontiguousarray(coeffs, dtype=np.float64)
+    nc = 2 if _model(model) == ACOUSTIC else 3
+    if cf.size != K * nc:
+        raise ValueError("coeffs must be [%d][%d], got %s" % (K, nc, cf.shape))
+    return cf
+
+
 def _model(model):
     if isinstance(model, str):
+        if model not in ("acoustic", "elastic"):
+            raise ValueError("model must be 'acoustic' or 'elastic', got %r" % model)
         return ACOUSTIC if model == "acoustic" else ELASTIC
     return int(model)
 
@@ -153,7 +168,7 @@ def _buf(x, dtype, count, write=False):
 
 def suggest_dt(verts, tets, coeffs, N, model, cfl=0.5):
     m, keep = make_mesh(verts, tets)
-    cf = np.ascontiguousarray(coeffs, dtype=np.float64)
+    cf = _coeffs(coeffs, keep[1].shape[0], model)
     out = C.c_double()
     check(lib().dg_suggest_dt(C.byref(m), _dptr(cf), int(N), _model(model), float(cfl), C.byref(out)))
     return out.value
@@ -187,7 +202,7 @@ class Solver:
     def __init__(self, verts, tets, coeffs, N, model="acoustic", flux="upwind", bc=None, dt=0.0,
                  stream=None, block_elems=0, precision="fp32", strategy="fused"):
         m, keep = make_mesh(verts, tets)
-        cf = np.ascontiguousarray(coeffs, dtype=np.float64)
+        cf = _coeffs(coeffs, keep[1].shape[0], model)
         o = Opts(FLUX[flux], BC[bc], PRECISION[precision], int(block_elems), float(dt),
                  C.c_void_p(stream or 0), STRATEGY[strategy])
         h = C.c_void_p()
@@ -350,7 +365,7 @@ class Server:
     def submit(self, verts, tets, coeffs, N, model="acoustic", q0=None, dt=0.0, nsteps=1, flux="upwind",
                bc=None, source=None, amp=None, direction=(0.0, 0.0, 1.0)):
         m, keep = make_mesh(verts, tets)
-        cf = np.ascontiguousarray(coeffs, dtype=np.float64)
+        cf = _coeffs(coeffs, keep[1].shape[0], model)
         model = _model(model)
         Nf = 4 if model == ACOUSTIC else 9
         Np = (N + 1) * (N + 2) * (N + 3) // 6
@@ -363,6 +378,8 @@ class Server:
         q0a = None
         if q0 is not None:
             q0a = np.ascontiguousarray(q0, dtype=np.float32)
+            if q0a.size != K * Nf * Np:
+                raise ValueError("q0 must have K Nf Np = %d values, got %d" % (K * Nf * Np, q0a.size))
             r.q0 = q0a.ctypes.data_as(C.POINTER(C.c_float))
         xs = d = a = None
         if source is not None and amp is not None:

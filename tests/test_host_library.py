@@ -93,3 +93,17 @@ def test_strategy_and_precision_combinations_checked_before_device_use(P):
         with pytest.raises(P.DGError) as e:
             P.Solver(verts, tets, c, 2, "acoustic", strategy=strategy, precision=precision)
         assert e.value.code == -1, (strategy, precision)
+
+
+def test_binding_checks_array_shapes(P):
+    """The binding refuses arrays whose size would make the library read past
+    them (mesh, coefficients), before any call into the library."""
+    verts, tets = W.kuhn_cube_mesh(2, 0.1, seed=1)
+    K = tets.shape[0]
+    for v, t, c, model in ((verts[:, :2], tets, np.ones((K, 2)), "acoustic"),    # 2-D vertices
+                           (verts, tets[:, :3], np.ones((K, 2)), "acoustic"),    # triangles
+                           (verts, tets, np.ones((K, 3)), "acoustic"),           # elastic coefficients
+                           (verts, tets, np.ones((K, 2)), "elastic"),
+                           (verts, tets, np.ones((K - 1, 2)), "acoustic")):
+        with pytest.raises(ValueError):
+            P.suggest_dt(v, t, c, 2, model, 0.4)
