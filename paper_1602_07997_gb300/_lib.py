@@ -135,6 +135,14 @@ def _coeffs(coeffs, K, model):
     return cf
 
 
+def _point(x):
+    """Three contiguous float64 values (a position or a direction)."""
+    p = np.ascontiguousarray(x, dtype=np.float64)
+    if p.size != 3:
+        raise ValueError("expected 3 coordinates, got %s" % (np.shape(x),))
+    return p
+
+
 def _model(model):
     if isinstance(model, str):
         if model not in ("acoustic", "elastic"):
@@ -317,15 +325,13 @@ class Solver:
         if amp is None:
             check(lib().dg_set_source(self.h, None, None, None, 0))
             return
-        xs = np.ascontiguousarray(xs, dtype=np.float64)
-        d = np.ascontiguousarray(direction, dtype=np.float64)
+        xs, d = _point(xs), _point(direction)
         a = np.ascontiguousarray(amp, dtype=np.float64)
         check(lib().dg_set_source(self.h, _dptr(xs), _dptr(d), _dptr(a), a.size))
 
     def add_source(self, xs, amp, direction=(0.0, 0.0, 1.0)):
         """One more point source (several sources add their terms)."""
-        xs = np.ascontiguousarray(xs, dtype=np.float64)
-        d = np.ascontiguousarray(direction, dtype=np.float64)
+        xs, d = _point(xs), _point(direction)
         a = np.ascontiguousarray(amp, dtype=np.float64)
         check(lib().dg_add_source(self.h, _dptr(xs), _dptr(d), _dptr(a), a.size))
 
@@ -386,6 +392,8 @@ class Server:
             # one source: source [3], amp [namp]; several: source [n][3],
             # amp [n][namp], direction [3] (for all) or [n][3]
             xs = np.ascontiguousarray(np.atleast_2d(source), dtype=np.float64)
+            if xs.ndim != 2 or xs.shape[1] != 3:
+                raise ValueError("source must be [3] or [n][3], got %s" % (np.shape(source),))
             ns = xs.shape[0]
             a = np.ascontiguousarray(np.atleast_2d(amp), dtype=np.float64)
             if a.shape[0] != ns:

@@ -107,3 +107,15 @@ def test_binding_checks_array_shapes(P):
                            (verts, tets, np.ones((K - 1, 2)), "acoustic")):
         with pytest.raises(ValueError):
             P.suggest_dt(v, t, c, 2, model, 0.4)
+
+
+def test_binding_checks_source_points(P):
+    """Source positions and directions are three coordinates (checked before
+    the handle is touched)."""
+    import types
+    fake = types.SimpleNamespace(h=None)
+    for xs, d in (((0.5, 0.5), (0.0, 0.0, 1.0)), ((0.5, 0.5, 0.5), (1.0, 0.0))):
+        with pytest.raises(ValueError):
+            P.Solver.set_source(fake, xs, [1.0], d)
+        with pytest.raises(ValueError):
+            P.Solver.add_source(fake, xs, [1.0], d)
