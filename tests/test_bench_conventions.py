@@ -129,3 +129,18 @@ def test_reference_arm_line(capsys):
     assert d["value"] > 0 and d["steps"] == 2 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_sweep_meshes_have_the_documented_sizes():
+    """The ~2 M-node sweep: 6 n^3 Kuhn tets per degree with n = 44, 32, 26,
+    21, 18, 16, 14, 13 (6 n^3 Np closest to 2 M), as the measured tables
+    and profiles quote them."""
+    import workloads as W
+    expect = {1: 44, 2: 32, 3: 26, 4: 21, 5: 18, 6: 16, 7: 14, 8: 13}
+    for N, n in expect.items():
+        assert W.n_for_target_nodes(N) == n
+        Np = (N + 1) * (N + 2) * (N + 3) // 6
+        nodes = 6 * n ** 3 * Np
+        assert 1.9e6 < nodes < 2.2e6
+    verts, tets = W.kuhn_cube_mesh(3, jitter=0.1, seed=1)
+    assert tets.shape == (6 * 27, 4) and verts.shape == (64, 3)
