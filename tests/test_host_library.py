@@ -119,3 +119,14 @@ def test_binding_checks_source_points(P):
             P.Solver.set_source(fake, xs, [1.0], d)
         with pytest.raises(ValueError):
             P.Solver.add_source(fake, xs, [1.0], d)
+
+
+def test_empty_mesh_is_refused(P):
+    """K = 0 (or fewer than 4 vertices): DG_EINVAL from the host checks."""
+    verts, tets = W.kuhn_cube_mesh(2, 0.1, seed=1)
+    with pytest.raises(P.DGError) as e:
+        P.suggest_dt(verts, tets[:0], np.ones((0, 2)), 2, "acoustic", 0.4)
+    assert e.value.code == -1
+    with pytest.raises(P.DGError) as e:
+        P.suggest_dt(verts[:3], tets[:0], np.ones((0, 2)), 2, "acoustic", 0.4)
+    assert e.value.code == -1
