@@ -54,7 +54,11 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 
 
-def peaks():
+def peaks(fp32=None):
+    """Roofline denominators: HBM from MEASURED_PEAKS.json (burst copy), FP32
+    from the live FMA microbenchmark (dg_fp32_peak, the better of its scalar
+    and packed forms) when given, else the unit-count derivation at the
+    maximum SM clock, which is also kept as a cross-check."""
     p = {"hbm_gbs": 6758.9, "source": "fallback"}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -63,9 +67,31 @@ def peaks():
         p["source"] = "measured"
     except Exception:
         pass
-    # FP32 CUDA-core peak from unit counts and the maximum SM clock
-    p["fp32_tflops"] = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    p["fp32_unit_count_tflops"] = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    if fp32 and fp32.get("tflops"):
+        p["fp32_tflops"] = fp32["tflops"]
+        p["fp32_source"] = "measured"
+    else:
+        p["fp32_tflops"] = p["fp32_unit_count_tflops"]
+        p["fp32_source"] = "unit count"
     return p
+
+
+def measure_fp32_peak(P, stream, device):
+    """FP32 FMA throughput measured on this GPU (scalar and packed FMA forms,
+    best launch of each) with the SM clock sampled while it runs."""
+    with ClockSampler(device) as clk:
+        t_wait = time.perf_counter()
+        while clk.proc and not clk.lines and time.perf_counter() - t_wait < 3.0:
+            time.sleep(0.01)
+        t0 = time.perf_counter()
+        r = P.fp32_peak(stream.cuda_stream, reps=10, target_ms=40.0)
+        t1 = time.perf_counter()
+    c = clk.summary(t0, t1)
+    r["tflops"] = max(r["scalar_tflops"], r["packed_tflops"])
+    r["sm_mhz"] = c["sm_mhz"]
+    r["reasons"] = c["reasons"]
+    return r
 
 
 def algorithmic(model, N, K):
@@ -569,6 +595,7 @@ def run(args, rank, world, local_rank):
         raise SystemExit("--variants needs one index per degree")
     solvers = make_solvers(P, cfgs, model, args.precision, stream, not args.no_tune, variants, args.strategy)
     torch.cuda.synchronize()
+    fp32 = None if args.no_peak else measure_fp32_peak(P, stream, local_rank)
 
     def barrier():
         if world > 1:
@@ -614,7 +641,7 @@ def run(args, rank, world, local_rank):
     t_job, upd_job = aggregate(t_local, updates, world)
     value = upd_job / t_job
 
-    pk = peaks()
+    pk = peaks(fp32)
     per_N = {}
     dom = None
     for g, ms in zip(solvers, per_ms):
@@ -652,8 +679,12 @@ def run(args, rank, world, local_rank):
                       % (model, g.N, ki["block_elems"], ki["tile_elems"], ki["variant"]) if not ki["split"] else
                       "split step, %s N=%d (front half + %s GEMM, variant %d)"
                       % (model, g.N, "tcgen05" if ki["split"] == 2 else "FP32", ki["variant"]))
-    roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs (burst copy)" if bound == "hbm"
-                           else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz")
+    roof["kernel_short"] = ("fused %s N=%d v%d" % (model, g.N, ki["variant"]) if not ki["split"] else
+                            "split %s N=%d (%s GEMM) v%d" % (model, g.N, "tcgen05" if ki["split"] == 2 else "FP32",
+                                                            ki["variant"]))
+    roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs (burst copy)" if bound == "hbm" else
+                           "measured: dg_fp32_peak FMA microbenchmark" if pk["fp32_source"] == "measured" else
+                           "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz")
 
     # e2e through the C ABI: pinned host buffers, H2D of the state and D2H of the
     # result inside the timed region, every step
@@ -692,34 +723,164 @@ def run(args, rank, world, local_rank):
     if rank == 0 and not args.no_serve:
         served = served_benchmark(P, count=args.serve_requests, steps=args.serve_steps)
 
+    large = None
+    if rank == 0 and not args.no_large:
+        large = large_elastic(P, args, stream, pk)
+
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.precision == "fp32" else args.precision + " (f32 accumulate)",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD if model == "acoustic" else WORKLOAD_ELASTIC, "degrees": Ns,
-                           "meshes": {str(g.N): g.K for g in solvers},
-                           "l2": "inputs larger than L2: the 8 meshes hold ~1.3 GB, each ~130 MB",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
-                "gpu_launches": launches, "roofline": roof, "per_N": per_N, "sweeps": sweeps,
-                "cpu_baseline": cpu, "e2e": e2e, "served": served, "clocks": clocks}
-        print(json.dumps(line), flush=True)
+        detail = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                  "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps, "higher_is_better": True,
+                  "scaling": "weak", "vs_baseline": None,
+                  "dtype": "f32" if args.precision == "fp32" else args.precision + " (f32 accumulate)",
+                  "data": "synthetic",
+                  "config": {"workload": WORKLOAD if model == "acoustic" else WORKLOAD_ELASTIC, "degrees": Ns,
+                             "meshes": {str(g.N): g.K for g in solvers},
+                             "l2": "inputs larger than L2: the 8 meshes hold ~1.3 GB, each ~130 MB",
+                             "parallelism": "replicas" if world > 1 else "single GPU"},
+                  "gpu_launches": launches, "roofline": roof, "per_N": per_N, "sweeps": sweeps,
+                  "cpu_baseline": cpu, "e2e": e2e, "served": served, "large_elastic": large, "clocks": clocks,
+                  "fp32_peak": fp32, "peaks": pk}
+        print(json.dumps({"bench_detail": detail}), flush=True)
+        print(json.dumps(headline(detail)), flush=True)
+
+
+def _r(x, d=4):
+    """Round to d significant digits (None passes through)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return float("%.*g" % (d, x))
+
+
+def headline(d):
+    """The final stdout line: the contract's keys and a short summary of the
+    detail line printed before it (kept well under 2 KB, so that a reader
+    that keeps only the end of the output still has all of it)."""
+    roof = d["roofline"]
+    line = {k: d[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "gpu_launches")}
+    line["value"] = _r(line["value"], 6)
+    line["ms_per_step"] = _r(line["ms_per_step"], 5)
+    c = d["config"]
+    line["config"] = {"workload": c["workload"], "degrees": c["degrees"], "l2": "inputs > L2 (~1.3 GB)",
+                      "parallelism": c["parallelism"]}
+    line["roofline"] = {"bound": roof["bound"], "achieved": _r(roof["achieved"]), "peak": _r(roof["peak"]),
+                        "unit": roof["unit"], "frac": _r(roof["frac"], 3), "traffic": roof.get("traffic"),
+                        "kernel": roof.get("kernel_short"), "peak_source": roof.get("peak_source")}
+    cpu = d.get("cpu_baseline")
+    if cpu:
+        line["cpu_baseline"] = {"value": _r(cpu.get("value")), "unit": cpu.get("unit"), "cores": cpu.get("cores"),
+                                "kind": cpu.get("kind"), "sample": cpu.get("sample_short", cpu.get("sample")),
+                                "one_core": _r((cpu.get("single_core") or {}).get("value"))}
+    else:
+        line["cpu_baseline"] = None
+    e = d.get("e2e")
+    line["e2e"] = None if not e else {"value": _r(e["value"]), "unit": e["unit"],
+                                      "h2d_bytes_per_step": e["h2d_bytes_per_step"],
+                                      "d2h_bytes_per_step": e["d2h_bytes_per_step"]}
+    ck = d.get("clocks") or {}
+    line["clocks"] = {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons")}
+    # per degree: [ms per step, roofline fraction] (HBM at the degrees whose
+    # operational intensity is below the ridge, else FP32)
+    line["per_N"] = {n: [_r(r["ms"]), _r(r["roofline_frac"], 3)] for n, r in d["per_N"].items()}
+    pk = d.get("fp32_peak")
+    if pk:
+        line["fp32_peak_tflops"] = {"scalar": _r(pk["scalar_tflops"]), "packed": _r(pk["packed_tflops"]),
+                                    "sm_mhz": pk.get("sm_mhz")}
+    sv = d.get("served")
+    if sv:
+        line["served"] = {k: _r(sv[k]) for k in ("p50_s", "p99_s", "plain_p50_s", "plain_p99_s",
+                                                 "batched_all_at_once_makespan_s", "plain_all_at_once_makespan_s")}
+    lg = d.get("large_elastic")
+    if lg:
+        line["large_elastic"] = {"ms": _r(lg["ms"]), "updates_per_s": _r(lg["updates_per_s"]),
+                                 "hbm_frac": _r(lg["hbm_frac"], 3), "alu_frac": _r(lg["alu_frac"], 3),
+                                 "traffic": lg.get("traffic")}
+    return line
+
+
+def large_elastic(P, args, stream, pk):
+    """The large elastic workload: N = 7 on the n = 28 Kuhn mesh (131 712
+    tets, 15.8 M nodes, layered lambda, mu, rho with +-30 % per tet), the
+    autotuned FP32 step, CUDA events over --large-steps steps after three
+    warm-up steps; algorithmic GB/s and GFLOP/s against both peaks."""
+    import workloads as W
+    cfg = W.config5_elastic_large()
+    g = make_solvers(P, [cfg], "elastic", "fp32", stream, not args.no_tune)[0]
+    ms = time_sweep([g], args.large_steps, stream)[0]
+    byt, flop = algorithmic("elastic", g.N, g.K)
+    ki = g.kernel_info()
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            ent = json.load(f).get("elastic_N7_fp32_v%d_large" % ki["variant"])
+        if ent and ent.get("kernel_rev") == kernel_rev():
+            traffic = ent["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    out = {"K": g.K, "nodes": g.K * g.Np, "N": g.N, "ms": ms, "steps": args.large_steps,
+           "updates_per_s": g.K * g.Np * g.Nf / (ms * 1e-3),
+           "alg_GBs": byt / (ms * 1e-3) / 1e9, "alg_GFLOPs": flop / (ms * 1e-3) / 1e9,
+           "hbm_frac": byt / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+           "alu_frac": flop / (ms * 1e-3) / 1e12 / pk["fp32_tflops"],
+           "kernel": ki, "traffic": traffic,
+           "state_bytes": 5 * 4 * g.K * g.Np * g.Nf}
+    g.close()
+    return out
+
+
+KERNEL_SOURCES = ("dg_args.h", "dg_kernels.cuh", "dg_gemm.cuh", "dg_tc.cuh", "dg_launch.cuh", "dg_dispatch.cu",
+                  "dg_kernels_acoustic.cu", "dg_kernels_elastic.cu", "dg_kernels_tc_acoustic.cu",
+                  "dg_kernels_tc_elastic.cu")
 
 
 def kernel_rev():
-    """Hash of the kernel sources without their comments (a traffic figure is
-    only valid for the code it was measured on)."""
+    """Hash of the step kernels' sources without their comments (a traffic
+    figure is only valid for the code it was measured on)."""
     import hashlib
     import re
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_1602_07997_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, f), encoding="utf-8") as fh:
-                src = re.sub(r"/\*.*?\*/", "", re.sub(r"//[^\n]*", "", fh.read()), flags=re.S)
-            h.update("\n".join(l.rstrip() for l in src.splitlines() if l.strip()).encode())
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(d, f), encoding="utf-8") as fh:
+            src = re.sub(r"/\*.*?\*/", "", re.sub(r"//[^\n]*", "", fh.read()), flags=re.S)
+        h.update("\n".join(l.rstrip() for l in src.splitlines() if l.strip()).encode())
     return h.hexdigest()[:12]
+
+
+def ingest_traffic(csv_path, key, note):
+    """Record the DRAM bytes per step of one degree's step kernels from an ncu
+    CSV (--metrics dram__bytes_read.sum,dram__bytes_write.sum --csv) into
+    profiles/traffic.json under `key`, with the current kernel_rev.  A step is
+    one launch of the front/fused kernel (dg_step_kernel) plus, for the split
+    step, its GEMM launch; bytes per step = captured bytes / front launches."""
+    import csv
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1024, "MB": 1024 ** 2, "GB": 1024 ** 3}
+    rows = list(csv.reader(open(csv_path, encoding="utf-8", errors="replace")))
+    hdr = next(i for i, r in enumerate(rows) if "Metric Name" in r)
+    H = rows[hdr]
+    iid, ik, im, iu, iv = (H.index(x) for x in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value"))
+    per = {}
+    for r in rows[hdr + 1:]:
+        if len(r) <= iv or not r[im].startswith("dram__bytes_"):
+            continue
+        v = float(r[iv].replace(",", "")) * scale.get(r[iu], 1)
+        d = per.setdefault(r[iid], {"kernel": r[ik], "read": 0.0, "write": 0.0})
+        d["read" if "read" in r[im] else "write"] += v
+    fronts = sum(1 for d in per.values() if "dg_step_kernel" in d["kernel"])
+    if not fronts:
+        raise SystemExit("no dg_step_kernel launch in " + csv_path)
+    rd = sum(d["read"] for d in per.values()) / fronts
+    wr = sum(d["write"] for d in per.values()) / fronts
+    kernels = sorted({d["kernel"].split("(")[0] for d in per.values()})
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    tr = json.load(open(path)) if os.path.exists(path) else {}
+    tr[key] = {"kernel": " + ".join(kernels), "kernel_rev": kernel_rev(), "dram_bytes_per_launch": int(rd + wr),
+               "dram_read": int(rd), "dram_write": int(wr), "launches": len(per), "steps": fronts, "source": note}
+    with open(path, "w") as f:
+        json.dump(tr, f, indent=1, sort_keys=True)
+    print(json.dumps({key: tr[key]}))
 
 
 def main():
@@ -745,7 +906,16 @@ def main():
     ap.add_argument("--variants", default="",
                     help="kernel variant index per degree instead of autotuning (e.g. to replay a run's choice)")
     ap.add_argument("--sweep-steps", type=int, default=50)
+    ap.add_argument("--no-peak", action="store_true", help="skip the FP32 FMA peak measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the large elastic workload")
+    ap.add_argument("--large-steps", type=int, default=20)
+    ap.add_argument("--ingest-ncu", default="", help="ncu CSV of DRAM bytes to record in profiles/traffic.json")
+    ap.add_argument("--traffic-key", default="", help="key of the --ingest-ncu entry, e.g. acoustic_N8_fp32_v0")
+    ap.add_argument("--traffic-note", default="", help="where the --ingest-ncu capture came from")
     args = ap.parse_args()
+    if args.ingest_ncu:
+        ingest_traffic(args.ingest_ncu, args.traffic_key, args.traffic_note)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -216,22 +216,48 @@ int dg_get_traces(dg_handle *h, float *out, int64_t *nsamples, int on_device);
  * buffer r_out [K][Nf][Np] -- but without allocating device memory: dg_rhs
  * stages the RHS in a device buffer it allocates per call, this function
  * stages it in a fixed 16 MiB array (4 Mi floats) that the library holds on
- * every device that loads it until the process exits.  It is meant for
- * callers that cannot allocate device memory when they need the RHS, e.g.
- * an application whose device memory is already committed to another
- * allocator (a framework's caching allocator or a fixed memory budget),
- * where a fresh allocation could fail or force a device synchronisation.
- * dg_setup still allocates the handle's state once, beforehand.
+ * every device where a handle has been set up, until the process exits.  It
+ * is meant for callers that cannot allocate device memory when they need the
+ * RHS, e.g. an application whose device memory is already committed to
+ * another allocator (a framework's caching allocator or a fixed memory
+ * budget), where a fresh allocation could fail or force a device
+ * synchronisation.
+ *  - Set-up: dg_setup, with the handle's device current, looks up the
+ *    array's device address (cudaGetSymbolAddress; the first lookup on a
+ *    device loads the array there, 16 MiB) and does the first-use set-up of
+ *    the kernels this call launches; it still allocates the handle's state
+ *    once.  A call then allocates nothing, so the device's free memory is
+ *    the same before and after it.  cudaDeviceReset ends the context that
+ *    address belongs to, and with it every handle of that device.
  *  - K*Nf*Np must not exceed 4194304; larger meshes get DG_EINVAL (use
- *    dg_rhs).  The handle's device must be the current device.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.  The call synchronises the handle's stream.
+ *    dg_rhs).  The handle's device must be the current device.  The call
+ *    synchronises the handle's stream.
+ *  - Kernel: the fused FP32 step in RHS mode, whatever the handle's
+ *    precision and strategy (the same RHS within FP32 rounding): the
+ *    handle's own variant if it is the fused FP32 step, else the process's
+ *    FP32 choice for (model, N) at dg_setup (autotuned or the default) if
+ *    that is fused, else the first fused variant compiled for N.  A split
+ *    variant is never used: it would need its input buffer, which is
+ *    allocated on first use.
  *  - Every call shares the one array and leaves its contents behind; calls
  *    whose work overlaps on the GPU (other host threads, other handles on the
  *    same device) race on it and must be serialised by the caller.  Nothing
  *    in it needs clearing: the RHS kernel overwrites every value read back.  */
 int dg_rhs_host_noalloc(dg_handle *h, float *r_out);
+
+/* Measurement helper (the paper states its GPU's FP32 peak in Section 4.1;
+ * this measures the current device's): FP32 fused multiply-add throughput in
+ * TFLOP/s (one FMA = 2 flops).  Every thread of a grid that fills every SM
+ * runs 8 independent FMA chains whose operands are kernel arguments; the
+ * scalar FP32 FMA and the packed two-lane form (fma.rn.f32x2) are timed
+ * separately, `reps` launches of about `target_ms` each after one sizing
+ * launch, and the best launch of each form is returned (*scalar_tflops,
+ * *packed_tflops; *ms_per_launch = the longer of the two best launches; any
+ * pointer may be NULL).  Runs on `stream` (cudaStream_t, NULL = legacy
+ * default stream) of the current device and synchronises it; allocates
+ * nothing.  DG_EINVAL for reps < 1 or target_ms outside (0, 10000].        */
+int dg_fp32_peak(void *stream, int reps, double target_ms, double *scalar_tflops,
+                 double *packed_tflops, double *ms_per_launch);
 
 /* Wait for the handle's stream; DG_ETIMEOUT if a device wait expired.       */
 int dg_sync(dg_handle *h);

@@ -26,7 +26,7 @@ EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", 
            "dg_set_dt", "dg_sync", "dg_autotune", "dg_kernel_info", "dg_set_variant", "dg_node_coords", "dg_set_source", "dg_add_source", "dg_suggest_dt",
            "dg_reference_element", "dg_last_error", "dg_server_create", "dg_submit", "dg_poll",
            "dg_cancel", "dg_server_stats", "dg_server_destroy", "dg_rhs_host_noalloc", "dg_set_receivers",
-           "dg_get_traces")
+           "dg_get_traces", "dg_fp32_peak")
 
 
 class DGError(RuntimeError):
@@ -95,6 +95,7 @@ def lib():
         "dg_rhs_host_noalloc": (i32, [vp, vp]),
         "dg_set_receivers": (i32, [vp, P(dbl), i32]),
         "dg_get_traces": (i32, [vp, vp, P(i64), i32]),
+        "dg_fp32_peak": (i32, [vp, i32, dbl, P(dbl), P(dbl), P(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -192,6 +193,15 @@ def reference_element(N):
     check(lib().dg_reference_element(int(N), _dptr(nodes), _dptr(Dr), _dptr(Ds), _dptr(Dt), _dptr(LIFT),
                                      fm.ctypes.data_as(C.POINTER(C.c_int32))))
     return dict(nodes=nodes, Dr=Dr, Ds=Ds, Dt=Dt, LIFT=LIFT, fmask=fm)
+
+
+def fp32_peak(stream=None, reps=5, target_ms=20.0):
+    """FP32 FMA throughput of the current device (dg_fp32_peak): best TFLOP/s
+    of the scalar and of the packed two-lane FMA form, and the longer of the
+    two best launch times in ms."""
+    s, p, ms = C.c_double(), C.c_double(), C.c_double()
+    check(lib().dg_fp32_peak(stream, int(reps), float(target_ms), C.byref(s), C.byref(p), C.byref(ms)))
+    return {"scalar_tflops": s.value, "packed_tflops": p.value, "ms": ms.value}
 
 
 class Solver:

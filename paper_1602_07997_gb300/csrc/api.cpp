@@ -239,7 +239,7 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
   r1slot = 0;
   step = 0;
   have = 0;
-  return DG_OK;
+  return noalloc_prepare();
 }
 
 Handle::~Handle() {

@@ -120,6 +120,10 @@ struct KernelCfg {
 const KernelCfg* kernel_variants(int model, int N, int* count, int precision = 0);
 const KernelCfg* kernel_cfg(int model, int N);
 
+// Opt the step kernel of `cfg` into its shared memory and read its occupancy
+// on the current device, and load the small source kernel: everything
+// launch_step (non-split cfg) and launch_xsrc set up on their first call.
+cudaError_t prepare_step(const KernelCfg* cfg);
 // Launch the persistent step kernel on `stream` (grid = min(blocks, SMs x occupancy)).
 cudaError_t launch_step(const KernelCfg* cfg, const StepArgs& args, cudaStream_t stream);
 // One batched step over every solve of `args` (same model and N); a split

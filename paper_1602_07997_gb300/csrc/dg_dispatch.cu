@@ -136,6 +136,15 @@ __global__ void __launch_bounds__(256) xsrc_batched_kernel(const BatchArgs b, in
   add_xsrc(d.xs, d.step, NfNp, 0, a.dt * a.a1, a.qn, a.r2, nullptr);
 }
 
+cudaError_t prepare_step(const KernelCfg* c) {
+  if (!c) return cudaErrorInvalidValue;
+  int cap = 0;
+  cudaError_t e = prepare_fn(c, reinterpret_cast<const void*>(c->fn), &cap);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  return cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(xsrc_kernel));
+}
+
 cudaError_t launch_xsrc(const XSrc& xs, long long step, int NfNp, const StepArgs& a, cudaStream_t stream) {
   if (xs.n <= 0) return cudaSuccess;
   xsrc_kernel<<<1, 256, 0, stream>>>(xs, step, NfNp, a.mode, a.dt * a.a1, a.qn, a.r2, a.rout);

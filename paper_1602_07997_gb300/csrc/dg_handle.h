@@ -80,8 +80,15 @@ struct Handle {
   float* d_traces = nullptr;  // [trace_cap][nrec][Nf]
   int64_t trace_cap = 0, nsamples = 0;
   std::vector<double> Vinv;   // inverse Vandermonde, on first use
+  // dg_rhs_host_noalloc: device address of the library's fixed scratch array
+  // and the fused FP32 variant it runs, both resolved (and that kernel
+  // loaded) by init; null when the mesh's RHS does not fit the array
+  float* noalloc_scratch = nullptr;
+  const dgk::KernelCfg* noalloc_cfg = nullptr;
 
   int init(const dg_mesh* mesh, const double* coeffs, int N, int model, const dg_opts* o);
+  // set-up of dg_rhs_host_noalloc (rhs_noalloc.cu), called at the end of init
+  int noalloc_prepare();
   // element whose smallest barycentric coordinate of x is largest, and the
   // reference coordinates of x in it; -1 if x is outside the mesh
   int64_t locate(const double x[3], double rst[3]) const;
