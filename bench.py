@@ -486,15 +486,6 @@ def make_solvers(P, cfgs, model, precision, stream, tune, variants=None, strateg
     return solvers
 
 
-def launches_per_step(g, strategy="fused"):
-    """Kernels of this library launched per step (cuBLAS GEMMs not counted)."""
-    if strategy == "library":
-        return 2  # front half + epilogue
-    if strategy == "plain":
-        return 3  # volume, surface, update
-    return 2 if g.kernel_info()["split"] else 1
-
-
 def per_degree(model, g, ms, pk, tensor=False, factored=False):
     """One row of the per-degree table: algorithmic bytes and FLOPs over the
     measured time, and the roofline that bounds the path (tensor-core modes:
@@ -620,6 +611,7 @@ def run(args, rank, world, local_rank):
                 g.step(1)
             torch.cuda.synchronize()
         barrier()
+        lc0 = [g.launch_count() for g in solvers]
         t0 = time.perf_counter()
         e_all0.record(stream)
         for s in range(args.steps):
@@ -651,7 +643,8 @@ def run(args, rank, world, local_rank):
         if dom is None or ms > dom[1]:
             byt, flop = algorithmic(model, g.N, g.K)
             dom = (g, ms, byt, flop, row["bound"])
-    launches = sum(launches_per_step(g, args.strategy) for g in solvers) * args.steps
+    # kernels of the library launched in the timed region, as the handles count them
+    launches = sum(g.launch_count() - c for g, c in zip(solvers, lc0))
     g, ms, byt, flop, bound = dom
     traffic = None
     try:

@@ -259,8 +259,33 @@ int dg_rhs_host_noalloc(dg_handle *h, float *r_out);
 int dg_fp32_peak(void *stream, int reps, double target_ms, double *scalar_tflops,
                  double *packed_tflops, double *ms_per_launch);
 
-/* Wait for the handle's stream; DG_ETIMEOUT if a device wait expired.       */
+/* Wait for the handle's stream and report what the kernels flagged since the
+ * last report: DG_ETIMEOUT if a bounded device wait expired (the results of
+ * those steps are not valid), else DG_ENONFINITE if a finite-state check
+ * found a NaN or an infinity in q.  The flag is cleared when it is reported,
+ * so the handle stays usable (e.g. dg_set_state and step again).           */
 int dg_sync(dg_handle *h);
+
+/* Failure detection (the paper's method has no counterpart; these guard its
+ * time loop).
+ * dg_set_finite_check: after every `every`-th step of dg_step (step index m
+ * a multiple of `every`) a small kernel reads q^m and flags a NaN or an
+ * infinity for dg_sync (DG_ENONFINITE); every = 0 turns it off.  Default
+ * 100 (one extra read of q per 100 steps).  DG_EINVAL for every < 0.
+ * dg_set_wait_limit: every bounded device wait of the handle's kernels (a
+ * wait for a bulk copy or for the tensor cores) gives up after `cycles` SM
+ * clock cycles and flags DG_ETIMEOUT for dg_sync; 0 = the default 2^31
+ * (about a second).  A negative value makes the first wait of every CTA
+ * give up at once without looking: a test hook that exercises the expiry
+ * path, after which each CTA waits (with the default limit) for the copies
+ * and products it has in flight and leaves.  Neither call launches work.  */
+int dg_set_finite_check(dg_handle *h, int every);
+int dg_set_wait_limit(dg_handle *h, int64_t cycles);
+
+/* Kernels of this library the handle has launched so far (step kernels,
+ * split-step GEMMs, source, receiver and finite-check kernels; the cuBLAS
+ * GEMMs of DG_STRATEGY_LIBRARY are not counted).                           */
+int dg_launch_count(const dg_handle *h, int64_t *launches);
 
 /* Physical node coordinates, double [K][Np][3].                             */
 int dg_node_coords(const dg_handle *h, double *xyz);

@@ -23,8 +23,9 @@ mesh     per-element geometry (Jacobian, inverse metric, normals, Fscale)
          and face / face-node connectivity.
 dg       acoustic and elastic right-hand sides (volume + flux + lift),
          boundary ghosts, AB3 time stepping, discrete energy, sources.
-brute    an independent weak-form evaluation by physical-coordinate
-         quadrature, used only to pin ``dg`` on tiny meshes.
+
+The independent weak-form evaluation by physical-coordinate quadrature that
+pins ``dg`` on tiny meshes lives with its test (tests/test_oracle_brute.py).
 """
 
 from . import refelem, mesh, dg  # noqa: F401

@@ -26,7 +26,7 @@ EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", 
            "dg_set_dt", "dg_sync", "dg_autotune", "dg_kernel_info", "dg_set_variant", "dg_node_coords", "dg_set_source", "dg_add_source", "dg_suggest_dt",
            "dg_reference_element", "dg_last_error", "dg_server_create", "dg_submit", "dg_poll",
            "dg_cancel", "dg_server_stats", "dg_server_destroy", "dg_rhs_host_noalloc", "dg_set_receivers",
-           "dg_get_traces", "dg_fp32_peak")
+           "dg_get_traces", "dg_fp32_peak", "dg_set_finite_check", "dg_set_wait_limit", "dg_launch_count")
 
 
 class DGError(RuntimeError):
@@ -96,6 +96,9 @@ def lib():
         "dg_set_receivers": (i32, [vp, P(dbl), i32]),
         "dg_get_traces": (i32, [vp, vp, P(i64), i32]),
         "dg_fp32_peak": (i32, [vp, i32, dbl, P(dbl), P(dbl), P(dbl)]),
+        "dg_set_finite_check": (i32, [vp, i32]),
+        "dg_set_wait_limit": (i32, [vp, i64]),
+        "dg_launch_count": (i32, [vp, P(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -302,8 +305,23 @@ class Solver:
         check(lib().dg_step(self.h, int(n)))
 
     def sync(self):
-        """Wait for the stream; raises DGError (DG_ETIMEOUT) if a bounded device wait expired."""
+        """Wait for the stream; raises DGError with DG_ETIMEOUT if a bounded device
+        wait expired, or DG_ENONFINITE if a finite-state check found NaN/Inf."""
         check(lib().dg_sync(self.h))
+
+    def set_finite_check(self, every):
+        """Check q for NaN/Inf after every `every`-th step (0 = never; default 100)."""
+        check(lib().dg_set_finite_check(self.h, int(every)))
+
+    def set_wait_limit(self, cycles):
+        """Cycles before a bounded device wait gives up (0 = default; < 0 = at once, a test hook)."""
+        check(lib().dg_set_wait_limit(self.h, int(cycles)))
+
+    def launch_count(self):
+        """Kernels of this library launched by the handle so far."""
+        n = C.c_int64()
+        check(lib().dg_launch_count(self.h, C.byref(n)))
+        return n.value
 
     def autotune(self, reps=5):
         """Time every compiled kernel variant on this mesh and keep the fastest.

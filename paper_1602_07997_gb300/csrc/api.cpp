@@ -295,9 +295,11 @@ int Handle::ensure_strategy() {
 }
 
 int Handle::launch(dgk::StepArgs a) {
+  const int nx = xs.n > 0 ? 1 : 0;  // the kernel of the sources beyond the first
   if (opts.strategy == DG_STRATEGY_FUSED) {
     DG_CUDA(dgk::launch_step(cfg, a, stream));
     DG_CUDA(dgk::launch_xsrc(xs, step, Nf * Np, a, stream));
+    launches += (cfg->split ? 2 : 1) + nx;
     return DG_OK;
   }
   int rc = ensure_strategy();
@@ -305,6 +307,7 @@ int Handle::launch(dgk::StepArgs a) {
   if (opts.strategy == DG_STRATEGY_PLAIN) {
     DG_CUDA(dgk::launch_plain_step(model, N, a, d_r0, stream));
     DG_CUDA(dgk::launch_xsrc(xs, step, Nf * Np, a, stream));
+    launches += 3 + nx;
     return DG_OK;
   }
   // library route: front half, GEMMs, epilogue
@@ -317,6 +320,7 @@ int Handle::launch(dgk::StepArgs a) {
   if (st != 0) return fail(DG_ECUDA, "cuBLAS SGEMM failed with status " + std::to_string(st));
   DG_CUDA(dgk::launch_library_epilogue(model, N, a, d_liby, libyprod, stream));
   DG_CUDA(dgk::launch_xsrc(xs, step, Nf * Np, a, stream));
+  launches += 2 + nx;  // front half and epilogue (the cuBLAS GEMMs are not this library's kernels)
   return DG_OK;
 }
 
@@ -434,6 +438,7 @@ dgk::StepArgs Handle::args(int mode) const {
   else if (have == 1) { a.a1 = 1.5f; a.a2 = -0.5f; a.a3 = 0.0f; }
   else { a.a1 = float(23.0 / 12.0); a.a2 = float(-16.0 / 12.0); a.a3 = float(5.0 / 12.0); }
   a.err = d_err;
+  a.wait_limit = wait_limit;
   split_ptrs(a, cfg);
   return a;
 }
@@ -475,6 +480,11 @@ int Handle::advance(int nsteps) {
       DG_CUDA(dgk::launch_sample(d_q[qcur], d_recel, d_recvec, nrec, Nf, Np,
                                  d_traces + size_t(nsamples) * nrec * Nf, stream));
       ++nsamples;
+      ++launches;
+    }
+    if (finite_every > 0 && step % finite_every == 0) {
+      DG_CUDA(dgk::launch_finite_check(d_q[qcur], (long long)K * Nf * Np, d_err, stream));
+      ++launches;
     }
   }
   return DG_OK;
@@ -678,7 +688,29 @@ int dg_sync(dg_handle* h) {
   DG_CUDA(cudaStreamSynchronize(h->stream));
   int err = 0;
   DG_CUDA(cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost));
-  if (err) return fail(DG_ETIMEOUT, "a bounded device-side wait expired");
+  if (!err) return DG_OK;
+  // report once: the error word starts over for the next steps
+  DG_CUDA(cudaMemsetAsync(h->d_err, 0, 4, h->stream));
+  DG_CUDA(cudaStreamSynchronize(h->stream));
+  if (err & 1) return fail(DG_ETIMEOUT, "a bounded device-side wait expired");
+  return fail(DG_ENONFINITE, "the state holds a NaN or an infinity");
+}
+
+int dg_set_wait_limit(dg_handle* h, int64_t cycles) {
+  if (!h) return fail(DG_EINVAL, "NULL handle");
+  h->wait_limit = (long long)cycles;
+  return DG_OK;
+}
+
+int dg_set_finite_check(dg_handle* h, int every) {
+  if (!h || every < 0) return fail(DG_EINVAL, "NULL handle or negative interval");
+  h->finite_every = every;
+  return DG_OK;
+}
+
+int dg_launch_count(const dg_handle* h, int64_t* launches) {
+  if (!h || !launches) return fail(DG_EINVAL, "NULL handle or output");
+  *launches = h->launches;
   return DG_OK;
 }
 
@@ -888,7 +920,10 @@ int dg_autotune(dg_handle* h, int reps, int* block_elems, double* ms_per_step, d
   if (rc) return rc;
   int err = 0;
   DG_CUDA(cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost));
-  if (err) return fail(DG_ETIMEOUT, "a bounded device-side wait expired during tuning");
+  if (err & 1) {
+    DG_CUDA(cudaMemset(h->d_err, 0, 4));
+    return fail(DG_ETIMEOUT, "a bounded device-side wait expired during tuning");
+  }
   h->cfg = &v[best];
   {
     std::lock_guard<std::mutex> lock(dg::g_tune_mu);

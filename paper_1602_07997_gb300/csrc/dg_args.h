@@ -54,6 +54,7 @@ struct StepArgs {
   float* xg;             // split step: GEMM inputs X[tile][row][NE]
   const float* ops2;     // split step (FP32): operator blob [3Np + 4Nfp][rows padded to 32]
   const void* opstc;     // split step (tensor cores): BF16 operator pieces, core-matrix layout
+  long long wait_limit;  // bounded device waits: cycles before giving up (0 = 2^31; < 0 = at once, a test hook)
 };
 
 // Per-solve device state of a batched launch (served mode).  The step index,
@@ -93,6 +94,7 @@ struct BatchArgs {
   const int* tile_start;   // [nsolves + 1] first global tile of each solve
   const int* tile_solve;   // [total_tiles] solve of each global tile
   int total_tiles;
+  long long wait_limit;    // as StepArgs::wait_limit
 };
 
 // Host-visible launch configuration of one (model, N) instantiation.  A
@@ -137,6 +139,8 @@ cudaError_t launch_advance(SolveDev* solves, int nsolves, cudaStream_t stream);
 cudaError_t launch_xsrc(const XSrc& xs, long long step, int NfNp, const StepArgs& a, cudaStream_t stream);
 // The same for every solve of a batch with sources, before its advance.
 cudaError_t launch_xsrc_batched(const BatchArgs& b, int NfNp, cudaStream_t stream);
+// Finite-state check: sets bit 1 of *err if any of q[0..n) is NaN or +-Inf.
+cudaError_t launch_finite_check(const float* q, long long n, int* err, cudaStream_t stream);
 // Receiver sample: out[r][f] = sum_i vec[r][i] q[elem[r]][f][i].
 cudaError_t launch_sample(const float* q, const int* elem, const float* vec, int nrec, int Nf, int Np, float* out,
                           cudaStream_t stream);

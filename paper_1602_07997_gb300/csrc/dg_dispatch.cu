@@ -81,6 +81,30 @@ cudaError_t launch_step(const KernelCfg* c, const StepArgs& args, cudaStream_t s
                           c->smem_gemm, stream);
 }
 
+// Non-finite = exponent bits all ones (NaN or +-Inf).  Grid-stride float4
+// loads (q is 256-byte aligned), then one vote per CTA.
+__device__ __forceinline__ bool nonfinite(float x) { return (__float_as_uint(x) & 0x7f800000u) == 0x7f800000u; }
+
+__global__ void __launch_bounds__(256) finite_kernel(const float* __restrict__ q, long long n, int* err) {
+  bool bad = false;
+  const long long n4 = n >> 2, stride = (long long)gridDim.x * 256;
+  const float4* q4 = reinterpret_cast<const float4*>(q);
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n4; i += stride) {
+    const float4 v = __ldg(q4 + i);
+    bad |= nonfinite(v.x) | nonfinite(v.y) | nonfinite(v.z) | nonfinite(v.w);
+  }
+  for (long long i = 4 * n4 + (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += stride) bad |= nonfinite(q[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, 2);
+}
+
+cudaError_t launch_finite_check(const float* q, long long n, int* err, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const long long blocks = ((n >> 2) + 255) / 256;
+  const int grid = int(blocks < 1 ? 1 : (blocks > 152 * 8 ? 152 * 8 : blocks));
+  finite_kernel<<<grid, 256, 0, stream>>>(q, n, err);
+  return cudaGetLastError();
+}
+
 // one warp per (receiver, field): lanes over the nodes, then a warp sum
 __global__ void sample_kernel(const float* __restrict__ q, const int* __restrict__ elem,
                               const float* __restrict__ vec, int nrec, int Nf, int Np, float* __restrict__ out) {

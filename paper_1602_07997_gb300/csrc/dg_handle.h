@@ -60,6 +60,9 @@ struct Handle {
   size_t libyprod = 0;
   float* d_r0 = nullptr;
 
+  long long wait_limit = 0;  // bounded device waits (StepArgs::wait_limit)
+  int finite_every = 100;    // check the state for NaN/Inf after every this many steps (0 = never)
+  int64_t launches = 0;      // kernels of this library launched by the handle
   int qcur = 0;    // which q buffer holds q^m
   int r1slot = 0;  // which r buffer holds r^{m-1}; the other holds r^{m-2}
   int64_t step = 0;

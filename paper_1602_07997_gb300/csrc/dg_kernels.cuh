@@ -109,13 +109,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after ~2^31 clock cycles (about a second) and
-// reports through the error word.  Returns false on expiry.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+// Bounded wait: gives up after `limit` clock cycles (0 = the default 2^31,
+// about a second) and sets bit 0 of the error word.  limit < 0 gives up at
+// once without looking at the barrier (a test hook: every first wait of a
+// kernel expires).  Returns false on expiry.  Drains after an expiry always
+// use the default limit.
+constexpr long long kWaitLimit = 1ll << 31;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err,
+                                                  long long limit = kWaitLimit) {
+  if (limit < 0) {
+    if (err) atomicOr(err, 1);
+    return false;
+  }
+  const long long lim = limit > 0 ? limit : kWaitLimit;
   long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1ll << 31)) {
-      if (err) atomicExch(err, 1);
+    if (clock64() - t0 > lim) {
+      if (err) atomicOr(err, 1);
       return false;
     }
   }
@@ -420,6 +430,7 @@ struct SingleSolve {
   __device__ const int* ftab() const { return a.ftab; }
   __device__ int* err() const { return a.err; }
   __device__ int mode() const { return a.mode; }
+  __device__ long long limit() const { return a.wait_limit; }
 };
 
 // Step arguments of one solve of a batch, from its device-side state.
@@ -447,6 +458,7 @@ __device__ __forceinline__ void solve_args(const BatchArgs& B, const SolveDev& d
     else if (d.have == 1) { A.a1 = 1.5f; A.a2 = -0.5f; A.a3 = 0.f; }
     else { A.a1 = 23.f / 12.f; A.a2 = -16.f / 12.f; A.a3 = 5.f / 12.f; }
     A.err = B.err;
+    A.wait_limit = B.wait_limit;
     A.xg = d.xg;
     A.ops2 = B.ops2;
     A.opstc = nullptr;
@@ -465,6 +477,7 @@ struct SolveBatch {
   __device__ const int* ftab() const { return B.ftab; }
   __device__ int* err() const { return B.err; }
   __device__ int mode() const { return 0; }
+  __device__ long long limit() const { return B.wait_limit; }
 };
 
 // ---------------------------------------------------------------- kernel body
@@ -509,6 +522,27 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
   constexpr uint32_t kQBytes = uint32_t(P::nQ * 4);
   constexpr uint32_t kRecBytes = uint32_t(EB * REC * 4);
   constexpr uint32_t kStageBytes = kQBytes + kRecBytes + uint32_t(EB * 16);
+
+  // Copies in flight, for the drain after an expired wait: bit i of pmask is
+  // set while barrier i (stages 0/1, history 2, halo buffers 3/4) has a phase
+  // with copies issued and not yet seen complete, bit i of ppar is that
+  // phase's parity.  The issue conditions are CTA-uniform, so every thread
+  // keeps the same bits (cp.async gathers are drained per thread, bulk stores
+  // by the thread that issued them).
+  const long long lim = prov.limit();
+  uint32_t pmask = 0, ppar = 0;
+  auto pend_set = [&](int i, uint32_t par) {
+    pmask |= 1u << i;
+    ppar = (ppar & ~(1u << i)) | (par << i);
+  };
+  auto pend_clr = [&](int i) { pmask &= ~(1u << i); };
+  auto drain = [&]() {
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      if (pmask & (1u << i)) mbar_wait_bounded(&bars[i], (ppar >> i) & 1u, nullptr);
+    cp_async_wait_all();
+    if (tid == 0) bulk_wait_all();
+  };
 
   auto stage = [&](int s) { return smem + (s ? P::oStage1 : P::oStage0); };
   auto issue_stage = [&](const StepArgs& a, int lb, int s, bool with_ops) {
@@ -590,6 +624,7 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
   int nxt_lb = 0;
   if ((int)blockIdx.x < nblk) prov.get(blockIdx.x, nxt_a, nxt_lb);
   if (tid == 0 && (int)blockIdx.x < nblk) issue_stage(nxt_a, nxt_lb, 0, true);
+  if ((int)blockIdx.x < nblk) pend_set(0, 0u);
   for (int i = tid; i < 10 * Nfp; i += NT) sFtab[i] = prov.ftab()[i];
   __syncthreads();
   if constexpr (FACT) {
@@ -601,11 +636,13 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     }
   }
   if ((int)blockIdx.x < nblk) {
-    if (!__syncthreads_and(mbar_wait_bounded(&bars[0], 0u, err))) {
-      mbar_wait_bounded(&bars[0], 0u, nullptr);
+    if (!__syncthreads_and(mbar_wait_bounded(&bars[0], 0u, err, lim))) {
+      drain();
       return;
     }
+    pend_clr(0);
     issue_gathers(nxt_a, nxt_lb, 0);
+    if constexpr (HALO) pend_set(3, 0u);
   }
 
   int it = 0;
@@ -615,14 +652,15 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     const int lb = nxt_lb;
     const int k0 = lb * EB;
     if (b + G < nblk) prov.get(b + G, nxt_a, nxt_lb);
-    bool ok = mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), err);
-    if constexpr (HALO) ok = mbar_wait_bounded(&bars[3 + s], uint32_t((it >> 1) & 1), err) && ok;
+    bool ok = mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), err, lim);
+    if constexpr (HALO) ok = mbar_wait_bounded(&bars[3 + s], uint32_t((it >> 1) & 1), err, lim) && ok;
     else cp_async_wait_all();  // this block's neighbour traces
     if (!__syncthreads_and(ok)) {
-      mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), nullptr);
-      if constexpr (HALO) mbar_wait_bounded(&bars[3 + s], uint32_t((it >> 1) & 1), nullptr);
+      drain();
       return;
     }
+    pend_clr(s);
+    if constexpr (HALO) pend_clr(3 + s);
     // everyone is past the previous block: stage s^1, sR, the inputs and trace buffer s^1 are free
     const float* sQ = stage(s) + P::sQ;
     const float* sRec = stage(s) + P::sRec;
@@ -637,6 +675,9 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
         tma_bulk_g2s(sR + P::nQ, a.r2 + size_t(k0) * Nf * Np, kQBytes, &bars[2]);
       }
     }
+    const uint32_t pnext = uint32_t(((it + 1) >> 1) & 1);  // phase of stage s^1 for the next block
+    if (b + G < nblk) pend_set(s ^ 1, pnext);
+    if (R_SMEM && mode == 0) pend_set(2, uint32_t(it & 1));
 
     // -------- face normals and Fscale (n = g N_f / |g N_f|); the per-face
     // arrays are face-major, entry f EBF + e (element-fastest lanes read
@@ -813,16 +854,30 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       // neighbour gathers (its trace buffer was last read before the
       // barrier at the top of this block) and move on
       static_assert(SPLIT % 4 == 0 && (SPLIT % EB == 0 || EB % SPLIT == 0), "element blocks inside column tiles");
+      // (cp.async gathers: a thread whose wait expired issues none of its own;
+      // its wait at the top of the next block expires again and the CTA stops)
       if (b + G < nblk) {
-        if (mbar_wait_bounded(&bars[s ^ 1], uint32_t(((it + 1) >> 1) & 1), err)) issue_gathers(nxt_a, nxt_lb, s ^ 1);
+        if (mbar_wait_bounded(&bars[s ^ 1], pnext, err, lim)) {
+          pend_clr(s ^ 1);
+          issue_gathers(nxt_a, nxt_lb, s ^ 1);
+        }
       }
       continue;
     }
-    __syncthreads();
     // the next block's stage was issued at the top of this block: once it has
     // landed, start its neighbour gathers so that they overlap the products
+    // (a CTA-wide decision: halo copies need every thread's arrival)
+    {
+      const bool okn = b + G < nblk ? mbar_wait_bounded(&bars[s ^ 1], pnext, err, lim) : true;
+      if (!__syncthreads_and(okn)) {
+        drain();
+        return;
+      }
+    }
     if (b + G < nblk) {
-      if (mbar_wait_bounded(&bars[s ^ 1], uint32_t(((it + 1) >> 1) & 1), err)) issue_gathers(nxt_a, nxt_lb, s ^ 1);
+      pend_clr(s ^ 1);
+      issue_gathers(nxt_a, nxt_lb, s ^ 1);
+      if constexpr (HALO) pend_set(3 + (s ^ 1), pnext);
     }
 
     if constexpr (SPLIT > 0 && XP > 0) {
@@ -1094,11 +1149,12 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
       return make_float4(o[0], o[1], o[2], o[3]);
     };
     bool okr = true;
-    if constexpr (R_SMEM) okr = mbar_wait_bounded(&bars[2], uint32_t(it & 1), err);  // history landed
+    if constexpr (R_SMEM) okr = mbar_wait_bounded(&bars[2], uint32_t(it & 1), err, lim);  // history landed
     if (!__syncthreads_and(okr)) {
-      if (R_SMEM) mbar_wait_bounded(&bars[2], uint32_t(it & 1), nullptr);
+      drain();
       return;
     }
+    if constexpr (R_SMEM) pend_clr(2);
     const float a1 = a.a1, a2 = a.a2, a3 = a.a3, dt = a.dt;
     if constexpr (R_SMEM) {
       // q^{m+1} replaces r^{m-1} and r^m replaces r^{m-2} in sR, then both are bulk-stored

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(192, 1) dg_tc_gemm_kernel(const StepArgs a) {
         const int t = int(blockIdx.x) + j * int(gridDim.x);
         const int mtile = t % MTILES, ntile = t / MTILES;
         const int rb = j & 1;
-        if (j >= 2 && !mbar_wait_bounded(&rempty[rb], uint32_t(((j >> 1) - 1) & 1), a.err)) {
+        if (j >= 2 && !mbar_wait_bounded(&rempty[rb], uint32_t(((j >> 1) - 1) & 1), a.err, a.wait_limit)) {
           ok = false;
           break;
         }
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(192, 1) dg_tc_gemm_kernel(const StepArgs a) {
         const uint8_t* XT = reinterpret_cast<const uint8_t*>(a.xg) + size_t(ntile) * TX::TILE;
         for (int c = 0; c < NCH; ++c, ++g) {
           const int s = g % NS;
-          if (g >= NS && !mbar_wait_bounded(&empty[s], uint32_t(((g / NS) - 1) & 1), a.err)) {
+          if (g >= NS && !mbar_wait_bounded(&empty[s], uint32_t(((g / NS) - 1) & 1), a.err, a.wait_limit)) {
             ok = false;
             break;
           }
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(192, 1) dg_tc_gemm_kernel(const StepArgs a) {
       for (int j = 0; j < nmine && ok; ++j) {
         const int b = j % NBUF;
         if (j >= NBUF) {
-          if (!mbar_wait_bounded(&tempty[b], uint32_t(((j / NBUF) - 1) & 1), a.err)) {
+          if (!mbar_wait_bounded(&tempty[b], uint32_t(((j / NBUF) - 1) & 1), a.err, a.wait_limit)) {
             ok = false;
             break;
           }
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(192, 1) dg_tc_gemm_kernel(const StepArgs a) {
         const uint32_t tacc = tmem + uint32_t(b * TS::TCOLS);
         for (int c = 0; c < NCH; ++c, ++g) {
           const int s = g % NS;
-          if (!mbar_wait_bounded(&full[s], uint32_t((g / NS) & 1), a.err)) {
+          if (!mbar_wait_bounded(&full[s], uint32_t((g / NS) & 1), a.err, a.wait_limit)) {
             ok = false;
             break;
           }
@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(192, 1) dg_tc_gemm_kernel(const StepArgs a) {
         if (ok) tc_commit(&tfull[b]);
       }
       tc_commit(done);  // arrives once every product issued above has completed
+      // (always the default limit: TMEM is freed only after this wait)
       if (!mbar_wait_bounded(done, 0u, a.err)) ok = false;
     }
     __syncwarp();
@@ -339,8 +340,8 @@ __global__ void __launch_bounds__(192, 1) dg_tc_gemm_kernel(const StepArgs a) {
       const int t = int(blockIdx.x) + j * int(gridDim.x);
       const int mtile = t % MTILES, ntile = t / MTILES;
       const int b = j % NBUF, rb = j & 1;
-      bool got = mbar_wait_bounded(&tfull[b], uint32_t((j / NBUF) & 1), a.err);
-      got = got && mbar_wait_bounded(&rfull[rb], uint32_t((j >> 1) & 1), a.err);
+      bool got = mbar_wait_bounded(&tfull[b], uint32_t((j / NBUF) & 1), a.err, a.wait_limit);
+      got = got && mbar_wait_bounded(&rfull[rb], uint32_t((j >> 1) & 1), a.err, a.wait_limit);
       if (!__all_sync(0xffffffffu, got)) {
         ok = false;
         break;
