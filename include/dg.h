@@ -324,15 +324,16 @@ int dg_reference_element(int N, double *nodes, double *Dr, double *Ds, double *D
 const char *dg_last_error(void);
 
 /* ----------------------------------------------------------------------------
- * Served solves.  A server owns a host thread and one CUDA stream.  Each
+ * Served solves.  A server owns a host thread and its CUDA streams.  Each
  * request is an independent time-domain solve (mesh, coefficients, N, model,
  * initial state, source, nsteps).  Requests are admitted while free device
  * memory (cudaMemGetInfo) minus a safety margin, and the optional budget,
  * cover their state; admitted solves of the same degree and model are
  * advanced together, one batched step per (model, N) class per time step
- * (one launch, or two for the split step, then a small launch that advances
- * every solve's step counter and AB3 phase), and new requests join between
- * steps (continuous batching).  A finished
+ * (one launch, or two for the split step; the classes' launches run
+ * concurrently, each class on its own stream of the tick's CUDA graph, then
+ * a small launch per class advances every solve's step counter and AB3
+ * phase), and new requests join between steps (continuous batching).  A finished
  * solve's q is copied to host memory owned by the server until dg_poll
  * copies it out.
  * ------------------------------------------------------------------------ */

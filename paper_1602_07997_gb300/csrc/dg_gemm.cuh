@@ -48,6 +48,15 @@ __device__ __forceinline__ void cp_async_wait_n() {
   asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
 }
 
+// Two FP32 FMAs lane by lane, d = a b + c: one packed instruction
+// (fma.rn.f32x2) when PK, else two scalar FMAs; the same rounding either way.
+template <bool PK>
+__device__ __forceinline__ float2 fma2(const float2 a, const float2 b, const float2 c) {
+  if constexpr (PK) return __ffma2_rn(a, b, c);
+  else return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 dup2(const float x) { return make_float2(x, x); }
+
 // AB3 update (a.mode 0) or RHS store (mode 1) of U values: every load of the
 // batch is issued before the first store, so that their latencies overlap.
 template <int U>
@@ -467,7 +476,7 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
 // registers sized for two resident CTAs per SM.  HALF (narrow only): a CTA
 // takes half of a column tile of X (32 acoustic elements), so that two CTAs
 // fit per SM with the registers of the narrow design.
-template <int MODEL, int N, bool NARROW = false, bool SMALL = false, bool HALF = false>
+template <int MODEL, int N, bool NARROW = false, bool SMALL = false, bool HALF = false, bool PK = false>
 struct GemmB {
   using S = Sz<N>;
   static constexpr int Np = S::Np, NFN = S::NFN;
@@ -522,9 +531,9 @@ struct GemmB {
   static_assert(NS >= 2, "the copy of a chunk is issued after the barrier that retires its stage");
 };
 
-template <int MODEL, int N, bool NARROW = false, bool SMALL = false, bool HALF = false>
+template <int MODEL, int N, bool NARROW = false, bool SMALL = false, bool HALF = false, bool PK = false>
 __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l, const int ntile) {
-  using SS = GemmB<MODEL, N, NARROW, SMALL, HALF>;
+  using SS = GemmB<MODEL, N, NARROW, SMALL, HALF, PK>;
   // NE: elements of this CTA; XNE: row stride of X (elements per column tile)
   constexpr int Np = SS::Np, NFN = SS::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NEG, TM = SS::TM, TE = SS::TE;
   constexpr int XNE = SS::NE;
@@ -595,28 +604,29 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
   const int ct = tid % CT, rt = tid / CT;
   const int il = TM * rt, e0 = TE * ct;
 
-  float acc[NACC][TE][TM];
+  // accumulators in pairs of consecutive rows (the operands of the packed
+  // FMAs); ACC(x, t, v) is row v of element column t of accumulator x
+  float2 acc2[NACC][TE][TM / 2];
+#define ACC(I_, T_, V_) (((V_) & 1) ? acc2[I_][T_][(V_) >> 1].y : acc2[I_][T_][(V_) >> 1].x)
 #pragma unroll
   for (int x = 0; x < NACC; ++x)
 #pragma unroll
     for (int t = 0; t < TE; ++t)
 #pragma unroll
-      for (int v = 0; v < TM; ++v) acc[x][t][v] = 0.f;
-  float lf[MODEL == 0 ? TE : 1][TM];  // acoustic: LIFT_f psi of the current face f
+      for (int v = 0; v < TM / 2; ++v) acc2[x][t][v] = make_float2(0.f, 0.f);
+  float2 lf2[MODEL == 0 ? TE : 1][TM / 2];  // acoustic: LIFT_f psi of the current face f
 #pragma unroll
   for (int t = 0; t < (MODEL == 0 ? TE : 1); ++t)
 #pragma unroll
-    for (int v = 0; v < TM; ++v) lf[t][v] = 0.f;
+    for (int v = 0; v < TM / 2; ++v) lf2[t][v] = make_float2(0.f, 0.f);
   float lamv[TE], muv[TE];  // elastic: Lame coefficients of the element columns (set at the boundary)
 
-  auto ldA = [&](const float* p, float* o) {  // TM consecutive rows, as float4s
+  auto ldA = [&](const float* p, float2* o) {  // TM consecutive rows, as float4s, in row pairs
 #pragma unroll
     for (int q = 0; q < TM / 4; ++q) {
       const float4 v = *reinterpret_cast<const float4*>(p + 4 * q);
-      o[4 * q] = v.x;
-      o[4 * q + 1] = v.y;
-      o[4 * q + 2] = v.z;
-      o[4 * q + 3] = v.w;
+      o[2 * q] = make_float2(v.x, v.y);
+      o[2 * q + 1] = make_float2(v.z, v.w);
     }
   };
   auto ldB = [&](const float* p, float* o) {  // TE consecutive elements
@@ -652,7 +662,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
       const int nj = !rows_live ? 0 : Np - c * KC < KC ? Np - c * KC : KC;
 #pragma unroll 2
       for (int jj = 0; jj < nj; ++jj) {
-        float ad[3][TM];
+        float2 ad[3][TM / 2];
 #pragma unroll
         for (int d = 0; d < 3; ++d) ldA(A + (d * KC + jj) * MT, ad[d]);
         if constexpr (MODEL == 0) {
@@ -661,16 +671,18 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
 #pragma unroll
           for (int d = 0; d < 3; ++d) ldB(B + ((1 + d) * KC + jj) * NE, xw[d]);
 #pragma unroll
-          for (int t = 0; t < TE; ++t)
+          for (int t = 0; t < TE; ++t) {
+            const float2 p2 = dup2(xp[t]), w0 = dup2(xw[0][t]), w1 = dup2(xw[1][t]), w2 = dup2(xw[2][t]);
 #pragma unroll
-            for (int v = 0; v < TM; ++v) {
-              acc[0][t][v] = fmaf(ad[0][v], xp[t], acc[0][t][v]);
-              acc[1][t][v] = fmaf(ad[1][v], xp[t], acc[1][t][v]);
-              acc[2][t][v] = fmaf(ad[2][v], xp[t], acc[2][t][v]);
-              acc[3][t][v] = fmaf(ad[0][v], xw[0][t], acc[3][t][v]);
-              acc[3][t][v] = fmaf(ad[1][v], xw[1][t], acc[3][t][v]);
-              acc[3][t][v] = fmaf(ad[2][v], xw[2][t], acc[3][t][v]);
+            for (int v = 0; v < TM / 2; ++v) {
+              acc2[0][t][v] = fma2<PK>(ad[0][v], p2, acc2[0][t][v]);
+              acc2[1][t][v] = fma2<PK>(ad[1][v], p2, acc2[1][t][v]);
+              acc2[2][t][v] = fma2<PK>(ad[2][v], p2, acc2[2][t][v]);
+              acc2[3][t][v] = fma2<PK>(ad[0][v], w0, acc2[3][t][v]);
+              acc2[3][t][v] = fma2<PK>(ad[1][v], w1, acc2[3][t][v]);
+              acc2[3][t][v] = fma2<PK>(ad[2][v], w2, acc2[3][t][v]);
             }
+          }
         } else {
 #pragma unroll
           for (int cc = 0; cc < 3; ++cc) {
@@ -679,16 +691,18 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
 #pragma unroll
             for (int d = 0; d < 3; ++d) ldB(B + ((3 + 3 * cc + d) * KC + jj) * NE, xs[d]);
 #pragma unroll
-            for (int t = 0; t < TE; ++t)
+            for (int t = 0; t < TE; ++t) {
+              const float2 v2 = dup2(xv[t]), s0 = dup2(xs[0][t]), s1 = dup2(xs[1][t]), s2 = dup2(xs[2][t]);
 #pragma unroll
-              for (int v = 0; v < TM; ++v) {
-                acc[3 * cc + 0][t][v] = fmaf(ad[0][v], xv[t], acc[3 * cc + 0][t][v]);
-                acc[3 * cc + 1][t][v] = fmaf(ad[1][v], xv[t], acc[3 * cc + 1][t][v]);
-                acc[3 * cc + 2][t][v] = fmaf(ad[2][v], xv[t], acc[3 * cc + 2][t][v]);
-                acc[9 + cc][t][v] = fmaf(ad[0][v], xs[0][t], acc[9 + cc][t][v]);
-                acc[9 + cc][t][v] = fmaf(ad[1][v], xs[1][t], acc[9 + cc][t][v]);
-                acc[9 + cc][t][v] = fmaf(ad[2][v], xs[2][t], acc[9 + cc][t][v]);
+              for (int v = 0; v < TM / 2; ++v) {
+                acc2[3 * cc + 0][t][v] = fma2<PK>(ad[0][v], v2, acc2[3 * cc + 0][t][v]);
+                acc2[3 * cc + 1][t][v] = fma2<PK>(ad[1][v], v2, acc2[3 * cc + 1][t][v]);
+                acc2[3 * cc + 2][t][v] = fma2<PK>(ad[2][v], v2, acc2[3 * cc + 2][t][v]);
+                acc2[9 + cc][t][v] = fma2<PK>(ad[0][v], s0, acc2[9 + cc][t][v]);
+                acc2[9 + cc][t][v] = fma2<PK>(ad[1][v], s1, acc2[9 + cc][t][v]);
+                acc2[9 + cc][t][v] = fma2<PK>(ad[2][v], s2, acc2[9 + cc][t][v]);
               }
+            }
           }
         }
       }
@@ -706,10 +720,10 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
             const float rinv = __ldg(gk + 10);
 #pragma unroll
             for (int v = 0; v < TM; ++v) {
-              const float G0 = acc[0][t][v], G1 = acc[1][t][v], G2 = acc[2][t][v];
+              const float G0 = ACC(0, t, v), G1 = ACC(1, t, v), G2 = ACC(2, t, v);
 #pragma unroll
               for (int cc = 0; cc < 3; ++cc)
-                acc[cc][t][v] = -rinv * (g[3 * cc] * G0 + g[3 * cc + 1] * G1 + g[3 * cc + 2] * G2);
+                ACC(cc, t, v) = -rinv * (g[3 * cc] * G0 + g[3 * cc + 1] * G1 + g[3 * cc + 2] * G2);
             }
           } else {
             const float lam = __ldg(gk + 9), mu = __ldg(gk + 10);
@@ -722,16 +736,16 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
               for (int cc = 0; cc < 3; ++cc)
 #pragma unroll
                 for (int x = 0; x < 3; ++x)
-                  gv[cc][x] = g[3 * x] * acc[3 * cc][t][v] + g[3 * x + 1] * acc[3 * cc + 1][t][v] +
-                              g[3 * x + 2] * acc[3 * cc + 2][t][v];
+                  gv[cc][x] = g[3 * x] * ACC(3 * cc, t, v) + g[3 * x + 1] * ACC(3 * cc + 1, t, v) +
+                              g[3 * x + 2] * ACC(3 * cc + 2, t, v);
               const float div = gv[0][0] + gv[1][1] + gv[2][2];
-              acc[0][t][v] = lam * div + 2.f * mu * gv[0][0];
-              acc[1][t][v] = lam * div + 2.f * mu * gv[1][1];
-              acc[2][t][v] = lam * div + 2.f * mu * gv[2][2];
-              acc[3][t][v] = mu * (gv[0][1] + gv[1][0]);
-              acc[4][t][v] = mu * (gv[0][2] + gv[2][0]);
-              acc[5][t][v] = mu * (gv[1][2] + gv[2][1]);
-              acc[6][t][v] = acc[7][t][v] = acc[8][t][v] = 0.f;  // W: LIFT_f dv of the current face
+              ACC(0, t, v) = lam * div + 2.f * mu * gv[0][0];
+              ACC(1, t, v) = lam * div + 2.f * mu * gv[1][1];
+              ACC(2, t, v) = lam * div + 2.f * mu * gv[2][2];
+              ACC(3, t, v) = mu * (gv[0][1] + gv[1][0]);
+              ACC(4, t, v) = mu * (gv[0][2] + gv[2][0]);
+              ACC(5, t, v) = mu * (gv[1][2] + gv[2][1]);
+              ACC(6, t, v) = ACC(7, t, v) = ACC(8, t, v) = 0.f;  // W: LIFT_f dv of the current face
             }
           }
         }
@@ -749,17 +763,20 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
           const int ce = fe < nc ? fe : nc;
 #pragma unroll 2
           for (; cc < ce; ++cc) {
-            float l[TM], pp[TE], ps[TE];
+            float2 l[TM / 2];
+            float pp[TE], ps[TE];
             ldA(A + cc * MT, l);
             ldB(B + (0 * KC + cc) * NE, pp);
             ldB(B + (1 * KC + cc) * NE, ps);
 #pragma unroll
-            for (int t = 0; t < TE; ++t)
+            for (int t = 0; t < TE; ++t) {
+              const float2 p2 = dup2(pp[t]), s2 = dup2(ps[t]);
 #pragma unroll
-              for (int v = 0; v < TM; ++v) {
-                acc[3][t][v] = fmaf(l[v], pp[t], acc[3][t][v]);
-                lf[t][v] = fmaf(l[v], ps[t], lf[t][v]);
+              for (int v = 0; v < TM / 2; ++v) {
+                acc2[3][t][v] = fma2<PK>(l[v], p2, acc2[3][t][v]);
+                lf2[t][v] = fma2<PK>(l[v], s2, lf2[t][v]);
               }
+            }
           }
           if (cc == fe) {
 #pragma unroll
@@ -767,14 +784,16 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
               float nv[TE];
               ldB(B + (2 * KC + 3 * f + x) * NE, nv);
 #pragma unroll
-              for (int t = 0; t < TE; ++t)
+              for (int t = 0; t < TE; ++t) {
+                const float2 n2 = dup2(nv[t]);
 #pragma unroll
-                for (int v = 0; v < TM; ++v) acc[x][t][v] = fmaf(nv[t], lf[t][v], acc[x][t][v]);
+                for (int v = 0; v < TM / 2; ++v) acc2[x][t][v] = fma2<PK>(n2, lf2[t][v], acc2[x][t][v]);
+              }
             }
 #pragma unroll
             for (int t = 0; t < TE; ++t)
 #pragma unroll
-              for (int v = 0; v < TM; ++v) lf[t][v] = 0.f;
+              for (int v = 0; v < TM / 2; ++v) lf2[t][v] = make_float2(0.f, 0.f);
           }
         }
       } else {
@@ -788,7 +807,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
           const int ce = fe < nc ? fe : nc;
 #pragma unroll 2
           for (; cc < ce; ++cc) {
-            float l[TM];
+            float2 l[TM / 2];
             ldA(A + cc * MT, l);
 #pragma unroll
             for (int x = 0; x < 6; ++x) {
@@ -796,9 +815,11 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
               ldB(B + (x * KC + cc) * NE, pf);
               const int slot = x < 3 ? 9 + x : 3 + x;
 #pragma unroll
-              for (int t = 0; t < TE; ++t)
+              for (int t = 0; t < TE; ++t) {
+                const float2 p2 = dup2(pf[t]);
 #pragma unroll
-                for (int v = 0; v < TM; ++v) acc[slot][t][v] = fmaf(l[v], pf[t], acc[slot][t][v]);
+                for (int v = 0; v < TM / 2; ++v) acc2[slot][t][v] = fma2<PK>(l[v], p2, acc2[slot][t][v]);
+              }
             }
           }
           if (cc == fe) {
@@ -809,16 +830,16 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
             for (int t = 0; t < TE; ++t)
 #pragma unroll
               for (int v = 0; v < TM; ++v) {
-                const float w0 = acc[6][t][v], w1 = acc[7][t][v], w2 = acc[8][t][v];
+                const float w0 = ACC(6, t, v), w1 = ACC(7, t, v), w2 = ACC(8, t, v);
                 const float nx = nv[0][t], ny = nv[1][t], nz = nv[2][t];
                 const float lnw = lamv[t] * (nx * w0 + ny * w1 + nz * w2), m2 = 2.f * muv[t];
-                acc[0][t][v] += lnw + m2 * nx * w0;
-                acc[1][t][v] += lnw + m2 * ny * w1;
-                acc[2][t][v] += lnw + m2 * nz * w2;
-                acc[3][t][v] += muv[t] * (nx * w1 + ny * w0);
-                acc[4][t][v] += muv[t] * (nx * w2 + nz * w0);
-                acc[5][t][v] += muv[t] * (ny * w2 + nz * w1);
-                acc[6][t][v] = acc[7][t][v] = acc[8][t][v] = 0.f;
+                ACC(0, t, v) += lnw + m2 * nx * w0;
+                ACC(1, t, v) += lnw + m2 * ny * w1;
+                ACC(2, t, v) += lnw + m2 * nz * w2;
+                ACC(3, t, v) += muv[t] * (nx * w1 + ny * w0);
+                ACC(4, t, v) += muv[t] * (nx * w2 + nz * w0);
+                ACC(5, t, v) += muv[t] * (ny * w2 + nz * w1);
+                ACC(6, t, v) = ACC(7, t, v) = ACC(8, t, v) = 0.f;
               }
           }
         }
@@ -838,7 +859,7 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
 #pragma unroll
     for (int t = 0; t < TE; ++t)
 #pragma unroll
-      for (int v = 0; v < TM; ++v) sOut[(il + v) * NEP + e0 + t] = acc[slot][t][v];
+      for (int v = 0; v < TM; ++v) sOut[(il + v) * NEP + e0 + t] = ACC(slot, t, v);
     __syncthreads();
     constexpr int U = 8;  // values per thread in flight
     for (int p0 = tid; p0 < NE * MT; p0 += NT * U) {
@@ -862,6 +883,8 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
     __syncthreads();
   }
 }
+
+#undef ACC
 
 // Design V of the FP32 GEMM (V = 2: design B, V = 3: design B with half the
 // elements per thread, V = 4: V = 3 with short row tiles and two CTAs per SM,
@@ -894,6 +917,37 @@ struct GemmOf<MODEL, N, 5> {
   using T = GemmB<MODEL, N, true, false, true>;
   __device__ static void body(const StepArgs& a, int mtile, int ntile) {
     gemm_b_body<MODEL, N, true, false, true>(a, mtile, ntile);
+  }
+};
+
+// V = 6..9: designs 2..5 with the packed two-lane FMA (fma.rn.f32x2) in
+// the operator products -- half the FMA instructions, the same results.
+template <int MODEL, int N>
+struct GemmOf<MODEL, N, 6> {
+  using T = GemmB<MODEL, N, false, false, false, true>;
+  __device__ static void body(const StepArgs& a, int mtile, int ntile) {
+    gemm_b_body<MODEL, N, false, false, false, true>(a, mtile, ntile);
+  }
+};
+template <int MODEL, int N>
+struct GemmOf<MODEL, N, 7> {
+  using T = GemmB<MODEL, N, true, false, false, true>;
+  __device__ static void body(const StepArgs& a, int mtile, int ntile) {
+    gemm_b_body<MODEL, N, true, false, false, true>(a, mtile, ntile);
+  }
+};
+template <int MODEL, int N>
+struct GemmOf<MODEL, N, 8> {
+  using T = GemmB<MODEL, N, true, true, false, true>;
+  __device__ static void body(const StepArgs& a, int mtile, int ntile) {
+    gemm_b_body<MODEL, N, true, true, false, true>(a, mtile, ntile);
+  }
+};
+template <int MODEL, int N>
+struct GemmOf<MODEL, N, 9> {
+  using T = GemmB<MODEL, N, true, false, true, true>;
+  __device__ static void body(const StepArgs& a, int mtile, int ntile) {
+    gemm_b_body<MODEL, N, true, false, true, true>(a, mtile, ntile);
   }
 };
 

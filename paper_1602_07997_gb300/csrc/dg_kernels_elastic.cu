@@ -16,34 +16,36 @@ const KernelCfg* kernel_variants_elastic(int N, int* count) {
   static const KernelCfg v3[] = {make_split_cfg<1, 3, 8, 3, 256>(), make_cfg<1, 3, 4, true, true>(),
                                  make_cfg<1, 3, 16, true, true>(), make_cfg<1, 3, 8, true, true, 1, 128>(),
                                  make_cfg<1, 3, 8, true, true>(), make_cfg<1, 3, 8, true, true, 1, 256>(),
-                                 make_split_cfg<1, 3, 8, 2, 256>()};
+                                 make_split_cfg<1, 3, 8, 2, 256>(), make_split_cfg<1, 3, 8, 7, 256>()};
   static const KernelCfg v4[] = {make_split_cfg<1, 4, 8, 3, 256>(), make_cfg<1, 4, 8, false, true>(),
                                  make_cfg<1, 4, 4, false, true>(), make_split_cfg<1, 4, 8>(),
                                  make_split_cfg<1, 4, 8, 2>(), make_cfg<1, 4, 4, true, true, 1, 128>(),
                                  make_cfg<1, 4, 4, true, true, 1, 256>(), make_split_cfg<1, 4, 4, 3, 256>(),
-                                 make_cfg<1, 4, 4, true, true>()};
+                                 make_cfg<1, 4, 4, true, true>(), make_split_cfg<1, 4, 8, 7, 256>()};
   static const KernelCfg v5[] = {make_split_cfg<1, 5, 8, 5, 512>(), make_cfg<1, 5, 4, false, false>(),
                                  make_split_cfg<1, 5, 4>(), make_split_cfg<1, 5, 4, 2>(),
                                  make_cfg<1, 5, 4, false, true>(), make_split_cfg<1, 5, 4, 3, 256>(),
                                  make_split_cfg<1, 5, 4, 3, 384>(), make_split_cfg<1, 5, 4, 3>(),
-                                 make_split_cfg<1, 5, 4, 3, 512>(), make_split_cfg<1, 5, 8, 3, 512>()};
+                                 make_split_cfg<1, 5, 4, 3, 512>(), make_split_cfg<1, 5, 8, 3, 512>(),
+                                 make_split_cfg<1, 5, 8, 9, 512>()};
   static const KernelCfg v6[] = {make_split_cfg<1, 6, 8, 5, 512>(), make_cfg<1, 6, 4, false, false, 2>(),
                                  make_split_cfg<1, 6, 4>(), make_split_cfg<1, 6, 4, 2>(),
                                  make_cfg<1, 6, 4, false, false>(), make_split_cfg<1, 6, 4, 3, 256>(),
                                  make_split_cfg<1, 6, 4, 3, 384>(), make_split_cfg<1, 6, 4, 3>(),
                                  make_split_cfg<1, 6, 4, 5, 512>(), make_split_cfg<1, 6, 4, 3, 512>(),
-                                 make_split_cfg<1, 6, 8, 3, 512>()};
+                                 make_split_cfg<1, 6, 8, 3, 512>(), make_split_cfg<1, 6, 8, 9, 512>()};
   static const KernelCfg v7[] = {make_split_cfg<1, 7, 8, 5, 512>(), make_cfg<1, 7, 4, false, false, 2>(),
                                  make_split_cfg<1, 7, 4>(), make_split_cfg<1, 7, 4, 2>(),
                                  make_cfg<1, 7, 4, false, false>(), make_split_cfg<1, 7, 4, 3, 256>(),
                                  make_split_cfg<1, 7, 4, 3, 384>(), make_split_cfg<1, 7, 4, 3>(),
                                  make_split_cfg<1, 7, 4, 3, 512>(), make_split_cfg<1, 7, 8, 3, 512>(),
-                                 make_split_cfg<1, 7, 4, 5, 512>()};
+                                 make_split_cfg<1, 7, 4, 5, 512>(), make_split_cfg<1, 7, 8, 9, 512>()};
   static const KernelCfg v8[] = {make_split_cfg<1, 8, 4, 5, 384>(), make_cfg<1, 8, 4, false, false, 2>(),
                                  make_split_cfg<1, 8, 4>(), make_cfg<1, 8, 4, false, false>(),
                                  make_split_cfg<1, 8, 4, 3>(), make_split_cfg<1, 8, 4, 3, 256>(),
                                  make_split_cfg<1, 8, 4, 3, 384>(), make_split_cfg<1, 8, 4, 2>(),
-                                 make_split_cfg<1, 8, 4, 2, 384>(), make_split_cfg<1, 8, 4, 5, 512>()};
+                                 make_split_cfg<1, 8, 4, 2, 384>(), make_split_cfg<1, 8, 4, 5, 512>(),
+                                 make_split_cfg<1, 8, 4, 9, 384>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
   static const int cnt[8] = {count_of(v1), count_of(v2), count_of(v3), count_of(v4),
                              count_of(v5), count_of(v6), count_of(v7), count_of(v8)};

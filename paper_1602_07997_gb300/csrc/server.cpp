@@ -115,6 +115,11 @@ struct Server {
   cudaGraphExec_t graph = nullptr;
   bool dirty = true;
   int* d_err = nullptr;
+  // one side stream per (model, N) group in the tick graph, so that the
+  // groups' batched kernels overlap on the device; fork and join events
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
 
   ~Server();
   void loop();
@@ -389,18 +394,44 @@ int Server::rebuild() {
     b.total_tiles = 0;
     if (dgk::launch_step_batched(g.cfg, b, stream) != cudaSuccess) return fail(DG_ECUDA, "batched warm-up");
   }
+  // side streams and events for the groups (created once, kept)
+  int ngroups = 0;
+  for (auto& kv : groups)
+    if (!kv.second.members.empty()) ++ngroups;
+  if (!fork && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+    return fail(DG_ECUDA, "server fork event");
+  while (int(side.size()) < ngroups) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(DG_ECUDA, "server side stream");
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaStreamDestroy(st);
+      return fail(DG_ECUDA, "server join event");
+    }
+    side.push_back(st);
+    join.push_back(ev);
+  }
+  // the tick: fork, every group's step kernels on its own stream, join, then
+  // the advance kernels (they change the state the step kernels read)
   cudaGraph_t gr = nullptr;
   if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return fail(DG_ECUDA, "graph capture");
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = cudaEventRecord(fork, stream);
+  int gi = 0;
   for (auto& kv : groups) {
     Group& g = kv.second;
     const int n = int(g.members.size());
     if (n == 0) continue;
+    cudaStream_t st = side[gi];
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, fork, 0);
     dgk::BatchArgs b = batch_args(g, d_err);
-    if (e == cudaSuccess) e = dgk::launch_step_batched(g.cfg, b, stream);
+    if (e == cudaSuccess) e = dgk::launch_step_batched(g.cfg, b, st);
     if (e == cudaSuccess && g.has_xs)
-      e = dgk::launch_xsrc_batched(b, dg::num_fields(g.model) * dg::num_nodes(g.N), stream);
+      e = dgk::launch_xsrc_batched(b, dg::num_fields(g.model) * dg::num_nodes(g.N), st);
+    if (e == cudaSuccess) e = cudaEventRecord(join[gi], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, join[gi], 0);
+    ++gi;
   }
   for (auto& kv : groups) {
     Group& g = kv.second;
@@ -540,6 +571,9 @@ Server::~Server() {
   }
   if (graph) cudaGraphExecDestroy(graph);
   if (d_err) cudaFree(d_err);
+  for (auto st : side) cudaStreamDestroy(st);
+  for (auto ev : join) cudaEventDestroy(ev);
+  if (fork) cudaEventDestroy(fork);
   if (stream) cudaStreamDestroy(stream);
   if (prep_stream) cudaStreamDestroy(prep_stream);
 }

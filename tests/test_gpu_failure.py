@@ -129,7 +129,7 @@ def test_short_wait_limit_then_recovery(model, N, precision):
         try:
             g.sync()
         except P.DGError as e:
-            assert e.value.code == -5
+            assert e.code == -5
     g.set_wait_limit(0)
     _steps_match_oracle(o, g, q, dt)
     g.close()
