@@ -18,7 +18,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["dg_kernels_acoustic.cu", "dg_kernels_elastic.cu", "dg_kernels_tc_acoustic.cu", "dg_strategies.cu",
               "dg_kernels_tc_elastic.cu", "dg_dispatch.cu", "rhs_noalloc.cu",
-              "fp32_peak.cu"]
+              "fp32_peak.cu", "dg_ept.cu"]
 CPP_SOURCES = ["api.cpp", "refelem.cpp", "mesh.cpp", "server.cpp"]
 
 

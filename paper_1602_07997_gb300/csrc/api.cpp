@@ -14,6 +14,7 @@
 #include "dg_args.h"
 #include "dg_strategies.h"
 #include "dg_internal.h"
+#include "dg_facemask.h"
 #include "dg_handle.h"
 
 namespace dg {
@@ -202,6 +203,15 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
   std::vector<int32_t> nbr;
   pack_records(hm, coeffs.data(), model, Kpad, geo, nbr);
   pack_ops(ref, ops, ftab);
+  if (model == DG_ACOUSTIC && N <= 2) {
+    // the element-per-thread kernels unroll their face loops over the
+    // compile-time face masks: they must be the tables built here
+    for (int f = 0; f < 4; ++f)
+      for (int m = 0; m < Nfp; ++m)
+        if (dgk::face_node(N, f, m) != ref.fmask[f * Nfp + m])
+          return fail(DG_EINVAL, "internal: compile-time face masks disagree with the reference element");
+    DG_CUDA(dgk::ept_upload_ops(N, ops.data(), ops.size()));
+  }
 
   const size_t nstate = size_t(Kpad) * Nf * Np;
   state_bytes = nstate * 4;

@@ -476,7 +476,8 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
 // registers sized for two resident CTAs per SM.  HALF (narrow only): a CTA
 // takes half of a column tile of X (32 acoustic elements), so that two CTAs
 // fit per SM with the registers of the narrow design.
-template <int MODEL, int N, bool NARROW = false, bool SMALL = false, bool HALF = false, bool PK = false>
+template <int MODEL, int N, bool NARROW = false, bool SMALL = false, bool HALF = false, bool PK = false,
+          bool THIRD = false>
 struct GemmB {
   using S = Sz<N>;
   static constexpr int Np = S::Np, NFN = S::NFN;
@@ -502,14 +503,17 @@ struct GemmB {
   // 64-row tiles; three short tiles at N = 7, 8 re-read X and spill)
   static constexpr int MT_SMALL = MODEL == 0 && N == 5 ? 56 : MT_NARROW;
   // (HALF: 16 lanes per row group, so an even number of row groups: MT_WIDE)
-  static constexpr int MT = SMALL ? MT_SMALL : (NARROW && !HALF) ? MT_NARROW : MT_WIDE;
-  static constexpr int MINB = SMALL || HALF ? 2 : 1;  // resident CTAs the registers are sized for
+  // THIRD (narrow): three row tiles of about Np / 3 rows (multiple of TM),
+  // registers and shared memory sized for two resident CTAs per SM
+  static constexpr int MT_THIRD = ((Np + 2) / 3 + TM - 1) / TM * TM;
+  static constexpr int MT = THIRD ? MT_THIRD : SMALL ? MT_SMALL : (NARROW && !HALF) ? MT_NARROW : MT_WIDE;
+  static constexpr int MINB = SMALL || HALF || THIRD ? 2 : 1;  // resident CTAs the registers are sized for
   static constexpr int MP2 = (Np + MT - 1) / MT * MT;     // padded rows of the split operator blob
   static constexpr int KC = 16;                           // K chunk (volume indices or face nodes)
   // cp.async stages: 4 for the acoustic tiles that have the SM to themselves,
   // 3 where two CTAs share it (SMALL, HALF) and for the elastic tiles (a
   // fourth stage cost elastic N = 3 a third of its resident CTAs)
-  static constexpr int NS = (MODEL == 0 && !SMALL && !HALF) ? 4 : 3;
+  static constexpr int NS = (MODEL == 0 && !SMALL && !HALF && !THIRD) ? 4 : 3;
   static constexpr int NT = (MT / TM) * (NEG / TE);       // threads per CTA
   static constexpr int MTILES_R = (Np + MT - 1) / MT;     // row tiles
   static constexpr int MTILES_L = MTILES_R * NSUB;        // CTAs per column tile (launch grid: x column tiles)
@@ -531,9 +535,10 @@ struct GemmB {
   static_assert(NS >= 2, "the copy of a chunk is issued after the barrier that retires its stage");
 };
 
-template <int MODEL, int N, bool NARROW = false, bool SMALL = false, bool HALF = false, bool PK = false>
+template <int MODEL, int N, bool NARROW = false, bool SMALL = false, bool HALF = false, bool PK = false,
+          bool THIRD = false>
 __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l, const int ntile) {
-  using SS = GemmB<MODEL, N, NARROW, SMALL, HALF, PK>;
+  using SS = GemmB<MODEL, N, NARROW, SMALL, HALF, PK, THIRD>;
   // NE: elements of this CTA; XNE: row stride of X (elements per column tile)
   constexpr int Np = SS::Np, NFN = SS::NFN, Nf = SS::Nf, NV = SS::NV, NE = SS::NEG, TM = SS::TM, TE = SS::TE;
   constexpr int XNE = SS::NE;
@@ -948,6 +953,15 @@ struct GemmOf<MODEL, N, 9> {
   using T = GemmB<MODEL, N, true, false, true, true>;
   __device__ static void body(const StepArgs& a, int mtile, int ntile) {
     gemm_b_body<MODEL, N, true, false, true, true>(a, mtile, ntile);
+  }
+};
+
+// V = 10: design 3 with the packed FMA and three row tiles, two CTAs per SM (THIRD).
+template <int MODEL, int N>
+struct GemmOf<MODEL, N, 10> {
+  using T = GemmB<MODEL, N, true, false, false, true, true>;
+  __device__ static void body(const StepArgs& a, int mtile, int ntile) {
+    gemm_b_body<MODEL, N, true, false, false, true, true>(a, mtile, ntile);
   }
 };
 

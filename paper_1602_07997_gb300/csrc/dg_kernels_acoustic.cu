@@ -14,12 +14,13 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_cfg<0, 1, 32, true, true, 1, 128>(), make_cfg<0, 1, 64, true, true>(),
                                  make_cfg<0, 1, 32, true, true>(), make_cfg<0, 1, 128, true, true>(),
                                  make_cfg<0, 1, 16, true, true>(), make_cfg<0, 1, 64, true, true, 1, 256>(),
-                                 make_cfg<0, 1, 32, true, true, 1, 256>(), make_cfg<0, 1, 64, true, true, 1, 512>()};
+                                 make_cfg<0, 1, 32, true, true, 1, 256>(), make_cfg<0, 1, 64, true, true, 1, 512>(),
+                                 ept_variant(1, 0), ept_variant(1, 1)};
   static const KernelCfg v2[] = {make_cfg<0, 2, 24, true, true, 1, 256>(), make_cfg<0, 2, 32, true, true>(),
                                  make_cfg<0, 2, 16, true, true>(), make_cfg<0, 2, 64, true, true>(),
                                  make_cfg<0, 2, 16, true, true, 1, 128>(), make_cfg<0, 2, 8, true, true>(),
                                  make_cfg<0, 2, 16, true, true, 1, 256>(), make_cfg<0, 2, 32, true, true, 1, 512>(),
-                                 make_cfg<0, 2, 32, true, true, 1, 256>()};
+                                 make_cfg<0, 2, 32, true, true, 1, 256>(), ept_variant(2, 0), ept_variant(2, 1)};
   static const KernelCfg v3[] = {make_cfg<0, 3, 12, true, true, 1, 256>(), make_cfg<0, 3, 4, true, true>(),
                                  make_cfg<0, 3, 16, true, true>(), make_cfg<0, 3, 32, true, true>(),
                                  make_cfg<0, 3, 16, true, true, 1, 128>(), make_cfg<0, 3, 8, true, true>(),
@@ -44,7 +45,7 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_split_cfg<0, 6, 4, 2>(), make_split_cfg<0, 6, 8>(),
                                  make_split_cfg<0, 6, 8, 1, 512>(), make_split_cfg<0, 6, 8, 1, 384>(),
                                  make_split_cfg<0, 6, 8, 5, 384>(), make_split_cfg<0, 6, 8, 7, 384>(),
-                                 make_split_cfg<0, 6, 8, 9, 384>()};
+                                 make_split_cfg<0, 6, 8, 9, 384>(), make_split_cfg<0, 6, 8, 10, 384>()};
   static const KernelCfg v7[] = {make_split_cfg<0, 7, 8, 5, 512>(), make_cfg<0, 7, 4, false, true, 2>(),
                                  make_cfg<0, 7, 8, false, true, 2>(), make_cfg<0, 7, 4, false, true, 4>(),
                                  make_split_cfg<0, 7, 8>(), make_split_cfg<0, 7, 4>(),
@@ -52,14 +53,14 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_split_cfg<0, 7, 4, 3>(), make_split_cfg<0, 7, 8, 3>(),
                                  make_split_cfg<0, 7, 8, 3, 768>(), make_split_cfg<0, 7, 8, 1, 512>(),
                                  make_split_cfg<0, 7, 8, 3, 512>(), make_split_cfg<0, 7, 8, 9, 512>(),
-                                 make_split_cfg<0, 7, 8, 7, 512>()};
+                                 make_split_cfg<0, 7, 8, 7, 512>(), make_split_cfg<0, 7, 8, 10, 512>()};
   static const KernelCfg v8[] = {make_split_cfg<0, 8, 8, 3, 512>(), make_cfg<0, 8, 4, false, true, 2>(),
                                  make_cfg<0, 8, 4, false, true, 4>(), make_cfg<0, 8, 8, false, true, 2>(),
                                  make_split_cfg<0, 8, 4>(), make_split_cfg<0, 8, 8>(),
                                  make_split_cfg<0, 8, 8, 2>(), make_cfg<0, 8, 4, false, true>(),
                                  make_split_cfg<0, 8, 4, 3>(), make_split_cfg<0, 8, 8, 2, 512>(),
                                  make_split_cfg<0, 8, 8, 5, 768>(), make_split_cfg<0, 8, 8, 7, 512>(),
-                                 make_split_cfg<0, 8, 8, 9, 512>()};
+                                 make_split_cfg<0, 8, 8, 9, 512>(), make_split_cfg<0, 8, 8, 10, 512>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
   static const int cnt[8] = {count_of(v1), count_of(v2), count_of(v3), count_of(v4),
                              count_of(v5), count_of(v6), count_of(v7), count_of(v8)};
