@@ -577,6 +577,12 @@ def run(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    if args.large_only:
+        # the large elastic workload alone (e.g. to capture its kernels)
+        lg = large_elastic(P, args, torch.cuda.Stream(device=dev), peaks(None))
+        if rank == 0:
+            print(json.dumps({"large_elastic": lg}), flush=True)
+        return
     model = args.model
     Ns = [int(x) for x in args.degrees.split(",")]
     stream = torch.cuda.Stream(device=dev)
@@ -800,7 +806,8 @@ def large_elastic(P, args, stream, pk):
     warm-up steps; algorithmic GB/s and GFLOP/s against both peaks."""
     import workloads as W
     cfg = W.config5_elastic_large()
-    g = make_solvers(P, [cfg], "elastic", "fp32", stream, not args.no_tune)[0]
+    fixed = [args.large_variant] if args.large_variant >= 0 else None
+    g = make_solvers(P, [cfg], "elastic", "fp32", stream, not args.no_tune, fixed)[0]
     ms = time_sweep([g], args.large_steps, stream)[0]
     byt, flop = algorithmic("elastic", g.N, g.K)
     ki = g.kernel_info()
@@ -902,6 +909,9 @@ def main():
     ap.add_argument("--no-peak", action="store_true", help="skip the FP32 FMA peak measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the large elastic workload")
     ap.add_argument("--large-steps", type=int, default=20)
+    ap.add_argument("--large-only", action="store_true", help="time only the large elastic workload")
+    ap.add_argument("--large-variant", type=int, default=-1,
+                    help="kernel variant of the large elastic workload instead of autotuning")
     ap.add_argument("--ingest-ncu", default="", help="ncu CSV of DRAM bytes to record in profiles/traffic.json")
     ap.add_argument("--traffic-key", default="", help="key of the --ingest-ncu entry, e.g. acoustic_N8_fp32_v0")
     ap.add_argument("--traffic-note", default="", help="where the --ingest-ncu capture came from")
