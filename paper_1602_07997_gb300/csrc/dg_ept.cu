@@ -98,8 +98,11 @@ __device__ __forceinline__ int outside_rank(const int4 nb, int f, int k0, int EB
   return r;
 }
 
-template <int N, int EB>
-__global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
+// Body shared by one solve per launch and by a batch of solves (served
+// mode): the provider maps a global block to its solve's arguments and local
+// block, as for the block kernel.
+template <int N, int EB, class Prov>
+__device__ __forceinline__ void ept_body(const Prov& prov) {
   using P = EptPlan<N, EB>;
   constexpr int Nf = P::Nf, Np = P::Np, Nfp = P::Nfp, QS = P::QS, QSP = P::QSP, REC = P::REC;
   constexpr int Mpad = Sz<N>::Mpad, EBP = P::EBP, SLOTS = P::SLOTS;
@@ -114,9 +117,11 @@ __global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P::oBar);
 
   const int tid = threadIdx.x;
-  const int nblk = (a.K + EB - 1) / EB;
+  const int nblk = prov.nblocks();
   const int G = gridDim.x;
-  const long long lim = a.wait_limit;
+  const long long lim = prov.limit();
+  int* const err = prov.err();
+  const int mode = prov.mode();
   constexpr uint32_t kQBytes = uint32_t(EB * QS * 4);
   constexpr uint32_t kStageBytes = kQBytes + uint32_t(EB * REC * 4) + uint32_t(EB * 16);
 
@@ -138,9 +143,9 @@ __global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
   // (warp 0) the stage of block b: one bulk copy per element's fields (padded
   // rows), the records and the neighbour words; lane 0 registers the bytes
   // before any lane issues a copy
-  auto issue_stage = [&](int b, int s) {
+  auto issue_stage = [&](const StepArgs& a, int lb, int s) {
     float* st = stage(s);
-    const int k0 = b * EB;
+    const int k0 = lb * EB;
     if (tid == 0) mbar_arrive_expect_tx(&bars[s], kStageBytes);
     __syncwarp();
     for (int e = tid; e < EB; e += 32)
@@ -152,8 +157,8 @@ __global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
   };
   // traces of the outside neighbours of block b (stage s): thread e fetches
   // its own element's, face by face, into the element's slots
-  auto issue_gathers = [&](int b, int s) {
-    const int k0 = b * EB;
+  auto issue_gathers = [&](const StepArgs& a, int lb, int s) {
+    const int k0 = lb * EB;
     const int e = tid;
     const int4 nb = reinterpret_cast<const int4*>(stage(s) + P::sNbr)[e];
     int slot = 0;
@@ -186,28 +191,34 @@ __global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
     fence_barrier_init();
   }
   __syncthreads();
-  if (tid < 32 && (int)blockIdx.x < nblk) issue_stage(blockIdx.x, 0);
+  // arguments of the block being processed and of the next one
+  StepArgs nxt_a;
+  int nxt_lb = 0;
+  if ((int)blockIdx.x < nblk) prov.get(blockIdx.x, nxt_a, nxt_lb);
+  if (tid < 32 && (int)blockIdx.x < nblk) issue_stage(nxt_a, nxt_lb, 0);
   if ((int)blockIdx.x < nblk) pend_set(0, 0u);
-  for (int i = tid; i < 10 * Nfp; i += NT) sFtab[i] = a.ftab[i];
+  for (int i = tid; i < 10 * Nfp; i += NT) sFtab[i] = prov.ftab()[i];
   __syncthreads();
   for (int i = tid; i < 24 * Nfp; i += NT) {
     const int m = i % Nfp, fr = i / Nfp;
     sPtab[i] = sFtab[(fr / 6) * Nfp + sFtab[4 * Nfp + (fr % 6) * Nfp + m]];
   }
   if ((int)blockIdx.x < nblk) {
-    if (!__syncthreads_and(mbar_wait_bounded(&bars[0], 0u, a.err, lim))) {
+    if (!__syncthreads_and(mbar_wait_bounded(&bars[0], 0u, err, lim))) {
       drain();
       return;
     }
     pend_clr(0);
-    issue_gathers(blockIdx.x, 0);
+    issue_gathers(nxt_a, nxt_lb, 0);
   }
 
   int it = 0;
   for (int b = blockIdx.x; b < nblk; b += G, ++it) {
     const int s = it & 1;
-    const int k0 = b * EB;
-    bool ok = mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), a.err, lim);
+    const StepArgs a = nxt_a;
+    const int k0 = nxt_lb * EB;
+    if (b + G < nblk) prov.get(b + G, nxt_a, nxt_lb);
+    bool ok = mbar_wait_bounded(&bars[s], uint32_t((it >> 1) & 1), err, lim);
     cp_async_wait_all();  // this block's gathered traces
     if (!__syncthreads_and(ok)) {
       drain();
@@ -215,9 +226,9 @@ __global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
     }
     pend_clr(s);
     const uint32_t pnext = uint32_t(((it + 1) >> 1) & 1);
-    if (tid < 32 && b + G < nblk) issue_stage(b + G, s ^ 1);
+    if (tid < 32 && b + G < nblk) issue_stage(nxt_a, nxt_lb, s ^ 1);
     if (tid == 0) {
-      if (a.mode == 0) {
+      if (mode == 0) {
         // this block's AB3 history into L2 for the update pass
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.r1 + size_t(k0) * QS), "r"(kQBytes)
                      : "memory");
@@ -377,7 +388,7 @@ __global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
 #pragma unroll
         for (int x = 0; x < QS; ++x) r[x] = fmaf(a.src_amp, __ldg(a.srcvec + x), r[x]);
       }
-      if (a.mode == 0) {
+      if (mode == 0) {
         float4* dst = reinterpret_cast<float4*>(sRhs + e * QSP);
 #pragma unroll
         for (int x = 0; x < QS / 4; ++x) dst[x] = make_float4(r[4 * x], r[4 * x + 1], r[4 * x + 2], r[4 * x + 3]);
@@ -390,7 +401,7 @@ __global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
     __syncthreads();  // every RHS of the block is in sRhs
 
     // -------- AB3 update, a flat float4 pass over the block's elements
-    if (a.mode == 0) {
+    if (mode == 0) {
       const int ne = a.K - k0 < EB ? a.K - k0 : EB;
       const int n4 = ne * QS / 4;
       const size_t g0 = size_t(k0) * QS / 4;
@@ -428,7 +439,7 @@ __global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
     // the next block's stage was issued at the top: once it has landed,
     // gather its outside traces (the trace slots were last read above)
     {
-      const bool okn = b + G < nblk ? mbar_wait_bounded(&bars[s ^ 1], pnext, a.err, lim) : true;
+      const bool okn = b + G < nblk ? mbar_wait_bounded(&bars[s ^ 1], pnext, err, lim) : true;
       if (!__syncthreads_and(okn)) {
         drain();
         return;
@@ -436,9 +447,23 @@ __global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
     }
     if (b + G < nblk) {
       pend_clr(s ^ 1);
-      issue_gathers(b + G, s ^ 1);
+      issue_gathers(nxt_a, nxt_lb, s ^ 1);
     }
   }
+}
+
+// one solve per launch (dg_step / dg_rhs)
+template <int N, int EB>
+__global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
+  SingleSolve p{a, EB};
+  ept_body<N, EB>(p);
+}
+
+// every solve of a batch (same N) in one persistent launch (served mode)
+template <int N, int EB>
+__global__ void __launch_bounds__(EB) dg_ept_batched_kernel(const BatchArgs b) {
+  SolveBatch p{b};
+  ept_body<N, EB>(p);
 }
 
 template <int N, int EB>
@@ -453,7 +478,7 @@ KernelCfg make_ept_cfg() {
   c.r_smem = false;
   c.smem = P::bytes;
   c.fn = dg_ept_kernel<N, EB>;
-  c.fn_batched = nullptr;
+  c.fn_batched = dg_ept_batched_kernel<N, EB>;
   c.split = 0;
   c.fn_gemm = nullptr;
   c.fn_gemm_batched = nullptr;
