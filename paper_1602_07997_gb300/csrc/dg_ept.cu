@@ -27,8 +27,7 @@
 #include <mutex>
 #include <set>
 
-#include "dg_facemask.h"
-#include "dg_kernels.cuh"
+#include "dg_ept.cuh"
 
 namespace dgk {
 
@@ -40,21 +39,6 @@ __device__ __forceinline__ float opc(int idx) {
   if constexpr (N == 1) return c_ops1[idx];
   else return c_ops2[idx];
 }
-
-// compile-time face masks: FaceNodes<N>::v[f][m] = volume node of face node m of face f
-template <int N>
-struct FaceNodes {
-  struct T {
-    int v[4][Sz<N>::Nfp];
-  };
-  static constexpr T make() {
-    T t{};
-    for (int f = 0; f < 4; ++f)
-      for (int m = 0; m < Sz<N>::Nfp; ++m) t.v[f][m] = face_node(N, f, m);
-    return t;
-  }
-  static constexpr T tab = make();
-};
 
 template <int N, int EB>
 struct EptPlan {
@@ -80,23 +64,6 @@ struct EptPlan {
   static_assert(EB % 32 == 0, "whole warps, one element per thread");
   static_assert((QS * 4) % 16 == 0, "16-byte bulk copies of the fields");
 };
-
-// neighbour word of face f
-__device__ __forceinline__ int nbr_word(const int4 nb, int f) {
-  return (f == 0) ? nb.x : (f == 1) ? nb.y : (f == 2) ? nb.z : nb.w;
-}
-// slot of face f among the outside faces of an element (0, 1, ... in face order)
-__device__ __forceinline__ int outside_rank(const int4 nb, int f, int k0, int EB) {
-  int r = 0;
-  for (int g = 0; g < f; ++g) {
-    const int w = nbr_word(nb, g);
-    if (w >= 0) {
-      const int le = (w >> kNbrShift) - k0;
-      r += (le < 0 || le >= EB) ? 1 : 0;
-    }
-  }
-  return r;
-}
 
 // Body shared by one solve per launch and by a batch of solves (served
 // mode): the provider maps a global block to its solve's arguments and local
