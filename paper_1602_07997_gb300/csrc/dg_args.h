@@ -123,7 +123,7 @@ const KernelCfg* kernel_variants(int model, int N, int* count, int precision = 0
 const KernelCfg* kernel_cfg(int model, int N);
 
 // Acoustic fused step with one element per thread (N = 1, 2): variant
-// `which` (0, 1: elements per CTA), and the upload of the operator blob
+// `which` (0, 1, 2 (N = 1 only): elements per CTA), and the upload of the operator blob
 // ([3 Np + 4 Nfp][Mpad] as the block kernel's) to its constant memory on
 // the current device (once per device and N).
 KernelCfg ept_variant(int N, int which);

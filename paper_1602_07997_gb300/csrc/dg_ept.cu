@@ -457,7 +457,7 @@ KernelCfg make_ept_cfg() {
 }
 
 KernelCfg ept_variant(int N, int which) {
-  if (N == 1) return which == 0 ? make_ept_cfg<1, 64>() : make_ept_cfg<1, 128>();
+  if (N == 1) return which == 0 ? make_ept_cfg<1, 64>() : which == 1 ? make_ept_cfg<1, 128>() : make_ept_cfg<1, 32>();
   return which == 0 ? make_ept_cfg<2, 32>() : make_ept_cfg<2, 64>();
 }
 

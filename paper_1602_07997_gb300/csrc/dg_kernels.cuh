@@ -229,7 +229,10 @@ struct Plan {
   static constexpr int oXvol = round4(oR + nR);
   static constexpr int oXsur = round4(oXvol + nXvol);
   static constexpr int oT0 = round4(oXsur + nXsur);
-  static constexpr int oT1 = round4(oT0 + nT);
+  // one trace buffer unless DIRECT: every other path gathers the next
+  // block's traces after the barrier that follows this block's last read of
+  // them; the DIRECT front half has no such barrier and keeps two
+  static constexpr int oT1 = DIRECT ? round4(oT0 + nT) : oT0;
   static constexpr int oOps = round4(oT1 + nT);
   static constexpr int oFn = round4(oOps + nOps);          // [4][EBF] float4: n, Fscale
   static constexpr int oNt = oFn + EBF * 16;               // [4 x 3][EBP]: normals, element fastest (FACT)

@@ -15,7 +15,7 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_cfg<0, 1, 32, true, true>(), make_cfg<0, 1, 128, true, true>(),
                                  make_cfg<0, 1, 16, true, true>(), make_cfg<0, 1, 64, true, true, 1, 256>(),
                                  make_cfg<0, 1, 32, true, true, 1, 256>(), make_cfg<0, 1, 64, true, true, 1, 512>(),
-                                 ept_variant(1, 0), ept_variant(1, 1)};
+                                 ept_variant(1, 0), ept_variant(1, 1), ept_variant(1, 2)};
   static const KernelCfg v2[] = {make_cfg<0, 2, 24, true, true, 1, 256>(), make_cfg<0, 2, 32, true, true>(),
                                  make_cfg<0, 2, 16, true, true>(), make_cfg<0, 2, 64, true, true>(),
                                  make_cfg<0, 2, 16, true, true, 1, 128>(), make_cfg<0, 2, 8, true, true>(),
@@ -25,11 +25,14 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_cfg<0, 3, 16, true, true>(), make_cfg<0, 3, 32, true, true>(),
                                  make_cfg<0, 3, 16, true, true, 1, 128>(), make_cfg<0, 3, 8, true, true>(),
                                  make_cfg<0, 3, 32, true, true, 1, 256>(), make_cfg<0, 3, 32, true, true, 1, 512>(),
-                                 make_cfg<0, 3, 16, true, true, 1, 256>(), make_cfg<0, 3, 12, true, true, 1, 192>()};
+                                 make_cfg<0, 3, 16, true, true, 1, 256>(), make_cfg<0, 3, 12, true, true, 1, 192>(),
+                                 make_cfg<0, 3, 12, true, false, 1, 256>(), make_cfg<0, 3, 16, true, false, 1, 256>()};
   static const KernelCfg v4[] = {make_cfg<0, 4, 12, true, true, 1, 256>(), make_cfg<0, 4, 4, true, true>(),
                                  make_cfg<0, 4, 8, true, true, 2>(), make_cfg<0, 4, 8, true, true>(),
                                  make_cfg<0, 4, 8, true, true, 1, 128>(), make_cfg<0, 4, 16, true, true, 1, 256>(),
-                                 make_cfg<0, 4, 12, true, true>(), make_cfg<0, 4, 8, true, true, 1, 256>()};
+                                 make_cfg<0, 4, 12, true, true>(), make_cfg<0, 4, 8, true, true, 1, 256>(),
+                                 make_cfg<0, 4, 12, true, false, 1, 256>(), make_cfg<0, 4, 16, true, false, 1, 256>(),
+                                 make_cfg<0, 4, 8, true, false, 1, 256>()};
   static const KernelCfg v5[] = {make_split_cfg<0, 5, 8, 4, 384>(), make_split_cfg<0, 5, 8, 2, 256>(),
                                  make_split_cfg<0, 5, 8, 8, 384>(), make_split_cfg<0, 5, 8, 6, 256>(),
                                  make_split_cfg<0, 5, 8, 7, 384>(),
