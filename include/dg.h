@@ -173,6 +173,24 @@ int dg_set_dt(dg_handle *h, double dt);
  * variant_ms (NULL or [variants]) receives every variant's time per step.
  * Allocates and frees scratch device memory of 4 state sizes; synchronous. */
 int dg_autotune(dg_handle *h, int reps, int *block_elems, double *ms_per_step, double *variant_ms);
+/* Autotuner choices across processes (the paper has no counterpart; its
+ * kernels were tuned by hand, Section 4).  dg_tune_save writes every choice
+ * of this process (dg_autotune, dg_set_variant) to a text file, one line per
+ * (device, model, N, precision): the device's name and compute capability,
+ * the variant index and the variant's shape (elements per block, threads,
+ * split form, GEMM threads).  dg_tune_load makes the file's choices the
+ * process's for the current device -- lines of another device name or
+ * compute capability, or naming a variant this build compiles differently,
+ * are skipped -- so handles created afterwards start with them (as after
+ * dg_autotune); *applied (may be NULL) = lines taken.  dg_tune_clear
+ * forgets every choice of the process (handles created afterwards take
+ * their default variant).  DG_EINVAL: NULL path, unreadable or unwritable
+ * file, or a file that is not such a cache or has a malformed line (nothing
+ * is applied then); DG_ECUDA: a device query failed.                       */
+int dg_tune_save(const char *path);
+int dg_tune_load(const char *path, int *applied);
+int dg_tune_clear(void);
+
 /* Launch configuration in use: elements per CTA, threads per CTA, dynamic
  * shared memory per CTA, number of compiled variants (of the handle's
  * precision mode), elements per thread tile, and the step's form in *split:

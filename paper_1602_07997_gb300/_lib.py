@@ -26,7 +26,8 @@ EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", 
            "dg_set_dt", "dg_sync", "dg_autotune", "dg_kernel_info", "dg_set_variant", "dg_node_coords", "dg_set_source", "dg_add_source", "dg_suggest_dt",
            "dg_reference_element", "dg_last_error", "dg_server_create", "dg_submit", "dg_poll",
            "dg_cancel", "dg_server_stats", "dg_server_destroy", "dg_rhs_host_noalloc", "dg_set_receivers",
-           "dg_get_traces", "dg_fp32_peak", "dg_set_finite_check", "dg_set_wait_limit", "dg_launch_count")
+           "dg_get_traces", "dg_fp32_peak", "dg_set_finite_check", "dg_set_wait_limit", "dg_launch_count",
+           "dg_tune_save", "dg_tune_load", "dg_tune_clear")
 
 
 class DGError(RuntimeError):
@@ -99,6 +100,9 @@ def lib():
         "dg_set_finite_check": (i32, [vp, i32]),
         "dg_set_wait_limit": (i32, [vp, i64]),
         "dg_launch_count": (i32, [vp, P(i64)]),
+        "dg_tune_save": (i32, [C.c_char_p]),
+        "dg_tune_load": (i32, [C.c_char_p, P(i32)]),
+        "dg_tune_clear": (i32, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -205,6 +209,23 @@ def fp32_peak(stream=None, reps=5, target_ms=20.0):
     s, p, ms = C.c_double(), C.c_double(), C.c_double()
     check(lib().dg_fp32_peak(stream, int(reps), float(target_ms), C.byref(s), C.byref(p), C.byref(ms)))
     return {"scalar_tflops": s.value, "packed_tflops": p.value, "ms": ms.value}
+
+
+def tune_save(path):
+    """Write this process's autotuner choices to `path` (dg_tune_save)."""
+    check(lib().dg_tune_save(os.fsencode(path)))
+
+
+def tune_load(path):
+    """Take the choices of a saved cache for the current device; returns how many were taken."""
+    n = C.c_int()
+    check(lib().dg_tune_load(os.fsencode(path), C.byref(n)))
+    return n.value
+
+
+def tune_clear():
+    """Forget every autotuner choice of this process."""
+    check(lib().dg_tune_clear())
 
 
 class Solver:

@@ -2,6 +2,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1007,3 +1009,116 @@ int dg_reference_element(int N, double* nodes, double* Dr, double* Ds, double* D
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- autotune cache
+// One line per choice: device name (spaces as '_'), compute capability,
+// model, N, precision, variant index and the variant's shape (elements per
+// block, threads, split form, GEMM threads), so that a stale line (another
+// build's variant table) is recognised and skipped.
+namespace {
+const char* kTuneHeader = "# libdg autotune cache v1";
+
+int device_tag(int dev, std::string* name, int* major, int* minor) {
+  cudaDeviceProp p;
+  cudaError_t e = cudaGetDeviceProperties(&p, dev);
+  if (e != cudaSuccess) return dg::cuda_fail(e, "cudaGetDeviceProperties");
+  std::string n(p.name);
+  for (auto& ch : n)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  *name = n;
+  *major = p.major;
+  *minor = p.minor;
+  return DG_OK;
+}
+}  // namespace
+
+extern "C" int dg_tune_save(const char* path) {
+  if (!path) return fail(DG_EINVAL, "NULL path");
+  std::map<std::tuple<int, int, int, int>, int> tuned;
+  {
+    std::lock_guard<std::mutex> lock(dg::g_tune_mu);
+    tuned = dg::g_tuned;
+  }
+  std::ostringstream out;
+  out << kTuneHeader << "\n";
+  for (const auto& kv : tuned) {
+    const int dev = std::get<0>(kv.first), model = std::get<1>(kv.first), N = std::get<2>(kv.first),
+              prec = std::get<3>(kv.first), idx = kv.second;
+    int n = 0;
+    const dgk::KernelCfg* v = dgk::kernel_variants(model, N, &n, prec);
+    if (!v || idx < 0 || idx >= n) continue;
+    std::string name;
+    int major = 0, minor = 0;
+    int rc = device_tag(dev, &name, &major, &minor);
+    if (rc) return rc;
+    out << name << " " << major << "." << minor << " " << model << " " << N << " " << prec << " " << idx << " "
+        << v[idx].EB << " " << v[idx].NT << " " << v[idx].split << " " << v[idx].gemm_threads << "\n";
+  }
+  std::ofstream f(path);
+  if (!f) return fail(DG_EINVAL, std::string("cannot write ") + path);
+  f << out.str();
+  if (!f) return fail(DG_EINVAL, std::string("cannot write ") + path);
+  return DG_OK;
+}
+
+extern "C" int dg_tune_load(const char* path, int* applied) {
+  if (applied) *applied = 0;
+  if (!path) return fail(DG_EINVAL, "NULL path");
+  std::ifstream f(path);
+  if (!f) return fail(DG_EINVAL, std::string("cannot read ") + path);
+  struct Line {
+    std::string name;
+    int major, minor, model, N, prec, idx, EB, NT, split, gthreads;
+  };
+  std::vector<Line> lines;
+  std::string ln;
+  bool header = false;
+  int lineno = 0;
+  while (std::getline(f, ln)) {
+    ++lineno;
+    if (ln.empty()) continue;
+    if (ln[0] == '#') {
+      if (ln == kTuneHeader) header = true;
+      continue;
+    }
+    std::istringstream is(ln);
+    Line L;
+    std::string cc;
+    char dot = 0;
+    if (!(is >> L.name >> cc >> L.model >> L.N >> L.prec >> L.idx >> L.EB >> L.NT >> L.split >> L.gthreads))
+      return fail(DG_EINVAL, std::string(path) + ": malformed line " + std::to_string(lineno));
+    std::istringstream cs(cc);
+    if (!(cs >> L.major >> dot >> L.minor) || dot != '.')
+      return fail(DG_EINVAL, std::string(path) + ": malformed compute capability on line " + std::to_string(lineno));
+    lines.push_back(L);
+  }
+  if (!header) return fail(DG_EINVAL, std::string(path) + ": not a libdg autotune cache");
+  if (lines.empty()) return DG_OK;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return dg::cuda_fail(e, "cudaGetDevice");
+  std::string name;
+  int major = 0, minor = 0;
+  int rc = device_tag(dev, &name, &major, &minor);
+  if (rc) return rc;
+  int taken = 0;
+  for (const auto& L : lines) {
+    if (L.name != name || L.major != major || L.minor != minor) continue;
+    int n = 0;
+    const dgk::KernelCfg* v = dgk::kernel_variants(L.model, L.N, &n, L.prec);
+    if (!v || L.idx < 0 || L.idx >= n) continue;
+    const dgk::KernelCfg& c = v[L.idx];
+    if (c.EB != L.EB || c.NT != L.NT || c.split != L.split || c.gemm_threads != L.gthreads) continue;
+    std::lock_guard<std::mutex> lock(dg::g_tune_mu);
+    dg::g_tuned[std::make_tuple(dev, L.model, L.N, L.prec)] = L.idx;
+    ++taken;
+  }
+  if (applied) *applied = taken;
+  return DG_OK;
+}
+
+extern "C" int dg_tune_clear(void) {
+  std::lock_guard<std::mutex> lock(dg::g_tune_mu);
+  dg::g_tuned.clear();
+  return DG_OK;
+}

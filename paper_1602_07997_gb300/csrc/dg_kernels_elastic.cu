@@ -16,12 +16,14 @@ const KernelCfg* kernel_variants_elastic(int N, int* count) {
   static const KernelCfg v3[] = {make_split_cfg<1, 3, 8, 3, 256>(), make_cfg<1, 3, 4, true, true>(),
                                  make_cfg<1, 3, 16, true, true>(), make_cfg<1, 3, 8, true, true, 1, 128>(),
                                  make_cfg<1, 3, 8, true, true>(), make_cfg<1, 3, 8, true, true, 1, 256>(),
-                                 make_split_cfg<1, 3, 8, 2, 256>(), make_split_cfg<1, 3, 8, 7, 256>()};
+                                 make_split_cfg<1, 3, 8, 2, 256>(), make_split_cfg<1, 3, 8, 7, 256>(),
+                                 make_cfg<1, 3, 8, true, false, 1, 256>(), make_cfg<1, 3, 12, true, false, 1, 256>()};
   static const KernelCfg v4[] = {make_split_cfg<1, 4, 8, 3, 256>(), make_cfg<1, 4, 8, false, true>(),
                                  make_cfg<1, 4, 4, false, true>(), make_split_cfg<1, 4, 8>(),
                                  make_split_cfg<1, 4, 8, 2>(), make_cfg<1, 4, 4, true, true, 1, 128>(),
                                  make_cfg<1, 4, 4, true, true, 1, 256>(), make_split_cfg<1, 4, 4, 3, 256>(),
-                                 make_cfg<1, 4, 4, true, true>(), make_split_cfg<1, 4, 8, 7, 256>()};
+                                 make_cfg<1, 4, 4, true, true>(), make_split_cfg<1, 4, 8, 7, 256>(),
+                                 make_cfg<1, 4, 8, true, false, 1, 256>(), make_cfg<1, 4, 4, true, false, 1, 128>()};
   static const KernelCfg v5[] = {make_split_cfg<1, 5, 8, 5, 512>(), make_cfg<1, 5, 4, false, false>(),
                                  make_split_cfg<1, 5, 4>(), make_split_cfg<1, 5, 4, 2>(),
                                  make_cfg<1, 5, 4, false, true>(), make_split_cfg<1, 5, 4, 3, 256>(),

@@ -130,3 +130,22 @@ def test_empty_mesh_is_refused(P):
     with pytest.raises(P.DGError) as e:
         P.suggest_dt(verts[:3], tets[:0], np.ones((0, 2)), 2, "acoustic", 0.4)
     assert e.value.code == -1
+
+
+def test_tune_cache_file_handling(P, tmp_path):
+    """The autotune cache: a save with no choices writes only the header, and
+    loading it takes nothing; files that are not such a cache or have a
+    malformed line are refused with DG_EINVAL before anything is applied."""
+    P.tune_clear()
+    path = tmp_path / "tune.txt"
+    P.tune_save(str(path))
+    assert path.read_text().splitlines() == ["# libdg autotune cache v1"]
+    assert P.tune_load(str(path)) == 0
+    for bad in ("no header\n", "# libdg autotune cache v1\nGB300 10.3 0 4\n",
+                "# libdg autotune cache v1\nGB300 103 0 4 0 1 12 256 0 0\n"):
+        path.write_text(bad)
+        with pytest.raises(P.DGError) as e:
+            P.tune_load(str(path))
+        assert e.value.code == -1
+    with pytest.raises(P.DGError):
+        P.tune_load(str(tmp_path / "missing.txt"))
