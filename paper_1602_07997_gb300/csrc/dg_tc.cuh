@@ -18,8 +18,10 @@
 //     512 TMEM columns, so that a tile's products run while the previous
 //     tile's epilogue drains): NSPLIT = 2 gives the three products of bf16x3,
 //     NSPLIT = 3 the six products that leave only terms of relative size 2^-24;
-//   - warps 2-5, epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its
-//     output rows) and does the geometric combination, the point source and
+//   - warps 2-9, epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its
+//     output rows; two warps per lane quarter, each half of the tile's
+//     element columns, so that twice as many AB3 loads are in flight) and
+//     does the geometric combination, the point source and
 //     the AB3 update (Eq. updateScheme) as in the fused kernel, rows across
 //     lanes: global accesses are coalesced; the AB3 inputs of a group of
 //     elements are all in flight before the first store.
@@ -59,7 +61,8 @@ struct TcShape {
   static constexpr int B16 = TX::CD > TX::CL ? TX::CD : TX::CL;
   static constexpr int STAGE = A_D + B16;
   static constexpr int RECB = NE * Rec<MODEL>::size * 4;  // element records of one tile
-  static constexpr int NT = 192;                  // 6 warps: producer, MMA, 4 epilogue
+  static constexpr int NEPI = 8;                  // epilogue warps: two per TMEM lane quarter
+  static constexpr int NT = 64 + 32 * NEPI;       // producer, MMA, epilogue warps
   static constexpr size_t OPS_PER_MTILE = size_t(NKD) * A_D + size_t(NKL) * A_L;
   static constexpr size_t FIXED = 2 * RECB + 256;
   static constexpr int NSF = int((225 * 1024 - FIXED) / STAGE);
@@ -110,7 +113,7 @@ __device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-// 32 lanes x 32 bits, 4 or 8 consecutive columns per thread
+// 32 lanes x 32 bits, 2, 4 or 8 consecutive columns per thread
 __device__ __forceinline__ void tc_ld4(uint32_t taddr, float* v) {
   uint32_t r0, r1, r2, r3;
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
@@ -118,6 +121,12 @@ __device__ __forceinline__ void tc_ld4(uint32_t taddr, float* v) {
                : "r"(taddr)
                : "memory");
   v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
+}
+__device__ __forceinline__ void tc_ld2(uint32_t taddr, float* v) {
+  uint32_t r0, r1;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr) : "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
 }
 __device__ __forceinline__ void tc_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
@@ -161,7 +170,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
 }
 
 template <int MODEL, int N, int NSPLIT>
-__global__ void __launch_bounds__(192, 1) dg_tc_gemm_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(TcShape<MODEL, N, NSPLIT>::NT, 1) dg_tc_gemm_kernel(const StepArgs a) {
   using TS = TcShape<MODEL, N, NSPLIT>;
   using TX = typename TS::TX;
   constexpr int Np = TS::Np, Nf = TS::Nf, NV = TS::NV, NE = TS::NE;
@@ -191,9 +200,9 @@ __global__ void __launch_bounds__(192, 1) dg_tc_gemm_kernel(const StepArgs a) {
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], TS::NEPI);
       mbar_init(&rfull[b], 1);
-      mbar_init(&rempty[b], 4);
+      mbar_init(&rempty[b], TS::NEPI);
     }
     mbar_init(done, 1);
     fence_barrier_init();
@@ -335,7 +344,11 @@ __global__ void __launch_bounds__(192, 1) dg_tc_gemm_kernel(const StepArgs a) {
   } else {
     // -------- epilogue: warp w reads TMEM lanes 32 (w mod 4) .. 32 (w mod 4) + 31
     const int quarter = warp & 3;
-    constexpr int EC = MODEL == 0 ? 8 : 4;  // elements per group: TMEM loads and AB3 inputs in flight together
+    // the two warps of a lane quarter split the tile's element columns
+    constexpr int NEH = NE / (TS::NEPI / 4);
+    const int ehalf = (warp - 2) / 4;
+    constexpr int EC = MODEL == 0 ? 4 : 2;  // elements per group: TMEM loads and AB3 inputs in flight together
+    static_assert(NEH % EC == 0 && TS::NEPI % 4 == 0, "whole element groups per epilogue warp");
     for (int j = 0; j < nmine; ++j) {
       const int t = int(blockIdx.x) + j * int(gridDim.x);
       const int mtile = t % MTILES, ntile = t / MTILES;
@@ -351,14 +364,16 @@ __global__ void __launch_bounds__(192, 1) dg_tc_gemm_kernel(const StepArgs a) {
       const int i = mtile * 128 + quarter * 32 + lane;  // output row of this thread
       const bool row_ok = i < Np;
       const uint32_t trow = tmem + uint32_t(b * TS::TCOLS) + (uint32_t(quarter * 32) << 16);
-      for (int e0 = 0; e0 < NE; e0 += EC) {
+      for (int e0 = ehalf * NEH; e0 < (ehalf + 1) * NEH; e0 += EC) {
         float v[TS::NACC][EC];
 #pragma unroll
         for (int p = 0; p < TS::NACC; ++p) {
           if constexpr (EC == 8)
             tc_ld8(trow + uint32_t(p * NE + e0), v[p]);
-          else
+          else if constexpr (EC == 4)
             tc_ld4(trow + uint32_t(p * NE + e0), v[p]);
+          else
+            tc_ld2(trow + uint32_t(p * NE + e0), v[p]);
         }
         // AB3 inputs of the whole group before any store (rows across lanes)
         float qa[EC][Nf], r1a[EC][Nf], r2a[EC][Nf];
