@@ -205,7 +205,7 @@ int Handle::init(const dg_mesh* mesh, const double* coeffs_, int N_, int model_,
   std::vector<int32_t> nbr;
   pack_records(hm, coeffs.data(), model, Kpad, geo, nbr);
   pack_ops(ref, ops, ftab);
-  if (model == DG_ACOUSTIC && N <= 2) {
+  if ((model == DG_ACOUSTIC && N <= 2) || (model == DG_ELASTIC && N == 1)) {
     // the element-per-thread kernels unroll their face loops over the
     // compile-time face masks: they must be the tables built here
     for (int f = 0; f < 4; ++f)

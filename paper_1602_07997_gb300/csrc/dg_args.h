@@ -122,11 +122,12 @@ struct KernelCfg {
 const KernelCfg* kernel_variants(int model, int N, int* count, int precision = 0);
 const KernelCfg* kernel_cfg(int model, int N);
 
-// Acoustic fused step with one element per thread (N = 1, 2): variant
-// `which` (0, 1, 2 (N = 1 only): elements per CTA), and the upload of the operator blob
-// ([3 Np + 4 Nfp][Mpad] as the block kernel's) to its constant memory on
-// the current device (once per device and N).
-KernelCfg ept_variant(int N, int which);
+// Fused step with one element per thread (acoustic N = 1, 2; elastic N =
+// 1): variant `which` (0, 1, 2 (acoustic N = 1 only): elements per CTA), and
+// the upload of the operator blob ([3 Np + 4 Nfp][Mpad] as the block
+// kernel's) to its constant memory on the current device (once per device
+// and N).
+KernelCfg ept_variant(int model, int N, int which);
 cudaError_t ept_upload_ops(int N, const float* ops, size_t n);
 // Opt the step kernel of `cfg` into its shared memory and read its occupancy
 // on the current device, and load the small source kernel: everything

@@ -1,4 +1,4 @@
-// Fused acoustic step with one element per thread (N = 1, 2).
+// Fused step with one element per thread (acoustic N = 1, 2; elastic N = 1).
 //
 // At low degree an element is a few dozen values and the operator products
 // are tiny (Np x Np, Np x 4 Nfp), so the staged block kernel spends its time
@@ -40,10 +40,10 @@ __device__ __forceinline__ float opc(int idx) {
   else return c_ops2[idx];
 }
 
-template <int N, int EB>
+template <int MODEL, int N, int EB>
 struct EptPlan {
   using S = Sz<N>;
-  static constexpr int Nf = 4, Np = S::Np, Nfp = S::Nfp, NFN = S::NFN, REC = Rec<0>::size;
+  static constexpr int Nf = MODEL == 0 ? 4 : 9, Np = S::Np, Nfp = S::Nfp, NFN = S::NFN, REC = Rec<MODEL>::size;
   static constexpr int QS = Nf * Np;   // floats per element
   // element stride in shared memory: + 4 words when QS is a multiple of 8,
   // so that the float4 rows of 8 consecutive elements fall in 8 different
@@ -68,9 +68,9 @@ struct EptPlan {
 // Body shared by one solve per launch and by a batch of solves (served
 // mode): the provider maps a global block to its solve's arguments and local
 // block, as for the block kernel.
-template <int N, int EB, class Prov>
+template <int MODEL, int N, int EB, class Prov>
 __device__ __forceinline__ void ept_body(const Prov& prov) {
-  using P = EptPlan<N, EB>;
+  using P = EptPlan<MODEL, N, EB>;
   constexpr int Nf = P::Nf, Np = P::Np, Nfp = P::Nfp, QS = P::QS, QSP = P::QSP, REC = P::REC;
   constexpr int Mpad = Sz<N>::Mpad, EBP = P::EBP, SLOTS = P::SLOTS;
   constexpr int NT = EB;
@@ -216,7 +216,6 @@ __device__ __forceinline__ void ept_body(const Prov& prov) {
       float g[9];
 #pragma unroll
       for (int x = 0; x < 9; ++x) g[x] = gk[x];
-      const float kap = gk[9], rinv = gk[10], ZM = gk[11];
       float qv[QS];
 #pragma unroll
       for (int x = 0; x < QS / 4; ++x) {
@@ -226,130 +225,225 @@ __device__ __forceinline__ void ept_body(const Prov& prov) {
         qv[4 * x + 2] = t.z;
         qv[4 * x + 3] = t.w;
       }
-      const float* p = qv;
-      const float* v0 = qv + Np;
-      const float* v1 = qv + 2 * Np;
-      const float* v2 = qv + 3 * Np;
-      float R[Np], rv[3][Np];
+      const int4 nb = sNbr[e];
+      // where the neighbour's traces across face f are read: the outer
+      // boundary reads the element's own trace (its ghost state follows from
+      // it); a neighbour in this block its staged fields through the
+      // face-node permutation; a gathered one its slot (already in this
+      // face's node order); a third or fourth outside face global memory
+      struct Src {
+        bool bnd, glob;
+        const float* base;  // field 0 of the traces (shared memory)
+        int cs;             // stride between fields
+        const int* pt;      // neighbour volume node of each face node (in-block, global)
+        const float* gq;    // the neighbour's fields in global memory
+        bool inblk;
+      };
+      auto face_src = [&](int f) {
+        const int w = nbr_word(nb, f);
+        Src S;
+        S.bnd = w < 0;
+        const int kn = S.bnd ? 0 : (w >> kNbrShift);
+        const int le = kn - k0;
+        S.inblk = !S.bnd && le >= 0 && le < EB;
+        const int slot = (S.bnd || S.inblk) ? 0 : outside_rank(nb, f, k0, EB);
+        S.glob = !S.bnd && !S.inblk && slot >= SLOTS;
+        S.pt = sPtab + (S.bnd ? 0 : ((w & 3) * 6 + ((w >> 2) & 7)) * Nfp);
+        S.base = S.bnd ? qe : S.inblk ? sQ + le * QSP : sT + slot * Nf * Nfp * EBP + e;
+        S.cs = (S.bnd || S.inblk) ? Np : Nfp * EBP;
+        S.gq = a.q + size_t(kn) * QS;
+        return S;
+      };
+      // the Nf neighbour values at face node m (own node nM)
+      auto nbr_trace = [&](const Src& S, int m, int nM, float* qP) {
+        if (!S.glob) {
+          const int idx = S.bnd ? nM : S.inblk ? S.pt[m] : m * EBP;
 #pragma unroll
-      for (int i = 0; i < Np; ++i) {
-        R[i] = 0.f;
-        rv[0][i] = rv[1][i] = rv[2][i] = 0.f;
-      }
-      // volume term: R = sum_d D_d w_d with w_d = -kappa sum_c g_cd v_c; the
-      // pressure gradient G_d = D_d p joins r_v,c = -(1/rho) sum_d g_cd G_d
+          for (int c = 0; c < Nf; ++c) qP[c] = S.base[idx + c * S.cs];
+        } else {
+          const int nP = S.pt[m];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        float wd[Np];
-#pragma unroll
-        for (int j = 0; j < Np; ++j) wd[j] = -kap * (g[d] * v0[j] + g[3 + d] * v1[j] + g[6 + d] * v2[j]);
-        float Gd[Np];
+          for (int c = 0; c < Nf; ++c) qP[c] = __ldg(S.gq + c * Np + nP);
+        }
+      };
+      float r[QS];
+      if constexpr (MODEL == 0) {
+        const float kap = gk[9], rinv = gk[10], ZM = gk[11];
+        const float* p = qv;
+        const float* v0 = qv + Np;
+        const float* v1 = qv + 2 * Np;
+        const float* v2 = qv + 3 * Np;
+        float R[Np], rv[3][Np];
 #pragma unroll
         for (int i = 0; i < Np; ++i) {
-          float accR = R[i], accG = 0.f;
-#pragma unroll
-          for (int j = 0; j < Np; ++j) {
-            const float Dij = opc<N>((d * Np + j) * Mpad + i);
-            accR = fmaf(Dij, wd[j], accR);
-            accG = fmaf(Dij, p[j], accG);
-          }
-          R[i] = accR;
-          Gd[i] = accG;
+          R[i] = 0.f;
+          rv[0][i] = rv[1][i] = rv[2][i] = 0.f;
         }
+        // volume term: R = sum_d D_d w_d with w_d = -kappa sum_c g_cd v_c; the
+        // pressure gradient G_d = D_d p joins r_v,c = -(1/rho) sum_d g_cd G_d
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float sc = -rinv * g[3 * c + d];
+        for (int d = 0; d < 3; ++d) {
+          float wd[Np];
 #pragma unroll
-          for (int i = 0; i < Np; ++i) rv[c][i] = fmaf(sc, Gd[i], rv[c][i]);
-        }
-      }
-      // surface term, face by face: penalties pen_p = A jp + B jvn and
-      // psi = C jp + D jvn (jp = [[p]]/2, jvn = [[v]].n/2, Fscale folded in),
-      // R += LIFT_f pen_p, r_v += n_f LIFT_f psi
-      const int4 nb = sNbr[e];
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const float4 fn = face_normal(g, f);
-        const float fs = fn.w, zP = gk[12 + f];
-        float A, B, C, D;
-        if (a.flux == 0) {
-          const float kc = 2.f / (ZM + zP);
-          A = fs * kap * kc;
-          B = -A * zP;
-          C = -fs * (ZM * rinv) * kc;
-          D = -C * zP;
-        } else {
-          A = 0.f;
-          B = -fs * kap;
-          C = -fs * rinv;
-          D = 0.f;
-        }
-        const int w = nbr_word(nb, f);
-        // where the neighbour's traces are read: the outer boundary reads the
-        // element's own trace and mirrors it (rigid wall: p+ = p-, v+ = v- -
-        // 2 (v-.n) n); a neighbour in this block its staged fields through the
-        // face-node permutation; a gathered one its slot (already in this
-        // face's node order); a third or fourth outside face global memory
-        const bool bnd = w < 0;
-        const int kn = bnd ? 0 : (w >> kNbrShift);
-        const int le = kn - k0;
-        const bool inblk = !bnd && le >= 0 && le < EB;
-        const int slot = (bnd || inblk) ? 0 : outside_rank(nb, f, k0, EB);
-        const bool glob = !bnd && !inblk && slot >= SLOTS;
-        const int* pt = sPtab + (bnd ? 0 : ((w & 3) * 6 + ((w >> 2) & 7)) * Nfp);
-        const float* base = bnd ? qe : inblk ? sQ + le * QSP : sT + slot * Nf * Nfp * EBP + e;
-        const int cs = (bnd || inblk) ? Np : Nfp * EBP;  // stride between fields
-        const float mir = bnd ? 2.f : 0.f;
-        const float* gq = a.q + size_t(kn) * QS;
-        float L[Np];
-#pragma unroll
-        for (int i = 0; i < Np; ++i) L[i] = 0.f;
-#pragma unroll
-        for (int m = 0; m < Nfp; ++m) {
-          const int nM = FN.v[f][m];
-          const float pM = p[nM], vM0 = v0[nM], vM1 = v1[nM], vM2 = v2[nM];
-          float pP, vP0, vP1, vP2;
-          if (!glob) {
-            const int idx = bnd ? nM : inblk ? pt[m] : m * EBP;
-            pP = base[idx];
-            vP0 = base[idx + cs];
-            vP1 = base[idx + 2 * cs];
-            vP2 = base[idx + 3 * cs];
-          } else {
-            const int nP = pt[m];
-            pP = __ldg(gq + nP);
-            vP0 = __ldg(gq + Np + nP);
-            vP1 = __ldg(gq + 2 * Np + nP);
-            vP2 = __ldg(gq + 3 * Np + nP);
-          }
-          const float vn = mir * (vP0 * fn.x + vP1 * fn.y + vP2 * fn.z);
-          vP0 -= vn * fn.x;
-          vP1 -= vn * fn.y;
-          vP2 -= vn * fn.z;
-          const float jp = 0.5f * (pP - pM);
-          const float jvn = 0.5f * ((vP0 - vM0) * fn.x + (vP1 - vM1) * fn.y + (vP2 - vM2) * fn.z);
-          const float pp = A * jp + B * jvn, ps = C * jp + D * jvn;
+          for (int j = 0; j < Np; ++j) wd[j] = -kap * (g[d] * v0[j] + g[3 + d] * v1[j] + g[6 + d] * v2[j]);
+          float Gd[Np];
 #pragma unroll
           for (int i = 0; i < Np; ++i) {
-            const float l = opc<N>((3 * Np + f * Nfp + m) * Mpad + i);
-            R[i] = fmaf(l, pp, R[i]);
-            L[i] = fmaf(l, ps, L[i]);
+            float accR = R[i], accG = 0.f;
+#pragma unroll
+            for (int j = 0; j < Np; ++j) {
+              const float Dij = opc<N>((d * Np + j) * Mpad + i);
+              accR = fmaf(Dij, wd[j], accR);
+              accG = fmaf(Dij, p[j], accG);
+            }
+            R[i] = accR;
+            Gd[i] = accG;
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float sc = -rinv * g[3 * c + d];
+#pragma unroll
+            for (int i = 0; i < Np; ++i) rv[c][i] = fmaf(sc, Gd[i], rv[c][i]);
+          }
+        }
+        // surface term, face by face: penalties pen_p = A jp + B jvn and
+        // psi = C jp + D jvn (jp = [[p]]/2, jvn = [[v]].n/2, Fscale folded in),
+        // R += LIFT_f pen_p, r_v += n_f LIFT_f psi; the rigid wall mirrors the
+        // own trace (p+ = p-, v+ = v- - 2 (v-.n) n)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const float4 fn = face_normal(g, f);
+          const float fs = fn.w, zP = gk[12 + f];
+          float A, B, C, D;
+          if (a.flux == 0) {
+            const float kc = 2.f / (ZM + zP);
+            A = fs * kap * kc;
+            B = -A * zP;
+            C = -fs * (ZM * rinv) * kc;
+            D = -C * zP;
+          } else {
+            A = 0.f;
+            B = -fs * kap;
+            C = -fs * rinv;
+            D = 0.f;
+          }
+          const Src S = face_src(f);
+          const float mir = S.bnd ? 2.f : 0.f;
+          float L[Np];
+#pragma unroll
+          for (int i = 0; i < Np; ++i) L[i] = 0.f;
+#pragma unroll
+          for (int m = 0; m < Nfp; ++m) {
+            const int nM = FN.v[f][m];
+            const float pM = p[nM], vM0 = v0[nM], vM1 = v1[nM], vM2 = v2[nM];
+            float qP[Nf];
+            nbr_trace(S, m, nM, qP);
+            const float vn = mir * (qP[1] * fn.x + qP[2] * fn.y + qP[3] * fn.z);
+            const float vP0 = qP[1] - vn * fn.x, vP1 = qP[2] - vn * fn.y, vP2 = qP[3] - vn * fn.z;
+            const float jp = 0.5f * (qP[0] - pM);
+            const float jvn = 0.5f * ((vP0 - vM0) * fn.x + (vP1 - vM1) * fn.y + (vP2 - vM2) * fn.z);
+            const float pp = A * jp + B * jvn, ps = C * jp + D * jvn;
+#pragma unroll
+            for (int i = 0; i < Np; ++i) {
+              const float l = opc<N>((3 * Np + f * Nfp + m) * Mpad + i);
+              R[i] = fmaf(l, pp, R[i]);
+              L[i] = fmaf(l, ps, L[i]);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < Np; ++i) {
+            rv[0][i] = fmaf(fn.x, L[i], rv[0][i]);
+            rv[1][i] = fmaf(fn.y, L[i], rv[1][i]);
+            rv[2][i] = fmaf(fn.z, L[i], rv[2][i]);
           }
         }
 #pragma unroll
         for (int i = 0; i < Np; ++i) {
-          rv[0][i] = fmaf(fn.x, L[i], rv[0][i]);
-          rv[1][i] = fmaf(fn.y, L[i], rv[1][i]);
-          rv[2][i] = fmaf(fn.z, L[i], rv[2][i]);
+          r[i] = R[i];
+          r[Np + i] = rv[0][i];
+          r[2 * Np + i] = rv[1][i];
+          r[3 * Np + i] = rv[2][i];
         }
-      }
-      float r[QS];
+      } else {
+        // volume term (elastic): U_cd = D_d v_c and Rv_c = sum_d D_d s_cd with
+        // s_cd = (1/rho) sum_m g_md sigma_cm; then the stress part lambda
+        // (div v) I + mu (grad v + grad v^T) with grad v from U and g
+        const float lam = gk[9], mu = gk[10], rinv = gk[11];
+        float U[3][3][Np], Rv[3][Np];
 #pragma unroll
-      for (int i = 0; i < Np; ++i) {
-        r[i] = R[i];
-        r[Np + i] = rv[0][i];
-        r[2 * Np + i] = rv[1][i];
-        r[3 * Np + i] = rv[2][i];
+        for (int i = 0; i < Np; ++i)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            Rv[c][i] = 0.f;
+            U[c][0][i] = U[c][1][i] = U[c][2][i] = 0.f;
+          }
+#pragma unroll
+        for (int j = 0; j < Np; ++j) {
+          float sg[3][3];
+          sg[0][0] = qv[3 * Np + j];
+          sg[1][1] = qv[4 * Np + j];
+          sg[2][2] = qv[5 * Np + j];
+          sg[0][1] = sg[1][0] = qv[6 * Np + j];
+          sg[0][2] = sg[2][0] = qv[7 * Np + j];
+          sg[1][2] = sg[2][1] = qv[8 * Np + j];
+          float sv[3][3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sv[c][d] = rinv * (g[d] * sg[c][0] + g[3 + d] * sg[c][1] + g[6 + d] * sg[c][2]);
+#pragma unroll
+          for (int i = 0; i < Np; ++i)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              const float Dij = opc<N>((d * Np + j) * Mpad + i);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                U[c][d][i] = fmaf(Dij, qv[c * Np + j], U[c][d][i]);
+                Rv[c][i] = fmaf(Dij, sv[c][d], Rv[c][i]);
+              }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < Np; ++i) {
+          float gv[3][3];  // gv[c][x] = d v_c / d x_x = sum_d g[x][d] U[c][d]
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int x = 0; x < 3; ++x) gv[c][x] = g[3 * x] * U[c][0][i] + g[3 * x + 1] * U[c][1][i] + g[3 * x + 2] * U[c][2][i];
+          const float div = gv[0][0] + gv[1][1] + gv[2][2];
+          r[i] = Rv[0][i];
+          r[Np + i] = Rv[1][i];
+          r[2 * Np + i] = Rv[2][i];
+          r[3 * Np + i] = lam * div + 2.f * mu * gv[0][0];
+          r[4 * Np + i] = lam * div + 2.f * mu * gv[1][1];
+          r[5 * Np + i] = lam * div + 2.f * mu * gv[2][2];
+          r[6 * Np + i] = mu * (gv[0][1] + gv[1][0]);
+          r[7 * Np + i] = mu * (gv[0][2] + gv[2][0]);
+          r[8 * Np + i] = mu * (gv[1][2] + gv[2][1]);
+        }
+        // surface term: the nine penalty terms of Section 2.1 at every face
+        // node (face_penalty: upwind or centred flux, mirror ghosts on the
+        // outer boundary), lifted onto every field
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const float4 fn = face_normal(g, f);
+          const Src S = face_src(f);
+#pragma unroll
+          for (int m = 0; m < Nfp; ++m) {
+            const int nM = FN.v[f][m];
+            float qM[Nf], qP[Nf], pen[Nf];
+#pragma unroll
+            for (int c = 0; c < Nf; ++c) qM[c] = qv[c * Np + nM];
+            nbr_trace(S, m, nM, qP);
+            face_penalty<1>(gk, f, S.bnd, qM, qP, fn, a.flux, a.bc, pen);
+#pragma unroll
+            for (int i = 0; i < Np; ++i) {
+              const float l = opc<N>((3 * Np + f * Nfp + m) * Mpad + i);
+#pragma unroll
+              for (int c = 0; c < Nf; ++c) r[c * Np + i] = fmaf(l, pen[c], r[c * Np + i]);
+            }
+          }
+        }
       }
       if (k == a.src_elem && a.srcvec) {
 #pragma unroll
@@ -420,22 +514,22 @@ __device__ __forceinline__ void ept_body(const Prov& prov) {
 }
 
 // one solve per launch (dg_step / dg_rhs)
-template <int N, int EB>
+template <int MODEL, int N, int EB>
 __global__ void __launch_bounds__(EB) dg_ept_kernel(const StepArgs a) {
   SingleSolve p{a, EB};
-  ept_body<N, EB>(p);
+  ept_body<MODEL, N, EB>(p);
 }
 
-// every solve of a batch (same N) in one persistent launch (served mode)
-template <int N, int EB>
+// every solve of a batch (same model and N) in one persistent launch (served mode)
+template <int MODEL, int N, int EB>
 __global__ void __launch_bounds__(EB) dg_ept_batched_kernel(const BatchArgs b) {
   SolveBatch p{b};
-  ept_body<N, EB>(p);
+  ept_body<MODEL, N, EB>(p);
 }
 
-template <int N, int EB>
+template <int MODEL, int N, int EB>
 KernelCfg make_ept_cfg() {
-  using P = EptPlan<N, EB>;
+  using P = EptPlan<MODEL, N, EB>;
   static_assert(P::bytes <= 227 * 1024, "shared memory budget");
   KernelCfg c{};
   c.EB = EB;
@@ -444,8 +538,8 @@ KernelCfg make_ept_cfg() {
   c.ops_smem = false;
   c.r_smem = false;
   c.smem = P::bytes;
-  c.fn = dg_ept_kernel<N, EB>;
-  c.fn_batched = dg_ept_batched_kernel<N, EB>;
+  c.fn = dg_ept_kernel<MODEL, N, EB>;
+  c.fn_batched = dg_ept_batched_kernel<MODEL, N, EB>;
   c.split = 0;
   c.fn_gemm = nullptr;
   c.fn_gemm_batched = nullptr;
@@ -456,9 +550,11 @@ KernelCfg make_ept_cfg() {
   return c;
 }
 
-KernelCfg ept_variant(int N, int which) {
-  if (N == 1) return which == 0 ? make_ept_cfg<1, 64>() : which == 1 ? make_ept_cfg<1, 128>() : make_ept_cfg<1, 32>();
-  return which == 0 ? make_ept_cfg<2, 32>() : make_ept_cfg<2, 64>();
+KernelCfg ept_variant(int model, int N, int which) {
+  if (model == 1) return which == 0 ? make_ept_cfg<1, 1, 32>() : make_ept_cfg<1, 1, 64>();
+  if (N == 1)
+    return which == 0 ? make_ept_cfg<0, 1, 64>() : which == 1 ? make_ept_cfg<0, 1, 128>() : make_ept_cfg<0, 1, 32>();
+  return which == 0 ? make_ept_cfg<0, 2, 32>() : make_ept_cfg<0, 2, 64>();
 }
 
 cudaError_t ept_upload_ops(int N, const float* ops, size_t n) {

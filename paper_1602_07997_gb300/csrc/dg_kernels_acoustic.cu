@@ -15,12 +15,12 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_cfg<0, 1, 32, true, true>(), make_cfg<0, 1, 128, true, true>(),
                                  make_cfg<0, 1, 16, true, true>(), make_cfg<0, 1, 64, true, true, 1, 256>(),
                                  make_cfg<0, 1, 32, true, true, 1, 256>(), make_cfg<0, 1, 64, true, true, 1, 512>(),
-                                 ept_variant(1, 0), ept_variant(1, 1), ept_variant(1, 2)};
+                                 ept_variant(0, 1, 0), ept_variant(0, 1, 1), ept_variant(0, 1, 2)};
   static const KernelCfg v2[] = {make_cfg<0, 2, 24, true, true, 1, 256>(), make_cfg<0, 2, 32, true, true>(),
                                  make_cfg<0, 2, 16, true, true>(), make_cfg<0, 2, 64, true, true>(),
                                  make_cfg<0, 2, 16, true, true, 1, 128>(), make_cfg<0, 2, 8, true, true>(),
                                  make_cfg<0, 2, 16, true, true, 1, 256>(), make_cfg<0, 2, 32, true, true, 1, 512>(),
-                                 make_cfg<0, 2, 32, true, true, 1, 256>(), ept_variant(2, 0), ept_variant(2, 1)};
+                                 make_cfg<0, 2, 32, true, true, 1, 256>(), ept_variant(0, 2, 0), ept_variant(0, 2, 1)};
   static const KernelCfg v3[] = {make_cfg<0, 3, 12, true, true, 1, 256>(), make_cfg<0, 3, 4, true, true>(),
                                  make_cfg<0, 3, 16, true, true>(), make_cfg<0, 3, 32, true, true>(),
                                  make_cfg<0, 3, 16, true, true, 1, 128>(), make_cfg<0, 3, 8, true, true>(),

@@ -9,7 +9,7 @@ namespace dgk {
 const KernelCfg* kernel_variants_elastic(int N, int* count) {
   static const KernelCfg v1[] = {make_cfg<1, 1, 16, true, true, 1, 128>(), make_cfg<1, 1, 8, true, true>(),
                                  make_cfg<1, 1, 32, true, true>(), make_cfg<1, 1, 16, true, true>(),
-                                 make_cfg<1, 1, 32, true, true, 1, 256>()};
+                                 make_cfg<1, 1, 32, true, true, 1, 256>(), ept_variant(1, 1, 0), ept_variant(1, 1, 1)};
   static const KernelCfg v2[] = {make_cfg<1, 2, 8, true, true, 1, 128>(), make_cfg<1, 2, 4, true, true>(),
                                  make_cfg<1, 2, 16, true, true>(), make_cfg<1, 2, 8, true, true>(),
                                  make_cfg<1, 2, 16, true, true, 1, 256>()};
