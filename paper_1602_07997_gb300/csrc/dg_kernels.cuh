@@ -229,10 +229,9 @@ struct Plan {
   static constexpr int oXvol = round4(oR + nR);
   static constexpr int oXsur = round4(oXvol + nXvol);
   static constexpr int oT0 = round4(oXsur + nXsur);
-  // one trace buffer unless DIRECT: every other path gathers the next
-  // block's traces after the barrier that follows this block's last read of
-  // them; the DIRECT front half has no such barrier and keeps two
-  static constexpr int oT1 = DIRECT ? round4(oT0 + nT) : oT0;
+  // one trace buffer: every path gathers the next block's traces after the
+  // barrier that follows this block's last read of them
+  static constexpr int oT1 = oT0;
   static constexpr int oOps = round4(oT1 + nT);
   static constexpr int oFn = round4(oOps + nOps);          // [4][EBF] float4: n, Fscale
   static constexpr int oNt = oFn + EBF * 16;               // [4 x 3][EBP]: normals, element fastest (FACT)
@@ -854,16 +853,20 @@ __device__ __forceinline__ void step_body(const Prov& prov) {
     }
     if constexpr (DIRECT) {
       // every GEMM input of the block is in X: start the next block's
-      // neighbour gathers (its trace buffer was last read before the
-      // barrier at the top of this block) and move on
+      // neighbour gathers and move on
       static_assert(SPLIT % 4 == 0 && (SPLIT % EB == 0 || EB % SPLIT == 0), "element blocks inside column tiles");
-      // (cp.async gathers: a thread whose wait expired issues none of its own;
-      // its wait at the top of the next block expires again and the CTA stops)
-      if (b + G < nblk) {
-        if (mbar_wait_bounded(&bars[s ^ 1], pnext, err, lim)) {
-          pend_clr(s ^ 1);
-          issue_gathers(nxt_a, nxt_lb, s ^ 1);
+      // (after a barrier: the gathers overwrite the trace buffer this block
+      // has just read; the decision is CTA-wide)
+      {
+        const bool okn = b + G < nblk ? mbar_wait_bounded(&bars[s ^ 1], pnext, err, lim) : true;
+        if (!__syncthreads_and(okn)) {
+          drain();
+          return;
         }
+      }
+      if (b + G < nblk) {
+        pend_clr(s ^ 1);
+        issue_gathers(nxt_a, nxt_lb, s ^ 1);
       }
       continue;
     }
