@@ -141,6 +141,16 @@ void dg_destroy(dg_handle *h);
 /* Sizes: number of elements, nodes per element, nodes per face, fields.     */
 int dg_info(const dg_handle *h, int64_t *K, int *Np, int *Nfp, int *Nf);
 
+/* State transfers take `on_device` = 0 (host memory; the call returns when
+ * its copies are complete), 1 (device memory on the handle's device) or
+ * DG_HOST_ASYNC = 2 (page-locked host memory, e.g. cudaHostAlloc'd or a
+ * pinned torch tensor: the copies are ordered on the handle's stream and
+ * complete at the next dg_sync or any later synchronising call; the caller
+ * must not touch the buffer before then; memory that is not page-locked is
+ * refused with DG_EINVAL).  Several handles on separate streams then
+ * overlap their transfers with one another's kernels.                      */
+enum { DG_HOST_ASYNC = 2 };
+
 /* Replace the state.  q [K][Nf][Np].  r1 = r^{m-1} and r2 = r^{m-2} (same
  * layout) are either both NULL -- the next steps then start AB3 with a
  * forward-Euler step and an AB2 step -- or both given (full AB3 history).
@@ -276,6 +286,11 @@ int dg_rhs_host_noalloc(dg_handle *h, float *r_out);
  * nothing.  DG_EINVAL for reps < 1 or target_ms outside (0, 10000].        */
 int dg_fp32_peak(void *stream, int reps, double target_ms, double *scalar_tflops,
                  double *packed_tflops, double *ms_per_launch);
+
+/* Move the handle to another CUDA stream (cudaStream_t; NULL = legacy
+ * default stream): the work already issued on its stream finishes first
+ * (the call waits for it), later calls issue on the new one.               */
+int dg_set_stream(dg_handle *h, void *stream);
 
 /* Wait for the handle's stream and report what the kernels flagged since the
  * last report: DG_ETIMEOUT if a bounded device wait expired (the results of

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libdg.so")
 
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONFINITE, DG_ETIMEOUT, DG_EAGAIN, DG_ECANCELED, DG_ENOENT = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
+DG_HOST_ASYNC = 2
 ACOUSTIC, ELASTIC = 0, 1
 FLUX = {"upwind": 0, "centered": 1, "centred": 1}
 BC = {None: 0, "default": 0, "rigid": 1, "free": 2}
@@ -27,7 +28,7 @@ EXPORTS = ("dg_setup", "dg_destroy", "dg_info", "dg_set_state", "dg_get_state", 
            "dg_reference_element", "dg_last_error", "dg_server_create", "dg_submit", "dg_poll",
            "dg_cancel", "dg_server_stats", "dg_server_destroy", "dg_rhs_host_noalloc", "dg_set_receivers",
            "dg_get_traces", "dg_fp32_peak", "dg_set_finite_check", "dg_set_wait_limit", "dg_launch_count",
-           "dg_tune_save", "dg_tune_load", "dg_tune_clear")
+           "dg_tune_save", "dg_tune_load", "dg_tune_clear", "dg_set_stream")
 
 
 class DGError(RuntimeError):
@@ -103,6 +104,7 @@ def lib():
         "dg_tune_save": (i32, [C.c_char_p]),
         "dg_tune_load": (i32, [C.c_char_p, P(i32)]),
         "dg_tune_clear": (i32, []),
+        "dg_set_stream": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -267,30 +269,42 @@ class Solver:
 
     __del__ = close
 
-    def set_state(self, q, r1=None, r2=None, step=0):
+    def set_state(self, q, r1=None, r2=None, step=0, asynchronous=False):
         """Replace the state by q; r1 = r^{m-1} and r2 = r^{m-2} give the AB3
         history (both or neither: without them the next steps start with Euler
-        and AB2).  step = the time-step index of q (it indexes source amplitudes)."""
+        and AB2).  step = the time-step index of q (it indexes source amplitudes).
+        asynchronous: q (and r1, r2) are pinned host tensors and the copy stays
+        in stream order (complete at the next sync); leave them untouched until then."""
         if (r1 is None) != (r2 is None):
             raise ValueError("r1 and r2 are given together or not at all")
         pq, dq, kq = _buf(q, np.float32, self.size)
+        if asynchronous:
+            if dq:
+                raise ValueError("asynchronous transfers take pinned host memory")
+            dq = DG_HOST_ASYNC
         p1 = p2 = None
         keep = []
         if r1 is not None:
             p1, d1, k1 = _buf(r1, np.float32, self.size)
             p2, d2, k2 = _buf(r2, np.float32, self.size)
             keep += [k1, k2]
-            if not (dq == d1 == d2):
+            if not (min(dq, 1) == d1 == d2):
                 raise ValueError("q, r1 and r2 must all be host or all device")
         check(lib().dg_set_state(self.h, pq, p1, p2, int(step), dq))
 
-    def get_state(self, q=None, r1=None, r2=None):
+    def get_state(self, q=None, r1=None, r2=None, asynchronous=False):
         """The state q (a new host array, or into q / r1 / r2 if given); sets
-        self.step_index and self.history (stored RHS levels, 0..2)."""
+        self.step_index and self.history (stored RHS levels, 0..2).
+        asynchronous: the outputs are pinned host tensors, filled in stream
+        order (complete at the next sync)."""
         ret = q is None
         if q is None:
             q = np.empty(self.shape, dtype=np.float32)
         pq, dq, _ = _buf(q, np.float32, self.size, write=True)
+        if asynchronous:
+            if dq:
+                raise ValueError("asynchronous transfers take pinned host memory")
+            dq = DG_HOST_ASYNC
         p1 = _buf(r1, np.float32, self.size, write=True)[0] if r1 is not None else None
         p2 = _buf(r2, np.float32, self.size, write=True)[0] if r2 is not None else None
         step, hist = C.c_int64(), C.c_int()
@@ -317,6 +331,11 @@ class Solver:
             raise ValueError("rhs_host_noalloc writes host memory")
         check(lib().dg_rhs_host_noalloc(self.h, p))
         return out if ret else None
+
+    def set_stream(self, stream):
+        """Issue later work on `stream` (a cudaStream_t as an int, e.g.
+        torch.cuda.Stream().cuda_stream); work already issued finishes first."""
+        check(lib().dg_set_stream(self.h, C.c_void_p(int(stream) if stream else 0)))
 
     def set_dt(self, dt):
         check(lib().dg_set_dt(self.h, float(dt)))

@@ -622,12 +622,29 @@ int dg_info(const dg_handle* h, int64_t* K, int* Np, int* Nfp, int* Nf) {
   return DG_OK;
 }
 
+// Memory kind of a dg_set_state / dg_get_state buffer: 0 host (the call
+// waits for its copies), 1 device, 2 page-locked host memory (the copies
+// stay in stream order).  Mode 2 refuses memory that is not page-locked.
+static int check_transfer(const void* p, int on_device) {
+  if (on_device < 0 || on_device > 2) return fail(DG_EINVAL, "on_device must be 0, 1 or 2");
+  if (on_device != 2 || !p) return DG_OK;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) return dg::cuda_fail(e, "cudaPointerGetAttributes");
+  if (at.type != cudaMemoryTypeHost) return fail(DG_EINVAL, "on_device = 2 needs page-locked host memory");
+  return DG_OK;
+}
+
 int dg_set_state(dg_handle* h, const float* q, const float* r1, const float* r2, int64_t step,
                  int on_device) {
   if (!h || !q) return fail(DG_EINVAL, "NULL handle or state");
   if ((r1 == nullptr) != (r2 == nullptr)) return fail(DG_EINVAL, "give both r1 and r2 or neither");
+  for (const void* p : {static_cast<const void*>(q), static_cast<const void*>(r1), static_cast<const void*>(r2)}) {
+    int rc = check_transfer(p, on_device);
+    if (rc) return rc;
+  }
   const size_t bytes = size_t(h->K) * h->Nf * h->Np * 4;
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kind = on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   DG_CUDA(cudaMemcpyAsync(h->d_q[h->qcur], q, bytes, kind, h->stream));
   if (r1) {
     DG_CUDA(cudaMemcpyAsync(h->d_r[h->r1slot], r1, bytes, kind, h->stream));
@@ -639,21 +656,33 @@ int dg_set_state(dg_handle* h, const float* q, const float* r1, const float* r2,
     h->have = 0;
   }
   h->step = step;
-  if (!on_device) DG_CUDA(cudaStreamSynchronize(h->stream));
+  if (on_device == 0) DG_CUDA(cudaStreamSynchronize(h->stream));
   return DG_OK;
 }
 
 int dg_get_state(dg_handle* h, float* q, float* r1, float* r2, int64_t* step, int* history,
                  int on_device) {
   if (!h) return fail(DG_EINVAL, "NULL handle");
+  for (const void* p : {static_cast<const void*>(q), static_cast<const void*>(r1), static_cast<const void*>(r2)}) {
+    int rc = check_transfer(p, on_device);
+    if (rc) return rc;
+  }
   const size_t bytes = size_t(h->K) * h->Nf * h->Np * 4;
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const cudaMemcpyKind kind = on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (q) DG_CUDA(cudaMemcpyAsync(q, h->d_q[h->qcur], bytes, kind, h->stream));
   if (r1) DG_CUDA(cudaMemcpyAsync(r1, h->d_r[h->r1slot], bytes, kind, h->stream));
   if (r2) DG_CUDA(cudaMemcpyAsync(r2, h->d_r[1 - h->r1slot], bytes, kind, h->stream));
   if (step) *step = h->step;
   if (history) *history = h->have;
-  if (!on_device) DG_CUDA(cudaStreamSynchronize(h->stream));
+  if (on_device == 0) DG_CUDA(cudaStreamSynchronize(h->stream));
+  return DG_OK;
+}
+
+int dg_set_stream(dg_handle* h, void* stream) {
+  if (!h) return fail(DG_EINVAL, "NULL handle");
+  DG_CUDA(cudaStreamSynchronize(h->stream));  // work already issued finishes on the old stream
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->opts.stream = stream;
   return DG_OK;
 }
 

@@ -222,3 +222,35 @@ def test_every_kernel_variant_rhs_and_steps(dg, model, N):
         else:
             assert rel_l2(model, s, ref_state.astype(np.float64)) <= 1e-5, (v, g.kernel_info())
     g.close()
+
+
+@pytest.mark.gpu
+def test_async_pinned_transfers_on_another_stream(dg):
+    """dg_set_state / dg_get_state with page-locked host memory in stream
+    order (on_device = 2) on a stream set by dg_set_stream give the same
+    state, bit for bit, as the synchronous host path; memory that is not
+    page-locked is refused."""
+    import torch
+    verts, tets, coeffs = _mesh("acoustic", 3, 90)
+    ref = dg.Solver(verts, tets, coeffs, 4, "acoustic", dt=1e-3)
+    g = dg.Solver(verts, tets, coeffs, 4, "acoustic", dt=1e-3)
+    st = torch.cuda.Stream()
+    g.set_stream(st.cuda_stream)
+    q = W.random_state(ref.K, ref.Nf, ref.Np, seed=5).astype(np.float32)
+    pin = torch.from_numpy(q.copy()).pin_memory()
+    out = torch.empty(g.shape, dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        ref.set_state(q)
+        ref.step(2)
+        q = ref.get_state()
+        g.set_state(pin, asynchronous=True)
+        g.step(2)
+        g.get_state(out, asynchronous=True)
+        g.sync()
+        pin.copy_(out)
+        assert np.array_equal(out.numpy(), q)
+    with pytest.raises(dg.DGError) as e:
+        g.set_state(np.zeros(g.shape, np.float32), asynchronous=True)
+    assert e.value.code == -1
+    g.close()
+    ref.close()
