@@ -213,8 +213,10 @@ cudaError_t launch_step_batched(const KernelCfg* c, const BatchArgs& args, cudaS
   e = cudaLaunchKernel(reinterpret_cast<const void*>(c->fn_batched), dim3(grid), dim3(c->NT), params, c->smem,
                        stream);
   if (e != cudaSuccess || !c->split || args.total_tiles == 0) return e;
-  return cudaLaunchKernel(reinterpret_cast<const void*>(c->fn_gemm_batched), dim3(unsigned(args.total_tiles)),
-                          dim3(c->gemm_threads), params, c->smem_gemm, stream);
+  const unsigned tiles = unsigned(args.total_tiles);
+  const unsigned ggrid = c->gemm_persistent && tiles > unsigned(gcap) ? unsigned(gcap) : tiles;
+  return cudaLaunchKernel(reinterpret_cast<const void*>(c->fn_gemm_batched), dim3(ggrid), dim3(c->gemm_threads),
+                          params, c->smem_gemm, stream);
 }
 
 cudaError_t launch_advance(SolveDev* solves, int nsolves, cudaStream_t stream) {

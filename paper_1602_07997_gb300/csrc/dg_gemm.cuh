@@ -471,6 +471,308 @@ __device__ __forceinline__ void gemm_a_body(const StepArgs& a, const int mtile, 
   }
 }
 
+// Register tile of design B's (and W's) operator products: TM rows x TE
+// element columns of every accumulator, in pairs of consecutive rows (the
+// operands of the packed FMAs).  The chunk walks read a stage in shared
+// memory: A = operator rows [KC-deep chunk][MTS] from the thread's first row,
+// B = X rows [vector][KC][NES] from the thread's first element.
+template <int MODEL, int N, int TM, int TE, bool PK, int MTS, int NES>
+struct ProdTile {
+  static constexpr int Np = Sz<N>::Np, NFN = Sz<N>::NFN, Nfp = Sz<N>::Nfp;
+  static constexpr int KC = 16;
+  static constexpr int NXS = XRows<MODEL, N>::NXS;
+  static constexpr int NACC = MODEL == 0 ? 4 : 12;
+  static constexpr int REC = Rec<MODEL>::size;
+  static constexpr int kTM = TM, kTE = TE;
+  // acoustic: 0..2 G_d then T_c (velocity), 3 R then r_p; elastic: 0..8
+  // U_cd then the stress components (0..5) and W (6..8), 9..11 Rv_c
+  float2 acc2[NACC][TE][TM / 2];
+  float2 lf2[MODEL == 0 ? TE : 1][TM / 2];  // acoustic: LIFT_f psi of the current face f
+  float lamv[TE], muv[TE];                  // elastic: Lame coefficients of the element columns
+
+  // row v of element column t of accumulator x
+  __device__ __forceinline__ float& acc(int x, int t, int v) {
+    return (v & 1) ? acc2[x][t][v >> 1].y : acc2[x][t][v >> 1].x;
+  }
+  // accumulator holding field f of the RHS once the K loop is done
+  __device__ static constexpr int slot_of_field(int f) {
+    return MODEL == 0 ? (f == 0 ? 3 : f - 1) : (f < 3 ? 9 + f : f - 3);
+  }
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int x = 0; x < NACC; ++x)
+#pragma unroll
+      for (int t = 0; t < TE; ++t)
+#pragma unroll
+        for (int v = 0; v < TM / 2; ++v) acc2[x][t][v] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < (MODEL == 0 ? TE : 1); ++t)
+#pragma unroll
+      for (int v = 0; v < TM / 2; ++v) lf2[t][v] = make_float2(0.f, 0.f);
+  }
+
+  __device__ __forceinline__ static void ldA(const float* p, float2* o) {  // TM rows as float4s, in row pairs
+#pragma unroll
+    for (int q = 0; q < TM / 4; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(p + 4 * q);
+      o[2 * q] = make_float2(v.x, v.y);
+      o[2 * q + 1] = make_float2(v.z, v.w);
+    }
+  }
+  __device__ __forceinline__ static void ldB(const float* p, float* o) {  // TE consecutive elements
+    if constexpr (TE == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p);
+      o[0] = v.x;
+      o[1] = v.y;
+      o[2] = v.z;
+      o[3] = v.w;
+    } else if constexpr (TE == 2) {
+      const float2 v = *reinterpret_cast<const float2*>(p);
+      o[0] = v.x;
+      o[1] = v.y;
+    } else {
+      o[0] = *p;
+    }
+  }
+
+  // a volume chunk of nj indices j: acoustic G_d += D_d p, R += sum_d D_d w_d;
+  // elastic U_cd += D_d v_c, Rv_c += sum_d D_d s_cd
+  __device__ __forceinline__ void volume(const float* A, const float* B, const int nj) {
+#pragma unroll 2
+    for (int jj = 0; jj < nj; ++jj) {
+      float2 ad[3][TM / 2];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) ldA(A + (d * KC + jj) * MTS, ad[d]);
+      if constexpr (MODEL == 0) {
+        float xp[TE], xw[3][TE];
+        ldB(B + (0 * KC + jj) * NES, xp);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ldB(B + ((1 + d) * KC + jj) * NES, xw[d]);
+#pragma unroll
+        for (int t = 0; t < TE; ++t) {
+          const float2 p2 = dup2(xp[t]), w0 = dup2(xw[0][t]), w1 = dup2(xw[1][t]), w2 = dup2(xw[2][t]);
+#pragma unroll
+          for (int v = 0; v < TM / 2; ++v) {
+            acc2[0][t][v] = fma2<PK>(ad[0][v], p2, acc2[0][t][v]);
+            acc2[1][t][v] = fma2<PK>(ad[1][v], p2, acc2[1][t][v]);
+            acc2[2][t][v] = fma2<PK>(ad[2][v], p2, acc2[2][t][v]);
+            acc2[3][t][v] = fma2<PK>(ad[0][v], w0, acc2[3][t][v]);
+            acc2[3][t][v] = fma2<PK>(ad[1][v], w1, acc2[3][t][v]);
+            acc2[3][t][v] = fma2<PK>(ad[2][v], w2, acc2[3][t][v]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          float xv[TE], xs[3][TE];
+          ldB(B + (cc * KC + jj) * NES, xv);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) ldB(B + ((3 + 3 * cc + d) * KC + jj) * NES, xs[d]);
+#pragma unroll
+          for (int t = 0; t < TE; ++t) {
+            const float2 v2 = dup2(xv[t]), s0 = dup2(xs[0][t]), s1 = dup2(xs[1][t]), s2 = dup2(xs[2][t]);
+#pragma unroll
+            for (int v = 0; v < TM / 2; ++v) {
+              acc2[3 * cc + 0][t][v] = fma2<PK>(ad[0][v], v2, acc2[3 * cc + 0][t][v]);
+              acc2[3 * cc + 1][t][v] = fma2<PK>(ad[1][v], v2, acc2[3 * cc + 1][t][v]);
+              acc2[3 * cc + 2][t][v] = fma2<PK>(ad[2][v], v2, acc2[3 * cc + 2][t][v]);
+              acc2[9 + cc][t][v] = fma2<PK>(ad[0][v], s0, acc2[9 + cc][t][v]);
+              acc2[9 + cc][t][v] = fma2<PK>(ad[1][v], s1, acc2[9 + cc][t][v]);
+              acc2[9 + cc][t][v] = fma2<PK>(ad[2][v], s2, acc2[9 + cc][t][v]);
+            }
+          }
+        }
+      }
+    }
+  }
+
+  // volume/LIFT boundary: the derivative products -> RHS components with the
+  // geometric factors of element column t (element k0 + t)
+  __device__ __forceinline__ void boundary(const StepArgs& a, const int k0) {
+#pragma unroll
+    for (int t = 0; t < TE; ++t) {
+      const int k = k0 + t;
+      const int kk = k < a.K ? k : a.K - 1;  // padding columns: any valid record
+      const float* gk = a.rec + size_t(kk) * REC;
+      float g[9];
+#pragma unroll
+      for (int x = 0; x < 9; ++x) g[x] = __ldg(gk + x);
+      if constexpr (MODEL == 0) {
+        const float rinv = __ldg(gk + 10);
+#pragma unroll
+        for (int v = 0; v < TM; ++v) {
+          const float G0 = acc(0, t, v), G1 = acc(1, t, v), G2 = acc(2, t, v);
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc)
+            acc(cc, t, v) = -rinv * (g[3 * cc] * G0 + g[3 * cc + 1] * G1 + g[3 * cc + 2] * G2);
+        }
+      } else {
+        const float lam = __ldg(gk + 9), mu = __ldg(gk + 10);
+        lamv[t] = lam;
+        muv[t] = mu;
+#pragma unroll
+        for (int v = 0; v < TM; ++v) {
+          float gv[3][3];
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+              gv[cc][x] = g[3 * x] * acc(3 * cc, t, v) + g[3 * x + 1] * acc(3 * cc + 1, t, v) +
+                          g[3 * x + 2] * acc(3 * cc + 2, t, v);
+          const float div = gv[0][0] + gv[1][1] + gv[2][2];
+          acc(0, t, v) = lam * div + 2.f * mu * gv[0][0];
+          acc(1, t, v) = lam * div + 2.f * mu * gv[1][1];
+          acc(2, t, v) = lam * div + 2.f * mu * gv[2][2];
+          acc(3, t, v) = mu * (gv[0][1] + gv[1][0]);
+          acc(4, t, v) = mu * (gv[0][2] + gv[2][0]);
+          acc(5, t, v) = mu * (gv[1][2] + gv[2][1]);
+          acc(6, t, v) = acc(7, t, v) = acc(8, t, v) = 0.f;  // W: LIFT_f dv of the current face
+        }
+      }
+    }
+  }
+
+  // a LIFT chunk of nc face nodes from face node c0; the chunk's face normals
+  // follow its streams in B (rows NXS KC + 3 f + c)
+  __device__ __forceinline__ void lift(const float* A, const float* B, const int c0, const int nc) {
+    if constexpr (MODEL == 0) {
+      // P_p onto r_p; psi face by face onto lf, which joins the velocity
+      // components as n_f,c lf once face f is complete
+      int cc = 0;
+      while (cc < nc) {
+        const int f = (c0 + cc) / Nfp;
+        const int fe = (f + 1) * Nfp - c0;  // end of face f, chunk-relative
+        const int ce = fe < nc ? fe : nc;
+#pragma unroll 2
+        for (; cc < ce; ++cc) {
+          float2 l[TM / 2];
+          float pp[TE], ps[TE];
+          ldA(A + cc * MTS, l);
+          ldB(B + (0 * KC + cc) * NES, pp);
+          ldB(B + (1 * KC + cc) * NES, ps);
+#pragma unroll
+          for (int t = 0; t < TE; ++t) {
+            const float2 p2 = dup2(pp[t]), s2 = dup2(ps[t]);
+#pragma unroll
+            for (int v = 0; v < TM / 2; ++v) {
+              acc2[3][t][v] = fma2<PK>(l[v], p2, acc2[3][t][v]);
+              lf2[t][v] = fma2<PK>(l[v], s2, lf2[t][v]);
+            }
+          }
+        }
+        if (cc == fe) {
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            float nv[TE];
+            ldB(B + (NXS * KC + 3 * f + x) * NES, nv);
+#pragma unroll
+            for (int t = 0; t < TE; ++t) {
+              const float2 n2 = dup2(nv[t]);
+#pragma unroll
+              for (int v = 0; v < TM / 2; ++v) acc2[x][t][v] = fma2<PK>(n2, lf2[t][v], acc2[x][t][v]);
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < TE; ++t)
+#pragma unroll
+            for (int v = 0; v < TM / 2; ++v) lf2[t][v] = make_float2(0.f, 0.f);
+        }
+      }
+    } else {
+      // Fscale p_v onto Rv (accumulators 9..11); Fscale dv face by face
+      // onto W (6..8), which joins the stress components as
+      // lambda (n.W) I + mu (n W^T + W n^T) once face f is complete
+      int cc = 0;
+      while (cc < nc) {
+        const int f = (c0 + cc) / Nfp;
+        const int fe = (f + 1) * Nfp - c0;  // end of face f, chunk-relative
+        const int ce = fe < nc ? fe : nc;
+#pragma unroll 2
+        for (; cc < ce; ++cc) {
+          float2 l[TM / 2];
+          ldA(A + cc * MTS, l);
+#pragma unroll
+          for (int x = 0; x < 6; ++x) {
+            float pf[TE];
+            ldB(B + (x * KC + cc) * NES, pf);
+            const int slot = x < 3 ? 9 + x : 3 + x;
+#pragma unroll
+            for (int t = 0; t < TE; ++t) {
+              const float2 p2 = dup2(pf[t]);
+#pragma unroll
+              for (int v = 0; v < TM / 2; ++v) acc2[slot][t][v] = fma2<PK>(l[v], p2, acc2[slot][t][v]);
+            }
+          }
+        }
+        if (cc == fe) {
+          float nv[3][TE];
+#pragma unroll
+          for (int x = 0; x < 3; ++x) ldB(B + (NXS * KC + 3 * f + x) * NES, nv[x]);
+#pragma unroll
+          for (int t = 0; t < TE; ++t)
+#pragma unroll
+            for (int v = 0; v < TM; ++v) {
+              const float w0 = acc(6, t, v), w1 = acc(7, t, v), w2 = acc(8, t, v);
+              const float nx = nv[0][t], ny = nv[1][t], nz = nv[2][t];
+              const float lnw = lamv[t] * (nx * w0 + ny * w1 + nz * w2), m2 = 2.f * muv[t];
+              acc(0, t, v) += lnw + m2 * nx * w0;
+              acc(1, t, v) += lnw + m2 * ny * w1;
+              acc(2, t, v) += lnw + m2 * nz * w2;
+              acc(3, t, v) += muv[t] * (nx * w1 + ny * w0);
+              acc(4, t, v) += muv[t] * (nx * w2 + nz * w0);
+              acc(5, t, v) += muv[t] * (ny * w2 + nz * w1);
+              acc(6, t, v) = acc(7, t, v) = acc(8, t, v) = 0.f;
+            }
+        }
+      }
+    }
+  }
+};
+
+// Epilogue of a product tile: one field at a time through shared memory
+// sOut[MT][NEP] (rows il.. of the thread tile, element columns e0..), then the
+// point source and the AB3 update (or the RHS store) with the tile's values
+// spread over the NTH threads (index th) in element-major order, so that
+// consecutive threads touch consecutive nodes.  sync() makes the staged field
+// visible to, and later free from, every one of the NTH threads.
+template <int MODEL, int N, int MT, int NE, int NEP, int NTH, class PT, class Sync>
+__device__ __forceinline__ void tile_epilogue(const StepArgs& a, PT& pt, float* sOut, const int th, const int il,
+                                              const int e0, const int row0, const int kbase, Sync sync) {
+  constexpr int Np = Sz<N>::Np, Nf = MODEL == 0 ? 4 : 9;
+  const int rows = (Np - row0) < MT ? (Np - row0) : MT;
+#pragma unroll
+  for (int f = 0; f < Nf; ++f) {
+    const int slot = PT::slot_of_field(f);
+#pragma unroll
+    for (int t = 0; t < PT::kTE; ++t)
+#pragma unroll
+      for (int v = 0; v < PT::kTM; ++v)
+        sOut[(il + v) * NEP + e0 + t] = pt.acc(slot, t, v);
+    sync();
+    constexpr int U = 8;  // values per thread in flight
+    for (int p0 = th; p0 < NE * MT; p0 += NTH * U) {
+      size_t idx[U];
+      float rv[U];
+      bool on[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int p = p0 + u * NTH;
+        const int e = p / MT, rr = p - e * MT;
+        const int k = kbase + e;
+        on[u] = p < NE * MT && k < a.K && rr < rows;
+        const int i = row0 + rr;
+        float r = on[u] ? sOut[rr * NEP + e] : 0.f;
+        if (on[u] && k == a.src_elem && a.srcvec) r = fmaf(a.src_amp, __ldg(a.srcvec + f * Np + i), r);
+        rv[u] = r;
+        idx[u] = on[u] ? size_t(k) * Nf * Np + size_t(f) * Np + i : 0;
+      }
+      ab3_batch<U>(a, idx, rv, on);
+    }
+    sync();
+  }
+}
+
 // NARROW: elements per thread halved (fewer registers, two CTAs per SM).
 // SMALL (narrow only): short row tiles that divide Np (almost) exactly and
 // registers sized for two resident CTAs per SM.  HALF (narrow only): a CTA
@@ -544,11 +846,9 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
   constexpr int XNE = SS::NE;
   const int mtile = mtile_l % SS::MTILES_R, half = mtile_l / SS::MTILES_R;
   const int kbase = ntile * XNE + half * NE;  // first element of the CTA
-  constexpr int Nfp = Sz<N>::Nfp, NXS = XRows<MODEL, N>::NXS, KXM = XRows<MODEL, N>::KXM;
+  constexpr int NXS = XRows<MODEL, N>::NXS, KXM = XRows<MODEL, N>::KXM;
   constexpr int MT = SS::MT, MP2 = SplitShape<MODEL, N>::OPP, KC = SS::KC, NT = SS::NT, NS = SS::NS;
   constexpr int NVC = SS::NVC, NLC = SS::NLC, NCH = NVC + NLC;
-  constexpr int REC = Rec<MODEL>::size;
-  constexpr int NACC = MODEL == 0 ? 4 : 12;
 
   extern __shared__ __align__(16) float smem[];
   auto sA = [&](int s) { return smem + s * SS::nStage; };
@@ -608,47 +908,8 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
   constexpr int CT = NE / TE;
   const int ct = tid % CT, rt = tid / CT;
   const int il = TM * rt, e0 = TE * ct;
-
-  // accumulators in pairs of consecutive rows (the operands of the packed
-  // FMAs); ACC(x, t, v) is row v of element column t of accumulator x
-  float2 acc2[NACC][TE][TM / 2];
-#define ACC(I_, T_, V_) (((V_) & 1) ? acc2[I_][T_][(V_) >> 1].y : acc2[I_][T_][(V_) >> 1].x)
-#pragma unroll
-  for (int x = 0; x < NACC; ++x)
-#pragma unroll
-    for (int t = 0; t < TE; ++t)
-#pragma unroll
-      for (int v = 0; v < TM / 2; ++v) acc2[x][t][v] = make_float2(0.f, 0.f);
-  float2 lf2[MODEL == 0 ? TE : 1][TM / 2];  // acoustic: LIFT_f psi of the current face f
-#pragma unroll
-  for (int t = 0; t < (MODEL == 0 ? TE : 1); ++t)
-#pragma unroll
-    for (int v = 0; v < TM / 2; ++v) lf2[t][v] = make_float2(0.f, 0.f);
-  float lamv[TE], muv[TE];  // elastic: Lame coefficients of the element columns (set at the boundary)
-
-  auto ldA = [&](const float* p, float2* o) {  // TM consecutive rows, as float4s, in row pairs
-#pragma unroll
-    for (int q = 0; q < TM / 4; ++q) {
-      const float4 v = *reinterpret_cast<const float4*>(p + 4 * q);
-      o[2 * q] = make_float2(v.x, v.y);
-      o[2 * q + 1] = make_float2(v.z, v.w);
-    }
-  };
-  auto ldB = [&](const float* p, float* o) {  // TE consecutive elements
-    if constexpr (TE == 4) {
-      const float4 v = *reinterpret_cast<const float4*>(p);
-      o[0] = v.x;
-      o[1] = v.y;
-      o[2] = v.z;
-      o[3] = v.w;
-    } else if constexpr (TE == 2) {
-      const float2 v = *reinterpret_cast<const float2*>(p);
-      o[0] = v.x;
-      o[1] = v.y;
-    } else {
-      o[0] = *p;
-    }
-  };
+  ProdTile<MODEL, N, TM, TE, PK, MT, NE> pt;
+  pt.zero();
 
 #pragma unroll
   for (int s = 0; s < NS - 1; ++s) issue(s);
@@ -665,231 +926,21 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
     const float* B = sB(c % NS) + e0;
     if (c < NVC) {
       const int nj = !rows_live ? 0 : Np - c * KC < KC ? Np - c * KC : KC;
-#pragma unroll 2
-      for (int jj = 0; jj < nj; ++jj) {
-        float2 ad[3][TM / 2];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) ldA(A + (d * KC + jj) * MT, ad[d]);
-        if constexpr (MODEL == 0) {
-          float xp[TE], xw[3][TE];
-          ldB(B + (0 * KC + jj) * NE, xp);
-#pragma unroll
-          for (int d = 0; d < 3; ++d) ldB(B + ((1 + d) * KC + jj) * NE, xw[d]);
-#pragma unroll
-          for (int t = 0; t < TE; ++t) {
-            const float2 p2 = dup2(xp[t]), w0 = dup2(xw[0][t]), w1 = dup2(xw[1][t]), w2 = dup2(xw[2][t]);
-#pragma unroll
-            for (int v = 0; v < TM / 2; ++v) {
-              acc2[0][t][v] = fma2<PK>(ad[0][v], p2, acc2[0][t][v]);
-              acc2[1][t][v] = fma2<PK>(ad[1][v], p2, acc2[1][t][v]);
-              acc2[2][t][v] = fma2<PK>(ad[2][v], p2, acc2[2][t][v]);
-              acc2[3][t][v] = fma2<PK>(ad[0][v], w0, acc2[3][t][v]);
-              acc2[3][t][v] = fma2<PK>(ad[1][v], w1, acc2[3][t][v]);
-              acc2[3][t][v] = fma2<PK>(ad[2][v], w2, acc2[3][t][v]);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int cc = 0; cc < 3; ++cc) {
-            float xv[TE], xs[3][TE];
-            ldB(B + (cc * KC + jj) * NE, xv);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) ldB(B + ((3 + 3 * cc + d) * KC + jj) * NE, xs[d]);
-#pragma unroll
-            for (int t = 0; t < TE; ++t) {
-              const float2 v2 = dup2(xv[t]), s0 = dup2(xs[0][t]), s1 = dup2(xs[1][t]), s2 = dup2(xs[2][t]);
-#pragma unroll
-              for (int v = 0; v < TM / 2; ++v) {
-                acc2[3 * cc + 0][t][v] = fma2<PK>(ad[0][v], v2, acc2[3 * cc + 0][t][v]);
-                acc2[3 * cc + 1][t][v] = fma2<PK>(ad[1][v], v2, acc2[3 * cc + 1][t][v]);
-                acc2[3 * cc + 2][t][v] = fma2<PK>(ad[2][v], v2, acc2[3 * cc + 2][t][v]);
-                acc2[9 + cc][t][v] = fma2<PK>(ad[0][v], s0, acc2[9 + cc][t][v]);
-                acc2[9 + cc][t][v] = fma2<PK>(ad[1][v], s1, acc2[9 + cc][t][v]);
-                acc2[9 + cc][t][v] = fma2<PK>(ad[2][v], s2, acc2[9 + cc][t][v]);
-              }
-            }
-          }
-        }
-      }
-      if (c == NVC - 1) {
-        // boundary: derivative products -> RHS components (per element column)
-#pragma unroll
-        for (int t = 0; t < TE; ++t) {
-          const int k = kbase + e0 + t;
-          const int kk = k < a.K ? k : a.K - 1;  // padding columns: any valid record
-          const float* gk = a.rec + size_t(kk) * REC;
-          float g[9];
-#pragma unroll
-          for (int x = 0; x < 9; ++x) g[x] = __ldg(gk + x);
-          if constexpr (MODEL == 0) {
-            const float rinv = __ldg(gk + 10);
-#pragma unroll
-            for (int v = 0; v < TM; ++v) {
-              const float G0 = ACC(0, t, v), G1 = ACC(1, t, v), G2 = ACC(2, t, v);
-#pragma unroll
-              for (int cc = 0; cc < 3; ++cc)
-                ACC(cc, t, v) = -rinv * (g[3 * cc] * G0 + g[3 * cc + 1] * G1 + g[3 * cc + 2] * G2);
-            }
-          } else {
-            const float lam = __ldg(gk + 9), mu = __ldg(gk + 10);
-            lamv[t] = lam;
-            muv[t] = mu;
-#pragma unroll
-            for (int v = 0; v < TM; ++v) {
-              float gv[3][3];
-#pragma unroll
-              for (int cc = 0; cc < 3; ++cc)
-#pragma unroll
-                for (int x = 0; x < 3; ++x)
-                  gv[cc][x] = g[3 * x] * ACC(3 * cc, t, v) + g[3 * x + 1] * ACC(3 * cc + 1, t, v) +
-                              g[3 * x + 2] * ACC(3 * cc + 2, t, v);
-              const float div = gv[0][0] + gv[1][1] + gv[2][2];
-              ACC(0, t, v) = lam * div + 2.f * mu * gv[0][0];
-              ACC(1, t, v) = lam * div + 2.f * mu * gv[1][1];
-              ACC(2, t, v) = lam * div + 2.f * mu * gv[2][2];
-              ACC(3, t, v) = mu * (gv[0][1] + gv[1][0]);
-              ACC(4, t, v) = mu * (gv[0][2] + gv[2][0]);
-              ACC(5, t, v) = mu * (gv[1][2] + gv[2][1]);
-              ACC(6, t, v) = ACC(7, t, v) = ACC(8, t, v) = 0.f;  // W: LIFT_f dv of the current face
-            }
-          }
-        }
-      }
+      pt.volume(A, B, nj);
+      if (c == NVC - 1) pt.boundary(a, kbase + e0);
     } else {
       const int c0 = (c - NVC) * KC;
       const int nc = !rows_live ? 0 : NFN - c0 < KC ? NFN - c0 : KC;
-      if constexpr (MODEL == 0) {
-        // P_p onto r_p; psi face by face onto lf, which joins the velocity
-        // components as n_f,c lf once face f is complete
-        int cc = 0;
-        while (cc < nc) {
-          const int f = (c0 + cc) / Nfp;
-          const int fe = (f + 1) * Nfp - c0;  // end of face f, chunk-relative
-          const int ce = fe < nc ? fe : nc;
-#pragma unroll 2
-          for (; cc < ce; ++cc) {
-            float2 l[TM / 2];
-            float pp[TE], ps[TE];
-            ldA(A + cc * MT, l);
-            ldB(B + (0 * KC + cc) * NE, pp);
-            ldB(B + (1 * KC + cc) * NE, ps);
-#pragma unroll
-            for (int t = 0; t < TE; ++t) {
-              const float2 p2 = dup2(pp[t]), s2 = dup2(ps[t]);
-#pragma unroll
-              for (int v = 0; v < TM / 2; ++v) {
-                acc2[3][t][v] = fma2<PK>(l[v], p2, acc2[3][t][v]);
-                lf2[t][v] = fma2<PK>(l[v], s2, lf2[t][v]);
-              }
-            }
-          }
-          if (cc == fe) {
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
-              float nv[TE];
-              ldB(B + (2 * KC + 3 * f + x) * NE, nv);
-#pragma unroll
-              for (int t = 0; t < TE; ++t) {
-                const float2 n2 = dup2(nv[t]);
-#pragma unroll
-                for (int v = 0; v < TM / 2; ++v) acc2[x][t][v] = fma2<PK>(n2, lf2[t][v], acc2[x][t][v]);
-              }
-            }
-#pragma unroll
-            for (int t = 0; t < TE; ++t)
-#pragma unroll
-              for (int v = 0; v < TM / 2; ++v) lf2[t][v] = make_float2(0.f, 0.f);
-          }
-        }
-      } else {
-        // Fscale p_v onto Rv (accumulators 9..11); Fscale dv face by face
-        // onto W (6..8), which joins the stress components as
-        // lambda (n.W) I + mu (n W^T + W n^T) once face f is complete
-        int cc = 0;
-        while (cc < nc) {
-          const int f = (c0 + cc) / Nfp;
-          const int fe = (f + 1) * Nfp - c0;  // end of face f, chunk-relative
-          const int ce = fe < nc ? fe : nc;
-#pragma unroll 2
-          for (; cc < ce; ++cc) {
-            float2 l[TM / 2];
-            ldA(A + cc * MT, l);
-#pragma unroll
-            for (int x = 0; x < 6; ++x) {
-              float pf[TE];
-              ldB(B + (x * KC + cc) * NE, pf);
-              const int slot = x < 3 ? 9 + x : 3 + x;
-#pragma unroll
-              for (int t = 0; t < TE; ++t) {
-                const float2 p2 = dup2(pf[t]);
-#pragma unroll
-                for (int v = 0; v < TM / 2; ++v) acc2[slot][t][v] = fma2<PK>(l[v], p2, acc2[slot][t][v]);
-              }
-            }
-          }
-          if (cc == fe) {
-            float nv[3][TE];
-#pragma unroll
-            for (int x = 0; x < 3; ++x) ldB(B + (NXS * KC + 3 * f + x) * NE, nv[x]);
-#pragma unroll
-            for (int t = 0; t < TE; ++t)
-#pragma unroll
-              for (int v = 0; v < TM; ++v) {
-                const float w0 = ACC(6, t, v), w1 = ACC(7, t, v), w2 = ACC(8, t, v);
-                const float nx = nv[0][t], ny = nv[1][t], nz = nv[2][t];
-                const float lnw = lamv[t] * (nx * w0 + ny * w1 + nz * w2), m2 = 2.f * muv[t];
-                ACC(0, t, v) += lnw + m2 * nx * w0;
-                ACC(1, t, v) += lnw + m2 * ny * w1;
-                ACC(2, t, v) += lnw + m2 * nz * w2;
-                ACC(3, t, v) += muv[t] * (nx * w1 + ny * w0);
-                ACC(4, t, v) += muv[t] * (nx * w2 + nz * w0);
-                ACC(5, t, v) += muv[t] * (ny * w2 + nz * w1);
-                ACC(6, t, v) = ACC(7, t, v) = ACC(8, t, v) = 0.f;
-              }
-          }
-        }
-      }
+      pt.lift(A, B, c0, nc);
     }
   }
   cp_async_wait_n<0>();
   __syncthreads();
 
   // -------- epilogue: one field at a time through shared memory [MT][NEP]
-  float* sOut = smem;
-  constexpr int NEP = SS::NEP;
-  const int rows = (Np - row0) < MT ? (Np - row0) : MT;
-#pragma unroll
-  for (int f = 0; f < Nf; ++f) {
-    const int slot = MODEL == 0 ? (f == 0 ? 3 : f - 1) : (f < 3 ? 9 + f : f - 3);  // accumulator of field f
-#pragma unroll
-    for (int t = 0; t < TE; ++t)
-#pragma unroll
-      for (int v = 0; v < TM; ++v) sOut[(il + v) * NEP + e0 + t] = ACC(slot, t, v);
-    __syncthreads();
-    constexpr int U = 8;  // values per thread in flight
-    for (int p0 = tid; p0 < NE * MT; p0 += NT * U) {
-      size_t idx[U];
-      float rv[U];
-      bool on[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int p = p0 + u * NT;
-        const int e = p / MT, rr = p - e * MT;
-        const int k = kbase + e;
-        on[u] = p < NE * MT && k < a.K && rr < rows;
-        const int i = row0 + rr;
-        float r = on[u] ? sOut[rr * NEP + e] : 0.f;
-        if (on[u] && k == a.src_elem && a.srcvec) r = fmaf(a.src_amp, __ldg(a.srcvec + f * Np + i), r);
-        rv[u] = r;
-        idx[u] = on[u] ? size_t(k) * Nf * Np + size_t(f) * Np + i : 0;
-      }
-      ab3_batch<U>(a, idx, rv, on);
-    }
-    __syncthreads();
-  }
+  tile_epilogue<MODEL, N, MT, NE, SS::NEP, NT>(a, pt, smem, tid, il, e0, row0, kbase, [] { __syncthreads(); });
 }
 
-#undef ACC
 
 // Design V of the FP32 GEMM (V = 2: design B, V = 3: design B with half the
 // elements per thread, V = 4: V = 3 with short row tiles and two CTAs per SM,
@@ -965,6 +1016,233 @@ struct GemmOf<MODEL, N, 10> {
   }
 };
 
+// ---------------------------------------------------------------- design W
+// Warp-specialised, persistent form of design B (narrow thread tile, packed
+// FMA).  Warp 0 is the producer: per K chunk one 1-D bulk copy for each
+// operator row slice (MT floats of a row of the blob) and one for each X row
+// block (a vector's KC rows of the column tile, contiguous in X), all
+// completing on the stage's full barrier.  Warps 1..NC are the consumers, warp
+// w + 1 owning rows TM w .. TM w + TM - 1 of the CTA's MT rows for all NE
+// elements of the column tile (TE per lane); each waits on the stage's full
+// barrier, runs the chunk and arrives on its empty barrier.  There is no
+// CTA-wide barrier in the K loop, and the CTA walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... so that the producer fills the ring with the
+// next tile's chunks while the consumers run the epilogue (which syncs the
+// consumer warps only, on named barriers).
+//
+// Failure handling: every wait is bounded.  A consumer warp whose wait expires
+// stops; all consumer warps then leave the tile loop together at the vote
+// before the next epilogue (so the named barriers always see every consumer),
+// the producer stops at its next expired empty wait, and thread 0 waits for
+// the copies still in flight before the CTA leaves.
+template <int MODEL, int N, int NC, int NSTG, int MINB_>
+struct GemmW {
+  using S = Sz<N>;
+  static constexpr int Np = S::Np, NFN = S::NFN;
+  static constexpr int Nf = MODEL == 0 ? 4 : 9;
+  static constexpr int NV = XRows<MODEL, N>::NV, NXS = XRows<MODEL, N>::NXS, KXM = XRows<MODEL, N>::KXM;
+  static constexpr int NE = MODEL == 0 ? 64 : 32;   // elements per column tile of X
+  static constexpr int TM = MODEL == 0 ? 8 : 4;     // rows per consumer warp
+  static constexpr int TE = NE / 32;                // elements per lane
+  static constexpr int MT = NC * TM;                // output rows per CTA tile
+  static constexpr int KC = 16;
+  static constexpr int NS = NSTG;
+  static constexpr int NT = 32 * (NC + 1);
+  static constexpr int MINB = MINB_;
+  static constexpr int MTILES_R = (Np + MT - 1) / MT;
+  static constexpr int MTILES_L = MTILES_R;
+  static constexpr int NVC = (Np + KC - 1) / KC;
+  static constexpr int NLC = (NFN + KC - 1) / KC;
+  static constexpr int nA = 3 * KC * MT;             // operator rows of one stage
+  static constexpr int LB = NXS * KC + 12;           // X rows of a LIFT chunk (streams, normals)
+  static constexpr int nB = (NV * KC > LB ? NV * KC : LB) * NE;
+  static constexpr int nStage = nA + nB;
+  static constexpr int NEP = NE + 1;                 // row stride of the staged RHS field
+  static constexpr int nOut = MT * NEP;
+  static constexpr int oOut = NS * nStage;
+  static constexpr int oBar = (oOut + nOut + 3) / 4 * 4;
+  static constexpr size_t smem = size_t(oBar) * 4 + size_t(2 * NS) * 8;
+  static constexpr size_t x_floats_per_tile = size_t(XRows<MODEL, N>::KX) * NE;
+  static_assert(MT % 4 == 0 && nA % 4 == 0 && nB % 4 == 0, "16-byte aligned copies and stages");
+  static_assert(NV <= 32 && NXS < 32, "one X copy per producer lane");
+  static_assert(NT <= 1024 && NS >= 2, "launch shape");
+};
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// AND of p over the nthreads threads that meet at named barrier id
+__device__ __forceinline__ bool named_bar_and(int id, int nthreads, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, %2, %3, pi;\n\tselp.u32 %0, 1, 0, "
+      "po;\n\t}"
+      : "=r"(r)
+      : "r"(uint32_t(p)), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+// Tiles of one solve: tile t = (row tile t % MTILES, column tile t / MTILES).
+template <int MTILES, int NE>
+struct WTilesOne {
+  const StepArgs& a;
+  __device__ int ntiles() const { return MTILES * ((a.K + NE - 1) / NE); }
+  __device__ const StepArgs& tile(int t, int& mtile, int& ntile) {
+    mtile = t % MTILES;
+    ntile = t / MTILES;
+    return a;
+  }
+  __device__ int* err() const { return a.err; }
+  __device__ long long limit() const { return a.wait_limit; }
+};
+// Tiles of every solve of a batch: global tile -> (solve, local tile) through
+// the batch's tile tables, the solve's arguments from its device-side state.
+template <int MTILES>
+struct WTilesBatch {
+  const BatchArgs& b;
+  StepArgs a;
+  __device__ int ntiles() const { return b.total_tiles; }
+  __device__ const StepArgs& tile(int t, int& mtile, int& ntile) {
+    const int so = __ldg(b.tile_solve + t);
+    const int lt = t - __ldg(b.tile_start + so);
+    solve_args(b, b.solves[so], a);
+    mtile = lt % MTILES;
+    ntile = lt / MTILES;
+    return a;
+  }
+  __device__ int* err() const { return b.err; }
+  __device__ long long limit() const { return b.wait_limit; }
+};
+
+template <int MODEL, int N, int NC, int NSTG, int MINB, class Prov>
+__device__ __forceinline__ void gemm_w_body(Prov& prov) {
+  using W = GemmW<MODEL, N, NC, NSTG, MINB>;
+  constexpr int Np = W::Np, NFN = W::NFN, NV = W::NV, NXS = W::NXS, KXM = W::KXM;
+  constexpr int NE = W::NE, TM = W::TM, TE = W::TE, MT = W::MT, KC = W::KC, NS = W::NS;
+  constexpr int NVC = W::NVC, NCH = W::NVC + W::NLC, MTILES = W::MTILES_R;
+  constexpr int MP2 = SplitShape<MODEL, N>::OPP;
+  constexpr int NCT = 32 * NC;  // consumer threads
+  static_assert(MTILES * MT <= MP2, "row tiles inside the operator pitch");
+
+  extern __shared__ __align__(16) float smem[];
+  auto sA = [&](int s) { return smem + s * W::nStage; };
+  auto sB = [&](int s) { return smem + s * W::nStage + W::nA; };
+  float* sOut = smem + W::oOut;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + W::oBar);  // stage s holds chunk g (g % NS = s)
+  uint64_t* empty = full + NS;                                   // every consumer warp is done with stage s
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = prov.ntiles();
+  int* const err = prov.err();
+  const long long limit = prov.limit();
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NC);
+    }
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  bool ok = true;
+  int issued = 0;  // producer: chunks whose copies were issued
+  if (warp == 0) {
+    // -------- producer
+    int g = 0;
+    for (int t = int(blockIdx.x); t < ntiles && ok; t += int(gridDim.x)) {
+      int mtile, ntile;
+      const StepArgs& a = prov.tile(t, mtile, ntile);
+      const float* X = a.xg + size_t(ntile) * W::x_floats_per_tile;
+      const float* OP = a.ops2 + mtile * MT;  // [3 Np + NFN][MP2], this tile's row slice
+      if (lane == 0 && mtile == 0 && a.mode == 0) prefetch_tile_l2<W::Nf, Np, NE>(a, ntile * NE);
+      for (int c = 0; c < NCH; ++c, ++g) {
+        const int s = g % NS;
+        bool got = true;
+        if (lane == 0 && g >= NS) got = mbar_wait_bounded(&empty[s], uint32_t(((g / NS) - 1) & 1), err, limit);
+        if (!__shfl_sync(0xffffffffu, got, 0)) {
+          ok = false;
+          break;
+        }
+        float* A = sA(s);
+        float* B = sB(s);
+        if (c < NVC) {
+          const int j0 = c * KC;
+          const int nj = Np - j0 < KC ? Np - j0 : KC;
+          if (lane == 0) mbar_arrive_expect_tx(&full[s], uint32_t((3 * MT + NV * NE) * nj * 4));
+          __syncwarp();
+          for (int i = lane; i < 3 * nj; i += 32) {
+            const int d = i / nj, jj = i - d * nj;
+            tma_bulk_g2s(A + (d * KC + jj) * MT, OP + size_t(d * Np + j0 + jj) * MP2, uint32_t(MT * 4), &full[s]);
+          }
+          if (lane < NV)
+            tma_bulk_g2s(B + lane * KC * NE, X + size_t(lane * Np + j0) * NE, uint32_t(nj * NE * 4), &full[s]);
+        } else {
+          const int c0 = (c - NVC) * KC;
+          const int nc = NFN - c0 < KC ? NFN - c0 : KC;
+          if (lane == 0) mbar_arrive_expect_tx(&full[s], uint32_t(((MT + NXS * NE) * nc + 12 * NE) * 4));
+          __syncwarp();
+          if (lane < nc) tma_bulk_g2s(A + lane * MT, OP + size_t(3 * Np + c0 + lane) * MP2, uint32_t(MT * 4), &full[s]);
+          if (lane < NXS)
+            tma_bulk_g2s(B + lane * KC * NE, X + size_t(NV * Np + lane * NFN + c0) * NE, uint32_t(nc * NE * 4),
+                         &full[s]);
+          if (lane == NXS) tma_bulk_g2s(B + NXS * KC * NE, X + size_t(KXM) * NE, uint32_t(12 * NE * 4), &full[s]);
+        }
+        issued = g + 1;
+      }
+    }
+  } else {
+    // -------- consumers
+    const int w = warp - 1;
+    const int il = TM * w, e0 = TE * lane;
+    int g = 0;
+    for (int t = int(blockIdx.x); t < ntiles; t += int(gridDim.x)) {
+      int mtile, ntile;
+      const StepArgs& a = prov.tile(t, mtile, ntile);
+      const int row0 = mtile * MT, kbase = ntile * NE;
+      const bool rows_live = row0 + il < Np;  // row groups wholly past Np skip the products
+      ProdTile<MODEL, N, TM, TE, true, MT, NE> pt;
+      pt.zero();
+      for (int c = 0; c < NCH; ++c, ++g) {
+        const int s = g % NS;
+        const bool got = mbar_wait_bounded(&full[s], uint32_t((g / NS) & 1), err, limit);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        if (rows_live) {
+          const float* A = sA(s) + il;
+          const float* B = sB(s) + e0;
+          if (c < NVC) {
+            pt.volume(A, B, Np - c * KC < KC ? Np - c * KC : KC);
+            if (c == NVC - 1) pt.boundary(a, kbase + e0);
+          } else {
+            const int c0 = (c - NVC) * KC;
+            pt.lift(A, B, c0, NFN - c0 < KC ? NFN - c0 : KC);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+      }
+      // every consumer warp takes the same way out (the epilogue's named
+      // barriers need all of them)
+      if (!named_bar_and(1, NCT, ok)) {
+        ok = false;
+        break;
+      }
+      tile_epilogue<MODEL, N, MT, NE, W::NEP, NCT>(a, pt, sOut, tid - 32, il, e0, row0, kbase,
+                                                   [] { named_bar_sync(2, NCT); });
+    }
+  }
+
+  const bool abort = __syncthreads_or(!ok);
+  if (abort && tid == 0) {
+    // copies still in flight land before the CTA leaves
+    for (int g = (issued > NS ? issued - NS : 0); g < issued; ++g)
+      mbar_wait_bounded(&full[g % NS], uint32_t((g / NS) & 1), nullptr);
+  }
+}
+
 // One solve: row tiles fastest, so that the CTAs that share a column tile of
 // X run together and read it from L2.  V selects the design (1 = A, 2 = B).
 template <int MODEL, int N, int V>
@@ -987,6 +1265,23 @@ __global__ void __launch_bounds__(GemmOf<MODEL, N, V>::T::NT, GemmOf<MODEL, N, V
   StepArgs a;
   solve_args(b, b.solves[so], a);
   GemmOf<MODEL, N, V>::body(a, lt % MTILES, lt / MTILES);
+}
+
+// Design W: one persistent CTA per resident slot walks the tiles of a solve
+// (or of every solve of a batch).
+template <int MODEL, int N, int NC, int NS, int MINB>
+__global__ void __launch_bounds__(GemmW<MODEL, N, NC, NS, MINB>::NT, MINB)
+    dg_split_gemm_w_kernel(const StepArgs a) {
+  using W = GemmW<MODEL, N, NC, NS, MINB>;
+  WTilesOne<W::MTILES_L, W::NE> prov{a};
+  gemm_w_body<MODEL, N, NC, NS, MINB>(prov);
+}
+template <int MODEL, int N, int NC, int NS, int MINB>
+__global__ void __launch_bounds__(GemmW<MODEL, N, NC, NS, MINB>::NT, MINB)
+    dg_split_gemm_w_batched_kernel(const BatchArgs b) {
+  using W = GemmW<MODEL, N, NC, NS, MINB>;
+  WTilesBatch<W::MTILES_L> prov{b};
+  gemm_w_body<MODEL, N, NC, NS, MINB>(prov);
 }
 
 }  // namespace dgk

@@ -40,7 +40,8 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_cfg<0, 5, 12, false, true, 2>(),
                                  make_split_cfg<0, 5, 8>(), make_cfg<0, 5, 8, false, true>(),
                                  make_split_cfg<0, 5, 4, 2>(), make_split_cfg<0, 5, 8, 2>(),
-                                 make_split_cfg<0, 5, 8, 2, 384>(), make_split_cfg<0, 5, 8, 2, 512>()};
+                                 make_split_cfg<0, 5, 8, 2, 384>(), make_split_cfg<0, 5, 8, 2, 512>(),
+                                 make_split_w_cfg<0, 5, 8, 7, 3, 2, 384>()};
   static const KernelCfg v6[] = {make_split_cfg<0, 6, 8, 3, 384>(), make_cfg<0, 6, 4, false, true>(),
                                  make_cfg<0, 6, 8, false, true, 2>(), make_cfg<0, 6, 4, false, true, 2>(),
                                  make_cfg<0, 6, 8, false, true>(), make_split_cfg<0, 6, 4>(),
@@ -48,7 +49,8 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_split_cfg<0, 6, 4, 2>(), make_split_cfg<0, 6, 8>(),
                                  make_split_cfg<0, 6, 8, 1, 512>(), make_split_cfg<0, 6, 8, 1, 384>(),
                                  make_split_cfg<0, 6, 8, 5, 384>(), make_split_cfg<0, 6, 8, 7, 384>(),
-                                 make_split_cfg<0, 6, 8, 9, 384>(), make_split_cfg<0, 6, 8, 10, 384>()};
+                                 make_split_cfg<0, 6, 8, 9, 384>(), make_split_cfg<0, 6, 8, 10, 384>(),
+                                 make_split_w_cfg<0, 6, 8, 11, 4, 1, 384>()};
   static const KernelCfg v7[] = {make_split_cfg<0, 7, 8, 5, 512>(), make_cfg<0, 7, 4, false, true, 2>(),
                                  make_cfg<0, 7, 8, false, true, 2>(), make_cfg<0, 7, 4, false, true, 4>(),
                                  make_split_cfg<0, 7, 8>(), make_split_cfg<0, 7, 4>(),
@@ -56,14 +58,16 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_split_cfg<0, 7, 4, 3>(), make_split_cfg<0, 7, 8, 3>(),
                                  make_split_cfg<0, 7, 8, 3, 768>(), make_split_cfg<0, 7, 8, 1, 512>(),
                                  make_split_cfg<0, 7, 8, 3, 512>(), make_split_cfg<0, 7, 8, 9, 512>(),
-                                 make_split_cfg<0, 7, 8, 7, 512>(), make_split_cfg<0, 7, 8, 10, 512>()};
+                                 make_split_cfg<0, 7, 8, 7, 512>(), make_split_cfg<0, 7, 8, 10, 512>(),
+                                 make_split_w_cfg<0, 7, 8, 15, 4, 1, 512>(), make_split_w_cfg<0, 7, 8, 8, 4, 1, 512>()};
   static const KernelCfg v8[] = {make_split_cfg<0, 8, 8, 3, 512>(), make_cfg<0, 8, 4, false, true, 2>(),
                                  make_cfg<0, 8, 4, false, true, 4>(), make_cfg<0, 8, 8, false, true, 2>(),
                                  make_split_cfg<0, 8, 4>(), make_split_cfg<0, 8, 8>(),
                                  make_split_cfg<0, 8, 8, 2>(), make_cfg<0, 8, 4, false, true>(),
                                  make_split_cfg<0, 8, 4, 3>(), make_split_cfg<0, 8, 8, 2, 512>(),
                                  make_split_cfg<0, 8, 8, 5, 768>(), make_split_cfg<0, 8, 8, 7, 512>(),
-                                 make_split_cfg<0, 8, 8, 9, 512>(), make_split_cfg<0, 8, 8, 10, 512>()};
+                                 make_split_cfg<0, 8, 8, 9, 512>(), make_split_cfg<0, 8, 8, 10, 512>(),
+                                 make_split_w_cfg<0, 8, 8, 11, 4, 1, 512>(), make_split_w_cfg<0, 8, 8, 11, 5, 1, 512>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
   static const int cnt[8] = {count_of(v1), count_of(v2), count_of(v3), count_of(v4),
                              count_of(v5), count_of(v6), count_of(v7), count_of(v8)};

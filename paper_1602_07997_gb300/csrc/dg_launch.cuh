@@ -81,6 +81,25 @@ KernelCfg make_split_cfg() {
   return c;
 }
 
+// Split variant with the warp-specialised persistent GEMM (design W): NC
+// consumer warps of TM rows each, an NS-stage ring, MINB resident CTAs.
+template <int MODEL, int N, int EB, int NC, int NS, int MINB = 1, int NT = threads_for<N, EB, 1>()>
+KernelCfg make_split_w_cfg() {
+  using SS = SplitShape<MODEL, N>;
+  using G = GemmW<MODEL, N, NC, NS, MINB>;
+  static_assert(Plan<MODEL, N, EB, false, false, MODEL == 0, true>::bytes <= 227 * 1024, "shared memory budget");
+  static_assert(G::smem * MINB <= 227 * 1024, "shared memory budget (GEMM)");
+  KernelCfg c = make_split_cfg<MODEL, N, EB, 3, NT>();
+  c.fn_gemm = dg_split_gemm_w_kernel<MODEL, N, NC, NS, MINB>;
+  c.fn_gemm_batched = dg_split_gemm_w_batched_kernel<MODEL, N, NC, NS, MINB>;
+  c.smem_gemm = G::smem;
+  c.gemm_threads = G::NT;
+  c.gemm_mt = G::MT;
+  c.gemm_mtiles = G::MTILES_L;
+  c.gemm_persistent = true;
+  return c;
+}
+
 // Tensor-core split variant: front half with EB elements per block writing
 // the NSPLIT BF16 pieces of its GEMM inputs in the tensor-core chunk layout,
 // then the tcgen05 kernel.

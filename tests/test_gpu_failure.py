@@ -98,15 +98,24 @@ def test_default_finite_check_interval():
 
 # every kernel form: acoustic N = 1 (whole-neighbour halos), N = 3 (history
 # staged in shared memory), N = 6 (FP32 split step), N = 5 bf16x6 (tcgen05);
-# elastic N = 2 (fused) and N = 5 (split)
-FORMS = [("acoustic", 1, "fp32"), ("acoustic", 3, "fp32"), ("acoustic", 6, "fp32"), ("acoustic", 5, "bf16x6"),
-         ("elastic", 2, "fp32"), ("elastic", 5, "fp32")]
+# elastic N = 2 (fused) and N = 5 (split); the last compiled variant of N = 8
+# (the split step with the warp-specialised persistent GEMM) of both models
+FORMS = [("acoustic", 1, "fp32", 0), ("acoustic", 3, "fp32", 0), ("acoustic", 6, "fp32", 0),
+         ("acoustic", 5, "bf16x6", 0), ("elastic", 2, "fp32", 0), ("elastic", 5, "fp32", 0),
+         ("acoustic", 8, "fp32", -1), ("elastic", 8, "fp32", -1)]
+
+
+def _form(model, N, precision, variant):
+    P, o, g, q, dt = _setup(model, N, n=4, precision=precision)
+    if variant != 0:
+        g.set_variant(g.kernel_info()["variants"] + variant if variant < 0 else variant)
+    return P, o, g, q, dt
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("model,N,precision", FORMS)
-def test_forced_wait_expiry_is_reported_and_the_handle_recovers(model, N, precision):
-    P, o, g, q, dt = _setup(model, N, n=4, precision=precision)
+@pytest.mark.parametrize("model,N,precision,variant", FORMS)
+def test_forced_wait_expiry_is_reported_and_the_handle_recovers(model, N, precision, variant):
+    P, o, g, q, dt = _form(model, N, precision, variant)
     g.set_state(q)
     g.set_wait_limit(-1)
     g.step(2)
@@ -115,13 +124,14 @@ def test_forced_wait_expiry_is_reported_and_the_handle_recovers(model, N, precis
     assert e.value.code == -5  # DG_ETIMEOUT
     g.set_wait_limit(0)
     _steps_match_oracle(o, g, q, dt)
+    g.set_variant(0)  # the choice is process-wide
     g.close()
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("model,N,precision", FORMS)
-def test_short_wait_limit_then_recovery(model, N, precision):
-    P, o, g, q, dt = _setup(model, N, n=4, precision=precision)
+@pytest.mark.parametrize("model,N,precision,variant", FORMS)
+def test_short_wait_limit_then_recovery(model, N, precision, variant):
+    P, o, g, q, dt = _form(model, N, precision, variant)
     g.set_state(q)
     for limit in (64, 512):
         g.set_wait_limit(limit)
@@ -132,6 +142,7 @@ def test_short_wait_limit_then_recovery(model, N, precision):
             assert e.code == -5
     g.set_wait_limit(0)
     _steps_match_oracle(o, g, q, dt)
+    g.set_variant(0)
     g.close()
 
 
