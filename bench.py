@@ -3,9 +3,12 @@
 Workload: the acoustic degree sweep N = 1..8, one jittered Kuhn cube mesh of
 ~2 M nodes per degree (rho, c ~ U[1,3], rigid walls, upwind flux, random
 initial state), FP32.  One bench step = one AB3 time step on each of the
-eight meshes (eight launches of the fused kernel).  value = sum over meshes
-of K*Np*Nf field updates / device time of the step.  The eight meshes hold
-~1.3 GB, so consecutive steps on one mesh never find its state in L2.
+eight meshes (one or two kernel launches each), the meshes on streams of
+their own so that their kernels overlap (``--sequential``: one after another
+on one stream).  value = sum over meshes of K*Np*Nf field updates / device
+time of the step.  The eight meshes hold ~1.3 GB, so consecutive steps on
+one mesh never find its state in L2.  The per-degree table and the roofline
+come from a second pass over the same steps that times each degree alone.
 
 Before the timed region every mesh's kernel variant is autotuned.
 
@@ -599,10 +602,41 @@ def run(args, rank, world, local_rank):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    # The meshes of the sweep are independent problems: a step of the sweep
+    # runs them on streams of their own (forked from and joined to the timing
+    # stream), largest degree first, so that one degree's kernels fill the SMs
+    # that another's leave idle at its tail.  --sequential runs them one
+    # after another on one stream instead.  The per-degree times (per_N, the
+    # roofline) come from a separate sequential pass over the same number of
+    # steps, each degree timed alone.
+    order = sorted(range(len(solvers)), key=lambda i: -solvers[i].N)
+    conc = not args.sequential and len(solvers) > 1
+    sstreams = [torch.cuda.Stream(device=dev) for _ in solvers] if conc else None
+    e_fork = torch.cuda.Event()
+    e_join = [torch.cuda.Event() for _ in solvers]
+
+    def sweep_step():
+        if not conc:
+            for g in solvers:
+                g.step(1)
+            return
+        e_fork.record(stream)
+        for i in order:
+            sstreams[i].wait_event(e_fork)
+            solvers[i].step(1)
+            e_join[i].record(sstreams[i])
+        for i in order:
+            stream.wait_event(e_join[i])
+
+    def on_streams(own):
+        for i, g in enumerate(solvers):
+            g.set_stream((sstreams[i] if own else stream).cuda_stream)
+
+    if conc:
+        on_streams(True)
     # warm-up
     for _ in range(args.warmup):
-        for g in solvers:
-            g.step(1)
+        sweep_step()
     barrier()
     nN = len(solvers)
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -613,21 +647,28 @@ def run(args, rank, world, local_rank):
         # samples cover the timed region
         t_wait = time.perf_counter()
         while clk.proc and not clk.lines and time.perf_counter() - t_wait < 3.0:
-            for g in solvers:
-                g.step(1)
+            sweep_step()
             torch.cuda.synchronize()
         barrier()
         lc0 = [g.launch_count() for g in solvers]
         t0 = time.perf_counter()
         e_all0.record(stream)
         for s in range(args.steps):
+            sweep_step()
+        e_all1.record(stream)
+        barrier()
+        t1 = time.perf_counter()
+        # kernels of the library launched in the timed region, as the handles count them
+        launches = sum(g.launch_count() - c for g, c in zip(solvers, lc0))
+        # per-degree pass: every degree alone on the timing stream
+        if conc:
+            on_streams(False)
+        for s in range(args.steps):
             for i, g in enumerate(solvers):
                 ev[s][i][0].record(stream)
                 g.step(1)
                 ev[s][i][1].record(stream)
-        e_all1.record(stream)
         barrier()
-        t1 = time.perf_counter()
     clocks = clk.summary(t0, t1)
     total_ms = e_all0.elapsed_time(e_all1)
     per_ms = [statistics.mean(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
@@ -649,8 +690,6 @@ def run(args, rank, world, local_rank):
         if dom is None or ms > dom[1]:
             byt, flop = algorithmic(model, g.N, g.K)
             dom = (g, ms, byt, flop, row["bound"])
-    # kernels of the library launched in the timed region, as the handles count them
-    launches = sum(g.launch_count() - c for g, c in zip(solvers, lc0))
     g, ms, byt, flop, bound = dom
     traffic = None
     try:
@@ -744,7 +783,10 @@ def run(args, rank, world, local_rank):
                   "config": {"workload": WORKLOAD if model == "acoustic" else WORKLOAD_ELASTIC, "degrees": Ns,
                              "meshes": {str(g.N): g.K for g in solvers},
                              "l2": "inputs larger than L2: the 8 meshes hold ~1.3 GB, each ~130 MB",
-                             "parallelism": "replicas" if world > 1 else "single GPU"},
+                             "parallelism": "replicas" if world > 1 else "single GPU",
+                             "sweep": ("concurrent: one stream per degree, largest degree first" if conc else
+                                       "sequential: one stream")},
+                  "sequential_ms_per_step": round(sum(per_ms), 5),
                   "gpu_launches": launches, "roofline": roof, "per_N": per_N, "sweeps": sweeps,
                   "cpu_baseline": cpu, "e2e": e2e, "served": served, "large_elastic": large, "clocks": clocks,
                   "fp32_peak": fp32, "peaks": pk}
@@ -772,7 +814,8 @@ def headline(d):
     line["ms_per_step"] = _r(line["ms_per_step"], 5)
     c = d["config"]
     line["config"] = {"workload": c["workload"], "degrees": c["degrees"], "l2": "inputs > L2 (~1.3 GB)",
-                      "parallelism": c["parallelism"]}
+                      "parallelism": c["parallelism"], "sweep": c.get("sweep", "")[:10]}
+    line["sequential_ms_per_step"] = d.get("sequential_ms_per_step")
     line["roofline"] = {"bound": roof["bound"], "achieved": _r(roof["achieved"]), "peak": _r(roof["peak"]),
                         "unit": roof["unit"], "frac": _r(roof["frac"], 3), "traffic": roof.get("traffic"),
                         "kernel": roof.get("kernel_short"), "peak_source": roof.get("peak_source")}
@@ -915,6 +958,8 @@ def main():
     ap.add_argument("--variants", default="",
                     help="kernel variant index per degree instead of autotuning (e.g. to replay a run's choice)")
     ap.add_argument("--sweep-steps", type=int, default=50)
+    ap.add_argument("--sequential", action="store_true",
+                    help="time the sweep's degrees one after another on one stream (default: concurrently)")
     ap.add_argument("--no-peak", action="store_true", help="skip the FP32 FMA peak measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the large elastic workload")
     ap.add_argument("--large-steps", type=int, default=20)

@@ -60,14 +60,14 @@ const KernelCfg* kernel_variants_acoustic(int N, int* count) {
                                  make_split_cfg<0, 7, 8, 3, 512>(), make_split_cfg<0, 7, 8, 9, 512>(),
                                  make_split_cfg<0, 7, 8, 7, 512>(), make_split_cfg<0, 7, 8, 10, 512>(),
                                  make_split_w_cfg<0, 7, 8, 15, 4, 1, 512>(), make_split_w_cfg<0, 7, 8, 8, 4, 1, 512>()};
-  static const KernelCfg v8[] = {make_split_cfg<0, 8, 8, 3, 512>(), make_cfg<0, 8, 4, false, true, 2>(),
+  static const KernelCfg v8[] = {make_split_w_cfg<0, 8, 8, 11, 5, 1, 512>(), make_cfg<0, 8, 4, false, true, 2>(),
                                  make_cfg<0, 8, 4, false, true, 4>(), make_cfg<0, 8, 8, false, true, 2>(),
                                  make_split_cfg<0, 8, 4>(), make_split_cfg<0, 8, 8>(),
                                  make_split_cfg<0, 8, 8, 2>(), make_cfg<0, 8, 4, false, true>(),
                                  make_split_cfg<0, 8, 4, 3>(), make_split_cfg<0, 8, 8, 2, 512>(),
                                  make_split_cfg<0, 8, 8, 5, 768>(), make_split_cfg<0, 8, 8, 7, 512>(),
                                  make_split_cfg<0, 8, 8, 9, 512>(), make_split_cfg<0, 8, 8, 10, 512>(),
-                                 make_split_w_cfg<0, 8, 8, 11, 4, 1, 512>(), make_split_w_cfg<0, 8, 8, 11, 5, 1, 512>()};
+                                 make_split_w_cfg<0, 8, 8, 11, 4, 1, 512>(), make_split_cfg<0, 8, 8, 3, 512>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
   static const int cnt[8] = {count_of(v1), count_of(v2), count_of(v3), count_of(v4),
                              count_of(v5), count_of(v6), count_of(v7), count_of(v8)};

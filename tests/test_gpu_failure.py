@@ -98,11 +98,13 @@ def test_default_finite_check_interval():
 
 # every kernel form: acoustic N = 1 (whole-neighbour halos), N = 3 (history
 # staged in shared memory), N = 6 (FP32 split step), N = 5 bf16x6 (tcgen05);
-# elastic N = 2 (fused) and N = 5 (split); the last compiled variant of N = 8
-# (the split step with the warp-specialised persistent GEMM) of both models
+# elastic N = 2 (fused) and N = 5 (split); N = 8 of both models (the split
+# step with the warp-specialised persistent GEMM, their defaults) and the
+# last compiled variant of acoustic N = 8 (the split step with one CTA per
+# GEMM tile)
 FORMS = [("acoustic", 1, "fp32", 0), ("acoustic", 3, "fp32", 0), ("acoustic", 6, "fp32", 0),
          ("acoustic", 5, "bf16x6", 0), ("elastic", 2, "fp32", 0), ("elastic", 5, "fp32", 0),
-         ("acoustic", 8, "fp32", -1), ("elastic", 8, "fp32", -1)]
+         ("acoustic", 8, "fp32", 0), ("elastic", 8, "fp32", 0), ("acoustic", 8, "fp32", -1)]
 
 
 def _form(model, N, precision, variant):

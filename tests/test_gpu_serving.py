@@ -142,12 +142,13 @@ def test_requests_join_a_running_batch(P):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("N,which", [(5, 0), (5, -1), (8, -1)])
+@pytest.mark.parametrize("N,which", [(5, 0), (5, -1), (8, 0), (8, -1)])
 def test_batched_split_step_equals_solo_runs(P, N, which):
     """A server whose (model, N) variant is the split step (batched front half +
     batched operator GEMM) gives every request the bits of its solo run.  The
-    first and the last split variant of a degree: one CTA per GEMM tile, and
-    the warp-specialised persistent GEMM walking the tiles of every solve."""
+    first and the last split variant of a degree: at N = 5 one CTA per GEMM
+    tile and the warp-specialised persistent GEMM walking the tiles of every
+    solve, at N = 8 the other way round."""
     probe = _req(50, N, 2, 1, with_src=False)
     g = P.Solver(probe["verts"], probe["tets"], probe["coeffs"], N, "acoustic", dt=1e-3)
     split = [i for i in range(g.kernel_info()["variants"]) if (g.set_variant(i) or g.kernel_info()["split"])]
