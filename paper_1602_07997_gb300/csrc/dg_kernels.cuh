@@ -259,7 +259,10 @@ struct TcX {
   static constexpr int Np = S::Np, NFN = S::NFN;
   static constexpr int Nf = MODEL == 0 ? 4 : 9;
   static constexpr int NV = MODEL == 0 ? 4 : 12;
-  static constexpr int NE = MODEL == 0 ? 32 : 16;  // elements per column tile (the MMA N)
+  // elements per column tile (the MMA N): each operator piece in shared memory
+  // serves NE elements; acoustic N >= 7 takes 64 (7 x 64 TMEM columns, one
+  // accumulator), below 32 (two accumulators alternate)
+  static constexpr int NE = MODEL == 0 ? (N >= 7 ? 64 : 32) : 16;
   static constexpr int NKD = (Np + 15) / 16, NKL = (NFN + 15) / 16;
   static constexpr int BV = NE * 16 * 2;           // one piece of one vector of one chunk
   static constexpr int CD = NSPLIT * NV * BV;      // bytes of a volume chunk
