@@ -4,8 +4,9 @@ Workload: the acoustic degree sweep N = 1..8, one jittered Kuhn cube mesh of
 ~2 M nodes per degree (rho, c ~ U[1,3], rigid walls, upwind flux, random
 initial state), FP32.  One bench step = one AB3 time step on each of the
 eight meshes (one or two kernel launches each), the meshes on streams of
-their own so that their kernels overlap (``--sequential``: one after another
-on one stream).  value = sum over meshes of K*Np*Nf field updates / device
+their own so that their kernels overlap (joined once after the timed steps;
+``--join-every-step``: after each; ``--sequential``: one after another on one
+stream).  value = sum over meshes of K*Np*Nf field updates / device
 time of the step.  The eight meshes hold ~1.3 GB, so consecutive steps on
 one mesh never find its state in L2.  The per-degree table and the roofline
 come from a second pass over the same steps that times each degree alone.
@@ -602,11 +603,12 @@ def run(args, rank, world, local_rank):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # The meshes of the sweep are independent problems: a step of the sweep
-    # runs them on streams of their own (forked from and joined to the timing
-    # stream), largest degree first, so that one degree's kernels fill the SMs
-    # that another's leave idle at its tail.  --sequential runs them one
-    # after another on one stream instead.  The per-degree times (per_N, the
+    # The meshes of the sweep are independent problems: they run on streams
+    # of their own (forked from the timing stream, largest degree first, and
+    # joined to it after the timed steps; --join-every-step joins them after
+    # every sweep step), so that one degree's kernels fill the SMs that
+    # another's leave idle at its tail.  --sequential runs them one after
+    # another on one stream instead.  The per-degree times (per_N, the
     # roofline) come from a separate sequential pass over the same number of
     # steps, each degree timed alone.
     order = sorted(range(len(solvers)), key=lambda i: -solvers[i].N)
@@ -615,18 +617,20 @@ def run(args, rank, world, local_rank):
     e_fork = torch.cuda.Event()
     e_join = [torch.cuda.Event() for _ in solvers]
 
-    def sweep_step():
+    def sweep_steps(n):
         if not conc:
-            for g in solvers:
-                g.step(1)
+            for _ in range(n):
+                for g in solvers:
+                    g.step(1)
             return
-        e_fork.record(stream)
-        for i in order:
-            sstreams[i].wait_event(e_fork)
-            solvers[i].step(1)
-            e_join[i].record(sstreams[i])
-        for i in order:
-            stream.wait_event(e_join[i])
+        for _ in range(n if args.join_every_step else 1):
+            e_fork.record(stream)
+            for i in order:
+                sstreams[i].wait_event(e_fork)
+                solvers[i].step(1 if args.join_every_step else n)
+                e_join[i].record(sstreams[i])
+            for i in order:
+                stream.wait_event(e_join[i])
 
     def on_streams(own):
         for i, g in enumerate(solvers):
@@ -635,8 +639,7 @@ def run(args, rank, world, local_rank):
     if conc:
         on_streams(True)
     # warm-up
-    for _ in range(args.warmup):
-        sweep_step()
+    sweep_steps(args.warmup)
     barrier()
     nN = len(solvers)
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -647,14 +650,13 @@ def run(args, rank, world, local_rank):
         # samples cover the timed region
         t_wait = time.perf_counter()
         while clk.proc and not clk.lines and time.perf_counter() - t_wait < 3.0:
-            sweep_step()
+            sweep_steps(1)
             torch.cuda.synchronize()
         barrier()
         lc0 = [g.launch_count() for g in solvers]
         t0 = time.perf_counter()
         e_all0.record(stream)
-        for s in range(args.steps):
-            sweep_step()
+        sweep_steps(args.steps)
         e_all1.record(stream)
         barrier()
         t1 = time.perf_counter()
@@ -784,8 +786,9 @@ def run(args, rank, world, local_rank):
                              "meshes": {str(g.N): g.K for g in solvers},
                              "l2": "inputs larger than L2: the 8 meshes hold ~1.3 GB, each ~130 MB",
                              "parallelism": "replicas" if world > 1 else "single GPU",
-                             "sweep": ("concurrent: one stream per degree, largest degree first" if conc else
-                                       "sequential: one stream")},
+                             "sweep": (("concurrent: one stream per degree, largest degree first, joined "
+                                        + ("every step" if args.join_every_step else "after the timed steps"))
+                                       if conc else "sequential: one stream")},
                   "sequential_ms_per_step": round(sum(per_ms), 5),
                   "gpu_launches": launches, "roofline": roof, "per_N": per_N, "sweeps": sweeps,
                   "cpu_baseline": cpu, "e2e": e2e, "served": served, "large_elastic": large, "clocks": clocks,
@@ -960,6 +963,8 @@ def main():
     ap.add_argument("--sweep-steps", type=int, default=50)
     ap.add_argument("--sequential", action="store_true",
                     help="time the sweep's degrees one after another on one stream (default: concurrently)")
+    ap.add_argument("--join-every-step", action="store_true",
+                    help="concurrent sweep: join the degrees' streams after every sweep step")
     ap.add_argument("--no-peak", action="store_true", help="skip the FP32 FMA peak measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the large elastic workload")
     ap.add_argument("--large-steps", type=int, default=20)
