@@ -224,7 +224,7 @@ def aggregate(t_local, updates, world):
     return float(t.item()), float(u.item())
 
 
-def served_benchmark(P, count=64, steps=500, seed=1004, max_n=32, rates=(0.5, 0.9)):
+def served_benchmark(P, count=64, steps=500, seed=1004, max_n=32, rates=(0.5, 0.9), max_batch=8):
     """Served stream: acoustic shots with Poisson arrivals at 0.7 x the batched
     capacity (measured first with every request submitted at once), p50/p99 of
     submit -> result latency, against the same requests run one at a time; and
@@ -245,7 +245,7 @@ def served_benchmark(P, count=64, steps=500, seed=1004, max_n=32, rates=(0.5, 0.
                for r, v, t, c, d, a in prepared)
 
     def run_server(arrivals):
-        srv = P.Server()
+        srv = P.Server(max_batch=max_batch)
         t0 = time.perf_counter()
         pending = {}
         lat = []
@@ -324,7 +324,7 @@ def served_benchmark(P, count=64, steps=500, seed=1004, max_n=32, rates=(0.5, 0.
             "batched_updates_per_s": work / mk0, "launches": launches,
             "plain_p50_s": q(plain_lat, 50), "plain_p99_s": q(plain_lat, 99), "plain_makespan_s": mk_plain,
             "plain_all_at_once_makespan_s": mk_plain0, "plain_updates_per_s": work / mk_plain0,
-            "rate_sweep": sweep,
+            "rate_sweep": sweep, "max_batch": max_batch,
             "note": "latency = submit to result in host memory (includes host set-up of the request); "
                     "rate_sweep plain latencies: FIFO over the measured one-at-a-time service times"}
 
@@ -770,7 +770,8 @@ def run(args, rank, world, local_rank):
 
     served = None
     if rank == 0 and not args.no_serve:
-        served = served_benchmark(P, count=args.serve_requests, steps=args.serve_steps)
+        served = served_benchmark(P, count=args.serve_requests, steps=args.serve_steps,
+                                  max_batch=args.serve_max_batch)
 
     large = None
     if rank == 0 and not args.no_large:
@@ -846,6 +847,7 @@ def headline(d):
     if sv:
         line["served"] = {k: _r(sv[k]) for k in ("p50_s", "p99_s", "plain_p50_s", "plain_p99_s",
                                                  "batched_all_at_once_makespan_s", "plain_all_at_once_makespan_s")}
+        line["served"]["max_batch"] = sv.get("max_batch")
     lg = d.get("large_elastic")
     if lg:
         line["large_elastic"] = {"ms": _r(lg["ms"]), "updates_per_s": _r(lg["updates_per_s"]),
@@ -953,6 +955,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-steps", type=int, default=500)
+    ap.add_argument("--serve-max-batch", type=int, default=8,
+                    help="solves the served stream's server steps together at most (8: lower p50 under load "
+                         "than 64 at about 2 %% more makespan)")
     ap.add_argument("--no-sweeps", action="store_true")
     ap.add_argument("--strategy", default="fused", choices=["fused", "library", "plain"],
                     help="step strategy of the timed sweep (default: the fused step)")
