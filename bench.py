@@ -742,7 +742,8 @@ def run(args, rank, world, local_rank):
         barrier()
         t0 = time.perf_counter()
         for _ in range(e_steps):
-            for p, g in zip(pinned, solvers):
+            for i in order:  # largest degree first, as in the timed sweep
+                p, g = pinned[i], solvers[i]
                 g.set_state(p, asynchronous=True)
                 g.step(1)
                 g.get_state(p, asynchronous=True)
