@@ -1035,14 +1035,14 @@ struct GemmOf<MODEL, N, 10> {
 // before the next epilogue (so the named barriers always see every consumer),
 // the producer stops at its next expired empty wait, and thread 0 waits for
 // the copies still in flight before the CTA leaves.
-template <int MODEL, int N, int NC, int NSTG, int MINB_>
+template <int MODEL, int N, int NC, int NSTG, int MINB_, int TM_ = (MODEL == 0 ? 8 : 4)>
 struct GemmW {
   using S = Sz<N>;
   static constexpr int Np = S::Np, NFN = S::NFN;
   static constexpr int Nf = MODEL == 0 ? 4 : 9;
   static constexpr int NV = XRows<MODEL, N>::NV, NXS = XRows<MODEL, N>::NXS, KXM = XRows<MODEL, N>::KXM;
   static constexpr int NE = MODEL == 0 ? 64 : 32;   // elements per column tile of X
-  static constexpr int TM = MODEL == 0 ? 8 : 4;     // rows per consumer warp
+  static constexpr int TM = TM_;                    // rows per consumer warp (multiple of 4)
   static constexpr int TE = NE / 32;                // elements per lane
   static constexpr int MT = NC * TM;                // output rows per CTA tile
   static constexpr int KC = 16;
@@ -1115,9 +1115,9 @@ struct WTilesBatch {
   __device__ long long limit() const { return b.wait_limit; }
 };
 
-template <int MODEL, int N, int NC, int NSTG, int MINB, class Prov>
+template <int MODEL, int N, int NC, int NSTG, int MINB, int TM_, class Prov>
 __device__ __forceinline__ void gemm_w_body(Prov& prov) {
-  using W = GemmW<MODEL, N, NC, NSTG, MINB>;
+  using W = GemmW<MODEL, N, NC, NSTG, MINB, TM_>;
   constexpr int Np = W::Np, NFN = W::NFN, NV = W::NV, NXS = W::NXS, KXM = W::KXM;
   constexpr int NE = W::NE, TM = W::TM, TE = W::TE, MT = W::MT, KC = W::KC, NS = W::NS;
   constexpr int NVC = W::NVC, NCH = W::NVC + W::NLC, MTILES = W::MTILES_R;
@@ -1269,19 +1269,19 @@ __global__ void __launch_bounds__(GemmOf<MODEL, N, V>::T::NT, GemmOf<MODEL, N, V
 
 // Design W: one persistent CTA per resident slot walks the tiles of a solve
 // (or of every solve of a batch).
-template <int MODEL, int N, int NC, int NS, int MINB>
-__global__ void __launch_bounds__(GemmW<MODEL, N, NC, NS, MINB>::NT, MINB)
+template <int MODEL, int N, int NC, int NS, int MINB, int TM>
+__global__ void __launch_bounds__(GemmW<MODEL, N, NC, NS, MINB, TM>::NT, MINB)
     dg_split_gemm_w_kernel(const StepArgs a) {
-  using W = GemmW<MODEL, N, NC, NS, MINB>;
+  using W = GemmW<MODEL, N, NC, NS, MINB, TM>;
   WTilesOne<W::MTILES_L, W::NE> prov{a};
-  gemm_w_body<MODEL, N, NC, NS, MINB>(prov);
+  gemm_w_body<MODEL, N, NC, NS, MINB, TM>(prov);
 }
-template <int MODEL, int N, int NC, int NS, int MINB>
-__global__ void __launch_bounds__(GemmW<MODEL, N, NC, NS, MINB>::NT, MINB)
+template <int MODEL, int N, int NC, int NS, int MINB, int TM>
+__global__ void __launch_bounds__(GemmW<MODEL, N, NC, NS, MINB, TM>::NT, MINB)
     dg_split_gemm_w_batched_kernel(const BatchArgs b) {
-  using W = GemmW<MODEL, N, NC, NS, MINB>;
+  using W = GemmW<MODEL, N, NC, NS, MINB, TM>;
   WTilesBatch<W::MTILES_L> prov{b};
-  gemm_w_body<MODEL, N, NC, NS, MINB>(prov);
+  gemm_w_body<MODEL, N, NC, NS, MINB, TM>(prov);
 }
 
 }  // namespace dgk

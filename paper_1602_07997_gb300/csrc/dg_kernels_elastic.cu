@@ -36,7 +36,7 @@ const KernelCfg* kernel_variants_elastic(int N, int* count) {
                                  make_split_cfg<1, 6, 4, 3, 384>(), make_split_cfg<1, 6, 4, 3>(),
                                  make_split_cfg<1, 6, 4, 5, 512>(), make_split_cfg<1, 6, 4, 3, 512>(),
                                  make_split_cfg<1, 6, 8, 3, 512>(), make_split_cfg<1, 6, 8, 9, 512>(),
-                                 make_split_w_cfg<1, 6, 8, 11, 4, 1, 512>()};
+                                 make_split_w_cfg<1, 6, 8, 11, 4, 1, 512>(), make_split_w_cfg<1, 6, 8, 11, 4, 1, 512, 8>()};
   static const KernelCfg v7[] = {make_split_cfg<1, 7, 8, 5, 512>(), make_cfg<1, 7, 4, false, false, 2>(),
                                  make_split_cfg<1, 7, 4>(), make_split_cfg<1, 7, 4, 2>(),
                                  make_cfg<1, 7, 4, false, false>(), make_split_cfg<1, 7, 4, 3, 256>(),
@@ -49,7 +49,8 @@ const KernelCfg* kernel_variants_elastic(int N, int* count) {
                                  make_split_cfg<1, 8, 4, 3>(), make_split_cfg<1, 8, 4, 3, 256>(),
                                  make_split_cfg<1, 8, 4, 3, 384>(), make_split_cfg<1, 8, 4, 2>(),
                                  make_split_cfg<1, 8, 4, 2, 384>(), make_split_cfg<1, 8, 4, 5, 512>(),
-                                 make_split_cfg<1, 8, 4, 9, 384>(), make_split_cfg<1, 8, 4, 5, 384>()};
+                                 make_split_cfg<1, 8, 4, 9, 384>(), make_split_cfg<1, 8, 4, 5, 384>(),
+                                 make_split_w_cfg<1, 8, 4, 11, 4, 1, 384, 8>()};
   static const KernelCfg* tab[8] = {v1, v2, v3, v4, v5, v6, v7, v8};
   static const int cnt[8] = {count_of(v1), count_of(v2), count_of(v3), count_of(v4),
                              count_of(v5), count_of(v6), count_of(v7), count_of(v8)};

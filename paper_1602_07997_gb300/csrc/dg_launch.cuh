@@ -82,16 +82,17 @@ KernelCfg make_split_cfg() {
 }
 
 // Split variant with the warp-specialised persistent GEMM (design W): NC
-// consumer warps of TM rows each, an NS-stage ring, MINB resident CTAs.
-template <int MODEL, int N, int EB, int NC, int NS, int MINB = 1, int NT = threads_for<N, EB, 1>()>
+// consumer warps of TM rows each (acoustic 8, elastic 4 or 8), an NS-stage
+// ring, MINB resident CTAs.
+template <int MODEL, int N, int EB, int NC, int NS, int MINB = 1, int NT = threads_for<N, EB, 1>(),
+          int TM = (MODEL == 0 ? 8 : 4)>
 KernelCfg make_split_w_cfg() {
-  using SS = SplitShape<MODEL, N>;
-  using G = GemmW<MODEL, N, NC, NS, MINB>;
+  using G = GemmW<MODEL, N, NC, NS, MINB, TM>;
   static_assert(Plan<MODEL, N, EB, false, false, MODEL == 0, true>::bytes <= 227 * 1024, "shared memory budget");
   static_assert(G::smem * MINB <= 227 * 1024, "shared memory budget (GEMM)");
   KernelCfg c = make_split_cfg<MODEL, N, EB, 3, NT>();
-  c.fn_gemm = dg_split_gemm_w_kernel<MODEL, N, NC, NS, MINB>;
-  c.fn_gemm_batched = dg_split_gemm_w_batched_kernel<MODEL, N, NC, NS, MINB>;
+  c.fn_gemm = dg_split_gemm_w_kernel<MODEL, N, NC, NS, MINB, TM>;
+  c.fn_gemm_batched = dg_split_gemm_w_batched_kernel<MODEL, N, NC, NS, MINB, TM>;
   c.smem_gemm = G::smem;
   c.gemm_threads = G::NT;
   c.gemm_mt = G::MT;
