@@ -254,3 +254,42 @@ def test_async_pinned_transfers_on_another_stream(dg):
     assert e.value.code == -1
     g.close()
     ref.close()
+
+
+@pytest.mark.gpu
+def test_meshes_stepping_concurrently_on_their_own_streams(dg):
+    """Independent meshes of different degrees stepped at the same time, each
+    on a stream of its own forked from one stream and joined back (the
+    bench's sweep), end in the states they reach stepped one after another,
+    bit for bit: the kernels of different handles share no device state."""
+    import torch
+    cases = [("acoustic", 2, 4, 71), ("acoustic", 5, 3, 72), ("acoustic", 8, 2, 73), ("elastic", 3, 3, 74)]
+    solo, conc = [], []
+    for model, N, n, seed in cases:
+        verts, tets, coeffs = _mesh(model, n, seed)
+        q = W.random_state(tets.shape[0], 4 if model == "acoustic" else 9, (N + 1) * (N + 2) * (N + 3) // 6,
+                           seed=seed).astype(np.float32)
+        for lst in (solo, conc):
+            g = dg.Solver(verts, tets, coeffs, N, model, dt=1e-4)
+            g.set_state(q)
+            lst.append(g)
+    for g in solo:
+        g.step(7)
+        g.sync()
+    main = torch.cuda.Stream()
+    streams = [torch.cuda.Stream() for _ in conc]
+    fork, joins = torch.cuda.Event(), [torch.cuda.Event() for _ in conc]
+    fork.record(main)
+    for g, st, ev in zip(conc, streams, joins):
+        g.set_stream(st.cuda_stream)
+        st.wait_event(fork)
+        g.step(7)
+        ev.record(st)
+    for ev in joins:
+        main.wait_event(ev)
+    main.synchronize()
+    for a, b in zip(solo, conc):
+        b.sync()
+        assert np.array_equal(a.get_state(), b.get_state())
+        a.close()
+        b.close()
