@@ -32,6 +32,11 @@
 //                 r_v,c = Rv_c + LIFT (Fscale p_v,c) and, face by face,
 //                 W_f = LIFT_f (Fscale dv), which joins the stress as
 //                 lambda (n_f.W_f) I + mu (n_f W_f^T + W_f n_f^T).
+//   design W: design B's narrow packed thread tile in a warp-specialised,
+//     persistent CTA: a producer warp streams every chunk with 1-D bulk
+//     copies into an mbarrier ring, the consumer warps (one row group each)
+//     never meet a CTA-wide barrier in the K loop, and the CTA walks its
+//     tiles so that the next tile's chunks land during the epilogue.
 //   The epilogue stages one field at a time in shared memory and runs the
 //   point source and the AB3 update (Eq. updateScheme) with coalesced accesses.
 #pragma once
