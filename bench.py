@@ -823,7 +823,8 @@ def headline(d):
     line["sequential_ms_per_step"] = d.get("sequential_ms_per_step")
     line["roofline"] = {"bound": roof["bound"], "achieved": _r(roof["achieved"]), "peak": _r(roof["peak"]),
                         "unit": roof["unit"], "frac": _r(roof["frac"], 3), "traffic": roof.get("traffic"),
-                        "kernel": roof.get("kernel_short"), "peak_source": roof.get("peak_source")}
+                        "kernel": roof.get("kernel_short"),
+                        "peak_source": (roof.get("peak_source") or "").split(":")[0]}
     cpu = d.get("cpu_baseline")
     if cpu:
         line["cpu_baseline"] = {"value": _r(cpu.get("value")), "unit": cpu.get("unit"), "cores": cpu.get("cores"),
