@@ -90,7 +90,10 @@ __device__ __forceinline__ void ab3_batch(const StepArgs& a, const size_t* idx, 
 
 // The AB3 inputs of NE elements from element k0 into L2 while their products
 // run (q, r^{m-1}, r^{m-2} are padded past K: a whole tile stays inside the
-// allocation).
+// allocation).  The GEMMs issue it a few K chunks before a tile's epilogue
+// (ab3_prefetch_chunk): issued when the tile starts, the lines had left L2
+// again by the time the epilogue read them (measured: no faster than no
+// prefetch at all; 1-3 % faster steps at N = 5..8 issued late).
 template <int Nf, int Np, int NE>
 __device__ __forceinline__ void prefetch_tile_l2(const StepArgs& a, int k0) {
   const size_t e0 = size_t(k0) * Nf * Np;
@@ -863,7 +866,6 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
   const int row0 = mtile * MT;
   const float* X = a.xg + size_t(ntile) * SplitShape<MODEL, N>::x_floats_per_tile + half * NE;
   const float* OP = a.ops2;  // [3 Np + NFN][MP2]
-  if (tid == 0 && mtile == 0 && a.mode == 0) prefetch_tile_l2<Nf, Np, NE>(a, kbase);
 
   // chunk c -> stage c % NS: operator rows [KC][MT] (3 of them for a volume
   // chunk), X rows [vector][KC][NE]; rows past Np / 4 Nfp are neither copied
@@ -927,6 +929,9 @@ __device__ __forceinline__ void gemm_b_body(const StepArgs& a, const int mtile_l
     // stage the next copy refills: one barrier per chunk
     __syncthreads();
     issue(c + NS - 1);
+    // the tile's AB3 inputs into L2 a few chunks before the epilogue
+    if (tid == 0 && c == ab3_prefetch_chunk(NCH) && mtile == 0 && a.mode == 0)
+      prefetch_tile_l2<Nf, Np, NE>(a, kbase);
     const float* A = sA(c % NS) + il;
     const float* B = sB(c % NS) + e0;
     if (c < NVC) {
@@ -1160,7 +1165,6 @@ __device__ __forceinline__ void gemm_w_body(Prov& prov) {
       const StepArgs& a = prov.tile(t, mtile, ntile);
       const float* X = a.xg + size_t(ntile) * W::x_floats_per_tile;
       const float* OP = a.ops2 + mtile * MT;  // [3 Np + NFN][MP2], this tile's row slice
-      if (lane == 0 && mtile == 0 && a.mode == 0) prefetch_tile_l2<W::Nf, Np, NE>(a, ntile * NE);
       for (int c = 0; c < NCH; ++c, ++g) {
         const int s = g % NS;
         bool got = true;
@@ -1194,6 +1198,9 @@ __device__ __forceinline__ void gemm_w_body(Prov& prov) {
           if (lane == NXS) tma_bulk_g2s(B + NXS * KC * NE, X + size_t(KXM) * NE, uint32_t(12 * NE * 4), &full[s]);
         }
         issued = g + 1;
+        // the tile's AB3 inputs into L2 a few chunks before its epilogue
+        if (lane == 0 && c == ab3_prefetch_chunk(NCH) && mtile == 0 && a.mode == 0)
+          prefetch_tile_l2<W::Nf, Np, NE>(a, ntile * NE);
       }
     }
   } else {

@@ -56,6 +56,10 @@ struct Sz {
   static constexpr int KD = 3 * Np + NFN;
 };
 
+// K chunk of a split-step GEMM tile at which the tile's AB3 inputs are
+// prefetched into L2: six chunks before the epilogue (or the first chunk).
+__host__ __device__ constexpr int ab3_prefetch_chunk(int nch) { return nch > 6 ? nch - 6 : 0; }
+
 // Rows per element of the FP32 split step's GEMM input X: NV volume inputs
 // per node, NXS surface streams per face node (acoustic: the pressure penalty
 // and psi, the magnitude of the velocity penalty psi n_f; elastic: Fscale p_v

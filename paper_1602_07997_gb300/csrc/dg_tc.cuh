@@ -233,15 +233,6 @@ __global__ void __launch_bounds__(TcShape<MODEL, N, NSPLIT>::NT, 1) dg_tc_gemm_k
         mbar_arrive_expect_tx(&rfull[rb], TS::RECB);
         tma_bulk_g2s(recs + rb * NE * REC, a.rec + size_t(ntile) * NE * REC, TS::RECB, &rfull[rb]);
         rissued = j + 1;
-        if (a.mode == 0 && mtile == 0) {
-          // the epilogue's AB3 inputs of this tile: into L2 while the products run
-          // (q, r^{m-1}, r^{m-2} are padded past K: whole tiles stay in bounds)
-          const size_t e0 = size_t(ntile) * NE * Nf * Np;
-          constexpr uint32_t bytes = uint32_t(NE * Nf * Np * 4);
-          prefetch_l2(a.q + e0, bytes);
-          prefetch_l2(a.r1 + e0, bytes);
-          prefetch_l2(a.r2 + e0, bytes);
-        }
         const uint8_t* OPS = reinterpret_cast<const uint8_t*>(a.opstc) + size_t(mtile) * TS::OPS_PER_MTILE;
         const uint8_t* XT = reinterpret_cast<const uint8_t*>(a.xg) + size_t(ntile) * TX::TILE;
         for (int c = 0; c < NCH; ++c, ++g) {
@@ -259,6 +250,16 @@ __global__ void __launch_bounds__(TcShape<MODEL, N, NSPLIT>::NT, 1) dg_tc_gemm_k
                        abytes, &full[s]);
           tma_bulk_g2s(st + TS::A_D, XT + TX::chunk_off(c), xbytes, &full[s]);
           issued = g + 1;
+          if (a.mode == 0 && mtile == 0 && c == ab3_prefetch_chunk(NCH)) {
+            // the epilogue's AB3 inputs of this tile into L2, a few chunks
+            // before the epilogue reads them (q, r^{m-1}, r^{m-2} are padded
+            // past K: whole tiles stay in bounds)
+            const size_t e0 = size_t(ntile) * NE * Nf * Np;
+            constexpr uint32_t bytes = uint32_t(NE * Nf * Np * 4);
+            prefetch_l2(a.q + e0, bytes);
+            prefetch_l2(a.r1 + e0, bytes);
+            prefetch_l2(a.r2 + e0, bytes);
+          }
         }
       }
     }
