@@ -70,33 +70,52 @@ int HostMesh::build(const dg_mesh* m) {
       for (int i = 0; i < 3; ++i) nrm[12 * k + 3 * f + i] = nv3[i] / len;
     }
   }
-  // faces: sorted vertex triple -> (k, f)
+  // faces: sorted vertex triple -> (k, f).  With fewer than 2^21 vertices
+  // the triple packs into one 64-bit key and the sort moves 16-byte records
+  // (the served path builds a mesh per request on the host); otherwise the
+  // triple itself is the key.
   struct FaceKey {
     std::array<int64_t, 3> v;
     int64_t kf;
   };
-  std::vector<FaceKey> keys(size_t(K) * 4);
+  struct PackedKey {
+    uint64_t v;
+    int64_t kf;
+  };
+  const bool packed = nv <= (int64_t(1) << 21);
+  std::vector<FaceKey> keys;
+  std::vector<PackedKey> pkeys;
+  if (packed) pkeys.resize(size_t(K) * 4);
+  else keys.resize(size_t(K) * 4);
   for (int64_t k = 0; k < K; ++k)
     for (int f = 0; f < 4; ++f) {
       std::array<int64_t, 3> v;
       for (int a = 0; a < 3; ++a) v[a] = m->tets[4 * k + kFaceVerts[f][a]];
       std::sort(v.begin(), v.end());
-      keys[4 * k + f] = {v, 4 * k + f};
+      if (packed) pkeys[4 * k + f] = {(uint64_t(v[0]) << 42) | (uint64_t(v[1]) << 21) | uint64_t(v[2]), 4 * k + f};
+      else keys[4 * k + f] = {v, 4 * k + f};
     }
-  std::sort(keys.begin(), keys.end(), [](const FaceKey& a, const FaceKey& b) {
-    return a.v != b.v ? a.v < b.v : a.kf < b.kf;
-  });
+  if (packed)
+    std::sort(pkeys.begin(), pkeys.end(),
+              [](const PackedKey& a, const PackedKey& b) { return a.v != b.v ? a.v < b.v : a.kf < b.kf; });
+  else
+    std::sort(keys.begin(), keys.end(), [](const FaceKey& a, const FaceKey& b) {
+      return a.v != b.v ? a.v < b.v : a.kf < b.kf;
+    });
+  const size_t nkeys = size_t(K) * 4;
+  auto same = [&](size_t x, size_t y) { return packed ? pkeys[x].v == pkeys[y].v : keys[x].v == keys[y].v; };
+  auto kf_of = [&](size_t x) { return packed ? pkeys[x].kf : keys[x].kf; };
   nbr.assign(size_t(K) * 4, -1);
   code.assign(K, 0u);
   for (int64_t k = 0; k < K; ++k) code[k] = 0x80808080u;  // all faces boundary until matched
   size_t i = 0;
-  while (i < keys.size()) {
+  while (i < nkeys) {
     size_t j = i + 1;
-    while (j < keys.size() && keys[j].v == keys[i].v) ++j;
+    while (j < nkeys && same(j, i)) ++j;
     if (j - i > 2) return fail(DG_EINVAL, "non-conforming mesh: face shared by more than two tets");
     if (j - i == 2) {
       for (int side = 0; side < 2; ++side) {
-        int64_t kf = keys[i + side].kf, kf2 = keys[i + 1 - side].kf;
+        int64_t kf = kf_of(i + side), kf2 = kf_of(i + 1 - side);
         int64_t k = kf / 4, k2 = kf2 / 4;
         int f = int(kf % 4), f2 = int(kf2 % 4);
         if (k == k2) return fail(DG_EINVAL, "tet glued to itself");
