@@ -132,6 +132,36 @@ def test_empty_mesh_is_refused(P):
     assert e.value.code == -1
 
 
+def _spread_vertices(verts, tets, nv, seed):
+    """The same mesh with its vertices scattered over an array of nv vertices
+    (the unused ones far away), so that the face keys need wide indices."""
+    rng = np.random.default_rng(seed)
+    slots = np.sort(rng.choice(nv, size=verts.shape[0], replace=False))
+    slots[-1] = nv - 1  # the widest index is in use
+    big = np.full((nv, 3), 1.0e3)
+    big[slots] = verts
+    return big, slots[tets]
+
+
+@pytest.mark.parametrize("nv", [2 ** 21, 2 ** 21 + 1])
+def test_face_matching_with_wide_vertex_indices(P, nv):
+    """Face matching packs a face's sorted vertex triple into one 64-bit key
+    when every index fits 21 bits (nv <= 2^21) and sorts the triples
+    themselves otherwise.  On both sides of that boundary the host build must
+    accept the conforming mesh (every interior face matched with one of its
+    six vertex rotations, else "face vertex permutation not found"), give the
+    same dt as the compact mesh, and still refuse a face shared by three tets."""
+    verts, tets = W.kuhn_cube_mesh(3, 0.1, seed=2)
+    K = tets.shape[0]
+    c = W.acoustic_coefficients(K, 1, 3, seed=5)
+    big, btets = _spread_vertices(verts, tets, nv, seed=nv)
+    for N in (1, 5):
+        assert P.suggest_dt(big, btets, c, N, "acoustic", 0.4) == P.suggest_dt(verts, tets, c, N, "acoustic", 0.4)
+    with pytest.raises(P.DGError) as e:
+        P.suggest_dt(big, np.concatenate([btets, btets[:1]]), np.concatenate([c, c[:1]]), 2, "acoustic", 0.4)
+    assert e.value.code == -1 and "more than two" in str(e.value)
+
+
 def test_tune_cache_file_handling(P, tmp_path):
     """The autotune cache: a save with no choices writes only the header, and
     loading it takes nothing; files that are not such a cache or have a
