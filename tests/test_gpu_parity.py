@@ -293,3 +293,30 @@ def test_meshes_stepping_concurrently_on_their_own_streams(dg):
         assert np.array_equal(a.get_state(), b.get_state())
         a.close()
         b.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("model,N", [("acoustic", 3), ("acoustic", 6), ("elastic", 2), ("elastic", 5)])
+def test_wide_vertex_indices_give_the_same_solver(dg, model, N):
+    """A mesh whose vertex array holds more than 2^21 vertices is matched
+    face by face on whole index triples instead of 21-bit packed keys; the
+    same tets, numbered into such an array, must give the compact mesh's RHS
+    and AB3 steps bit for bit (same connectivity, same face rotations)."""
+    verts, tets, coeffs = _mesh(model, 3, 81)
+    nv = 2 ** 21 + 1
+    rng = np.random.default_rng(N)
+    slots = np.sort(rng.choice(nv, size=verts.shape[0], replace=False))
+    slots[-1] = nv - 1
+    big = np.full((nv, 3), 1.0e3)
+    big[slots] = verts
+    q = W.random_state(tets.shape[0], 4 if model == "acoustic" else 9, (N + 1) * (N + 2) * (N + 3) // 6,
+                       seed=N).astype(np.float32)
+    out = []
+    for vv, tt in ((verts, tets), (big, slots[tets])):
+        g = dg.Solver(vv, tt, coeffs, N, model, dt=1e-4)
+        g.set_state(q)
+        r = g.rhs()
+        g.step(5)
+        out.append((r, g.get_state()))
+        g.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
